@@ -1,0 +1,384 @@
+/*
+ * oasm_oracle.c -- plain, slow CPU oracle for Online Approximate String
+ * Matching (OASM), Cinti, Bianchi, Martino, Rizzi, arXiv:1712.03560.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the package's smoke check
+ * and the benchmark's CPU-baseline leg may load this library.  The product
+ * path (the CUDA library under paper_1712_03560_gb300/csrc) shares no code,
+ * header, table or constant with this file and never calls it.
+ *
+ * What it computes, step by step, in the paper's order and notation:
+ *   orc_lev            Eq. 1 (Sec. 3): full Levenshtein matrix C, unit costs.
+ *   orc_lev_prefixes   Eq. 1 from one start i: c[l_p][l] for every l, the
+ *                      shared-prefix reuse of Sec. 3 (Fig. 1(a) example).
+ *   orc_sellers        "Less Naive" column DP with a zero dummy row
+ *                      (Sec. 4.1): D[e] = min_i lev(p, t[i..e]).
+ *   orc_hits           the hit set of Eq. 2: every (i, l, k) with
+ *                      l in [l_p-K, l_p+K] and k = lev(p, t(i;l)) <= K.
+ *   orc_oasm           Algorithm 1 (Sec. 4): loop over starts i, inner loop
+ *                      over lengths l, priority rules R1-R3 (Sec. 4.1),
+ *                      validation counters r(k) and Eq. 3 (Sec. 4.2).
+ *
+ * Readings taken where the paper is ambiguous or garbled (each selectable):
+ *   A  same-priority replacement: CONTAINED (default) / SAME_END / NEVER
+ *   B  Eq. 3 comparator: GT (default, as printed in Eq. 3) / GE
+ *   C  accumulator: SUM of kept lengths (default) / LAST kept length
+ *   D  the flush fires at the iteration where r(idx) reaches l(idx); the
+ *      counter of a level is 1 at insertion and grows by one per iteration
+ *   E  with no pending occurrence any hit k <= K opens the window at level k
+ *   F  order of presentation: every length in ascending order (default) /
+ *      only the best (smallest k, then shortest) hit of each start
+ *   G  finite text: i runs to n-1 and lengths with i+l > n do not exist
+ *
+ * Parity status: every function here is pinned by the -m "not gpu" tests
+ * (worked example of Sec. 4.2, Fig. 1 values, brute force on tiny inputs,
+ * closed forms and invariants).  The non-default readings of A, B, C and F
+ * are pinned only by invariants and brute force of their own definitions.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef struct {
+    int32_t replace; /* 0 CONTAINED, 1 SAME_END, 2 NEVER */
+    int32_t order;   /* 0 PER_START_LENGTH, 1 PER_START_BEST */
+    int32_t acc;     /* 0 SUM, 1 LAST */
+    int32_t cmp;     /* 0 GT, 1 GE */
+} orc_rules;
+
+typedef struct {
+    int64_t start;      /* i */
+    int64_t decided_at; /* iteration of Algorithm 1 at which it was added to S */
+    int32_t len;        /* l */
+    int32_t k;          /* lev(p, t(i;l)) = priority level */
+} orc_hit;
+
+/* One row per non-empty level of mem at each validation (flush). */
+typedef struct {
+    int64_t decided_at;
+    int64_t start;
+    int64_t r;      /* validation counter r(j) at the flush */
+    int64_t acc;    /* value of acc when level j was examined */
+    int32_t level;  /* j */
+    int32_t len;
+    int32_t kept;   /* 1 if added to S */
+    int32_t is_idx; /* 1 for the highest-priority level idx */
+} orc_flush_row;
+
+static int imin3(int a, int b, int c) {
+    int m = a < b ? a : b;
+    return m < c ? m : c;
+}
+
+/* Eq. 1: c[n][m] with c[n][0] = n, c[0][m] = m and the unit-cost recurrence.
+ * The whole (l_p+1) x (l+1) matrix is built, exactly as written. */
+int orc_lev(const uint8_t *p, int lp, const uint8_t *s, int l) {
+    int rows = lp + 1, cols = l + 1;
+    int *c = (int *)malloc(sizeof(int) * (size_t)rows * (size_t)cols);
+    if (!c) return -1;
+    for (int n = 0; n <= lp; n++) {
+        for (int m = 0; m <= l; m++) {
+            int v;
+            if (m == 0) v = n;
+            else if (n == 0) v = m;
+            else {
+                int delta = (p[n - 1] != s[m - 1]);
+                v = imin3(c[(n - 1) * cols + m] + 1, c[n * cols + m - 1] + 1,
+                          c[(n - 1) * cols + m - 1] + delta);
+            }
+            c[n * cols + m] = v;
+        }
+    }
+    int r = c[lp * cols + l];
+    free(c);
+    return r;
+}
+
+/* Eq. 1 filled column by column (Sec. 3: only the previous column is kept)
+ * against s[0..L-1]; out[l] = c[l_p][l] = lev(p, s[0..l-1]) for l = 0..L.
+ * One matrix gives the distance of every prefix of s (Fig. 1(a)). */
+void orc_lev_prefixes(const uint8_t *p, int lp, const uint8_t *s, int L, int32_t *out) {
+    int *col = (int *)malloc(sizeof(int) * (size_t)(lp + 1));
+    for (int n = 0; n <= lp; n++) col[n] = n; /* column m = 0 */
+    out[0] = col[lp];
+    for (int m = 1; m <= L; m++) {
+        int diag = col[0]; /* c[0][m-1] */
+        col[0] = m;        /* c[0][m] */
+        for (int n = 1; n <= lp; n++) {
+            int left = col[n]; /* c[n][m-1]; col[n-1] already holds c[n-1][m] */
+            int delta = (p[n - 1] != s[m - 1]);
+            int v = imin3(left + 1, col[n - 1] + 1, diag + delta);
+            diag = left;
+            col[n] = v;
+        }
+        out[m] = col[lp];
+    }
+    free(col);
+}
+
+/* Less Naive (Sec. 4.1): the dummy row is all zeros, so c[l_p][e+1] is the
+ * smallest distance between p and any substring of t ending at e. */
+typedef struct {
+    const uint8_t *p;
+    int lp;
+    int *col;
+} sellers_state;
+
+static void sellers_init(sellers_state *st, const uint8_t *p, int lp) {
+    st->p = p;
+    st->lp = lp;
+    st->col = (int *)malloc(sizeof(int) * (size_t)(lp + 1));
+    for (int n = 0; n <= lp; n++) st->col[n] = n;
+}
+
+static int sellers_step(sellers_state *st, uint8_t sym) {
+    int *col = st->col;
+    int diag = col[0];
+    col[0] = 0; /* zero dummy row: a match may start anywhere */
+    for (int n = 1; n <= st->lp; n++) {
+        int left = col[n];
+        int delta = (st->p[n - 1] != sym);
+        int v = imin3(left + 1, col[n - 1] + 1, diag + delta);
+        diag = left;
+        col[n] = v;
+    }
+    return col[st->lp];
+}
+
+void orc_sellers(const uint8_t *p, int lp, const uint8_t *t, int64_t n, int32_t *D) {
+    sellers_state st;
+    sellers_init(&st, p, lp);
+    for (int64_t e = 0; e < n; e++) D[e] = sellers_step(&st, t[e]);
+    free(st.col);
+}
+
+/* Shared driver: for each start i, the distances k(l) = lev(p, t(i;l)) for
+ * l in [l_p-K, l_p+K] (absent when l < 1 or i+l > n, reading G).  A start
+ * whose reachable ends all have D[e] > K has no hit, because
+ * lev(p, t[i..e]) >= D[e]; the per-start matrix is only built otherwise. */
+typedef struct {
+    const uint8_t *p, *t;
+    int lp, K;
+    int64_t n;
+    sellers_state sl;
+    int64_t next_e;
+    int32_t *ring; /* D[e] for the most recent ends */
+    int ringmask;
+    int32_t *pref; /* c[l_p][0..l_p+K] */
+} start_scanner;
+
+static void scanner_init(start_scanner *sc, const uint8_t *p, int lp, int K,
+                         const uint8_t *t, int64_t n) {
+    sc->p = p; sc->t = t; sc->lp = lp; sc->K = K; sc->n = n;
+    sellers_init(&sc->sl, p, lp);
+    sc->next_e = 0;
+    int sz = 1;
+    while (sz < lp + K + 2) sz <<= 1;
+    sc->ring = (int32_t *)malloc(sizeof(int32_t) * (size_t)sz);
+    sc->ringmask = sz - 1;
+    sc->pref = (int32_t *)malloc(sizeof(int32_t) * (size_t)(lp + K + 1));
+}
+
+static void scanner_free(start_scanner *sc) {
+    free(sc->sl.col);
+    free(sc->ring);
+    free(sc->pref);
+}
+
+/* Fills kl[0..2K] with lev(p, t(i; l_p-K+j)) or -1 when that length does not
+ * exist; returns 1 when at least one of them is <= K. */
+static int scanner_start(start_scanner *sc, int64_t i, int32_t *kl) {
+    int lp = sc->lp, K = sc->K;
+    int64_t n = sc->n;
+    int lmin = lp - K < 1 ? 1 : lp - K;
+    int64_t hi = i + lp + K - 1;
+    if (hi > n - 1) hi = n - 1;
+    while (sc->next_e <= hi) {
+        sc->ring[sc->next_e & sc->ringmask] = sellers_step(&sc->sl, sc->t[sc->next_e]);
+        sc->next_e++;
+    }
+    for (int j = 0; j <= 2 * K; j++) kl[j] = -1;
+    int64_t lo = i + lmin - 1;
+    int any = 0;
+    for (int64_t e = lo; e <= hi; e++)
+        if (sc->ring[e & sc->ringmask] <= K) { any = 1; break; }
+    if (!any) return 0;
+    int L = (int)(hi - i + 1);
+    orc_lev_prefixes(sc->p, lp, sc->t + i, L, sc->pref);
+    int found = 0;
+    for (int l = lp - K; l <= lp + K; l++) {
+        if (l < 1 || l > L) continue;
+        kl[l - (lp - K)] = sc->pref[l];
+        if (sc->pref[l] <= K) found = 1;
+    }
+    return found;
+}
+
+/* Eq. 2: the hit set H in (i, l) order.  Returns |H|; writes at most cap. */
+int64_t orc_hits(const uint8_t *p, int lp, int K, const uint8_t *t, int64_t n,
+                 orc_hit *out, int64_t cap) {
+    if (lp < 1 || K < 0 || K >= lp) return -1;
+    start_scanner sc;
+    scanner_init(&sc, p, lp, K, t, n);
+    int32_t *kl = (int32_t *)malloc(sizeof(int32_t) * (size_t)(2 * K + 1));
+    int64_t cnt = 0;
+    for (int64_t i = 0; i < n; i++) {
+        if (!scanner_start(&sc, i, kl)) continue;
+        for (int j = 0; j <= 2 * K; j++) {
+            if (kl[j] < 0 || kl[j] > K) continue;
+            if (cnt < cap) {
+                out[cnt].start = i;
+                out[cnt].len = lp - K + j;
+                out[cnt].k = kl[j];
+                out[cnt].decided_at = i + lp - K + j - 1;
+            }
+            cnt++;
+        }
+    }
+    free(kl);
+    scanner_free(&sc);
+    return cnt;
+}
+
+/* Less Naive output: every end e with D[e] <= K, reported with the shortest
+ * length l in [l_p-K, l_p+K] whose substring ending at e attains D[e]. */
+int64_t orc_sellers_ends(const uint8_t *p, int lp, int K, const uint8_t *t, int64_t n,
+                         orc_hit *out, int64_t cap) {
+    if (lp < 1 || K < 0 || K >= lp) return -1;
+    sellers_state st;
+    sellers_init(&st, p, lp);
+    int32_t *pref = (int32_t *)malloc(sizeof(int32_t) * (size_t)(lp + K + 1));
+    uint8_t *rev_s = (uint8_t *)malloc((size_t)(lp + K));
+    uint8_t *rev_p = (uint8_t *)malloc((size_t)lp);
+    for (int a = 0; a < lp; a++) rev_p[a] = p[lp - 1 - a];
+    int64_t cnt = 0;
+    for (int64_t e = 0; e < n; e++) {
+        int d = sellers_step(&st, t[e]);
+        if (d > K) continue;
+        int L = lp + K;
+        if ((int64_t)L > e + 1) L = (int)(e + 1);
+        /* lev is unchanged when both strings are reversed, so one matrix of the
+         * reversed pattern against t[e], t[e-1], ... gives every length ending at e */
+        for (int a = 0; a < L; a++) rev_s[a] = t[e - a];
+        orc_lev_prefixes(rev_p, lp, rev_s, L, pref);
+        int best = -1;
+        for (int l = lp - K; l <= lp + K && l <= L; l++) {
+            if (l < 1) continue;
+            if (pref[l] == d) { best = l; break; }
+        }
+        if (cnt < cap) {
+            out[cnt].start = e - best + 1;
+            out[cnt].len = best;
+            out[cnt].k = d;
+            out[cnt].decided_at = e;
+        }
+        cnt++;
+    }
+    free(pref); free(rev_s); free(rev_p); free(st.col);
+    return cnt;
+}
+
+/* ---------------------------------------------------------------------------
+ * Algorithm 1 (Sec. 4).  mem is (K+1) x 3: position i, length l, counter r.
+ */
+typedef struct {
+    int valid;
+    int64_t i;
+    int32_t l;
+    int64_t r;
+} mem_row;
+
+static int same_priority_replaces(const orc_rules *ru, const mem_row *cur, int64_t i, int32_t l) {
+    int64_t cur_end = cur->i + cur->l - 1, new_end = i + l - 1;
+    switch (ru->replace) {
+    case 0: return i >= cur->i && new_end <= cur_end; /* CONTAINED */
+    case 1: return new_end == cur_end;                /* SAME_END */
+    default: return 0;                                /* NEVER: R2 literally */
+    }
+}
+
+/* Applies R1, R2 and R3 to one found substring t(i;l) with distance k. */
+static void apply_rules(const orc_rules *ru, mem_row *mem, int *idx, int *ins,
+                        int64_t i, int32_t l, int32_t k) {
+    if (!*ins) { /* reading E: an empty window opens at level k */
+        *idx = k; *ins = 1;
+        mem[k].valid = 1; mem[k].i = i; mem[k].l = l; mem[k].r = 1;
+    } else if (k < *idx) { /* R1: overlapping hit of strictly higher priority */
+        *idx = k;
+        mem[k].valid = 1; mem[k].i = i; mem[k].l = l; mem[k].r = 1;
+    } else if (k == *idx && same_priority_replaces(ru, &mem[*idx], i, l)) { /* R2/R3 */
+        mem[k].valid = 1; mem[k].i = i; mem[k].l = l; mem[k].r = 1;
+    }
+    /* otherwise the substring is discarded */
+}
+
+int64_t orc_oasm(const uint8_t *p, int lp, int K, const uint8_t *t, int64_t n,
+                 const orc_rules *rules_in, orc_hit *out, int64_t cap,
+                 orc_flush_row *trace, int64_t trace_cap, int64_t *trace_n) {
+    if (lp < 1 || K < 0 || K >= lp) return -1;
+    orc_rules ru = {0, 0, 0, 0};
+    if (rules_in) ru = *rules_in;
+    mem_row *mem = (mem_row *)calloc((size_t)(K + 1), sizeof(mem_row));
+    int32_t *kl = (int32_t *)malloc(sizeof(int32_t) * (size_t)(2 * K + 1));
+    start_scanner sc;
+    scanner_init(&sc, p, lp, K, t, n);
+    int idx = K, ins = 0;
+    int64_t acc = 0, cnt = 0, tcnt = 0;
+
+    for (int64_t i = 0; i < n; i++) {
+        /* inner loop over l: l_p-K -> l_p+K */
+        if (scanner_start(&sc, i, kl)) {
+            if (ru.order == 0) {
+                for (int j = 0; j <= 2 * K; j++)
+                    if (kl[j] >= 0 && kl[j] <= K)
+                        apply_rules(&ru, mem, &idx, &ins, i, lp - K + j, kl[j]);
+            } else { /* reading F, PER_START_BEST: smallest k, then shortest l */
+                int bj = -1;
+                for (int j = 0; j <= 2 * K; j++)
+                    if (kl[j] >= 0 && kl[j] <= K && (bj < 0 || kl[j] < kl[bj])) bj = j;
+                if (bj >= 0) apply_rules(&ru, mem, &idx, &ins, i, lp - K + bj, kl[bj]);
+            }
+        }
+        /* validation complete for the highest priority: r(idx) reached l(idx) */
+        if (ins && mem[idx].r == mem[idx].l) {
+            acc = 0;
+            for (int j = idx; j <= K; j++) {
+                if (!mem[j].valid) continue;
+                int64_t lhs = mem[j].r - acc; /* Eq. 3: r(k) - l(k*) vs l(k) */
+                int keep = (j == idx) || (ru.cmp == 0 ? lhs > mem[j].l : lhs >= mem[j].l);
+                if (trace && tcnt < trace_cap) {
+                    trace[tcnt].decided_at = i;
+                    trace[tcnt].start = mem[j].i;
+                    trace[tcnt].r = mem[j].r;
+                    trace[tcnt].acc = acc;
+                    trace[tcnt].level = j;
+                    trace[tcnt].len = mem[j].l;
+                    trace[tcnt].kept = keep;
+                    trace[tcnt].is_idx = (j == idx);
+                }
+                tcnt++;
+                if (keep) {
+                    if (cnt < cap) {
+                        out[cnt].start = mem[j].i;
+                        out[cnt].len = mem[j].l;
+                        out[cnt].k = j;
+                        out[cnt].decided_at = i;
+                    }
+                    cnt++;
+                    acc = (ru.acc == 0) ? acc + mem[j].l : mem[j].l;
+                }
+            }
+            idx = K; ins = 0; acc = 0;
+            memset(mem, 0, sizeof(mem_row) * (size_t)(K + 1));
+        }
+        /* every counter of a pending level grows by one per processed symbol */
+        if (ins)
+            for (int j = idx; j <= K; j++)
+                if (mem[j].valid) mem[j].r++;
+    }
+    if (trace_n) *trace_n = tcnt;
+    free(mem);
+    free(kl);
+    scanner_free(&sc);
+    return cnt;
+}
