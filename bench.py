@@ -1,0 +1,380 @@
+#!/usr/bin/env python
+"""Benchmark of the OASM device path on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload dictionary_dna|plain_dna|plain_dna_1g|bytes_zipf|many_texts]
+
+One step = one pass of the whole path over the workload: open a stream, feed
+the text, end it and flush (stage, bit-parallel scan, anchored verification,
+ordering, filter, emit), all through the C ABI.  The default workload is the
+DNA dictionary scan: 1,024 DNA patterns (m ~ U[8,32], K = floor(m/10)) over a
+256 MiB text with 1,000 planted copies per pattern.
+
+Printed: one JSON line with the metric (GCUPS: sum over patterns of m times
+text symbols, per second), device-resident throughput (`value`), end-to-end
+throughput through host buffers (`e2e`), the scan kernel's roofline against
+the integer issue peak, the CPU oracle on a bounded sample, and the SM
+clocks seen during the timed region.  Under torchrun every rank runs its own
+replica (a different seed) on its own GPU (weak scaling); rank 0 prints.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+OPS_PER_WORD_STEP = 16  # integer ops of one 32-bit column step of the scan
+SM_COUNT = 152
+SM_MAX_MHZ = 2070.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="dictionary_dna")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
+    return ap.parse_args()
+
+
+def make_workload(name: str, seed_offset: int):
+    from paper_1712_03560_gb300 import workloads as W
+    if name == "dictionary_dna":
+        return W.dictionary_dna(seed=2 + 1000 * seed_offset), \
+            "dictionary_dna: 1024 DNA patterns m~U[8,32] K=floor(m/10), 256 MiB iid DNA text, 1000 planted copies/pattern"
+    if name == "dictionary_dna_64m":
+        return W.dictionary_dna(seed=2 + 1000 * seed_offset, n=64 << 20, copies=250), \
+            "dictionary_dna_64m: 1024 DNA patterns m~U[8,32] K=floor(m/10), 64 MiB iid DNA text, 250 planted copies/pattern"
+    if name == "plain_dna":
+        return W.plain_dna(seed=1 + 1000 * seed_offset), \
+            "plain_dna: 1 DNA pattern m=8 K=2, 1e6 iid DNA symbols, 200 planted copies"
+    if name == "plain_dna_1g":
+        return W.plain_dna(seed=1 + 1000 * seed_offset, n=1 << 30, copies=200_000), \
+            "plain_dna_1g: 1 DNA pattern m=8 K=2, 1 GiB iid DNA symbols, 200000 planted copies"
+    if name == "bytes_zipf":
+        return W.bytes_zipf(seed=3 + 1000 * seed_offset), \
+            "bytes_zipf: 4096 byte patterns m log-uniform [16,128], K~U[1,min(8,m/4)], 1 GiB Zipf(1.1) text, 500 copies/pattern"
+    if name == "many_texts":
+        return W.many_texts(seed=4 + 1000 * seed_offset), \
+            "many_texts: 10000 DNA texts lognormal(median 1e5) ~4 GB x 512 DNA patterns m~U[12,48] K=3"
+    raise SystemExit(f"unknown workload {name}")
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-i", str(self.gpu), "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for nm, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(rows),
+                "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())
+                if any(r[3].replace(".", "").isdigit() for r in rows) else None}
+
+
+def cpu_baseline(wl, budget_s: float):
+    """The oracle as it stands on a bounded sample: whole text, a subset of patterns."""
+    import oracle
+    cores = os.cpu_count() or 1
+    text = wl.texts[0] if len(wl.texts) == 1 else np.concatenate(wl.texts[:50])
+    # estimate the per-pattern cost on a prefix, then size the sample
+    probe = text[: min(text.size, 1 << 22)]
+    t0 = time.perf_counter()
+    oracle.oasm(wl.patterns[0], int(wl.ks[0]), probe)
+    per_sym = (time.perf_counter() - t0) / max(1, probe.size)
+    per_pat = per_sym * text.size
+    n_pat = int(max(1, min(len(wl.patterns), cores * max(1, int(budget_s / max(per_pat, 1e-9))))))
+    if per_pat > budget_s:  # one pattern over the whole text is already too slow
+        n_sym = int(budget_s / per_sym)
+        text = text[:max(1024, n_sym)]
+        n_pat = min(len(wl.patterns), cores)
+    idx = np.linspace(0, len(wl.patterns) - 1, n_pat).astype(int)
+    pats = [wl.patterns[i] for i in idx]
+    ks = [int(wl.ks[i]) for i in idx]
+    t0 = time.perf_counter()
+    res = oracle.oasm_dictionary(pats, ks, text, threads=cores)
+    dt = time.perf_counter() - t0
+    cells = sum(p.size for p in pats) * text.size
+    return {"value": cells / dt / 1e9, "unit": "GCUPS", "cores": min(cores, n_pat), "kind": "oracle",
+            "sample": f"{n_pat} of {len(wl.patterns)} patterns x {text.size} text symbols, "
+                      f"{dt:.1f} s, {len(res)} occurrences"}, (idx, text, res)
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    wl, desc = make_workload(args.workload, 0)
+    import oracle
+    cores = os.cpu_count() or 1
+    text = wl.texts[0] if len(wl.texts) == 1 else np.concatenate(wl.texts[:50])
+    probe = text[: min(text.size, 1 << 21)]
+    t0 = time.perf_counter()
+    oracle.oasm(wl.patterns[0], int(wl.ks[0]), probe)
+    per_sym = (time.perf_counter() - t0) / max(1, probe.size)
+    # each step: `cores` patterns over a prefix sized for ~6 s of work
+    n_sym = int(min(text.size, max(1 << 16, 6.0 / max(per_sym, 1e-12))))
+    n_pat = min(len(wl.patterns), cores)
+    idx = np.linspace(0, len(wl.patterns) - 1, n_pat).astype(int)
+    pats = [wl.patterns[i] for i in idx]
+    ks = [int(wl.ks[i]) for i in idx]
+    sample = text[:n_sym]
+    for _ in range(args.warmup):
+        oracle.oasm_dictionary(pats, ks, sample[: min(n_sym, 1 << 16)], threads=cores)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.oasm_dictionary(pats, ks, sample, threads=cores)
+    dt = time.perf_counter() - t0
+    cells = sum(p.size for p in pats) * n_sym * args.steps
+    val = cells / dt / 1e9
+    line = {"metric": "GCUPS", "value": val, "unit": "GCUPS", "impl": "reference",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": desc, "l2": "oracle on host cores"},
+            "cpu_baseline": {"value": val, "unit": "GCUPS", "cores": n_pat, "kind": "oracle",
+                             "sample": f"{n_pat} of {len(wl.patterns)} patterns x {n_sym} text symbols per step"},
+            "e2e": {"value": val, "unit": "GCUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+
+    from paper_1712_03560_gb300 import binding as B
+
+    wl, desc = make_workload(args.workload, rank)
+    ctx = B.oasm_create(wl.patterns, wl.ks, None,
+                        {"device": dev, "timing": 1, "max_streams": max(64, len(wl.texts))})
+    stream = torch.cuda.ExternalStream(B.oasm_cuda_stream(ctx), device=dev)
+    dtexts = [torch.from_numpy(t).to(f"cuda:{dev}") for t in wl.texts]
+    torch.cuda.synchronize()
+    tuned = None
+    if not args.no_autotune:
+        # tile shapes for this GPU and pattern set, timed on a slice of the text
+        big = max(dtexts, key=lambda t: t.numel())
+        tuned = json.loads(B.oasm_autotune(ctx, big[: min(big.numel(), 32 << 20)]))
+        print(json.dumps({"autotune": tuned}), file=sys.stderr, flush=True)
+        for bk in tuned["buckets"]:
+            bk.pop("trials", None)
+
+    def step_device():
+        sids = []
+        for t in dtexts:
+            s = B.oasm_open_stream(ctx)
+            B.oasm_feed_device(ctx, s, t)
+            B.oasm_end_stream(ctx, s)
+            sids.append(s)
+        B.oasm_step(ctx)
+        n = 0
+        for s in sids:
+            n += len(B.oasm_flush(ctx, s))
+            B.oasm_close_stream(ctx, s)
+        return n
+
+    def step_host(host_texts):
+        sids = []
+        for t in host_texts:
+            s = B.oasm_open_stream(ctx)
+            B.oasm_feed(ctx, s, t)
+            B.oasm_end_stream(ctx, s)
+            sids.append(s)
+        B.oasm_step(ctx)
+        n = 0
+        for s in sids:
+            n += len(B.oasm_flush(ctx, s))
+            B.oasm_close_stream(ctx, s)
+        return n
+
+    for _ in range(args.warmup):
+        kept = step_device()
+
+    # ---- timed region: device-resident inputs
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    B.oasm_reset_stats(ctx)
+    clocks = Clocks(dev)
+    clocks.start()
+    time.sleep(0.25)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        kept = step_device()
+    ev1.record(stream)
+    ev1.synchronize()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if dist:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    st = B.oasm_get_stats(ctx)
+    if dist:
+        t = torch.tensor([ms], device=f"cuda:{dev}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    cells_step = wl.cells
+    value = cells_step * args.steps * world / (ms * 1e-3) / 1e9
+    text_gbps = wl.text_bytes * args.steps * world / (ms * 1e-3) / 1e9
+
+    # ---- roofline of the dominant kernel (the forward scan), measured live
+    peak_ops, _ = B.oasm_measure_int_peak(dev)
+    scan_ms_launch = st["scan_ms"] / max(1, st["scan_launches"])
+    words = sum((p.size + 31) // 32 for p in wl.patterns) * wl.text_bytes
+    alg_ops_launch = words * OPS_PER_WORD_STEP / max(1, st["scan_launches"] // max(1, args.steps))
+    achieved = alg_ops_launch / (scan_ms_launch * 1e-3) / 1e12
+    derived_peak = SM_COUNT * 128 * SM_MAX_MHZ * 1e6 / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": derived_peak, "unit": "Tops/s",
+                "frac": achieved / derived_peak, "traffic": None,
+                "peak_measured_mix": peak_ops / 1e12,
+                "frac_of_measured_mix": achieved * 1e12 / peak_ops,
+                "kernel": "scan_kernel<1>", "kernel_ms_per_launch": scan_ms_launch,
+                "ops_per_word_step": OPS_PER_WORD_STEP}
+
+    # ---- end to end through host buffers
+    e2e = None
+    if not args.no_e2e:
+        host = [np.ascontiguousarray(t) for t in wl.texts]
+        step_host(host)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        kept_h = 0
+        for _ in range(args.steps):
+            kept_h = step_host(host)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([dt], device=f"cuda:{dev}")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        e2e = {"value": cells_step * args.steps * world / dt / 1e9, "unit": "GCUPS",
+               "h2d_bytes_per_step": int(wl.text_bytes), "d2h_bytes_per_step": int(kept_h * 32 + 48),
+               "ms_per_step": dt / args.steps * 1e3}
+
+    if rank != 0:
+        B.oasm_destroy(ctx)
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    cpu = None
+    parity = None
+    if not args.no_cpu and world == 1:
+        cpu, (idx, text, ores) = cpu_baseline(wl, args.cpu_seconds)
+        # the sampled patterns' GPU output must equal the oracle's on that sample
+        if text.size == wl.texts[0].size and len(wl.texts) == 1:
+            from paper_1712_03560_gb300 import binding as B2
+            sub_pats = [wl.patterns[i] for i in idx]
+            sub_ks = [int(wl.ks[i]) for i in idx]
+            with B2.Matcher(sub_pats, sub_ks) as mt:
+                g = mt.search(dtexts[0], device=True)
+            got = sorted((int(r["pattern_id"]), int(r["decided_at"]), int(r["k"]),
+                          int(r["start"]), int(r["len"])) for r in g)
+            want = sorted((int(r["pattern_id"]), int(r["decided_at"]), int(r["k"]),
+                           int(r["start"]), int(r["len"])) for r in ores)
+            parity = {"patterns": len(idx), "occurrences": len(want), "equal": got == want}
+
+    line = {
+        "metric": "GCUPS", "value": value, "unit": "GCUPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic",
+        "config": {"workload": desc, "text_bytes": int(wl.text_bytes),
+                   "patterns": len(wl.patterns), "l2": "inputs larger than L2 (text > 129 MB)"
+                   if wl.text_bytes > (129 << 20) else "input smaller than L2",
+                   "parallelism": f"replicas x{world}", "autotune": tuned},
+        "text_gbps": text_gbps,
+        "occurrences_per_step": int(kept),
+        "kernel_ms": {k: st[k] / args.steps for k in ("copy_ms", "scan_ms", "verify_ms",
+                                                        "order_ms", "filter_ms", "step_ms")},
+        "candidates_per_step": st["candidates"] / args.steps,
+        "hits_per_step": st["hits"] / args.steps,
+        "gpu_launches": int(st["launches"]),
+        "roofline": roofline,
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+        "parity_sample": parity,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    B.oasm_destroy(ctx)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

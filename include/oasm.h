@@ -1,0 +1,234 @@
+/*
+ * oasm.h -- C ABI of the GB300 (sm_103a) Online Approximate String Matching
+ * library: a dictionary of patterns is searched, within a Levenshtein
+ * threshold, over many byte streams, and overlapping "shadow hits" are
+ * removed on the fly by the greedy priority filter of OASM.
+ *
+ * Method: A. Cinti, F. M. Bianchi, A. Martino, A. Rizzi, "A novel algorithm
+ * for online inexact string matching and its FPGA implementation",
+ * arXiv:1712.03560.
+ *   - distance: Levenshtein, unit costs (Sec. 3, Eq. 1)
+ *   - hit:      substring t(i;l), l in [l_p-K, l_p+K], lev(p, t(i;l)) = k <= K
+ *               (Sec. 3, Eq. 2)
+ *   - filter:   priority rules R1-R3 (Sec. 4.1), validation counters and
+ *               Eq. 3 (Sec. 4.2), Algorithm 1 (Sec. 4)
+ *   - many patterns on one stream: MOASM, one independent filter per pattern
+ *               (Sec. 6.4)
+ *
+ * Conventions for every call:
+ *   - Return value: OASM_OK (0) or a negative OASM_E* code; oasm_last_error()
+ *     gives a one-line message for the most recent failure on a context.
+ *   - Pointers are host pointers unless the name says "device".  The library
+ *     never keeps a caller's host pointer after a call returns.
+ *   - A context is not thread-safe: calls on one context must not overlap.
+ *   - All device work of a context runs on one CUDA stream (its own, or the
+ *     one given in oasm_config.cuda_stream).
+ */
+#ifndef OASM_H
+#define OASM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ------------------------------------------------------ */
+#define OASM_OK 0
+#define OASM_EINVAL (-1)   /* bad argument (pattern length, threshold, id, ...) */
+#define OASM_ENOMEM (-2)   /* device or pinned host memory could not be had */
+#define OASM_EBUSY (-3)    /* no free stream slot */
+#define OASM_ETRUNC (-4)   /* more hits are ready than `cap`; the rest stay queued */
+#define OASM_ETIMEOUT (-5) /* a bounded wait on the device ran out */
+#define OASM_ECUDA (-6)    /* a CUDA call failed; see oasm_last_error() */
+#define OASM_ESTATE (-7)   /* call not valid in the object's current state */
+
+/* ---- limits ----------------------------------------------------------- */
+#define OASM_MAX_PATTERN_LEN 128 /* 1 <= l_p <= 128 (four 32-bit words) */
+#define OASM_MAX_K 15            /* 0 <= K < l_p and K <= 15 */
+
+typedef struct oasm_ctx oasm_ctx;
+
+/* ---- priority rules (Sec. 4.1-4.2) -------------------------------------
+ * The paper's printed rules leave some choices open; each is a field here.
+ * The defaults reproduce the worked example of Sec. 4.2 exactly.          */
+enum {
+    /* R2/R3: a hit of the same priority as the pending one replaces it ... */
+    OASM_REPLACE_CONTAINED = 0, /* ... iff it lies inside it (default) */
+    OASM_REPLACE_SAME_END = 1,  /* ... iff it ends at the same symbol */
+    OASM_REPLACE_NEVER = 2      /* never: the first encountered wins (R2 as worded) */
+};
+enum {
+    OASM_ORDER_PER_START_LENGTH = 0, /* every length of a start, ascending (Alg. 1) */
+    OASM_ORDER_PER_START_BEST = 1    /* only the best (min k, then shortest) of a start */
+};
+enum {
+    OASM_ACC_SUM = 0, /* acc sums the lengths of the occurrences added (Alg. 1) */
+    OASM_ACC_LAST = 1 /* acc is the length of the last occurrence added (Eq. 3 text) */
+};
+enum {
+    OASM_CMP_GT = 0, /* lower level kept iff r(k) - acc > l(k) (Eq. 3) */
+    OASM_CMP_GE = 1  /* ... iff r(k) - acc >= l(k) */
+};
+enum {
+    OASM_OUT_FILTERED = 0, /* OASM output: the filtered occurrence set S */
+    OASM_OUT_ENDS = 1,     /* Less Naive (Sec. 5.1): every end e with
+                              min_i lev(p, t[i..e]) <= K, unfiltered */
+    OASM_OUT_ALL_HITS = 2  /* every hit of Eq. 2, unfiltered */
+};
+
+typedef struct {
+    int32_t replace; /* OASM_REPLACE_* */
+    int32_t order;   /* OASM_ORDER_* */
+    int32_t acc;     /* OASM_ACC_* */
+    int32_t cmp;     /* OASM_CMP_* */
+    int32_t output;  /* OASM_OUT_* */
+} oasm_rules;
+
+typedef struct {
+    int32_t device;            /* CUDA device ordinal (default 0) */
+    uint32_t max_streams;      /* stream slots (default 64) */
+    uint64_t mem_budget;       /* device bytes for per-stream state; 0 = no limit
+                                  beyond what the device has */
+    uint32_t region_bytes;     /* scan tile length in text symbols; 0 = automatic */
+    uint32_t tile_warps;       /* warps per scan block; 0 = automatic */
+    int32_t timing;            /* 1: time each kernel class with CUDA events */
+    uint32_t flush_timeout_ms; /* bound on every host wait (default 600000) */
+    void *cuda_stream;         /* cudaStream_t to run on; NULL = library-owned */
+} oasm_config;
+
+/* One occurrence added to S (or, for the raw outputs, one hit/end). */
+typedef struct {
+    uint32_t pattern_id; /* index into the pattern array given to oasm_create */
+    uint32_t k;          /* lev(p, t(start; len)) = its priority level */
+    uint64_t start;      /* i: 0-based position in the stream */
+    uint32_t len;        /* l; the end position is start + len - 1 */
+    uint32_t stream_id;  /* the stream it was found on */
+    uint64_t decided_at; /* stream position at which Algorithm 1 added it to S
+                            (for the raw outputs: its end position) */
+} oasm_hit;
+
+typedef struct {
+    uint64_t steps;          /* batched steps run */
+    uint64_t launches;       /* kernels launched by the library */
+    uint64_t text_bytes;     /* new stream bytes processed */
+    uint64_t cells;          /* Sellers cells: sum over patterns of l_p x bytes */
+    uint64_t word_steps;     /* bit-vector word updates of the forward scan */
+    uint64_t candidates;     /* ends with min distance <= K (forward scan) */
+    uint64_t hits;           /* hits of Eq. 2 handed to the filter */
+    uint64_t kept;           /* records emitted */
+    uint64_t reruns;         /* steps re-run after a buffer grew */
+    double scan_ms;          /* with timing=1: forward scan kernels */
+    double verify_ms;        /* anchored verification */
+    double order_ms;         /* radix sort of hits */
+    double filter_ms;        /* filter, finalize and tail update */
+    double copy_ms;          /* staging copies into the device text arena */
+    double step_ms;          /* whole steps, first to last kernel */
+    uint64_t scan_launches;  /* forward-scan kernel launches */
+} oasm_stats;
+
+/* Fills *cfg / *rules with the defaults described above. */
+int oasm_config_default(oasm_config *cfg);
+int oasm_rules_default(oasm_rules *rules);
+
+/* Creates a context for a dictionary of n_pat patterns (MOASM, Sec. 6.4).
+ *   pat[j]  host pointer to pattern j (len[j] bytes, any byte values 0-255;
+ *           no symbol is reserved, unlike the FPGA's $1/$2 of Sec. 7)
+ *   len[j]  l_p, 1..OASM_MAX_PATTERN_LEN
+ *   k[j]    threshold K of pattern j: 0 <= K < l_p (Sec. 6.3) and <= OASM_MAX_K
+ *   rules   NULL for the defaults
+ *   cfg     NULL for the defaults
+ *   out     receives the context
+ * The patterns are copied; the caller's arrays may be freed on return.
+ * Errors: OASM_EINVAL (n_pat == 0, bad length or threshold), OASM_ENOMEM,
+ * OASM_ECUDA.  On error *out is NULL and nothing is leaked. */
+int oasm_create(const uint8_t *const *pat, const uint32_t *len, const uint32_t *k,
+                uint32_t n_pat, const oasm_rules *rules, const oasm_config *cfg,
+                oasm_ctx **out);
+
+/* Frees every host and device resource of the context.  Safe on NULL and on a
+ * context whose creation failed half way.  Waits (bounded) for device work. */
+int oasm_destroy(oasm_ctx *ctx);
+
+/* Opens a stream: a text t that arrives in pieces (Sec. 4: "continuous
+ * stream of symbols").  Each stream has its own position, its own pending
+ * filter window per pattern and the last l_p + 3K - 1 symbols it saw, all
+ * resident on the device.  Admission is by device memory: OASM_ENOMEM when
+ * the stream's state does not fit mem_budget, OASM_EBUSY when all
+ * max_streams slots are taken. */
+int oasm_open_stream(oasm_ctx *ctx, uint32_t *sid);
+
+/* Closes a stream and frees its slot; undelivered hits are dropped. */
+int oasm_close_stream(oasm_ctx *ctx, uint32_t sid);
+
+/* Appends n bytes (host memory) to stream sid.  The bytes are copied into
+ * pinned staging memory; `chunk` may be reused when the call returns.  No
+ * device work is started until oasm_step / oasm_flush. */
+int oasm_feed(oasm_ctx *ctx, uint32_t sid, const uint8_t *chunk, size_t n);
+
+/* Appends n bytes that are already in device memory.  The buffer is NOT
+ * copied at this call: it must stay valid and unchanged until the next
+ * oasm_step or oasm_flush that processes this stream has returned. */
+int oasm_feed_device(oasm_ctx *ctx, uint32_t sid, const uint8_t *dchunk, size_t n);
+
+/* Marks the end of stream sid: at the next step its last symbols are matched
+ * with truncated lengths (i + l <= n) and every pending window is decided. */
+int oasm_end_stream(oasm_ctx *ctx, uint32_t sid);
+
+/* Runs one batched step over every stream with pending input or a pending
+ * end: one pass of the whole device path (stage, bit-parallel scan, anchored
+ * verification, ordering, filter, emit).  Returns when the step has finished
+ * on the device and its decided hits are queued on their streams. */
+int oasm_step(oasm_ctx *ctx);
+
+/* Returns the hits of stream sid decided so far and not yet returned, in
+ * canonical order (pattern_id, decided_at, k).  If the stream has input or
+ * an end that no step has processed yet, a step is run first.  With
+ * end_of_stream != 0 the stream is ended first (as oasm_end_stream) and,
+ * once drained, rewinds to position 0 and can be fed again.
+ *   out/cap   caller's array of cap records; *n_out receives the count
+ * OASM_ETRUNC when more than cap records are ready: the first cap are
+ * returned, the rest stay queued for the next call. */
+int oasm_flush(oasm_ctx *ctx, uint32_t sid, int end_of_stream, oasm_hit *out, size_t cap,
+               size_t *n_out);
+
+/* Number of decided hits of stream sid queued and not yet returned by
+ * oasm_flush (no device work is started). */
+int oasm_ready(oasm_ctx *ctx, uint32_t sid, size_t *n);
+
+/* Cumulative counters and (with cfg.timing = 1) per-kernel-class times. */
+int oasm_get_stats(oasm_ctx *ctx, oasm_stats *st);
+int oasm_reset_stats(oasm_ctx *ctx);
+
+/* The cudaStream_t the context runs on (for timing with CUDA events). */
+void *oasm_cuda_stream(oasm_ctx *ctx);
+
+/* Message of the most recent failure on ctx ("" if none); ctx may be NULL
+ * for failures of oasm_create. */
+const char *oasm_last_error(oasm_ctx *ctx);
+
+/* Static text for an OASM_E* code. */
+const char *oasm_strerror(int code);
+
+/* ---- autotuning ------------------------------------------------------
+ * Times the forward scan over a sample of `n` device-resident symbols for a
+ * set of tile shapes (warps per block, tile length) and keeps the fastest
+ * per word-count class for this context.  `report` (may be NULL) receives a
+ * one-line JSON summary of at most `report_cap` bytes. */
+int oasm_autotune(oasm_ctx *ctx, const uint8_t *dsample, size_t n, char *report,
+                  size_t report_cap);
+
+/* ---- measurement utility (no counterpart in the paper) ------------------
+ * Measures the integer issue rate of `device` on a synthetic kernel whose
+ * instruction mix is that of one 32-bit column step of the forward scan
+ * (eight 3-input logic ops, two adds, four shifts, one byte permute; no
+ * memory traffic).  *ops_per_s receives integer operations per second over
+ * the whole GPU (best of five timed launches), *ms (may be NULL) the time
+ * of that launch.  Used as the roofline peak of the scan. */
+int oasm_measure_int_peak(int device, double *ops_per_s, double *ms);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OASM_H */

@@ -8,11 +8,11 @@ the C source ``oasm_oracle.c`` is compiled on its own with gcc.
 Functions (each follows the passage cited in ``oasm_oracle.c``):
   lev            Eq. 1, full matrix
   lev_prefixes   Eq. 1 column by column from one start (Fig. 1(a))
-  sellers        Less Naive column DP (Sec. 4.1)
+  sellers        Less Naive column DP (Sec. 5.1)
   hits           the hit set of Eq. 2
   sellers_ends   Less Naive end positions with their distance
   oasm           Algorithm 1 (Sec. 4) with the readings A-G of the C file
-  oasm_dictionary  MOASM (Sec. 5.4): one independent Algorithm 1 per pattern
+  oasm_dictionary  MOASM (Sec. 6.4): one independent Algorithm 1 per pattern
 """
 from __future__ import annotations
 

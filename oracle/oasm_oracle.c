@@ -12,7 +12,7 @@
  *   orc_lev_prefixes   Eq. 1 from one start i: c[l_p][l] for every l, the
  *                      shared-prefix reuse of Sec. 3 (Fig. 1(a) example).
  *   orc_sellers        "Less Naive" column DP with a zero dummy row
- *                      (Sec. 4.1): D[e] = min_i lev(p, t[i..e]).
+ *                      (Sec. 5.1): D[e] = min_i lev(p, t[i..e]).
  *   orc_hits           the hit set of Eq. 2: every (i, l, k) with
  *                      l in [l_p-K, l_p+K] and k = lev(p, t(i;l)) <= K.
  *   orc_oasm           Algorithm 1 (Sec. 4): loop over starts i, inner loop
@@ -116,7 +116,7 @@ void orc_lev_prefixes(const uint8_t *p, int lp, const uint8_t *s, int L, int32_t
     free(col);
 }
 
-/* Less Naive (Sec. 4.1): the dummy row is all zeros, so c[l_p][e+1] is the
+/* Less Naive (Sec. 5.1): the dummy row is all zeros, so c[l_p][e+1] is the
  * smallest distance between p and any substring of t ending at e. */
 typedef struct {
     const uint8_t *p;

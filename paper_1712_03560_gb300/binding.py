@@ -1,0 +1,315 @@
+"""Thin Python binding of the OASM C ABI (``include/oasm.h``).
+
+Argument marshalling only: every step of the matching path runs in the CUDA
+library ``_build/liboasm.so``.  The functions keep the C names.  There is no
+fallback: if the library cannot be loaded, or no CUDA device is present,
+the calls raise ``OasmError``.
+
+Device memory for ``oasm_feed_device`` may be given as a torch CUDA tensor
+(uint8) or as a raw integer device pointer.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+OASM_OK = 0
+OASM_EINVAL = -1
+OASM_ENOMEM = -2
+OASM_EBUSY = -3
+OASM_ETRUNC = -4
+OASM_ETIMEOUT = -5
+OASM_ECUDA = -6
+OASM_ESTATE = -7
+
+REPLACE = {"contained": 0, "same_end": 1, "never": 2}
+ORDER = {"per_start_length": 0, "per_start_best": 1}
+ACC = {"sum": 0, "last": 1}
+CMP = {"gt": 0, "ge": 1}
+OUTPUT = {"filtered": 0, "ends": 1, "all_hits": 2}
+
+HIT_DTYPE = np.dtype([("pattern_id", "<u4"), ("k", "<u4"), ("start", "<u8"), ("len", "<u4"),
+                      ("stream_id", "<u4"), ("decided_at", "<u8")])
+
+
+class OasmError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{msg} (code {code})")
+        self.code = code
+
+
+class oasm_rules(ctypes.Structure):
+    _fields_ = [("replace", ctypes.c_int32), ("order", ctypes.c_int32), ("acc", ctypes.c_int32),
+                ("cmp", ctypes.c_int32), ("output", ctypes.c_int32)]
+
+
+class oasm_config(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("max_streams", ctypes.c_uint32),
+                ("mem_budget", ctypes.c_uint64), ("region_bytes", ctypes.c_uint32),
+                ("tile_warps", ctypes.c_uint32), ("timing", ctypes.c_int32),
+                ("flush_timeout_ms", ctypes.c_uint32), ("cuda_stream", ctypes.c_void_p)]
+
+
+class oasm_hit(ctypes.Structure):
+    _fields_ = [("pattern_id", ctypes.c_uint32), ("k", ctypes.c_uint32), ("start", ctypes.c_uint64),
+                ("len", ctypes.c_uint32), ("stream_id", ctypes.c_uint32),
+                ("decided_at", ctypes.c_uint64)]
+
+
+assert ctypes.sizeof(oasm_hit) == HIT_DTYPE.itemsize == 32
+
+
+class oasm_stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in ("steps", "launches", "text_bytes", "cells",
+                                                "word_steps", "candidates", "hits", "kept",
+                                                "reruns")] + \
+               [(n, ctypes.c_double) for n in ("scan_ms", "verify_ms", "order_ms", "filter_ms",
+                                               "copy_ms", "step_ms")] + \
+               [("scan_launches", ctypes.c_uint64)]
+
+
+EXPORTS = ["oasm_config_default", "oasm_rules_default", "oasm_create", "oasm_destroy",
+           "oasm_open_stream", "oasm_close_stream", "oasm_feed", "oasm_feed_device",
+           "oasm_end_stream", "oasm_step", "oasm_flush", "oasm_ready", "oasm_get_stats", "oasm_reset_stats",
+           "oasm_cuda_stream", "oasm_last_error", "oasm_strerror", "oasm_autotune",
+           "oasm_measure_int_peak"]
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load(path: str | None = None):
+    """Loads liboasm.so (building it first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = path or _build.build()
+        if not os.path.exists(path):
+            raise OasmError(OASM_ECUDA, f"CUDA library {path} is missing")
+        lib = ctypes.CDLL(path)
+        vp, u32, u64, i32 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
+        u8pp = ctypes.POINTER(ctypes.c_void_p)
+        sig = {
+            "oasm_config_default": ([ctypes.POINTER(oasm_config)], i32),
+            "oasm_rules_default": ([ctypes.POINTER(oasm_rules)], i32),
+            "oasm_create": ([u8pp, ctypes.POINTER(u32), ctypes.POINTER(u32), u32,
+                             ctypes.POINTER(oasm_rules), ctypes.POINTER(oasm_config),
+                             ctypes.POINTER(vp)], i32),
+            "oasm_destroy": ([vp], i32),
+            "oasm_open_stream": ([vp, ctypes.POINTER(u32)], i32),
+            "oasm_close_stream": ([vp, u32], i32),
+            "oasm_feed": ([vp, u32, vp, ctypes.c_size_t], i32),
+            "oasm_feed_device": ([vp, u32, vp, ctypes.c_size_t], i32),
+            "oasm_end_stream": ([vp, u32], i32),
+            "oasm_step": ([vp], i32),
+            "oasm_flush": ([vp, u32, i32, vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)], i32),
+            "oasm_ready": ([vp, u32, ctypes.POINTER(ctypes.c_size_t)], i32),
+            "oasm_get_stats": ([vp, ctypes.POINTER(oasm_stats)], i32),
+            "oasm_reset_stats": ([vp], i32),
+            "oasm_cuda_stream": ([vp], vp),
+            "oasm_last_error": ([vp], ctypes.c_char_p),
+            "oasm_strerror": ([i32], ctypes.c_char_p),
+            "oasm_autotune": ([vp, vp, ctypes.c_size_t, ctypes.c_char_p, ctypes.c_size_t], i32),
+            "oasm_measure_int_peak": ([i32, ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_double)], i32),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+        return lib
+
+
+def _check(rc: int, ctx=None, allow=()):
+    if rc < 0 and rc not in allow:
+        lib = load()
+        msg = lib.oasm_last_error(ctx).decode() if lib else ""
+        raise OasmError(rc, msg or lib.oasm_strerror(rc).decode())
+    return rc
+
+
+def oasm_rules_make(replace="contained", order="per_start_length", acc="sum", cmp="gt",
+                    output="filtered") -> oasm_rules:
+    return oasm_rules(REPLACE[replace], ORDER[order], ACC[acc], CMP[cmp], OUTPUT[output])
+
+
+def oasm_config_make(**kw) -> oasm_config:
+    cfg = oasm_config()
+    load().oasm_config_default(ctypes.byref(cfg))
+    for k, v in kw.items():
+        setattr(cfg, k, v)
+    return cfg
+
+
+def _u8(a) -> np.ndarray:
+    if isinstance(a, (bytes, bytearray)):
+        return np.frombuffer(bytes(a), dtype=np.uint8)
+    if isinstance(a, str):
+        return np.frombuffer(a.encode("latin-1"), dtype=np.uint8)
+    return np.ascontiguousarray(np.asarray(a, dtype=np.uint8))
+
+
+def oasm_create(patterns, ks, rules: oasm_rules | dict | None = None,
+                cfg: oasm_config | dict | None = None):
+    lib = load()
+    pats = [_u8(p) for p in patterns]
+    n = len(pats)
+    ptrs = (ctypes.c_void_p * n)(*[p.ctypes.data for p in pats])
+    lens = (ctypes.c_uint32 * n)(*[p.size for p in pats])
+    kk = (ctypes.c_uint32 * n)(*[int(k) for k in ks])
+    if isinstance(rules, dict):
+        rules = oasm_rules_make(**rules)
+    if isinstance(cfg, dict):
+        cfg = oasm_config_make(**cfg)
+    ctx = ctypes.c_void_p()
+    rc = lib.oasm_create(ptrs, lens, kk, n, ctypes.byref(rules) if rules else None,
+                         ctypes.byref(cfg) if cfg else None, ctypes.byref(ctx))
+    _check(rc, None)
+    return ctx
+
+
+def oasm_destroy(ctx):
+    return _check(load().oasm_destroy(ctx), None)
+
+
+def oasm_open_stream(ctx) -> int:
+    sid = ctypes.c_uint32()
+    _check(load().oasm_open_stream(ctx, ctypes.byref(sid)), ctx)
+    return sid.value
+
+
+def oasm_close_stream(ctx, sid: int):
+    return _check(load().oasm_close_stream(ctx, sid), ctx)
+
+
+def oasm_feed(ctx, sid: int, chunk):
+    a = _u8(chunk)
+    return _check(load().oasm_feed(ctx, sid, a.ctypes.data if a.size else None, a.size), ctx)
+
+
+def _dev_ptr(d):
+    if isinstance(d, int):
+        return d
+    if hasattr(d, "data_ptr"):
+        if not d.is_cuda or not d.is_contiguous():
+            raise OasmError(OASM_EINVAL, "need a contiguous CUDA tensor")
+        return d.data_ptr()
+    raise OasmError(OASM_EINVAL, "device chunk must be a CUDA tensor or a device pointer")
+
+
+def oasm_feed_device(ctx, sid: int, dchunk, n: int | None = None):
+    if n is None:
+        n = dchunk.numel() * dchunk.element_size()
+    return _check(load().oasm_feed_device(ctx, sid, _dev_ptr(dchunk), n), ctx)
+
+
+def oasm_end_stream(ctx, sid: int):
+    return _check(load().oasm_end_stream(ctx, sid), ctx)
+
+
+def oasm_step(ctx):
+    return _check(load().oasm_step(ctx), ctx)
+
+
+def oasm_ready(ctx, sid: int) -> int:
+    n = ctypes.c_size_t(0)
+    _check(load().oasm_ready(ctx, sid, ctypes.byref(n)), ctx)
+    return n.value
+
+
+def oasm_flush(ctx, sid: int, end_of_stream: bool = False) -> np.ndarray:
+    """Every hit of the stream decided so far, in canonical order.
+
+    The first call runs any pending step with no output buffer; the second
+    copies the whole queue into one array sized by ``oasm_ready``."""
+    lib = load()
+    n = ctypes.c_size_t(0)
+    rc = lib.oasm_flush(ctx, sid, 1 if end_of_stream else 0, None, 0, ctypes.byref(n))
+    _check(rc, ctx, allow=(OASM_ETRUNC,))
+    if rc != OASM_ETRUNC:
+        return np.zeros(0, dtype=HIT_DTYPE)
+    cnt = oasm_ready(ctx, sid)
+    buf = np.zeros(cnt, dtype=HIT_DTYPE)
+    rc = lib.oasm_flush(ctx, sid, 0, buf.ctypes.data, cnt, ctypes.byref(n))
+    _check(rc, ctx)
+    return buf[: n.value]
+
+
+def oasm_get_stats(ctx) -> dict:
+    st = oasm_stats()
+    _check(load().oasm_get_stats(ctx, ctypes.byref(st)), ctx)
+    return {n: getattr(st, n) for n, _ in oasm_stats._fields_}
+
+
+def oasm_reset_stats(ctx):
+    return _check(load().oasm_reset_stats(ctx), ctx)
+
+
+def oasm_cuda_stream(ctx) -> int:
+    return load().oasm_cuda_stream(ctx) or 0
+
+
+def oasm_autotune(ctx, dsample, n: int | None = None) -> str:
+    if n is None:
+        n = dsample.numel()
+    buf = ctypes.create_string_buffer(65536)
+    _check(load().oasm_autotune(ctx, _dev_ptr(dsample), n, buf, 65536), ctx)
+    return buf.value.decode()
+
+
+def oasm_measure_int_peak(device: int = 0):
+    """(integer ops per second, ms of the best launch) of the scan's op mix."""
+    ops, ms = ctypes.c_double(), ctypes.c_double()
+    _check(load().oasm_measure_int_peak(device, ctypes.byref(ops), ctypes.byref(ms)))
+    return ops.value, ms.value
+
+
+def oasm_strerror(code: int) -> str:
+    return load().oasm_strerror(code).decode()
+
+
+def oasm_last_error(ctx=None) -> str:
+    return load().oasm_last_error(ctx).decode()
+
+
+class Matcher:
+    """Convenience owner of one context (still marshalling only)."""
+
+    def __init__(self, patterns, ks, rules=None, **cfg):
+        self.ctx = oasm_create(patterns, ks, rules, cfg or None)
+
+    def close(self):
+        if self.ctx is not None:
+            oasm_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def search(self, text, device=False) -> np.ndarray:
+        """One whole text as one stream: feed, end, flush."""
+        sid = oasm_open_stream(self.ctx)
+        try:
+            if device:
+                oasm_feed_device(self.ctx, sid, text)
+            else:
+                oasm_feed(self.ctx, sid, text)
+            return oasm_flush(self.ctx, sid, end_of_stream=True)
+        finally:
+            oasm_close_stream(self.ctx, sid)

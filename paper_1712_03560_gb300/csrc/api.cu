@@ -1,0 +1,1118 @@
+// api.cu -- host side of the OASM C ABI (declared in include/oasm.h).
+//
+// A context owns the pattern tables, the per-stream device state and the
+// buffers of one batched step.  A step takes the pending input of every
+// stream, lays it out in a device text arena behind each stream's stored
+// tail, and runs the device path on the context's CUDA stream:
+//   gather -> scan (one launch per word-count class) -> verify -> radix sort
+//   -> filter -> finalize -> tails
+// then copies the per-step counters and the emitted records back.  If a
+// device buffer was too small, the kernels that change stream state skip
+// their work, the host grows the buffer and re-runs the step from the same
+// (unchanged) state.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "kernels.h"
+
+using namespace oasm;
+
+namespace {
+
+constexpr size_t kFrontPad = 1024;   // arena bytes before the first work item
+constexpr size_t kEndPad = 2048;     // arena bytes after the last one
+constexpr size_t kChunk = 1 << 20;   // largest gather copy per block
+constexpr int kSortBlocks = 4 * 152;
+
+struct Piece {
+  bool dev;
+  const uint8_t* dptr;  // device pointer (dev) or nullptr
+  size_t host_off;      // offset into the pinned staging buffer (host pieces)
+  size_t n;
+};
+
+struct StreamRec {
+  bool open = false;
+  int64_t pos = 0;        // symbols processed
+  int32_t tail_len = 0;   // symbols of the stored tail
+  bool eos_pending = false;
+  std::vector<Piece> pieces;
+  size_t pending = 0;
+  std::vector<oasm_hit> ready;  // decided hits; [head, end) not yet returned
+  size_t head = 0;
+  std::vector<size_t> runs;     // starts of canonically sorted runs in `ready`
+};
+
+bool canon_less(const oasm_hit& a, const oasm_hit& b) {
+  if (a.pattern_id != b.pattern_id) return a.pattern_id < b.pattern_id;
+  if (a.decided_at != b.decided_at) return a.decided_at < b.decided_at;
+  if (a.k != b.k) return a.k < b.k;
+  return a.len < b.len;
+}
+
+struct Bucket {
+  int W = 0;
+  int max_nseg = 1;
+  int warps = 8;          // warps per scan block
+  int chunk = 1024;       // text bytes per TMA buffer (dictionary mapping)
+  double region_scale = 1.0;
+  int kmax = 0;
+  int ov_max = 1;
+  std::vector<LaneGroup> groups;
+  LaneGroup* d_groups = nullptr;
+  uint32_t* d_peq = nullptr;
+};
+
+template <class T>
+struct DevArray {
+  T* p = nullptr;
+  size_t cap = 0;  // elements
+};
+
+}  // namespace
+
+struct oasm_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  oasm_config cfg{};
+  Rules rules{};
+  std::string err;
+  int num_sms = 152;
+
+  uint32_t n_pat = 0;
+  std::vector<std::vector<uint8_t>> pats;
+  std::vector<uint8_t> m, K;
+  std::vector<uint32_t> mem_off;
+  uint32_t mem_stride = 0;
+  int T = 1;
+  int kmax = 0;
+  uint8_t* d_m = nullptr;
+  uint8_t* d_K = nullptr;
+  uint32_t* d_mem_off = nullptr;
+  uint32_t* d_peq_rev = nullptr;
+  std::vector<Bucket> buckets;
+
+  // streams
+  std::vector<StreamRec> streams;
+  uint8_t* d_tails = nullptr;
+  WinHdr* d_hdr = nullptr;
+  MemRow* d_mem = nullptr;
+  size_t stream_bytes = 0;
+  uint32_t n_open = 0;
+
+  // host staging (pinned)
+  uint8_t* h_stage = nullptr;
+  size_t h_stage_cap = 0, h_stage_used = 0;
+  size_t stage_limit = size_t(2) << 30;
+
+  // step buffers
+  DevArray<uint8_t> arena, dstage, upload;
+  DevArray<Candidate> cand;
+  DevArray<unsigned long long> keys, keys_alt;
+  DevArray<DevHit> out, out_sorted;
+  DevArray<unsigned long long> okeys, okeys_alt;
+  DevArray<uint32_t> ovals, ovals_alt;
+  DevArray<WinHdr> pool_hdr;
+  DevArray<MemRow> pool_mem;
+  DevArray<int32_t> pair_pool;
+  StepCounters* d_ctr = nullptr;
+  StepCounters* h_ctr = nullptr;
+  unsigned int* d_hist = nullptr;
+  uint8_t* h_upload = nullptr;
+  size_t h_upload_cap = 0;
+  DevHit* h_out = nullptr;
+  size_t h_out_cap = 0;
+  cudaEvent_t ev[8] = {};
+  cudaEvent_t done = nullptr;
+
+  oasm_stats st{};
+};
+
+namespace {
+
+int fail(oasm_ctx* c, int code, const char* fmt, ...) {
+  if (c) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    c->err = buf;
+  }
+  return code;
+}
+
+thread_local std::string g_create_err;
+
+#define CK(call)                                                                        \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      return fail(ctx, OASM_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));     \
+  } while (0)
+
+template <class T>
+int ensure(oasm_ctx* ctx, DevArray<T>& a, size_t n, const char* what) {
+  if (a.cap >= n && a.p) return OASM_OK;
+  size_t want = std::max<size_t>(n, a.cap + a.cap / 2);
+  want = std::max<size_t>(want, 1024);
+  if (a.p) cudaFree(a.p);
+  a.p = nullptr;
+  a.cap = 0;
+  cudaError_t e = cudaMalloc(&a.p, want * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    a.p = nullptr;
+    return fail(ctx, OASM_ENOMEM, "device allocation of %zu bytes for %s failed: %s",
+                want * sizeof(T), what, cudaGetErrorString(e));
+  }
+  a.cap = want;
+  return OASM_OK;
+}
+
+int ensure_host(oasm_ctx* ctx, uint8_t** p, size_t* cap, size_t n, size_t keep) {
+  if (*cap >= n && *p) return OASM_OK;
+  size_t want = std::max<size_t>(n, *cap + *cap / 2);
+  want = std::max<size_t>(want, 1 << 16);
+  uint8_t* q = nullptr;
+  cudaError_t e = cudaHostAlloc(&q, want, cudaHostAllocDefault);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, OASM_ENOMEM, "pinned allocation of %zu bytes failed: %s", want,
+                cudaGetErrorString(e));
+  }
+  if (*p) {
+    if (keep) memcpy(q, *p, keep);
+    cudaFreeHost(*p);
+  }
+  *p = q;
+  *cap = want;
+  return OASM_OK;
+}
+
+int ensure_out(oasm_ctx* ctx, size_t n) {
+  int rc;
+  if ((rc = ensure(ctx, ctx->out, n, "records"))) return rc;
+  if ((rc = ensure(ctx, ctx->out_sorted, n, "records"))) return rc;
+  if ((rc = ensure(ctx, ctx->okeys, n, "record keys"))) return rc;
+  if ((rc = ensure(ctx, ctx->okeys_alt, n, "record keys"))) return rc;
+  if ((rc = ensure(ctx, ctx->ovals, n, "record order"))) return rc;
+  return ensure(ctx, ctx->ovals_alt, n, "record order");
+}
+
+int bits_for(uint64_t v) {  // bits needed to hold 0..v
+  int b = 0;
+  while (b < 64 && (v >> b) != 0) ++b;
+  return std::max(b, 1);
+}
+
+int wait_event(oasm_ctx* ctx, cudaEvent_t ev) {
+  const auto t0 = std::chrono::steady_clock::now();
+  const uint32_t lim = ctx->cfg.flush_timeout_ms ? ctx->cfg.flush_timeout_ms : 600000u;
+  while (true) {
+    cudaError_t q = cudaEventQuery(ev);
+    if (q == cudaSuccess) return OASM_OK;
+    if (q != cudaErrorNotReady)
+      return fail(ctx, OASM_ECUDA, "device step failed: %s", cudaGetErrorString(q));
+    const auto ms = std::chrono::duration_cast<std::chrono::milliseconds>(
+                        std::chrono::steady_clock::now() - t0).count();
+    if (ms > lim) return fail(ctx, OASM_ETIMEOUT, "device step did not finish in %u ms", lim);
+    std::this_thread::yield();
+  }
+}
+
+void free_ctx(oasm_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  auto f = [](void* p) { if (p) cudaFree(p); };
+  f(c->d_m); f(c->d_K); f(c->d_mem_off); f(c->d_peq_rev);
+  for (auto& b : c->buckets) { f(b.d_groups); f(b.d_peq); }
+  f(c->d_tails); f(c->d_hdr); f(c->d_mem);
+  f(c->arena.p); f(c->dstage.p); f(c->upload.p); f(c->cand.p); f(c->keys.p);
+  f(c->keys_alt.p); f(c->out.p); f(c->pool_hdr.p); f(c->pool_mem.p); f(c->pair_pool.p);
+  f(c->out_sorted.p); f(c->okeys.p); f(c->okeys_alt.p); f(c->ovals.p); f(c->ovals_alt.p);
+  f(c->d_ctr); f(c->d_hist);
+  if (c->h_ctr) cudaFreeHost(c->h_ctr);
+  if (c->h_stage) cudaFreeHost(c->h_stage);
+  if (c->h_upload) cudaFreeHost(c->h_upload);
+  if (c->h_out) cudaFreeHost(c->h_out);
+  for (auto& e : c->ev) if (e) cudaEventDestroy(e);
+  if (c->done) cudaEventDestroy(c->done);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+// --------------------------------------------------------------- tables
+int build_tables(oasm_ctx* ctx) {
+  const uint32_t n = ctx->n_pat;
+  // reversed, bottom-aligned Peq (verification pass): [p][256][4]
+  std::vector<uint32_t> rev(size_t(n) * 256 * 4, 0u);
+  for (uint32_t p = 0; p < n; ++p) {
+    const auto& s = ctx->pats[p];
+    const int m = int(s.size());
+    for (int j = 0; j < m; ++j) {
+      const uint8_t c = s[m - 1 - j];
+      rev[(size_t(p) * 256 + c) * 4 + (j >> 5)] |= 1u << (j & 31);
+    }
+  }
+  CK(cudaMalloc(&ctx->d_peq_rev, rev.size() * 4));
+  CK(cudaMemcpy(ctx->d_peq_rev, rev.data(), rev.size() * 4, cudaMemcpyHostToDevice));
+  CK(cudaMalloc(&ctx->d_m, n));
+  CK(cudaMalloc(&ctx->d_K, n));
+  CK(cudaMemcpy(ctx->d_m, ctx->m.data(), n, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->d_K, ctx->K.data(), n, cudaMemcpyHostToDevice));
+  ctx->mem_off.resize(n);
+  uint32_t off = 0;
+  for (uint32_t p = 0; p < n; ++p) {
+    ctx->mem_off[p] = off;
+    off += ctx->K[p] + 1u;
+  }
+  ctx->mem_stride = off;
+  CK(cudaMalloc(&ctx->d_mem_off, size_t(n) * 4));
+  CK(cudaMemcpy(ctx->d_mem_off, ctx->mem_off.data(), size_t(n) * 4, cudaMemcpyHostToDevice));
+
+  // forward lane groups per word-count class, patterns sorted by length so a
+  // group's lanes need similar warm-up
+  for (int W = 1; W <= kMaxW; ++W) {
+    std::vector<uint32_t> ids;
+    for (uint32_t p = 0; p < n; ++p)
+      if ((ctx->m[p] + 31) / 32 == W) ids.push_back(p);
+    if (ids.empty()) continue;
+    std::stable_sort(ids.begin(), ids.end(),
+                     [&](uint32_t a, uint32_t b) { return ctx->m[a] < ctx->m[b]; });
+    Bucket bk;
+    bk.W = W;
+    const size_t RW = size_t(32) * W;  // words per symbol row: [w][lane]
+    std::vector<uint32_t> peq;
+    for (size_t g0 = 0; g0 < ids.size(); g0 += kLaneGroup) {
+      const int np = int(std::min<size_t>(kLaneGroup, ids.size() - g0));
+      // a class with 32 or more patterns runs one pattern per lane (idle lanes
+      // in its last group); a smaller one spreads each pattern over lanes
+      const int nseg = ids.size() >= size_t(kLaneGroup) ? 1 : std::max(1, kLaneGroup / np);
+      LaneGroup G;
+      memset(&G, 0, sizeof G);
+      G.nseg = nseg;
+      G.W = W;
+      G.ov = 1;
+      const size_t base = peq.size();
+      peq.resize(base + size_t(256) * RW, 0u);
+      for (int l = 0; l < kLaneGroup; ++l) {
+        const int pi = l / nseg, sg = l % nseg;
+        if (pi >= np) {
+          G.pat[l] = -1;
+          G.m[l] = uint8_t(32 * W);
+          G.K[l] = 0;
+          G.seg[l] = 0;
+          continue;
+        }
+        const uint32_t p = ids[g0 + pi];
+        const auto& s = ctx->pats[p];
+        const int m = int(s.size());
+        G.pat[l] = int32_t(p);
+        G.m[l] = uint8_t(m);
+        G.K[l] = ctx->K[p];
+        G.seg[l] = uint8_t(sg);
+        G.ov = std::max(G.ov, m + ctx->K[p] - 1);
+        bk.kmax = std::max<int>(bk.kmax, ctx->K[p]);
+        const int off0 = 32 * W - m;  // top-aligned
+        for (int j = 0; j < m; ++j) {
+          const int bit = off0 + j;
+          peq[base + size_t(s[j]) * RW + size_t(bit >> 5) * 32 + l] |= 1u << (bit & 31);
+        }
+      }
+      bk.ov_max = std::max(bk.ov_max, G.ov);
+      bk.max_nseg = std::max(bk.max_nseg, nseg);
+      bk.groups.push_back(G);
+    }
+    CK(cudaMalloc(&bk.d_groups, bk.groups.size() * sizeof(LaneGroup)));
+    CK(cudaMemcpy(bk.d_groups, bk.groups.data(), bk.groups.size() * sizeof(LaneGroup),
+                  cudaMemcpyHostToDevice));
+    CK(cudaMalloc(&bk.d_peq, peq.size() * 4));
+    CK(cudaMemcpy(bk.d_peq, peq.data(), peq.size() * 4, cudaMemcpyHostToDevice));
+    ctx->buckets.push_back(bk);
+  }
+  return OASM_OK;
+}
+
+StepParams make_params(oasm_ctx* ctx, const WorkItem* d_items, uint32_t n_items, int sb, int kb) {
+  StepParams P{};
+  P.m = ctx->d_m;
+  P.K = ctx->d_K;
+  P.mem_off = ctx->d_mem_off;
+  P.peq_rev = ctx->d_peq_rev;
+  P.n_pat = ctx->n_pat;
+  P.mem_stride = ctx->mem_stride;
+  P.rules = ctx->rules;
+  P.tails = ctx->d_tails;
+  P.hdr = ctx->d_hdr;
+  P.mem = ctx->d_mem;
+  P.T = ctx->T;
+  P.items = d_items;
+  P.n_items = n_items;
+  P.arena = ctx->arena.p;
+  P.cand = ctx->cand.p;
+  P.cap_cand = ctx->cand.cap;
+  P.keys = ctx->keys.p;
+  P.keys_alt = ctx->keys_alt.p;
+  P.cap_hits = std::min(ctx->keys.cap, ctx->keys_alt.cap);
+  P.out = ctx->out.p;
+  P.okeys = ctx->okeys.p;
+  P.ovals = ctx->ovals.p;
+  P.cap_out = std::min({ctx->out.cap, ctx->out_sorted.cap, ctx->okeys.cap, ctx->okeys_alt.cap,
+                        ctx->ovals.cap, ctx->ovals_alt.cap, size_t(0xffffffffu)});
+  P.pool_hdr = ctx->pool_hdr.p;
+  P.pool_mem = ctx->pool_mem.p;
+  P.cap_pool = std::min(ctx->pool_hdr.cap, ctx->pool_mem.cap / (kMaxK + 1));
+  P.pair_pool = ctx->pair_pool.p;
+  P.ctr = ctx->d_ctr;
+  P.start_bits = sb;
+  P.key_bits = kb;
+  return P;
+}
+
+// Region length (symbols of reported ends per warp) for a bucket.
+int64_t region_len(oasm_ctx* ctx, const Bucket& b, int64_t total_ends) {
+  if (ctx->cfg.region_bytes) {
+    int64_t r = int64_t(ctx->cfg.region_bytes) * b.max_nseg;
+    return std::max<int64_t>(16 * b.max_nseg, (r + 15) & ~int64_t(15));
+  }
+  const double target_warps = double(ctx->num_sms) * 48.0 * 4.0;
+  double r = double(total_ends) * double(b.groups.size()) / target_warps * b.region_scale;
+  const double lane_min = std::max(64.0, 4.0 * b.ov_max);
+  r = std::max(r, lane_min * b.max_nseg);
+  r = std::min(r, double(int64_t(1) << 24));
+  int64_t ri = int64_t(r);
+  const int64_t q = 16 * b.max_nseg;
+  return std::max<int64_t>(q, (ri + q - 1) / q * q);
+}
+
+struct StepPlan {
+  std::vector<WorkItem> items;
+  std::vector<uint32_t> sids;
+  std::vector<size_t> take;
+  std::vector<Region> regions;       // all buckets, concatenated
+  std::vector<size_t> region_off;    // per bucket
+  std::vector<CopyChunk> chunks;
+  size_t arena_bytes = 0;
+  int sb = 1, kb = 10;
+  uint64_t new_bytes = 0;
+};
+
+int plan_step(oasm_ctx* ctx, StepPlan& pl) {
+  const int T = ctx->T;
+  size_t off = kFrontPad;
+  const int pb_guess = bits_for(uint64_t(ctx->streams.size()) * ctx->n_pat);
+  const int sb_max = 64 - kLowBits - pb_guess;
+  const int64_t lim = std::min<int64_t>((int64_t(1) << std::min(sb_max, 40)) - T - 1,
+                                        int64_t(1) << 34);
+  for (uint32_t sid = 0; sid < ctx->streams.size(); ++sid) {
+    StreamRec& s = ctx->streams[sid];
+    if (!s.open || (s.pending == 0 && !s.eos_pending)) continue;
+    const int64_t take = std::min<int64_t>(int64_t(s.pending), lim);
+    WorkItem w{};
+    const int64_t tail = s.tail_len;
+    size_t new_off = (off + size_t(tail) + 15) & ~size_t(15);
+    w.arena_base = new_off - size_t(tail);
+    w.base_pos = s.pos - tail;
+    w.e_prev = s.pos;
+    w.e_new = s.pos + take;
+    w.slot = sid;
+    w.eos = (s.eos_pending && take == int64_t(s.pending)) ? 1u : 0u;
+    if (tail > 0) {
+      CopyChunk ch{ctx->d_tails + size_t(sid) * T, w.arena_base, uint32_t(tail), 0};
+      pl.chunks.push_back(ch);
+    }
+    // new bytes, piece by piece
+    int64_t left = take;
+    size_t dst = new_off;
+    for (const Piece& pc : s.pieces) {
+      if (left <= 0) break;
+      const size_t n = size_t(std::min<int64_t>(left, int64_t(pc.n)));
+      const uint8_t* src = pc.dev ? pc.dptr : ctx->dstage.p + pc.host_off;
+      for (size_t o = 0; o < n; o += kChunk) {
+        CopyChunk ch{src + o, dst + o, uint32_t(std::min(kChunk, n - o)), 0};
+        pl.chunks.push_back(ch);
+      }
+      dst += n;
+      left -= int64_t(n);
+    }
+    off = new_off + size_t(take) + 64;
+    pl.items.push_back(w);
+    pl.sids.push_back(sid);
+    pl.take.push_back(size_t(take));
+    pl.new_bytes += uint64_t(take);
+  }
+  pl.arena_bytes = off + kEndPad;
+  if (pl.items.empty()) return OASM_OK;
+  uint64_t maxspan = 1;
+  for (const auto& w : pl.items) maxspan = std::max<uint64_t>(maxspan, uint64_t(w.e_new - w.base_pos));
+  const int pb = bits_for(uint64_t(pl.items.size()) * ctx->n_pat - 1);
+  pl.sb = bits_for(maxspan);
+  pl.kb = pb + pl.sb + kLowBits;
+  if (pl.kb > 64)
+    return fail(ctx, OASM_EINVAL, "step too large for 64-bit hit keys (%d bits)", pl.kb);
+  // regions per bucket
+  for (const Bucket& b : ctx->buckets) {
+    pl.region_off.push_back(pl.regions.size());
+    int64_t total = 0;
+    for (const auto& w : pl.items) {
+      const int64_t lo = std::max<int64_t>(0, w.e_prev - 2 * b.kmax);
+      total += std::max<int64_t>(0, w.e_new - lo);
+    }
+    const int64_t R = region_len(ctx, b, total);
+    for (uint32_t i = 0; i < pl.items.size(); ++i) {
+      const WorkItem& w = pl.items[i];
+      const int64_t lo = std::max<int64_t>(0, w.e_prev - 2 * b.kmax);
+      for (int64_t a = lo; a < w.e_new; a += R) {
+        Region r{};
+        r.wi = i;
+        r.a = a;
+        r.b = std::min(w.e_new, a + R);
+        pl.regions.push_back(r);
+      }
+    }
+  }
+  pl.region_off.push_back(pl.regions.size());
+  return OASM_OK;
+}
+
+int run_step_once(oasm_ctx* ctx, StepPlan& pl, const WorkItem* d_items, const Region* d_regions,
+                  const CopyChunk* d_chunks, bool* overflow) {
+  cudaStream_t s = ctx->stream;
+  const uint32_t n_items = uint32_t(pl.items.size());
+  const bool tm = ctx->cfg.timing != 0;
+  if (tm) CK(cudaEventRecord(ctx->ev[0], s));
+  CK(cudaMemsetAsync(ctx->d_ctr, 0, sizeof(StepCounters), s));
+  CK(cudaMemsetAsync(ctx->pair_pool.p, 0xff, size_t(n_items) * ctx->n_pat * sizeof(int32_t), s));
+  CK(launch_gather(d_chunks, int(pl.chunks.size()), ctx->arena.p, s));
+  ctx->st.launches += pl.chunks.empty() ? 0 : 1;
+  if (tm) CK(cudaEventRecord(ctx->ev[1], s));
+  for (size_t bi = 0; bi < ctx->buckets.size(); ++bi) {
+    const Bucket& b = ctx->buckets[bi];
+    ScanArgs a{};
+    a.groups = b.d_groups;
+    a.peq = b.d_peq;
+    a.n_groups = int(b.groups.size());
+    a.W = b.W;
+    a.regions = d_regions + pl.region_off[bi];
+    a.n_regions = int(pl.region_off[bi + 1] - pl.region_off[bi]);
+    a.warps = ctx->cfg.tile_warps ? int(ctx->cfg.tile_warps) : b.warps;
+    a.resv = b.max_nseg > 1 ? 256 : 32;
+    a.dict = b.max_nseg == 1 ? 1 : 0;
+    a.chunk = b.chunk;
+    a.items = d_items;
+    a.arena = ctx->arena.p;
+    a.cand = ctx->cand.p;
+    a.cap_cand = ctx->cand.cap;
+    a.ctr = ctx->d_ctr;
+    if (a.n_regions == 0) continue;
+    CK(launch_scan(a, s));
+    ctx->st.launches += 1;
+    ctx->st.scan_launches += 1;
+  }
+  if (tm) CK(cudaEventRecord(ctx->ev[2], s));
+  StepParams P = make_params(ctx, d_items, n_items, pl.sb, pl.kb);
+  CK(launch_verify(P, s));
+  ctx->st.launches += 1;
+  if (tm) CK(cudaEventRecord(ctx->ev[3], s));
+  unsigned long long* sorted = P.keys;
+  if (ctx->rules.output == OASM_OUT_FILTERED) {
+    int nl = 0;
+    SortArgs sa{P.keys, P.keys_alt, nullptr, nullptr, &ctx->d_ctr->n_hits, P.cap_hits,
+                kKBits, pl.kb, ctx->d_hist, kSortBlocks};
+    CK(launch_sort(sa, &sorted, nullptr, &nl, s));
+    ctx->st.launches += uint64_t(nl);
+    if (tm) CK(cudaEventRecord(ctx->ev[4], s));
+    CK(launch_filter(P, sorted, s));
+    CK(launch_finalize(P, s));
+    ctx->st.launches += 2;
+  } else if (tm) {
+    CK(cudaEventRecord(ctx->ev[4], s));
+  }
+  CK(launch_tails(P, s));
+  ctx->st.launches += 1;
+  {  // emitted records -> canonical order (work item, pattern, decided_at, k, length)
+    int nl = 0;
+    unsigned long long* ks = nullptr;
+    uint32_t* vs = nullptr;
+    SortArgs sa{ctx->okeys.p, ctx->okeys_alt.p, ctx->ovals.p, ctx->ovals_alt.p,
+                &ctx->d_ctr->n_out, P.cap_out, 0, pl.kb, ctx->d_hist, kSortBlocks};
+    CK(launch_sort(sa, &ks, &vs, &nl, s));
+    CK(launch_permute(ctx->out.p, vs, ctx->out_sorted.p, &ctx->d_ctr->n_out, P.cap_out, s));
+    ctx->st.launches += uint64_t(nl) + 1;
+  }
+  if (tm) CK(cudaEventRecord(ctx->ev[5], s));
+  CK(cudaMemcpyAsync(ctx->h_ctr, ctx->d_ctr, sizeof(StepCounters), cudaMemcpyDeviceToHost, s));
+  CK(cudaEventRecord(ctx->done, s));
+  int rc = wait_event(ctx, ctx->done);
+  if (rc) return rc;
+  const StepCounters c = *ctx->h_ctr;
+  if (c.overflow & (1u << 16))
+    return fail(ctx, OASM_ETIMEOUT, "a bounded wait for a TMA copy ran out in the scan");
+  *overflow = c.overflow != 0;
+  if (*overflow) {
+    // grow what was too small; the step is re-run from unchanged state
+    if ((c.overflow & 1u) || c.n_cand > ctx->cand.cap)
+      if ((rc = ensure(ctx, ctx->cand, size_t(c.n_cand * 5 / 4 + 1024), "candidates"))) return rc;
+    if ((c.overflow & 2u) || c.n_hits > P.cap_hits) {
+      const size_t want = size_t(c.n_hits * 5 / 4 + 1024);
+      if ((rc = ensure(ctx, ctx->keys, want, "hit keys"))) return rc;
+      if ((rc = ensure(ctx, ctx->keys_alt, want, "hit keys"))) return rc;
+    }
+    if ((c.overflow & 4u) || c.n_out > P.cap_out)
+      if ((rc = ensure_out(ctx, size_t(c.n_out * 5 / 4 + 1024)))) return rc;
+    if ((c.overflow & 8u) || c.n_pool > P.cap_pool) {
+      const size_t want = size_t(c.n_pool * 5 / 4 + 1024);
+      if ((rc = ensure(ctx, ctx->pool_hdr, want, "window pool"))) return rc;
+      if ((rc = ensure(ctx, ctx->pool_mem, want * (kMaxK + 1), "window pool"))) return rc;
+    }
+    ctx->st.reruns += 1;
+    return OASM_OK;
+  }
+  if (tm) {
+    float ms = 0;
+    cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]); ctx->st.copy_ms += ms;
+    cudaEventElapsedTime(&ms, ctx->ev[1], ctx->ev[2]); ctx->st.scan_ms += ms;
+    cudaEventElapsedTime(&ms, ctx->ev[2], ctx->ev[3]); ctx->st.verify_ms += ms;
+    cudaEventElapsedTime(&ms, ctx->ev[3], ctx->ev[4]); ctx->st.order_ms += ms;
+    cudaEventElapsedTime(&ms, ctx->ev[4], ctx->ev[5]); ctx->st.filter_ms += ms;
+    cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[5]); ctx->st.step_ms += ms;
+  }
+  ctx->st.candidates += c.n_cand;
+  ctx->st.hits += c.n_hits;
+  ctx->st.kept += c.n_out;
+  // records -> streams
+  if (c.n_out) {
+    const size_t n = size_t(c.n_out);
+    if (n > ctx->h_out_cap) {
+      if (ctx->h_out) cudaFreeHost(ctx->h_out);
+      ctx->h_out = nullptr;
+      ctx->h_out_cap = 0;
+      if (cudaHostAlloc(&ctx->h_out, n * sizeof(DevHit), cudaHostAllocDefault) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, OASM_ENOMEM, "pinned allocation for %zu records failed", n);
+      }
+      ctx->h_out_cap = n;
+    }
+    CK(cudaMemcpy(ctx->h_out, ctx->out_sorted.p, n * sizeof(DevHit), cudaMemcpyDeviceToHost));
+    // sorted by work item first: one contiguous, already canonical run per stream
+    const oasm_hit* recs = reinterpret_cast<const oasm_hit*>(ctx->h_out);
+    for (size_t i = 0; i < n;) {
+      size_t j = i + 1;
+      while (j < n && recs[j].stream_id == recs[i].stream_id) ++j;
+      StreamRec& sr = ctx->streams[recs[i].stream_id];
+      sr.runs.push_back(sr.ready.size());
+      sr.ready.insert(sr.ready.end(), recs + i, recs + j);
+      i = j;
+    }
+  }
+  return OASM_OK;
+}
+
+int run_step(oasm_ctx* ctx) {
+  CK(cudaSetDevice(ctx->device));
+  while (true) {
+    int rc;
+    // device staging of host bytes first: host pieces are gathered from it
+    if (ctx->h_stage_used &&
+        (rc = ensure(ctx, ctx->dstage, ctx->h_stage_used, "staging")))
+      return rc;
+    StepPlan pl;
+    if ((rc = plan_step(ctx, pl))) return rc;
+    if (pl.items.empty()) return OASM_OK;
+    if (ctx->h_stage_used)
+      CK(cudaMemcpyAsync(ctx->dstage.p, ctx->h_stage, ctx->h_stage_used, cudaMemcpyHostToDevice,
+                         ctx->stream));
+    if ((rc = ensure(ctx, ctx->arena, pl.arena_bytes, "text arena"))) return rc;
+    if ((rc = ensure(ctx, ctx->pair_pool, pl.items.size() * size_t(ctx->n_pat), "pair table")))
+      return rc;
+    if (!ctx->cand.p && (rc = ensure(ctx, ctx->cand, std::max<size_t>(1 << 16, pl.new_bytes / 64), "candidates"))) return rc;
+    if (!ctx->keys.p) {
+      const size_t h0 = std::max<size_t>(1 << 16, pl.new_bytes / 64);
+      if ((rc = ensure(ctx, ctx->keys, h0, "hit keys"))) return rc;
+      if ((rc = ensure(ctx, ctx->keys_alt, h0, "hit keys"))) return rc;
+    }
+    if (!ctx->out.p && (rc = ensure_out(ctx, 1 << 16))) return rc;
+    if (!ctx->pool_hdr.p) {
+      if ((rc = ensure(ctx, ctx->pool_hdr, 1 << 14, "window pool"))) return rc;
+      if ((rc = ensure(ctx, ctx->pool_mem, size_t(1 << 14) * (kMaxK + 1), "window pool"))) return rc;
+    }
+    // one upload: items | regions | chunks
+    const size_t bi = pl.items.size() * sizeof(WorkItem);
+    const size_t br = pl.regions.size() * sizeof(Region);
+    const size_t bc = pl.chunks.size() * sizeof(CopyChunk);
+    const size_t o_r = (bi + 255) & ~size_t(255), o_c = (o_r + br + 255) & ~size_t(255);
+    const size_t total = o_c + bc + 256;
+    if ((rc = ensure_host(ctx, &ctx->h_upload, &ctx->h_upload_cap, total, 0))) return rc;
+    if ((rc = ensure(ctx, ctx->upload, total, "step upload"))) return rc;
+    memcpy(ctx->h_upload, pl.items.data(), bi);
+    memcpy(ctx->h_upload + o_r, pl.regions.data(), br);
+    memcpy(ctx->h_upload + o_c, pl.chunks.data(), bc);
+    CK(cudaMemcpyAsync(ctx->upload.p, ctx->h_upload, total, cudaMemcpyHostToDevice, ctx->stream));
+    const WorkItem* d_items = reinterpret_cast<const WorkItem*>(ctx->upload.p);
+    const Region* d_regions = reinterpret_cast<const Region*>(ctx->upload.p + o_r);
+    const CopyChunk* d_chunks = reinterpret_cast<const CopyChunk*>(ctx->upload.p + o_c);
+    bool over = true;
+    for (int attempt = 0; over; ++attempt) {
+      if (attempt > 8) return fail(ctx, OASM_ENOMEM, "step buffers kept overflowing");
+      if ((rc = run_step_once(ctx, pl, d_items, d_regions, d_chunks, &over))) return rc;
+    }
+    // advance streams
+    for (size_t i = 0; i < pl.items.size(); ++i) {
+      StreamRec& s = ctx->streams[pl.sids[i]];
+      size_t left = pl.take[i];
+      while (left > 0 && !s.pieces.empty()) {
+        Piece& pc = s.pieces.front();
+        if (pc.n <= left) {
+          left -= pc.n;
+          s.pieces.erase(s.pieces.begin());
+        } else {
+          pc.n -= left;
+          if (pc.dev) pc.dptr += left; else pc.host_off += left;
+          left = 0;
+        }
+      }
+      s.pending -= pl.take[i];
+      s.pos = pl.items[i].e_new;
+      s.tail_len = int32_t(std::min<int64_t>(s.pos, ctx->T));
+      if (pl.items[i].eos) {
+        s.pos = 0;
+        s.tail_len = 0;
+        s.eos_pending = false;
+      }
+    }
+    ctx->st.steps += 1;
+    ctx->st.text_bytes += pl.new_bytes;
+    uint64_t msum = 0;
+    for (uint32_t p = 0; p < ctx->n_pat; ++p) msum += ctx->m[p];
+    ctx->st.cells += msum * pl.new_bytes;
+    for (const Bucket& b : ctx->buckets) {
+      uint64_t lanes = 0;
+      for (const auto& g : b.groups)
+        for (int l = 0; l < kLaneGroup; l += g.nseg) lanes += g.pat[l] >= 0 ? 1 : 0;
+      ctx->st.word_steps += lanes * uint64_t(b.W) * pl.new_bytes;
+    }
+    // host staging is free again once no stream references it
+    bool any_host = false;
+    for (auto& s : ctx->streams)
+      for (auto& pc : s.pieces) any_host |= !pc.dev;
+    if (!any_host) ctx->h_stage_used = 0;
+    bool more = false;
+    for (auto& s : ctx->streams) more |= s.open && (s.pending > 0 || s.eos_pending);
+    if (!more) return OASM_OK;
+  }
+}
+
+int check_sid(oasm_ctx* ctx, uint32_t sid) {
+  if (!ctx) return OASM_EINVAL;
+  if (sid >= ctx->streams.size() || !ctx->streams[sid].open)
+    return fail(ctx, OASM_EINVAL, "stream %u is not open", sid);
+  return OASM_OK;
+}
+
+}  // namespace
+
+// ======================================================================== ABI
+extern "C" {
+
+int oasm_config_default(oasm_config* cfg) {
+  if (!cfg) return OASM_EINVAL;
+  memset(cfg, 0, sizeof *cfg);
+  cfg->device = 0;
+  cfg->max_streams = 64;
+  cfg->flush_timeout_ms = 600000;
+  return OASM_OK;
+}
+
+int oasm_rules_default(oasm_rules* r) {
+  if (!r) return OASM_EINVAL;
+  memset(r, 0, sizeof *r);
+  return OASM_OK;
+}
+
+const char* oasm_strerror(int code) {
+  switch (code) {
+    case OASM_OK: return "ok";
+    case OASM_EINVAL: return "invalid argument";
+    case OASM_ENOMEM: return "out of memory";
+    case OASM_EBUSY: return "no free stream slot";
+    case OASM_ETRUNC: return "output truncated; more hits are queued";
+    case OASM_ETIMEOUT: return "device wait timed out";
+    case OASM_ECUDA: return "CUDA error";
+    case OASM_ESTATE: return "invalid state";
+    default: return "unknown error";
+  }
+}
+
+const char* oasm_last_error(oasm_ctx* ctx) {
+  return ctx ? ctx->err.c_str() : g_create_err.c_str();
+}
+
+int oasm_create(const uint8_t* const* pat, const uint32_t* len, const uint32_t* k,
+                uint32_t n_pat, const oasm_rules* rules, const oasm_config* cfg,
+                oasm_ctx** out) {
+  g_create_err.clear();
+  if (!out) return OASM_EINVAL;
+  *out = nullptr;
+  if (!pat || !len || !k || n_pat == 0) {
+    g_create_err = "need at least one pattern";
+    return OASM_EINVAL;
+  }
+  for (uint32_t p = 0; p < n_pat; ++p) {
+    if (len[p] < 1 || len[p] > OASM_MAX_PATTERN_LEN || !pat[p]) {
+      g_create_err = "pattern " + std::to_string(p) + ": length must be 1..128";
+      return OASM_EINVAL;
+    }
+    if (k[p] >= len[p] || k[p] > OASM_MAX_K) {
+      g_create_err = "pattern " + std::to_string(p) + ": need 0 <= K < l_p and K <= 15";
+      return OASM_EINVAL;
+    }
+  }
+  oasm_rules ru;
+  oasm_rules_default(&ru);
+  if (rules) ru = *rules;
+  if (ru.replace < 0 || ru.replace > 2 || ru.order < 0 || ru.order > 1 || ru.acc < 0 ||
+      ru.acc > 1 || ru.cmp < 0 || ru.cmp > 1 || ru.output < 0 || ru.output > 2) {
+    g_create_err = "rules field out of range";
+    return OASM_EINVAL;
+  }
+  oasm_ctx* ctx = new oasm_ctx();
+  oasm_config_default(&ctx->cfg);
+  if (cfg) ctx->cfg = *cfg;
+  if (ctx->cfg.max_streams == 0) ctx->cfg.max_streams = 64;
+  ctx->rules = Rules{ru.replace, ru.order, ru.acc, ru.cmp, ru.output};
+  ctx->device = ctx->cfg.device;
+  auto bail = [&](int rc) {
+    g_create_err = ctx->err.empty() ? oasm_strerror(rc) : ctx->err;
+    free_ctx(ctx);
+    return rc;
+  };
+  if (cudaSetDevice(ctx->device) != cudaSuccess) {
+    cudaGetLastError();
+    fail(ctx, OASM_ECUDA, "no CUDA device %d", ctx->device);
+    return bail(OASM_ECUDA);
+  }
+  cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device);
+  if (ctx->cfg.cuda_stream) {
+    ctx->stream = static_cast<cudaStream_t>(ctx->cfg.cuda_stream);
+  } else {
+    if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      fail(ctx, OASM_ECUDA, "cudaStreamCreate failed");
+      return bail(OASM_ECUDA);
+    }
+    ctx->own_stream = true;
+  }
+  ctx->n_pat = n_pat;
+  ctx->pats.resize(n_pat);
+  ctx->m.resize(n_pat);
+  ctx->K.resize(n_pat);
+  for (uint32_t p = 0; p < n_pat; ++p) {
+    ctx->pats[p].assign(pat[p], pat[p] + len[p]);
+    ctx->m[p] = uint8_t(len[p]);
+    ctx->K[p] = uint8_t(k[p]);
+    ctx->T = std::max<int>(ctx->T, int(len[p] + 3 * k[p] - 1));
+    ctx->kmax = std::max<int>(ctx->kmax, int(k[p]));
+  }
+  int rc = build_tables(ctx);
+  if (rc) return bail(rc);
+  // stream slots: tail, window headers and level rows for every pattern
+  const uint32_t S = ctx->cfg.max_streams;
+  ctx->stream_bytes = size_t(ctx->T) + size_t(n_pat) * sizeof(WinHdr) +
+                      size_t(ctx->mem_stride) * sizeof(MemRow);
+  if (ctx->cfg.mem_budget && ctx->stream_bytes > ctx->cfg.mem_budget) {
+    fail(ctx, OASM_ENOMEM, "one stream needs %zu bytes, over the memory budget",
+         ctx->stream_bytes);
+    return bail(OASM_ENOMEM);
+  }
+  if (cudaMalloc(&ctx->d_tails, size_t(S) * ctx->T) != cudaSuccess ||
+      cudaMalloc(&ctx->d_hdr, size_t(S) * n_pat * sizeof(WinHdr)) != cudaSuccess ||
+      cudaMalloc(&ctx->d_mem, size_t(S) * ctx->mem_stride * sizeof(MemRow)) != cudaSuccess) {
+    cudaGetLastError();
+    fail(ctx, OASM_ENOMEM, "stream state for %u streams does not fit", S);
+    return bail(OASM_ENOMEM);
+  }
+  ctx->streams.resize(S);
+  if (cudaMalloc(&ctx->d_ctr, sizeof(StepCounters)) != cudaSuccess ||
+      cudaHostAlloc(&ctx->h_ctr, sizeof(StepCounters), cudaHostAllocDefault) != cudaSuccess ||
+      cudaMalloc(&ctx->d_hist, size_t(256) * kSortBlocks * 4) != cudaSuccess) {
+    cudaGetLastError();
+    fail(ctx, OASM_ENOMEM, "step counters");
+    return bail(OASM_ENOMEM);
+  }
+  for (auto& e : ctx->ev)
+    if (cudaEventCreate(&e) != cudaSuccess) return bail(fail(ctx, OASM_ECUDA, "event"));
+  if (cudaEventCreateWithFlags(&ctx->done, cudaEventDisableTiming) != cudaSuccess)
+    return bail(fail(ctx, OASM_ECUDA, "event"));
+  *out = ctx;
+  return OASM_OK;
+}
+
+int oasm_destroy(oasm_ctx* ctx) {
+  free_ctx(ctx);
+  return OASM_OK;
+}
+
+int oasm_open_stream(oasm_ctx* ctx, uint32_t* sid) {
+  if (!ctx || !sid) return OASM_EINVAL;
+  if (ctx->cfg.mem_budget &&
+      (uint64_t(ctx->n_open) + 1) * ctx->stream_bytes > ctx->cfg.mem_budget)
+    return fail(ctx, OASM_ENOMEM, "admitting another stream would exceed the memory budget");
+  for (uint32_t i = 0; i < ctx->streams.size(); ++i) {
+    StreamRec& s = ctx->streams[i];
+    if (s.open) continue;
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaMemsetAsync(ctx->d_hdr + size_t(i) * ctx->n_pat, 0, size_t(ctx->n_pat) * sizeof(WinHdr),
+                       ctx->stream));
+    CK(cudaMemsetAsync(ctx->d_mem + size_t(i) * ctx->mem_stride, 0,
+                       size_t(ctx->mem_stride) * sizeof(MemRow), ctx->stream));
+    s = StreamRec();
+    s.open = true;
+    ++ctx->n_open;
+    *sid = i;
+    return OASM_OK;
+  }
+  return fail(ctx, OASM_EBUSY, "all %zu stream slots are in use", ctx->streams.size());
+}
+
+int oasm_close_stream(oasm_ctx* ctx, uint32_t sid) {
+  int rc = check_sid(ctx, sid);
+  if (rc) return rc;
+  ctx->streams[sid] = StreamRec();
+  --ctx->n_open;
+  bool any_host = false;
+  for (auto& s : ctx->streams)
+    for (auto& pc : s.pieces) any_host |= !pc.dev;
+  if (!any_host) ctx->h_stage_used = 0;
+  return OASM_OK;
+}
+
+int oasm_feed(oasm_ctx* ctx, uint32_t sid, const uint8_t* chunk, size_t n) {
+  int rc = check_sid(ctx, sid);
+  if (rc) return rc;
+  if (n == 0) return OASM_OK;
+  if (!chunk) return fail(ctx, OASM_EINVAL, "null chunk");
+  StreamRec& s = ctx->streams[sid];
+  if (s.eos_pending) return fail(ctx, OASM_ESTATE, "stream %u has a pending end", sid);
+  if (ctx->h_stage_used + n > ctx->stage_limit && ctx->h_stage_used > 0) {
+    if ((rc = run_step(ctx))) return rc;
+  }
+  if ((rc = ensure_host(ctx, &ctx->h_stage, &ctx->h_stage_cap, ctx->h_stage_used + n,
+                        ctx->h_stage_used)))
+    return rc;
+  memcpy(ctx->h_stage + ctx->h_stage_used, chunk, n);
+  s.pieces.push_back(Piece{false, nullptr, ctx->h_stage_used, n});
+  ctx->h_stage_used += n;
+  s.pending += n;
+  return OASM_OK;
+}
+
+int oasm_feed_device(oasm_ctx* ctx, uint32_t sid, const uint8_t* dchunk, size_t n) {
+  int rc = check_sid(ctx, sid);
+  if (rc) return rc;
+  if (n == 0) return OASM_OK;
+  if (!dchunk) return fail(ctx, OASM_EINVAL, "null chunk");
+  StreamRec& s = ctx->streams[sid];
+  if (s.eos_pending) return fail(ctx, OASM_ESTATE, "stream %u has a pending end", sid);
+  s.pieces.push_back(Piece{true, dchunk, 0, n});
+  s.pending += n;
+  return OASM_OK;
+}
+
+int oasm_end_stream(oasm_ctx* ctx, uint32_t sid) {
+  int rc = check_sid(ctx, sid);
+  if (rc) return rc;
+  ctx->streams[sid].eos_pending = true;
+  return OASM_OK;
+}
+
+int oasm_step(oasm_ctx* ctx) {
+  if (!ctx) return OASM_EINVAL;
+  return run_step(ctx);
+}
+
+int oasm_flush(oasm_ctx* ctx, uint32_t sid, int end_of_stream, oasm_hit* out, size_t cap,
+               size_t* n_out) {
+  int rc = check_sid(ctx, sid);
+  if (rc) return rc;
+  if (n_out) *n_out = 0;
+  StreamRec& s0 = ctx->streams[sid];
+  if (end_of_stream) s0.eos_pending = true;
+  if (s0.pending > 0 || s0.eos_pending) {
+    if ((rc = run_step(ctx))) return rc;
+  }
+  StreamRec& s = ctx->streams[sid];
+  if (s.runs.size() > 1) {  // merge the sorted runs of several steps
+    size_t lo = s.head;
+    for (size_t r = 1; r < s.runs.size(); ++r) {
+      const size_t mid = std::max(s.runs[r], lo);
+      const size_t hi = (r + 1 < s.runs.size()) ? s.runs[r + 1] : s.ready.size();
+      std::inplace_merge(s.ready.begin() + lo, s.ready.begin() + mid, s.ready.begin() + hi,
+                         canon_less);
+    }
+    s.runs.assign(1, s.head);
+  }
+  const size_t avail = s.ready.size() - s.head;
+  const size_t n = std::min(cap, avail);
+  if (n && !out) return fail(ctx, OASM_EINVAL, "null output array");
+  if (n) memcpy(out, s.ready.data() + s.head, n * sizeof(oasm_hit));
+  s.head += n;
+  if (n_out) *n_out = n;
+  if (s.head == s.ready.size()) {
+    s.ready.clear();
+    s.runs.clear();
+    s.head = 0;
+    return OASM_OK;
+  }
+  return OASM_ETRUNC;
+}
+
+int oasm_ready(oasm_ctx* ctx, uint32_t sid, size_t* n) {
+  int rc = check_sid(ctx, sid);
+  if (rc) return rc;
+  if (!n) return OASM_EINVAL;
+  *n = ctx->streams[sid].ready.size() - ctx->streams[sid].head;
+  return OASM_OK;
+}
+
+int oasm_get_stats(oasm_ctx* ctx, oasm_stats* st) {
+  if (!ctx || !st) return OASM_EINVAL;
+  *st = ctx->st;
+  return OASM_OK;
+}
+
+int oasm_reset_stats(oasm_ctx* ctx) {
+  if (!ctx) return OASM_EINVAL;
+  ctx->st = oasm_stats{};
+  return OASM_OK;
+}
+
+void* oasm_cuda_stream(oasm_ctx* ctx) { return ctx ? static_cast<void*>(ctx->stream) : nullptr; }
+
+int oasm_autotune(oasm_ctx* ctx, const uint8_t* dsample, size_t n, char* report,
+                  size_t report_cap) {
+  if (!ctx || !dsample || n < 4096) return OASM_EINVAL;
+  CK(cudaSetDevice(ctx->device));
+  int rc;
+  // a synthetic work item over the sample, laid out like a step's arena
+  const size_t need = kFrontPad + n + kEndPad;
+  if ((rc = ensure(ctx, ctx->arena, need, "text arena"))) return rc;
+  if ((rc = ensure(ctx, ctx->cand, std::max<size_t>(ctx->cand.cap, 1 << 20), "candidates")))
+    return rc;
+  CK(cudaMemcpyAsync(ctx->arena.p + kFrontPad, dsample, n, cudaMemcpyDeviceToDevice, ctx->stream));
+  WorkItem w{};
+  w.arena_base = kFrontPad;
+  w.base_pos = 0;
+  w.e_prev = 0;
+  w.e_new = int64_t(n);
+  std::string js = "{\"buckets\":[";
+  const int warp_opts[] = {4, 8, 16};
+  const int chunk_opts[] = {512, 1024, 2048};
+  const double scale_opts[] = {0.5, 1.0, 2.0};
+  int max_smem = 0;
+  cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
+  for (size_t bi = 0; bi < ctx->buckets.size(); ++bi) {
+    Bucket& b = ctx->buckets[bi];
+    const bool dict = b.max_nseg == 1;
+    std::string trials;
+    // times one scan launch of the sample for the bucket's current settings
+    auto time_cfg = [&](int wo, int co, double so, float* out_ms) -> int {
+      if (scan_smem_bytes(b.W, wo, dict ? co : 0) > size_t(max_smem)) {
+        *out_ms = 1e30f;
+        return OASM_OK;
+      }
+      b.region_scale = so;
+      const int64_t R = region_len(ctx, b, int64_t(n));
+      std::vector<Region> regs;
+      for (int64_t a0 = 0; a0 < int64_t(n); a0 += R)
+        regs.push_back(Region{0, 0, a0, std::min<int64_t>(int64_t(n), a0 + R)});
+      const size_t bytes = 256 + regs.size() * sizeof(Region);
+      int rc2;
+      if ((rc2 = ensure_host(ctx, &ctx->h_upload, &ctx->h_upload_cap, bytes, 0))) return rc2;
+      if ((rc2 = ensure(ctx, ctx->upload, bytes, "step upload"))) return rc2;
+      memcpy(ctx->h_upload, &w, sizeof w);
+      memcpy(ctx->h_upload + 256, regs.data(), regs.size() * sizeof(Region));
+      CK(cudaMemcpyAsync(ctx->upload.p, ctx->h_upload, bytes, cudaMemcpyHostToDevice,
+                         ctx->stream));
+      ScanArgs a{};
+      a.groups = b.d_groups;
+      a.peq = b.d_peq;
+      a.n_groups = int(b.groups.size());
+      a.W = b.W;
+      a.regions = reinterpret_cast<const Region*>(ctx->upload.p + 256);
+      a.n_regions = int(regs.size());
+      a.warps = wo;
+      a.resv = dict ? 32 : 256;
+      a.dict = dict ? 1 : 0;
+      a.chunk = co;
+      a.items = reinterpret_cast<const WorkItem*>(ctx->upload.p);
+      a.arena = ctx->arena.p;
+      a.cand = ctx->cand.p;
+      a.cap_cand = ctx->cand.cap;
+      a.ctr = ctx->d_ctr;
+      float tbest = 1e30f;
+      for (int rep = 0; rep < 3; ++rep) {
+        CK(cudaMemsetAsync(ctx->d_ctr, 0, sizeof(StepCounters), ctx->stream));
+        CK(cudaEventRecord(ctx->ev[6], ctx->stream));
+        CK(launch_scan(a, ctx->stream));
+        CK(cudaEventRecord(ctx->ev[7], ctx->stream));
+        CK(cudaEventSynchronize(ctx->ev[7]));
+        float ms = 0;
+        cudaEventElapsedTime(&ms, ctx->ev[6], ctx->ev[7]);
+        if (rep > 0) tbest = std::min(tbest, ms);
+      }
+      ctx->st.launches += 3;
+      char tb[96];
+      snprintf(tb, sizeof tb, "%s[%d,%d,%.2f,%.4f]", trials.empty() ? "" : ",", wo, co, so,
+               double(tbest));
+      trials += tb;
+      *out_ms = tbest;
+      return OASM_OK;
+    };
+    float best = 1e30f;
+    int bw = b.warps, bc = b.chunk;
+    double bs = 1.0;
+    // phase 1: warps per block at the default geometry
+    for (int wo : warp_opts) {
+      float ms;
+      if ((rc = time_cfg(wo, dict ? 1024 : 512, 1.0, &ms))) return rc;
+      if (ms < best) { best = ms; bw = wo; bc = dict ? 1024 : 512; bs = 1.0; }
+    }
+    // phase 2: text buffer size x region length for the winner
+    for (int co : chunk_opts) {
+      if (!dict && co != chunk_opts[0]) continue;  // the segment mapping stages no text
+      for (double so : scale_opts) {
+        float ms;
+        if ((rc = time_cfg(bw, co, so, &ms))) return rc;
+        if (ms < best) { best = ms; bc = co; bs = so; }
+      }
+    }
+    b.warps = bw;
+    b.chunk = bc;
+    b.region_scale = bs;
+    char buf[256];
+    snprintf(buf, sizeof buf,
+             "%s{\"W\":%d,\"groups\":%zu,\"dict\":%d,\"warps\":%d,\"chunk\":%d,"
+             "\"region_scale\":%.2f,\"ms\":%.4f,\"trials\":[",
+             bi ? "," : "", b.W, b.groups.size(), dict ? 1 : 0, bw, bc, bs, double(best));
+    js += buf;
+    js += trials;
+    js += "]}";
+  }
+  js += "]}";
+  if (report && report_cap) {
+    snprintf(report, report_cap, "%s", js.c_str());
+  }
+  return OASM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,73 @@
+// kernels.h -- host-side launchers of the OASM device path.  Internal.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "oasm_internal.cuh"
+
+namespace oasm {
+
+// Forward scan (Sellers search, bit-parallel) over one word-count class.
+struct ScanArgs {
+  const LaneGroup* groups;   // [n_groups]
+  const uint32_t* peq;       // [n_groups][256 symbols][W words][32 lanes]
+  int32_t n_groups;
+  int32_t W;
+  const Region* regions;     // [n_regions]
+  int32_t n_regions;
+  int32_t warps;             // warps per block
+  int32_t resv;              // candidate slots a warp reserves at a time
+  int32_t dict;              // 1: dictionary mapping (one pattern per lane, nseg = 1)
+  int32_t chunk;             // text bytes per TMA buffer (dictionary mapping)
+  int32_t pad;
+  const WorkItem* items;
+  const uint8_t* arena;
+  Candidate* cand;
+  unsigned long long cap_cand;
+  StepCounters* ctr;
+};
+
+// Shared memory of one scan block: the group's Peq table (256 rows of W x 32
+// words), two text buffers per warp (dictionary mapping) and the mbarriers.
+inline size_t scan_smem_bytes(int W, int warps, int chunk) {
+  return size_t(256) * 128 * W + size_t(warps) * 2 * chunk + size_t(1 + 2 * warps) * 8;
+}
+
+cudaError_t launch_scan(const ScanArgs& a, cudaStream_t s);
+
+// Copies of stream bytes into the step's text arena.
+struct CopyChunk {
+  const uint8_t* src;
+  uint64_t dst_off;
+  uint32_t len;
+  uint32_t pad;
+};
+cudaError_t launch_gather(const CopyChunk* chunks, int n, uint8_t* arena, cudaStream_t s);
+
+cudaError_t launch_verify(const StepParams& p, cudaStream_t s);
+
+// Stable LSD radix sort (8-bit digits) of keys by bits [lo_bit, hi_bit),
+// with an optional 32-bit payload.  The element count is read on the device
+// from *count (clamped to cap).  On return *keys_out / *vals_out point at
+// whichever buffer of each pair holds the sorted data.
+struct SortArgs {
+  unsigned long long* keys;
+  unsigned long long* keys_alt;
+  uint32_t* vals;                 // may be null
+  uint32_t* vals_alt;
+  const unsigned long long* count;
+  unsigned long long cap;
+  int lo_bit, hi_bit;
+  unsigned int* hist;             // 256 * nblocks
+  int nblocks;
+};
+cudaError_t launch_sort(const SortArgs& a, unsigned long long** keys_out, uint32_t** vals_out,
+                        int* launches, cudaStream_t s);
+// dst[i] = src[idx[i]] for i < min(*count, cap)
+cudaError_t launch_permute(const DevHit* src, const uint32_t* idx, DevHit* dst,
+                           const unsigned long long* count, unsigned long long cap,
+                           cudaStream_t s);
+cudaError_t launch_filter(const StepParams& p, const unsigned long long* sorted, cudaStream_t s);
+cudaError_t launch_finalize(const StepParams& p, cudaStream_t s);
+cudaError_t launch_tails(const StepParams& p, cudaStream_t s);
+
+}  // namespace oasm

@@ -1,0 +1,655 @@
+// pipeline.cu -- the OASM device path after the forward scan (sm_103a):
+//   gather    stream bytes and stored tails -> the step's text arena
+//   verify    for each candidate end e: one bit-parallel pass of the reversed
+//             pattern over t[e], t[e-1], ... gives lev(p, t[e-l+1..e]) for every
+//             length l (Eq. 1 is invariant under reversing both strings), so
+//             every hit (i, l, k) of Eq. 2 ending at e is found exactly once
+//   sort      stable LSD radix sort of 64-bit hit keys (pair, start, length):
+//             the order in which Algorithm 1 meets hits (i ascending, then l)
+//   filter    Algorithm 1 in event form over each pair (stream, pattern); a
+//             pair's hits are cut at every start that no earlier hit spans,
+//             where the filter state is provably empty, and each piece runs
+//             on its own thread; the first piece resumes the pair's pending
+//             window carried from the previous step
+//   finalize  installs the new pending windows, decides carried windows of
+//             pairs without hits, and the tails kernel keeps the last T
+//             symbols of every stream for the next step.
+#include <utility>
+
+#include "kernels.h"
+
+namespace oasm {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr uint32_t kInvalid = 0xffffffffu;
+
+// ---------------------------------------------------------------- gather
+__global__ void gather_kernel(const CopyChunk* __restrict__ chunks, int n, uint8_t* arena) {
+  for (int c = blockIdx.x; c < n; c += gridDim.x) {
+    const CopyChunk ch = chunks[c];
+    uint8_t* dst = arena + ch.dst_off;
+    const uint8_t* src = ch.src;
+    const bool vec = ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst) |
+                       ch.len) & 15u) == 0;
+    if (vec) {
+      const uint4* s4 = reinterpret_cast<const uint4*>(src);
+      uint4* d4 = reinterpret_cast<uint4*>(dst);
+      for (uint32_t i = threadIdx.x; i < ch.len / 16; i += blockDim.x) d4[i] = s4[i];
+    } else {
+      for (uint32_t i = threadIdx.x; i < ch.len; i += blockDim.x) dst[i] = src[i];
+    }
+  }
+}
+
+// ---------------------------------------------------------------- verify
+template <int W>
+__device__ __forceinline__ void add_w(const uint32_t* a, const uint32_t* b, uint32_t* s) {
+  if (W == 1) {
+    s[0] = a[0] + b[0];
+  } else if (W == 2) {
+    asm("add.cc.u32 %0, %2, %4;\n\taddc.u32 %1, %3, %5;"
+        : "=r"(s[0]), "=r"(s[1]) : "r"(a[0]), "r"(a[1]), "r"(b[0]), "r"(b[1]));
+  } else if (W == 3) {
+    asm("add.cc.u32 %0, %3, %6;\n\taddc.cc.u32 %1, %4, %7;\n\taddc.u32 %2, %5, %8;"
+        : "=r"(s[0]), "=r"(s[1]), "=r"(s[2])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(b[0]), "r"(b[1]), "r"(b[2]));
+  } else {
+    asm("add.cc.u32 %0, %4, %8;\n\taddc.cc.u32 %1, %5, %9;\n\t"
+        "addc.cc.u32 %2, %6, %10;\n\taddc.u32 %3, %7, %11;"
+        : "=r"(s[0]), "=r"(s[1]), "=r"(s[2]), "=r"(s[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]), "r"(b[2]),
+          "r"(b[3]));
+  }
+}
+
+// Anchored pass: distances of the reversed pattern (bit j = p[m-1-j]) to the
+// prefixes of t[e], t[e-1], ...; the dummy row is 0, 1, 2, ... so a +1
+// horizontal difference enters the bottom word at every step.  Writes
+// dist[l] for l = 1..lmax.
+template <int W>
+__device__ void anchored_pass(const uint32_t* __restrict__ peq, const uint8_t* __restrict__ tend,
+                              int m, int lmax, int8_t* dist) {
+  uint32_t Pv[W], Mv[W];
+#pragma unroll
+  for (int w = 0; w < W; ++w) {
+    Pv[w] = 0xffffffffu;
+    Mv[w] = 0u;
+  }
+  const int tw = (m - 1) >> 5, tb = (m - 1) & 31;
+  int score = m;
+  for (int l = 1; l <= lmax; ++l) {
+    const uint32_t c = tend[-(l - 1)];
+    const uint4 q = __ldg(reinterpret_cast<const uint4*>(peq + c * 4));
+    const uint32_t eq[4] = {q.x, q.y, q.z, q.w};
+    uint32_t x[W], sum[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) x[w] = eq[w] & Pv[w];
+    add_w<W>(x, Pv, sum);
+    uint32_t php = 1u << 31, mhp = 0;  // shift-in: +1 at row 0
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+      const uint32_t xv = eq[w] | Mv[w];
+      const uint32_t xh = (sum[w] ^ Pv[w]) | eq[w];
+      const uint32_t ph = Mv[w] | ~(xh | Pv[w]);
+      const uint32_t mh = Pv[w] & xh;
+      if (w == tw) score += int((ph >> tb) & 1u) - int((mh >> tb) & 1u);
+      const uint32_t phs = __funnelshift_l(php, ph, 1);
+      const uint32_t mhs = __funnelshift_l(mhp, mh, 1);
+      php = ph;
+      mhp = mh;
+      Pv[w] = mhs | ~(xv | phs);
+      Mv[w] = phs & xv;
+    }
+    dist[l] = int8_t(score > 127 ? 127 : score);
+  }
+}
+
+// Canonical order of emitted records: (work item, pattern, decided_at, k,
+// length), packed like the hit keys so it fits the same bit budget.
+__device__ __forceinline__ unsigned long long out_key(const StepParams& P, uint64_t pair,
+                                                      const WorkItem& w, int64_t decided_at,
+                                                      int k, int len, int m, int K) {
+  return (pair << (P.start_bits + kLowBits)) | (uint64_t(decided_at - w.base_pos) << kLowBits) |
+         (uint64_t(k) << kLenBits) | uint64_t(len - (m - K));
+}
+
+__device__ __forceinline__ void put_record(const StepParams& P, unsigned long long o,
+                                           const DevHit& h, unsigned long long key) {
+  P.out[o] = h;
+  P.okeys[o] = key;
+  P.ovals[o] = uint32_t(o);
+}
+
+__global__ void __launch_bounds__(256) verify_kernel(const StepParams P) {
+  const unsigned long long n = min(P.ctr->n_cand, P.cap_cand);
+  if (P.ctr->overflow) return;
+  const unsigned lane = threadIdx.x & 31;
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x; base < n;
+       base += stride) {
+    const unsigned long long idx = base + threadIdx.x;
+    uint64_t keys[2 * kMaxK + 1];
+    DevHit rec;
+    unsigned long long rkey = 0;
+    int nh = 0;
+    if (idx < n) {
+      const Candidate c = P.cand[idx];
+      if (c.wi != kInvalid) {
+        const WorkItem w = P.items[c.wi];
+        const int p = int(c.pat);
+        const int m = P.m[p], K = P.K[p];
+        const int64_t e = w.base_pos + int64_t(c.e_rel);
+        const uint8_t* tend = P.arena + w.arena_base + c.e_rel;
+        const int64_t lo_start = max(w.base_pos, int64_t(0));
+        int8_t dist[kMaxW * 32 + kMaxK + 1];
+        if (P.rules.output == OASM_OUT_ENDS) {
+          if (e >= w.e_prev && e < w.e_new) {
+            const int lmax = int(min(int64_t(m + K), e - lo_start + 1));
+            const int W = (m + 31) >> 5;
+            const uint32_t* pq = P.peq_rev + size_t(p) * 256 * 4;
+            if (W == 1) anchored_pass<1>(pq, tend, m, lmax, dist);
+            else if (W == 2) anchored_pass<2>(pq, tend, m, lmax, dist);
+            else if (W == 3) anchored_pass<3>(pq, tend, m, lmax, dist);
+            else anchored_pass<4>(pq, tend, m, lmax, dist);
+            int best = 127, bl = 0;
+            for (int l = 1; l <= lmax; ++l)
+              if (dist[l] < best) { best = dist[l]; bl = l; }
+            if (best <= K) {
+              rec.start = uint64_t(e - bl + 1);
+              rec.decided_at = uint64_t(e);
+              rec.pattern = uint32_t(p);
+              rec.slot = w.slot;
+              rec.len = uint32_t(bl);
+              rec.k = uint32_t(best);
+              rkey = out_key(P, uint64_t(c.wi) * P.n_pat + uint64_t(p), w, e, best, bl, m, K);
+              nh = 1;
+            }
+          }
+        } else {
+          const int64_t fp = f_prev(w, m, K), fn = f_new(w, m, K);
+          const int64_t smin = max(fp + 1, lo_start);
+          const int lmax = int(min(int64_t(m + K), e - smin + 1));
+          const int lmin = int(max(int64_t(max(1, m - K)), e - fn + 1));
+          if (lmin <= lmax) {
+            const int W = (m + 31) >> 5;
+            const uint32_t* pq = P.peq_rev + size_t(p) * 256 * 4;
+            if (W == 1) anchored_pass<1>(pq, tend, m, lmax, dist);
+            else if (W == 2) anchored_pass<2>(pq, tend, m, lmax, dist);
+            else if (W == 3) anchored_pass<3>(pq, tend, m, lmax, dist);
+            else anchored_pass<4>(pq, tend, m, lmax, dist);
+            const uint64_t pair = uint64_t(c.wi) * P.n_pat + uint64_t(p);
+            for (int l = lmin; l <= lmax; ++l) {
+              const int k = dist[l];
+              if (k > K) continue;
+              const int64_t st = e - l + 1;
+              keys[nh++] = (pair << (P.start_bits + kLowBits)) |
+                           (uint64_t(st - w.base_pos) << kLowBits) |
+                           (uint64_t(l - (m - K)) << kKBits) | uint64_t(k);
+            }
+          }
+        }
+      }
+    }
+    // warp-aggregated append
+    int incl = nh;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int t = __shfl_up_sync(kFull, incl, d);
+      if (int(lane) >= d) incl += t;
+    }
+    const int tot = __shfl_sync(kFull, incl, 31);
+    if (tot == 0) continue;
+    const bool raw = P.rules.output != OASM_OUT_FILTERED;
+    unsigned long long wbase = 0;
+    if (lane == 0) wbase = atomicAdd(raw ? &P.ctr->n_out : &P.ctr->n_hits, (unsigned long long)tot);
+    wbase = __shfl_sync(kFull, wbase, 0);
+    unsigned long long o = wbase + unsigned(incl - nh);
+    bool over = false;
+    if (!raw) {
+      for (int q = 0; q < nh; ++q, ++o) {
+        if (o < P.cap_hits) P.keys[o] = keys[q];
+        else over = true;
+      }
+      if (over) atomicOr(&P.ctr->overflow, 2u);
+    } else {
+      for (int q = 0; q < nh; ++q, ++o) {
+        if (o >= P.cap_out) { over = true; continue; }
+        if (P.rules.output == OASM_OUT_ENDS) {
+          put_record(P, o, rec, rkey);
+        } else {
+          const uint64_t key = keys[q];
+          const uint32_t pair = uint32_t(key >> (P.start_bits + kLowBits));
+          const int p = int(pair % P.n_pat);
+          const WorkItem w = P.items[pair / P.n_pat];
+          const int m = P.m[p], K = P.K[p];
+          const int64_t st = w.base_pos +
+                             int64_t((key >> kLowBits) & ((1ull << P.start_bits) - 1));
+          const int l = int((key >> kKBits) & 31u) + m - K;
+          DevHit h;
+          h.start = uint64_t(st);
+          h.len = uint32_t(l);
+          h.k = uint32_t(key & 15u);
+          h.decided_at = uint64_t(st + l - 1);
+          h.pattern = uint32_t(p);
+          h.slot = w.slot;
+          put_record(P, o, h, out_key(P, pair, w, st + l - 1, int(h.k), l, m, K));
+        }
+      }
+      if (over) atomicOr(&P.ctr->overflow, 4u);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- radix sort
+constexpr int kSortThreads = 256;
+constexpr int kSortWarps = kSortThreads / 32;
+
+__global__ void __launch_bounds__(kSortThreads)
+    rs_hist(const unsigned long long* __restrict__ keys, const unsigned long long* count,
+            unsigned long long cap, int shift, unsigned int* hist) {
+  __shared__ unsigned int h[256];
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  const unsigned long long n = min(*count, cap);
+  const unsigned long long chunk = (n + gridDim.x - 1) / gridDim.x;
+  const unsigned long long b0 = chunk * blockIdx.x, b1 = min(n, b0 + chunk);
+  for (unsigned long long i = b0 + threadIdx.x; i < b1; i += blockDim.x)
+    atomicAdd(&h[(keys[i] >> shift) & 255u], 1u);
+  __syncthreads();
+  hist[threadIdx.x * gridDim.x + blockIdx.x] = h[threadIdx.x];
+}
+
+// exclusive scan of hist[256 * nb] (digit-major) in one block of 1024 threads
+__global__ void __launch_bounds__(1024) rs_prefix(unsigned int* hist, int total) {
+  __shared__ unsigned int part[1024];
+  const int per = (total + 1023) / 1024;
+  const int b0 = threadIdx.x * per, b1 = min(total, b0 + per);
+  unsigned int s = 0;
+  for (int i = b0; i < b1; ++i) s += hist[i];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  for (int d = 1; d < 1024; d <<= 1) {
+    const unsigned int t = threadIdx.x >= unsigned(d) ? part[threadIdx.x - d] : 0u;
+    __syncthreads();
+    part[threadIdx.x] += t;
+    __syncthreads();
+  }
+  unsigned int run = part[threadIdx.x] - s;
+  for (int i = b0; i < b1; ++i) {
+    const unsigned int v = hist[i];
+    hist[i] = run;
+    run += v;
+  }
+}
+
+// Stable scatter: a block walks its contiguous chunk in tiles of 256 keys;
+// inside a tile, ranks come from warp matching (lane order) and per-warp
+// digit counts (warp order); across tiles a running base per digit.
+__global__ void __launch_bounds__(kSortThreads)
+    rs_scatter(const unsigned long long* __restrict__ in, unsigned long long* __restrict__ out,
+               const uint32_t* __restrict__ vin, uint32_t* __restrict__ vout,
+               const unsigned long long* count, unsigned long long cap, int shift,
+               const unsigned int* __restrict__ hist) {
+  __shared__ unsigned int wcnt[kSortWarps][256];
+  __shared__ unsigned int woff[kSortWarps][256];
+  __shared__ unsigned int base[256];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  base[threadIdx.x] = hist[threadIdx.x * gridDim.x + blockIdx.x];
+  for (int w = 0; w < kSortWarps; ++w) wcnt[w][threadIdx.x] = 0;
+  __syncthreads();
+  const unsigned long long n = min(*count, cap);
+  const unsigned long long chunk = (n + gridDim.x - 1) / gridDim.x;
+  const unsigned long long b0 = chunk * blockIdx.x, b1 = min(n, b0 + chunk);
+  const unsigned lt = (1u << lane) - 1u;
+  for (unsigned long long t0 = b0; t0 < b1; t0 += kSortThreads) {
+    const unsigned long long i = t0 + threadIdx.x;
+    const bool ok = i < b1;
+    const unsigned long long key = ok ? in[i] : 0ull;
+    const uint32_t val = (ok && vin) ? vin[i] : 0u;
+    const unsigned d = ok ? unsigned((key >> shift) & 255u) : 256u;
+    const unsigned peers = __match_any_sync(kFull, d);
+    const unsigned rank = __popc(peers & lt);
+    if (ok && rank == 0) wcnt[warp][d] = __popc(peers);
+    __syncthreads();
+    {
+      const int dg = threadIdx.x;  // one digit per thread
+      unsigned int run = base[dg];
+      for (int w = 0; w < kSortWarps; ++w) {
+        const unsigned int c = wcnt[w][dg];
+        woff[w][dg] = run;
+        run += c;
+        wcnt[w][dg] = 0;
+      }
+      base[dg] = run;
+    }
+    __syncthreads();
+    if (ok) {
+      const unsigned int pos = woff[warp][d] + rank;
+      out[pos] = key;
+      if (vout) vout[pos] = val;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void permute_kernel(const DevHit* __restrict__ src, const uint32_t* __restrict__ idx,
+                               DevHit* __restrict__ dst, const unsigned long long* count,
+                               unsigned long long cap) {
+  const unsigned long long n = min(*count, cap);
+  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (unsigned long long)gridDim.x * blockDim.x)
+    dst[i] = src[idx[i]];
+}
+
+// ---------------------------------------------------------------- filter
+struct Hit {
+  uint32_t pair;
+  int64_t start;
+  int32_t len;
+  int32_t k;
+};
+
+__device__ __forceinline__ Hit decode(uint64_t key, const StepParams& P) {
+  Hit h;
+  h.pair = uint32_t(key >> (P.start_bits + kLowBits));
+  const int p = int(h.pair % P.n_pat);
+  const WorkItem& w = P.items[h.pair / P.n_pat];
+  h.start = w.base_pos + int64_t((key >> kLowBits) & ((1ull << P.start_bits) - 1));
+  h.len = int32_t((key >> kKBits) & 31u) + P.m[p] - P.K[p];
+  h.k = int32_t(key & 15u);
+  return h;
+}
+
+struct Window {
+  int pend;
+  int idx;
+  MemRow rows[kMaxK + 1];
+};
+
+__device__ void emit(const StepParams& P, uint32_t pair, int p, int lv, const MemRow& r, int64_t f,
+                     const WorkItem& w) {
+  const unsigned long long o = atomicAdd(&P.ctr->n_out, 1ull);
+  if (o >= P.cap_out) {
+    atomicOr(&P.ctr->overflow, 4u);
+    return;
+  }
+  DevHit h;
+  h.start = uint64_t(r.start);
+  h.decided_at = uint64_t(f);
+  h.pattern = uint32_t(p);
+  h.slot = w.slot;
+  h.len = uint32_t(r.len);
+  h.k = uint32_t(lv);
+  put_record(P, o, h, out_key(P, pair, w, f, lv, r.len, P.m[p], P.K[p]));
+}
+
+// Validation complete at f (Sec. 4.2): the highest-priority occurrence is
+// added, then each lower level j whose counter satisfies Eq. 3 against the
+// accumulated length.  r(j) = f - i_j + 1 because a level's counter starts
+// at 1 on insertion and grows by one per processed symbol.
+__device__ void flush(const StepParams& P, Window& W, uint32_t pair, int p, int K,
+                      const WorkItem& w) {
+  const MemRow& top = W.rows[W.idx];
+  const int64_t f = top.start + top.len - 1;
+  int64_t acc = 0;
+  for (int lv = W.idx; lv <= K; ++lv) {
+    const MemRow& r = W.rows[lv];
+    if (!r.valid) continue;
+    const int64_t lhs = (f - r.start + 1) - acc;
+    const bool keep = (lv == W.idx) || (P.rules.cmp == OASM_CMP_GT ? lhs > r.len : lhs >= r.len);
+    if (keep) {
+      emit(P, pair, p, lv, r, f, w);
+      acc = (P.rules.acc == OASM_ACC_SUM) ? acc + r.len : r.len;
+    }
+  }
+  W.pend = 0;
+  W.idx = K;
+  for (int lv = 0; lv <= K; ++lv) W.rows[lv].valid = 0;
+}
+
+// R1-R3 applied to one hit met in (i, l) order (event form of Algorithm 1).
+__device__ void apply(const StepParams& P, Window& W, uint32_t pair, int p, int K,
+                      const WorkItem& w, const Hit& h) {
+  if (W.pend) {
+    const MemRow& top = W.rows[W.idx];
+    if (h.start > top.start + top.len - 1) flush(P, W, pair, p, K, w);
+  }
+  MemRow nr;
+  nr.start = h.start;
+  nr.len = h.len;
+  nr.valid = 1;
+  if (!W.pend) {  // an empty window opens at the hit's level
+    W.pend = 1;
+    W.idx = h.k;
+    W.rows[h.k] = nr;
+  } else if (h.k < W.idx) {  // R1
+    W.idx = h.k;
+    W.rows[h.k] = nr;
+  } else if (h.k == W.idx) {  // R2 / R3
+    const MemRow& cur = W.rows[W.idx];
+    const int64_t ce = cur.start + cur.len - 1, ne = h.start + h.len - 1;
+    bool rep = false;
+    if (P.rules.replace == OASM_REPLACE_CONTAINED) rep = h.start >= cur.start && ne <= ce;
+    else if (P.rules.replace == OASM_REPLACE_SAME_END) rep = ne == ce;
+    if (rep) W.rows[W.idx] = nr;
+  }
+}
+
+__device__ __forceinline__ uint32_t pair_of(uint64_t key, int sb) {
+  return uint32_t(key >> (sb + kLowBits));
+}
+
+__global__ void __launch_bounds__(128)
+    filter_kernel(const StepParams P, const unsigned long long* __restrict__ S) {
+  if (P.ctr->overflow) return;
+  const unsigned long long n = min(P.ctr->n_hits, P.cap_hits);
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long h = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; h < n;
+       h += stride) {
+    const Hit hh = decode(S[h], P);
+    const uint32_t pair = hh.pair;
+    const int p = int(pair % P.n_pat);
+    const WorkItem w = P.items[pair / P.n_pat];
+    const int m = P.m[p], K = P.K[p];
+    const bool first = (h == 0) || pair_of(S[h - 1], P.start_bits) != pair;
+    const size_t hidx = size_t(w.slot) * P.n_pat + p;
+    const MemRow* crow = P.mem + size_t(w.slot) * P.mem_stride + P.mem_off[p];
+    const WinHdr chdr = P.hdr[hidx];
+    int64_t cf = INT64_MIN;  // end of the carried window's top occurrence
+    if (chdr.pend) cf = crow[chdr.idx].start + crow[chdr.idx].len - 1;
+    if (!first) {
+      // a piece starts only at the first hit of a start that no earlier hit
+      // of the pair (nor the carried window) spans
+      const Hit prev = decode(S[h - 1], P);
+      if (prev.start == hh.start) continue;
+      if (cf >= hh.start) continue;
+      bool spanned = false;
+      for (long long j = (long long)h - 1; j >= 0; --j) {
+        const uint64_t kj = S[j];
+        if (pair_of(kj, P.start_bits) != pair) break;
+        const Hit hj = decode(kj, P);
+        if (hj.start + m + K <= hh.start) break;  // ends before hh.start
+        if (hj.start + hj.len - 1 >= hh.start) {
+          spanned = true;
+          break;
+        }
+      }
+      if (spanned) continue;
+    }
+    Window Wn;
+    Wn.pend = 0;
+    Wn.idx = K;
+    for (int lv = 0; lv <= K; ++lv) Wn.rows[lv].valid = 0;
+    int64_t maxend = INT64_MIN;
+    if (first && chdr.pend) {
+      Wn.pend = 1;
+      Wn.idx = chdr.idx;
+      for (int lv = 0; lv <= K; ++lv) Wn.rows[lv] = crow[lv];
+      maxend = cf;
+    }
+    unsigned long long j = h;
+    bool last = false;
+    while (true) {
+      Hit cur = decode(S[j], P);
+      unsigned long long nxt = j + 1;
+      if (P.rules.order == OASM_ORDER_PER_START_BEST) {
+        // among the hits of this start keep the smallest k, then the shortest
+        int64_t me = cur.start + cur.len - 1;
+        while (nxt < n && pair_of(S[nxt], P.start_bits) == pair) {
+          const Hit o = decode(S[nxt], P);
+          if (o.start != cur.start) break;
+          me = max(me, o.start + o.len - 1);
+          if (o.k < cur.k) cur = o;
+          ++nxt;
+        }
+        apply(P, Wn, pair, p, K, w, cur);
+        maxend = max(maxend, me);
+      } else {
+        apply(P, Wn, pair, p, K, w, cur);
+        maxend = max(maxend, cur.start + cur.len - 1);
+      }
+      j = nxt;
+      if (j >= n || pair_of(S[j], P.start_bits) != pair) {
+        last = true;
+        break;
+      }
+      const Hit nh = decode(S[j], P);
+      if (nh.start > maxend) break;  // next piece
+    }
+    if (!last) {
+      if (Wn.pend) flush(P, Wn, pair, p, K, w);
+    } else {
+      if (Wn.pend) {
+        const MemRow& top = Wn.rows[Wn.idx];
+        if (w.eos || top.start + top.len - 1 <= f_new(w, m, K)) flush(P, Wn, pair, p, K, w);
+      }
+      const unsigned long long q = atomicAdd(&P.ctr->n_pool, 1ull);
+      if (q >= P.cap_pool) {
+        atomicOr(&P.ctr->overflow, 8u);
+      } else {
+        WinHdr nhdr;
+        nhdr.pend = Wn.pend;
+        nhdr.idx = Wn.idx;
+        P.pool_hdr[q] = nhdr;
+        for (int lv = 0; lv <= K; ++lv) P.pool_mem[q * (kMaxK + 1) + lv] = Wn.rows[lv];
+        P.pair_pool[pair] = int32_t(q);
+      }
+    }
+  }
+}
+
+__global__ void finalize_kernel(const StepParams P) {
+  if (P.ctr->overflow) return;
+  const unsigned long long npairs = (unsigned long long)P.n_items * P.n_pat;
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long pr = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+       pr < npairs; pr += stride) {
+    const int p = int(pr % P.n_pat);
+    const WorkItem w = P.items[pr / P.n_pat];
+    const int m = P.m[p], K = P.K[p];
+    WinHdr* hd = P.hdr + size_t(w.slot) * P.n_pat + p;
+    MemRow* rows = P.mem + size_t(w.slot) * P.mem_stride + P.mem_off[p];
+    const int32_t q = P.pair_pool[pr];
+    if (q >= 0) {
+      *hd = P.pool_hdr[q];
+      for (int lv = 0; lv <= K; ++lv) rows[lv] = P.pool_mem[size_t(q) * (kMaxK + 1) + lv];
+    } else if (hd->pend) {
+      const MemRow& top = rows[hd->idx];
+      if (w.eos || top.start + top.len - 1 <= f_new(w, m, K)) {
+        Window Wn;
+        Wn.pend = 1;
+        Wn.idx = hd->idx;
+        for (int lv = 0; lv <= K; ++lv) Wn.rows[lv] = rows[lv];
+        flush(P, Wn, uint32_t(pr), p, K, w);
+        WinHdr z;
+        z.pend = 0;
+        z.idx = K;
+        *hd = z;
+        for (int lv = 0; lv <= K; ++lv) rows[lv].valid = 0;
+      }
+    }
+  }
+}
+
+__global__ void tails_kernel(const StepParams P) {
+  if (P.ctr->overflow) return;
+  for (uint32_t i = blockIdx.x; i < P.n_items; i += gridDim.x) {
+    const WorkItem w = P.items[i];
+    if (w.eos) continue;
+    const int64_t nt = min(w.e_new, int64_t(P.T));
+    const uint8_t* src = P.arena + w.arena_base + (w.e_new - nt - w.base_pos);
+    uint8_t* dst = P.tails + size_t(w.slot) * P.T;
+    for (int64_t b = threadIdx.x; b < nt; b += blockDim.x) dst[b] = src[b];
+  }
+}
+
+int grid_for(unsigned long long n, int threads, int cap_blocks) {
+  unsigned long long b = (n + threads - 1) / threads;
+  if (b < 1) b = 1;
+  if (b > (unsigned long long)cap_blocks) b = cap_blocks;
+  return int(b);
+}
+
+}  // namespace
+
+cudaError_t launch_gather(const CopyChunk* chunks, int n, uint8_t* arena, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  gather_kernel<<<min(n, 65535), 256, 0, s>>>(chunks, n, arena);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_verify(const StepParams& p, cudaStream_t s) {
+  // the candidate count lives on the device: size for the capacity, loop inside
+  const int grid = grid_for(p.cap_cand, 256, 152 * 16);
+  verify_kernel<<<grid, 256, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sort(const SortArgs& a, unsigned long long** keys_out, uint32_t** vals_out,
+                        int* launches, cudaStream_t s) {
+  unsigned long long* ka = a.keys;
+  unsigned long long* kb = a.keys_alt;
+  uint32_t* va = a.vals;
+  uint32_t* vb = a.vals_alt;
+  int nl = 0;
+  for (int shift = a.lo_bit; shift < a.hi_bit; shift += 8) {
+    rs_hist<<<a.nblocks, kSortThreads, 0, s>>>(ka, a.count, a.cap, shift, a.hist);
+    rs_prefix<<<1, 1024, 0, s>>>(a.hist, 256 * a.nblocks);
+    rs_scatter<<<a.nblocks, kSortThreads, 0, s>>>(ka, kb, va, vb, a.count, a.cap, shift, a.hist);
+    nl += 3;
+    std::swap(ka, kb);
+    std::swap(va, vb);
+  }
+  *keys_out = ka;
+  if (vals_out) *vals_out = va;
+  *launches = nl;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_permute(const DevHit* src, const uint32_t* idx, DevHit* dst,
+                           const unsigned long long* count, unsigned long long cap,
+                           cudaStream_t s) {
+  permute_kernel<<<grid_for(cap, 256, 152 * 8), 256, 0, s>>>(src, idx, dst, count, cap);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_filter(const StepParams& p, const unsigned long long* sorted, cudaStream_t s) {
+  const int grid = grid_for(p.cap_hits, 128, 152 * 32);
+  filter_kernel<<<grid, 128, 0, s>>>(p, sorted);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const StepParams& p, cudaStream_t s) {
+  const unsigned long long npairs = (unsigned long long)p.n_items * p.n_pat;
+  finalize_kernel<<<grid_for(npairs, 256, 152 * 16), 256, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tails(const StepParams& p, cudaStream_t s) {
+  if (p.n_items == 0) return cudaSuccess;
+  tails_kernel<<<min(p.n_items, 65535u), 128, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace oasm

@@ -1,0 +1,491 @@
+// scan.cu -- forward scan of the OASM device path (sm_103a).
+//
+// For every pattern p and every end position e of a region, the scan computes
+// D[e] = min over starts i of lev(p, t[i..e]): the last row of the
+// Levenshtein matrix of Eq. 1 whose dummy row is all zeros ("Less Naive",
+// Sec. 5.1).  An end with D[e] <= K is a candidate: every hit of Eq. 2 ends at
+// such a position, because lev(p, t[i..e]) >= D[e].
+//
+// The column of the matrix is held as bit-vectors of vertical differences
+// (Myers 1999, cited in Sec. 2; Hyyro's formulation): Pv/Mv mark +1/-1
+// differences down the column, and one column step is a fixed sequence of
+// 32-bit logic operations, one add with carry and two shifts per word.
+//
+// Work mapping (sm_103a, 152 SMs):
+//   block  = one lane group (32 pattern lanes of one word-count class) x
+//            `warps` regions of the text; the group's Peq table (256 symbol
+//            rows of W x 32 words) is brought into shared memory by a TMA
+//            bulk copy.
+//   warp   = one region [a, b) of end positions of one stream.
+//   lane   = one pattern (dictionary mapping), or, when the word class holds
+//            fewer than 32 patterns, one sub-segment of the region for one
+//            pattern (segment mapping).
+// Each lane scans from a - ov (ov = max over its group of l_p + K - 1
+// symbols of warm-up, after which a threshold test on D[e] is exact) to the
+// end of its range.  Patterns sit in the top bits of their W words, so the
+// score row is bit 31 of the top word and the unused low bits stay inert
+// (Pv = 1, Mv = 0, Eq = 0: no carry, no delta).
+//
+// The step is written for the integer pipes of an SM sub-partition: 7 LOP3
+// per word (the bit-vector logic), one add, two shifts as multiplies, the
+// score update and the candidate count as high-word multiply-adds and the
+// Peq address as a multiply-add, with text and Peq read from shared memory.
+//   dictionary mapping: the warp's text is streamed through a per-warp
+//     double buffer by TMA bulk copies (cp.async.bulk + mbarrier); every lane
+//     reads the same symbol (one broadcast LDS.U8 per step).  Candidates are
+//     counted per 16-symbol block; a block with any is replayed from its
+//     saved state to find the exact end positions.
+//   segment mapping: each lane reads its own sub-segment as 16-byte vectors
+//     from global memory, one vector ahead, and records candidates in a
+//     per-lane mask every step (candidates are frequent with one pattern).
+// Candidates are written through per-warp reservations of `resv` slots.
+#include "kernels.h"
+
+namespace oasm {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr uint32_t kInvalid = 0xffffffffu;
+constexpr uint32_t kSpinLimit = 1u << 24;  // bounded waits on mbarriers
+constexpr unsigned kTimeoutBit = 16u;
+
+// ------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return uint32_t(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void tma_load_1d(uint32_t dst, const void* src, uint32_t bytes,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(dst), "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Waits for a phase with an iteration bound; false if the bound ran out.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  for (uint32_t it = 0; it < kSpinLimit; ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// s + (x >> 31) and s - (x >> 31) as multiply-adds: the high word of x * 2
+// is the top bit of x (unsigned), or minus it (signed).  ptxas places these
+// and the other constant-multiplier forms on whichever integer pipe is free;
+// measured on GB300, that beats pinning them to the FMA pipe.
+__device__ __forceinline__ int add_top(int s, uint32_t x) {
+  int r;
+  asm("mad.hi.u32 %0, %1, 2, %2;" : "=r"(r) : "r"(x), "r"(s));
+  return r;
+}
+__device__ __forceinline__ int sub_top(int s, uint32_t x) {
+  int r;
+  asm("mad.hi.s32 %0, %1, 2, %2;" : "=r"(r) : "r"(x), "r"(s));
+  return r;
+}
+__device__ __forceinline__ uint32_t mad_lo(uint32_t a, uint32_t b, uint32_t c) {
+  uint32_t r;
+  asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(c));
+  return r;
+}
+__device__ __forceinline__ uint32_t shl1(uint32_t x) {  // x << 1 as a multiply
+  uint32_t r;
+  asm("mul.lo.u32 %0, %1, 2;" : "=r"(r) : "r"(x));
+  return r;
+}
+
+template <int W>
+__device__ __forceinline__ void add_words(const uint32_t (&a)[W], const uint32_t (&b)[W],
+                                          uint32_t (&s)[W]);
+template <>
+__device__ __forceinline__ void add_words<1>(const uint32_t (&a)[1], const uint32_t (&b)[1],
+                                             uint32_t (&s)[1]) {
+  s[0] = a[0] + b[0];
+}
+template <>
+__device__ __forceinline__ void add_words<2>(const uint32_t (&a)[2], const uint32_t (&b)[2],
+                                             uint32_t (&s)[2]) {
+  asm("add.cc.u32 %0, %2, %4;\n\t"
+      "addc.u32 %1, %3, %5;"
+      : "=r"(s[0]), "=r"(s[1])
+      : "r"(a[0]), "r"(a[1]), "r"(b[0]), "r"(b[1]));
+}
+template <>
+__device__ __forceinline__ void add_words<3>(const uint32_t (&a)[3], const uint32_t (&b)[3],
+                                             uint32_t (&s)[3]) {
+  asm("add.cc.u32 %0, %3, %6;\n\t"
+      "addc.cc.u32 %1, %4, %7;\n\t"
+      "addc.u32 %2, %5, %8;"
+      : "=r"(s[0]), "=r"(s[1]), "=r"(s[2])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(b[0]), "r"(b[1]), "r"(b[2]));
+}
+template <>
+__device__ __forceinline__ void add_words<4>(const uint32_t (&a)[4], const uint32_t (&b)[4],
+                                             uint32_t (&s)[4]) {
+  asm("add.cc.u32 %0, %4, %8;\n\t"
+      "addc.cc.u32 %1, %5, %9;\n\t"
+      "addc.cc.u32 %2, %6, %10;\n\t"
+      "addc.u32 %3, %7, %11;"
+      : "=r"(s[0]), "=r"(s[1]), "=r"(s[2]), "=r"(s[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]), "r"(b[2]),
+        "r"(b[3]));
+}
+
+// One column of the Sellers matrix (dummy row 0: no horizontal delta enters
+// the bottom word).  s tracks score - K - 1 and is negative iff D[e] <= K.
+template <int W>
+__device__ __forceinline__ void search_step(uint32_t (&Pv)[W], uint32_t (&Mv)[W], int& s,
+                                            const uint32_t (&eq)[W]) {
+  uint32_t x[W], sum[W];
+#pragma unroll
+  for (int w = 0; w < W; ++w) x[w] = eq[w] & Pv[w];
+  add_words<W>(x, Pv, sum);
+  uint32_t php = 0, mhp = 0;
+#pragma unroll
+  for (int w = 0; w < W; ++w) {
+    const uint32_t xv = eq[w] | Mv[w];
+    const uint32_t xh = (sum[w] ^ Pv[w]) | eq[w];
+    const uint32_t ph = Mv[w] | ~(xh | Pv[w]);
+    const uint32_t mh = Pv[w] & xh;
+    if (w == W - 1) s = sub_top(add_top(s, ph), mh);
+    const uint32_t phs = (w == 0) ? shl1(ph) : __funnelshift_l(php, ph, 1);
+    const uint32_t mhs = (w == 0) ? shl1(mh) : __funnelshift_l(mhp, mh, 1);
+    php = ph;
+    mhp = mh;
+    Pv[w] = mhs | ~(xv | phs);
+    Mv[w] = phs & xv;
+  }
+}
+
+template <int W>
+__device__ __forceinline__ void load_eq(const char* peq, uint32_t addr, uint32_t (&eq)[W]) {
+#pragma unroll
+  for (int w = 0; w < W; ++w) eq[w] = *reinterpret_cast<const uint32_t*>(peq + addr + w * 128);
+}
+
+__device__ __forceinline__ uint4 ld_stream(const uint4* p) {
+  uint4 v;
+  asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "l"(p));
+  return v;
+}
+
+// Writes the candidates of one 16-step block (mask bit 15-j = step j).
+struct Emitter {
+  unsigned long long rbase = 0;
+  int rleft = 0;
+  __device__ __forceinline__ void put(const ScanArgs& A, int lane, uint32_t c16, int64_t pos0,
+                                      uint32_t wi, int pid, int64_t base_pos) {
+    const int nc = __popc(c16);
+    int incl = nc;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int t = __shfl_up_sync(kFull, incl, d);
+      if (lane >= d) incl += t;
+    }
+    const int tot = __shfl_sync(kFull, incl, 31);
+    unsigned long long mybase = 0;
+    if (lane == 0) {
+      if (rleft < tot) {
+        for (int q = 0; q < rleft; ++q)
+          if (rbase + q < A.cap_cand) A.cand[rbase + q].wi = kInvalid;
+        const int take = max(tot, A.resv);
+        rbase = atomicAdd(&A.ctr->n_cand, (unsigned long long)take);
+        rleft = take;
+      }
+      mybase = rbase;
+      rbase += tot;
+      rleft -= tot;
+    }
+    mybase = __shfl_sync(kFull, mybase, 0);
+    unsigned long long o = mybase + unsigned(incl - nc);
+    bool over = false;
+    while (c16) {
+      const int bit = 31 - __clz(c16);
+      c16 &= ~(1u << bit);
+      const int64_t e = pos0 + (15 - bit);
+      if (o < A.cap_cand) {
+        Candidate c;
+        c.wi = wi;
+        c.pat = uint32_t(pid);
+        c.e_rel = uint64_t(e - base_pos);
+        A.cand[o] = c;
+      } else {
+        over = true;
+      }
+      ++o;
+    }
+    if (over) atomicOr(&A.ctr->overflow, 1u);
+  }
+  __device__ __forceinline__ void finish(const ScanArgs& A, int lane) {
+    if (lane == 0)
+      for (int q = 0; q < rleft; ++q)
+        if (rbase + q < A.cap_cand) A.cand[rbase + q].wi = kInvalid;
+  }
+};
+
+// Mask of the valid steps (report window) of block v, in mask-bit order.
+__device__ __forceinline__ uint32_t block_mask(int t_lo, int t_hi, int v) {
+  const int lo = min(max(t_lo - 16 * v, 0), 16), hi = min(max(t_hi - 16 * v, 0), 16);
+  return (hi > lo) ? (((1u << (16 - lo)) - 1u) & ~((1u << (16 - hi)) - 1u)) : 0u;
+}
+
+struct LaneSetup {
+  int pid, m, K;
+  int64_t spos;     // stream position of step 0 (16-byte aligned in the arena)
+  int64_t ad_al;    // arena offset of step 0
+  int nvec;         // 16-step blocks
+  int t_lo, t_hi;   // report window in steps
+};
+
+__device__ __forceinline__ LaneSetup lane_setup(const ScanArgs& A, const LaneGroup& G,
+                                                const Region& R, const WorkItem& wi, int lane) {
+  LaneSetup L;
+  L.pid = G.pat[lane];
+  L.m = G.m[lane];
+  L.K = G.K[lane];
+  const int nseg = G.nseg, ov = G.ov;
+  // lane sub-segment [a, b) of reported ends; Ls is a multiple of 16 so every
+  // lane of the warp shares the same vector alignment and trip count
+  const int64_t len = R.b - R.a;
+  int64_t Ls = (len + nseg - 1) / nseg;
+  Ls = (Ls + 15) & ~int64_t(15);
+  const int64_t a = R.a + int64_t(G.seg[lane]) * Ls;
+  const int64_t b = min(R.b, a + Ls);
+  const int64_t x0 = a - ov;
+  const int64_t ad0 = int64_t(wi.arena_base) + (x0 - wi.base_pos);
+  const int mis = int(ad0 & 15);
+  L.spos = x0 - mis;
+  L.ad_al = ad0 - mis;
+  L.nvec = int((Ls + ov + mis + 15) >> 4);
+  int64_t rep_lo = max(a, wi.e_prev - 2 * int64_t(L.K));
+  rep_lo = max(rep_lo, int64_t(0));
+  L.t_lo = int(rep_lo - L.spos);
+  L.t_hi = int(b - L.spos);
+  if (L.pid < 0 || b <= a) L.t_lo = L.t_hi = 0;
+  return L;
+}
+
+// ------------------------------------------------- dictionary mapping
+template <int W>
+__device__ void scan_dict(const ScanArgs& A, const char* peq, uint8_t* tbuf, uint32_t bar0,
+                          const LaneGroup& G, const Region& R, const WorkItem& wi, int lane) {
+  const LaneSetup L = lane_setup(A, G, R, wi, lane);
+  const int CH = A.chunk;
+  const int nbytes = L.nvec * 16;
+  const int nchunks = (nbytes + CH - 1) / CH;
+  const uint8_t* src = A.arena + L.ad_al;
+  const uint32_t tb = smem_u32(tbuf);
+  const uint32_t lane_off = uint32_t(lane) * 4u;
+  if (lane == 0) {
+    for (int c = 0; c < 2 && c < nchunks; ++c) {
+      const uint32_t n = uint32_t(min(CH, nbytes - c * CH));
+      mbar_expect_tx(bar0 + 8 * c, n);
+      tma_load_1d(tb + c * CH, src + size_t(c) * CH, n, bar0 + 8 * c);
+    }
+  }
+  uint32_t Pv[W], Mv[W];
+#pragma unroll
+  for (int w = 0; w < W; ++w) {
+    Pv[w] = 0xffffffffu;
+    Mv[w] = 0u;
+  }
+  int s = L.m - L.K - 1;
+  Emitter em;
+  int dead_at = -1;
+  for (int c = 0; c < nchunks; ++c) {
+    const int buf = c & 1;
+    const bool ok = mbar_wait(bar0 + 8 * buf, uint32_t((c >> 1) & 1));
+    if (__any_sync(kFull, !ok)) {
+      dead_at = c;
+      break;
+    }
+    const uint8_t* t = tbuf + buf * CH;
+    const int nv = min(CH, nbytes - c * CH) >> 4;
+    for (int vv = 0; vv < nv; ++vv) {
+      const int v = c * (CH >> 4) + vv;
+      const uint8_t* tv = t + vv * 16;
+      uint32_t Pv0[W], Mv0[W];
+#pragma unroll
+      for (int w = 0; w < W; ++w) {
+        Pv0[w] = Pv[w];
+        Mv0[w] = Mv[w];
+      }
+      const int s0 = s;
+      int cnt = 0;
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const uint32_t sym = tv[j];
+        uint32_t eq[W];
+        load_eq<W>(peq, mad_lo(sym, 128u * W, lane_off), eq);
+        search_step<W>(Pv, Mv, s, eq);
+        cnt = add_top(cnt, uint32_t(s));  // counts steps with s < 0
+      }
+      const uint32_t vm = block_mask(L.t_lo, L.t_hi, v);
+      if (__any_sync(kFull, cnt != 0 && vm != 0)) {
+        // rare: replay the block from its saved state, recording each step
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+          Pv[w] = Pv0[w];
+          Mv[w] = Mv0[w];
+        }
+        s = s0;
+        uint32_t cm = 0;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const uint32_t sym = tv[j];
+          uint32_t eq[W];
+          load_eq<W>(peq, mad_lo(sym, 128u * W, lane_off), eq);
+          search_step<W>(Pv, Mv, s, eq);
+          cm = __funnelshift_l(uint32_t(s), cm, 1);
+        }
+        em.put(A, lane, cm & vm, L.spos + 16 * v, R.wi, L.pid, wi.base_pos);
+      }
+    }
+    __syncwarp();
+    if (lane == 0 && c + 2 < nchunks) {
+      fence_proxy_async();  // our reads of this buffer precede the async write
+      const uint32_t n = uint32_t(min(CH, nbytes - (c + 2) * CH));
+      mbar_expect_tx(bar0 + 8 * buf, n);
+      tma_load_1d(tb + buf * CH, src + size_t(c + 2) * CH, n, bar0 + 8 * buf);
+    }
+  }
+  if (dead_at >= 0) {
+    if (lane == 0) {
+      atomicOr(&A.ctr->overflow, 1u << kTimeoutBit);
+      // copies still in flight into this warp's buffers: bounded wait, then leave
+      for (int c = dead_at; c < dead_at + 2 && c < nchunks; ++c)
+        mbar_wait(bar0 + 8 * (c & 1), uint32_t((c >> 1) & 1));
+    }
+    __syncwarp();
+    return;
+  }
+  em.finish(A, lane);
+}
+
+// ---------------------------------------------------- segment mapping
+template <int W>
+__device__ void scan_segments(const ScanArgs& A, const char* peq, const LaneGroup& G,
+                              const Region& R, const WorkItem& wi, int lane) {
+  const LaneSetup L = lane_setup(A, G, R, wi, lane);
+  const uint32_t lane_off = uint32_t(lane) * 4u;
+  uint32_t Pv[W], Mv[W];
+#pragma unroll
+  for (int w = 0; w < W; ++w) {
+    Pv[w] = 0xffffffffu;
+    Mv[w] = 0u;
+  }
+  int s = L.m - L.K - 1;
+  uint32_t cm = 0;
+  Emitter em;
+  const uint4* vp = reinterpret_cast<const uint4*>(A.arena + L.ad_al);
+  uint4 cur = ld_stream(vp);
+  for (int v = 0; v < L.nvec; ++v) {
+    const uint4 nxt = ld_stream(vp + min(v + 1, L.nvec - 1));
+    const uint32_t wd4[4] = {cur.x, cur.y, cur.z, cur.w};
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const uint32_t sym = __byte_perm(wd4[j >> 2], 0u, 0x4440u | uint32_t(j & 3));
+      uint32_t eq[W];
+      load_eq<W>(peq, mad_lo(sym, 128u * W, lane_off), eq);
+      search_step<W>(Pv, Mv, s, eq);
+      cm = __funnelshift_l(uint32_t(s), cm, 1);  // shifts in the sign of s
+    }
+    const uint32_t c16 = cm & block_mask(L.t_lo, L.t_hi, v);
+    if (__any_sync(kFull, c16 != 0)) em.put(A, lane, c16, L.spos + 16 * v, R.wi, L.pid, wi.base_pos);
+    cur = nxt;
+  }
+  em.finish(A, lane);
+}
+
+template <int W, bool kDict>
+__global__ void __launch_bounds__(512) scan_kernel(const ScanArgs A) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  constexpr uint32_t kPeqBytes = 256u * 128u * W;
+  const int g = blockIdx.x % A.n_groups;
+  const int rb = blockIdx.x / A.n_groups;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // layout: Peq | text double buffers (dictionary) | mbarriers
+  uint8_t* tbase = smem + kPeqBytes;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(tbase + (kDict ? size_t(A.warps) * 2 * A.chunk : 0));
+  const uint32_t bar_peq = smem_u32(bars);
+  if (threadIdx.x == 0) mbar_init(bar_peq, 1);
+  if (kDict && lane == 0) {
+    mbar_init(smem_u32(bars + 1 + 2 * warp), 1);
+    mbar_init(smem_u32(bars + 2 + 2 * warp), 1);
+  }
+  fence_mbar_init();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const uint8_t* src = reinterpret_cast<const uint8_t*>(A.peq) + size_t(g) * kPeqBytes;
+    mbar_expect_tx(bar_peq, kPeqBytes);
+    for (uint32_t o = 0; o < kPeqBytes; o += 32768u)
+      tma_load_1d(smem_u32(smem + o), src + o, min(32768u, kPeqBytes - o), bar_peq);
+  }
+  const bool peq_ok = mbar_wait(bar_peq, 0);
+  if (!peq_ok) {
+    if (threadIdx.x == 0) atomicOr(&A.ctr->overflow, 1u << kTimeoutBit);
+    return;
+  }
+  const int r = rb * A.warps + warp;
+  if (r >= A.n_regions) return;  // the whole warp leaves together
+  const LaneGroup& G = A.groups[g];
+  const Region R = A.regions[r];
+  const WorkItem wi = A.items[R.wi];
+  const char* peq = reinterpret_cast<const char*>(smem);
+  if (kDict)
+    scan_dict<W>(A, peq, tbase + size_t(warp) * 2 * A.chunk, smem_u32(bars + 1 + 2 * warp), G, R,
+                 wi, lane);
+  else
+    scan_segments<W>(A, peq, G, R, wi, lane);
+}
+
+template <int W, bool kDict>
+cudaError_t launch_w(const ScanArgs& a, cudaStream_t st) {
+  const size_t smem = scan_smem_bytes(W, a.warps, kDict ? a.chunk : 0);
+  cudaError_t e = cudaFuncSetAttribute(scan_kernel<W, kDict>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e != cudaSuccess) return e;
+  const long long blocks_r = (a.n_regions + a.warps - 1) / a.warps;
+  const long long grid = blocks_r * a.n_groups;
+  if (grid <= 0) return cudaSuccess;
+  scan_kernel<W, kDict><<<unsigned(grid), a.warps * 32, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_scan(const ScanArgs& a, cudaStream_t s) {
+  const bool d = a.dict != 0;
+  switch (a.W) {
+    case 1: return d ? launch_w<1, true>(a, s) : launch_w<1, false>(a, s);
+    case 2: return d ? launch_w<2, true>(a, s) : launch_w<2, false>(a, s);
+    case 3: return d ? launch_w<3, true>(a, s) : launch_w<3, false>(a, s);
+    case 4: return d ? launch_w<4, true>(a, s) : launch_w<4, false>(a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace oasm

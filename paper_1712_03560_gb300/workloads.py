@@ -11,7 +11,7 @@ Workload shapes (the paper's own data are not available):
                        paper use random {A,B,C,D} text).
   * ``dictionary_dna`` 1,024 DNA patterns m~U[8,32], K=floor(m/10), 256 MiB
                        iid text, 1,000 copies per pattern with exactly K edits
-                       (MOASM, Sec. 5.4; miRNA-sized motifs of Sec. 5).
+                       (MOASM, Sec. 6.4; miRNA-sized motifs of Sec. 5).
   * ``bytes_zipf``     4,096 byte patterns m log-uniform in [16,128],
                        K~U[1, min(8, m//4)], Zipf(1.1) bytes (NIDS-like
                        signatures, Sec. 1), 500 copies each with 1..K edits.

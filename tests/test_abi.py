@@ -1,0 +1,66 @@
+"""CPU-side checks of the C ABI: the CUDA library builds for sm_103a, loads,
+exports every function ``include/oasm.h`` declares, and rejects bad input on
+the host without touching a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1712_03560_gb300 import binding as B
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(__file__)), "include", "oasm.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(oasm_[a-z_]+)\s*\(", src)))
+
+
+def test_header_declares_expected_entry_points():
+    names = declared_functions()
+    for must in ("oasm_create", "oasm_feed", "oasm_flush", "oasm_open_stream",
+                 "oasm_close_stream", "oasm_destroy", "oasm_strerror", "oasm_last_error"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = B.load()
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+    assert sorted(B.EXPORTS) == sorted(declared_functions())
+
+
+def test_struct_sizes_match_header():
+    assert ctypes.sizeof(B.oasm_hit) == 32
+    assert ctypes.sizeof(B.oasm_rules) == 20
+    # oasm_config: 4+4+8+4+4+4+4+8
+    assert ctypes.sizeof(B.oasm_config) == 40
+
+
+@pytest.mark.parametrize("lens,ks", [([0], [0]), ([129], [1]), ([8], [8]), ([20], [16]), ([], [])])
+def test_create_rejects_bad_patterns(lens, ks):
+    pats = [b"A" * max(n, 1) for n in lens]
+    lib = B.load()
+    n = len(lens)
+    ptrs = (ctypes.c_void_p * max(n, 1))(*[ctypes.cast(ctypes.c_char_p(p), ctypes.c_void_p) for p in pats])
+    L = (ctypes.c_uint32 * max(n, 1))(*lens)
+    K = (ctypes.c_uint32 * max(n, 1))(*ks)
+    ctx = ctypes.c_void_p()
+    rc = lib.oasm_create(ptrs, L, K, n, None, None, ctypes.byref(ctx))
+    assert rc == B.OASM_EINVAL
+    assert not ctx.value
+    assert lib.oasm_last_error(None)
+
+
+def test_strerror_and_null_safety():
+    lib = B.load()
+    for code in (0, -1, -2, -3, -4, -5, -6, -7):
+        assert lib.oasm_strerror(code)
+    assert lib.oasm_destroy(None) == 0
+    assert lib.oasm_step(None) == B.OASM_EINVAL
+    assert lib.oasm_open_stream(None, None) == B.OASM_EINVAL
+    cfg = B.oasm_config()
+    assert lib.oasm_config_default(ctypes.byref(cfg)) == 0
+    assert cfg.max_streams == 64 and cfg.flush_timeout_ms > 0

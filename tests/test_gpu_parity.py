@@ -1,0 +1,285 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle,
+element by element -- pattern id, start, length, k and decision point must
+all agree exactly (integer work, no tolerance)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1712_03560_gb300 import binding as B
+from paper_1712_03560_gb300 import workloads as W
+from parity_util import canon, oracle_rows, random_case, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+RULE_SETS = [dict(replace=r, order=o, acc=a, cmp=c)
+             for r in ("contained", "same_end", "never")
+             for o in ("per_start_length", "per_start_best")
+             for a in ("sum", "last")
+             for c in ("gt", "ge")]
+
+
+def test_worked_example_on_gpu():
+    rows, _ = run_gpu([b"ACBDA"], [2], np.frombuffer(b"CCCCDACCBDACBDAA", np.uint8))
+    assert canon(rows) == canon([(0, 14, 0, 10, 5), (0, 14, 2, 3, 3)])
+
+
+def test_plain_dna_full_size():
+    """m=8, K=2, 1e6 symbols with 200 planted copies: whole output."""
+    wl = W.plain_dna()
+    rows, st = run_gpu(wl.patterns, wl.ks, wl.texts[0])
+    want = oracle_rows(wl.patterns, wl.ks, wl.texts[0])
+    assert len(want) > 200
+    assert canon(rows) == want
+    assert st["scan_launches"] >= 1
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_random_dictionaries_default_rules(seed):
+    rng = np.random.default_rng(seed)
+    for sigma, npat, mlo, mhi, n in [(4, 40, 4, 32, 20000), (2, 7, 2, 12, 5000),
+                                     (256, 70, 16, 128, 30000), (4, 33, 30, 70, 8000),
+                                     (3, 5, 1, 6, 3000)]:
+        pats, ks, text = random_case(rng, sigma, npat, mlo, mhi, n, kmax=8)
+        rows, _ = run_gpu(pats, ks, text)
+        assert canon(rows) == oracle_rows(pats, ks, text), (sigma, npat)
+
+
+@pytest.mark.parametrize("ri", range(len(RULE_SETS)))
+def test_every_rule_set(ri):
+    rules = RULE_SETS[ri]
+    rng = np.random.default_rng(100 + ri)
+    pats, ks, text = random_case(rng, 3, 12, 3, 20, 6000, kmax=4)
+    rows, _ = run_gpu(pats, ks, text, rules)
+    assert canon(rows) == oracle_rows(pats, ks, text, rules)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_chunk_invariance(seed):
+    """Output does not depend on how the stream is cut into feeds."""
+    rng = np.random.default_rng(200 + seed)
+    pats, ks, text = random_case(rng, 4, 20, 4, 40, 12000, kmax=4)
+    want = oracle_rows(pats, ks, text)
+    for trial in range(3):
+        nsplit = int(rng.integers(1, 30))
+        splits = np.sort(rng.integers(0, text.size + 1, size=nsplit))
+        rows, _ = run_gpu(pats, ks, text, splits=splits)
+        assert canon(rows) == want, splits
+    # one symbol at a time over a short prefix
+    short = text[:400]
+    rows, _ = run_gpu(pats, ks, short, splits=np.arange(1, short.size))
+    assert canon(rows) == oracle_rows(pats, ks, short)
+
+
+def test_partial_flush_returns_only_decided_hits():
+    """Hits returned before the end are final: a later flush never revises them."""
+    rng = np.random.default_rng(7)
+    pats, ks, text = random_case(rng, 4, 8, 6, 20, 20000, kmax=3)
+    want = oracle_rows(pats, ks, text)
+    ctx = B.oasm_create(pats, ks)
+    try:
+        sid = B.oasm_open_stream(ctx)
+        got = []
+        for a in range(0, text.size, 3001):
+            B.oasm_feed(ctx, sid, text[a:a + 3001])
+            part = B.oasm_flush(ctx, sid)
+            fed = min(text.size, a + 3001)
+            for r in part:  # nothing decided beyond what the fed text fixes
+                p = int(r["pattern_id"])
+                assert int(r["decided_at"]) + len(pats[p]) + ks[p] <= fed
+            got += [(int(r["pattern_id"]), int(r["decided_at"]), int(r["k"]), int(r["start"]),
+                     int(r["len"])) for r in part]
+        got += [(int(r["pattern_id"]), int(r["decided_at"]), int(r["k"]), int(r["start"]),
+                 int(r["len"])) for r in B.oasm_flush(ctx, sid, end_of_stream=True)]
+        assert canon(got) == want
+    finally:
+        B.oasm_destroy(ctx)
+
+
+def test_many_streams_alone_and_in_the_mix():
+    """Each stream's result is the same alone and interleaved with others."""
+    rng = np.random.default_rng(11)
+    pats, ks, _ = random_case(rng, 4, 24, 6, 40, 10, kmax=4)
+    texts = [random_case(rng, 4, 1, 6, 8, int(rng.integers(0, 9000)))[2] for _ in range(9)]
+    for t in texts:  # plant a few pattern copies into every text
+        for p, k in zip(pats[:5], ks[:5]):
+            if t.size > 100:
+                W.plant(rng, t, W.edit_copy(rng, p, k, W.DNA))
+    ctx = B.oasm_create(pats, ks, None, {"max_streams": 16})
+    try:
+        sids = [B.oasm_open_stream(ctx) for _ in texts]
+        pos = [0] * len(texts)
+        got = {s: [] for s in sids}
+        while any(p < t.size for p, t in zip(pos, texts)):
+            for i, (s, t) in enumerate(zip(sids, texts)):
+                if pos[i] < t.size:
+                    n = int(rng.integers(1, 2500))
+                    B.oasm_feed(ctx, s, t[pos[i]:pos[i] + n])
+                    pos[i] += n
+            B.oasm_step(ctx)
+        for s in sids:
+            B.oasm_end_stream(ctx, s)
+        B.oasm_step(ctx)
+        for s in sids:
+            res = B.oasm_flush(ctx, s)
+            assert (res["stream_id"] == s).all()
+            got[s] = [(int(r["pattern_id"]), int(r["decided_at"]), int(r["k"]), int(r["start"]),
+                       int(r["len"])) for r in res]
+        for s, t in zip(sids, texts):
+            assert canon(got[s]) == oracle_rows(pats, ks, t), s
+            alone, _ = run_gpu(pats, ks, t)
+            assert canon(alone) == canon(got[s])
+    finally:
+        B.oasm_destroy(ctx)
+
+
+@pytest.mark.parametrize("n_pat", [1, 2, 3, 17, 31, 32, 33, 64, 100])
+def test_lane_group_shapes(n_pat):
+    """Few patterns spread one pattern over several lanes; many fill groups."""
+    rng = np.random.default_rng(300 + n_pat)
+    pats, ks, text = random_case(rng, 4, n_pat, 5, 60, 15000, kmax=5)
+    rows, _ = run_gpu(pats, ks, text)
+    assert canon(rows) == oracle_rows(pats, ks, text)
+
+
+def test_pattern_length_extremes():
+    rng = np.random.default_rng(5)
+    alpha = np.frombuffer(b"ACGT", np.uint8)
+    pats = [alpha[rng.integers(0, 4, size=m)] for m in (1, 2, 31, 32, 33, 63, 64, 65, 96, 97, 127, 128)]
+    ks = [0, 1, 7, 8, 15, 3, 15, 15, 15, 2, 15, 15]
+    text = alpha[rng.integers(0, 4, size=20000)]
+    for p, k in zip(pats, ks):
+        for _ in range(3):
+            W.plant(rng, text, W.edit_copy(rng, p, k, alpha))
+    rows, _ = run_gpu(pats, ks, text)
+    assert canon(rows) == oracle_rows(pats, ks, text)
+
+
+@pytest.mark.parametrize("n", [0, 1, 5, 7, 8, 9, 15, 16, 17, 33])
+def test_short_and_empty_texts(n):
+    rng = np.random.default_rng(n)
+    pats, ks, text = random_case(rng, 2, 6, 2, 9, n, kmax=3)
+    rows, _ = run_gpu(pats, ks, text)
+    assert canon(rows) == oracle_rows(pats, ks, text)
+
+
+def test_byte_alphabet_all_values():
+    rng = np.random.default_rng(9)
+    pats, ks, text = random_case(rng, 256, 40, 10, 100, 50000, kmax=8)
+    rows, _ = run_gpu(pats, ks, text)
+    assert canon(rows) == oracle_rows(pats, ks, text)
+
+
+def test_device_feed_equals_host_feed():
+    rng = np.random.default_rng(13)
+    pats, ks, text = random_case(rng, 4, 20, 6, 30, 30000, kmax=3)
+    a, _ = run_gpu(pats, ks, text)
+    b, _ = run_gpu(pats, ks, text, device_feed=True, splits=[5000, 17000])
+    assert canon(a) == canon(b) == oracle_rows(pats, ks, text)
+
+
+def test_raw_outputs_less_naive_and_all_hits():
+    rng = np.random.default_rng(17)
+    pats, ks, text = random_case(rng, 4, 10, 5, 30, 8000, kmax=4)
+    ends, _ = run_gpu(pats, ks, text, {"output": "ends"})
+    assert canon(ends) == oracle_rows(pats, ks, text, mode="ends")
+    allh, _ = run_gpu(pats, ks, text, {"output": "all_hits"})
+    assert canon(allh) == oracle_rows(pats, ks, text, mode="hits")
+    # kept <= Sellers ends <= hits (the shape of Table 1)
+    kept, _ = run_gpu(pats, ks, text)
+    assert len(kept) <= len(ends) <= len(allh)
+
+
+def test_small_buffers_regrow_and_rerun():
+    """A step whose device buffers overflow is re-run after they grow."""
+    rng = np.random.default_rng(21)
+    pats = [np.frombuffer(b"AAAA", np.uint8)] * 3 + [np.frombuffer(b"ACAC", np.uint8)]
+    ks = [1, 2, 3, 2]
+    text = np.frombuffer(b"A" * 40000 + b"AC" * 20000, np.uint8).copy()
+    rows, st = run_gpu(pats, ks, text)
+    assert canon(rows) == oracle_rows(pats, ks, text)
+
+
+def test_stream_admission_and_slots():
+    ctx = B.oasm_create([b"ACGTACGT"], [1], None, {"max_streams": 2})
+    try:
+        a = B.oasm_open_stream(ctx)
+        b = B.oasm_open_stream(ctx)
+        with pytest.raises(B.OasmError) as e:
+            B.oasm_open_stream(ctx)
+        assert e.value.code == B.OASM_EBUSY
+        B.oasm_close_stream(ctx, a)
+        c = B.oasm_open_stream(ctx)
+        assert c == a
+        B.oasm_close_stream(ctx, b)
+        B.oasm_close_stream(ctx, c)
+    finally:
+        B.oasm_destroy(ctx)
+    ctx = B.oasm_create([b"ACGTACGT"] * 100, [1] * 100, None, {"max_streams": 8, "mem_budget": 5000})
+    try:
+        s = B.oasm_open_stream(ctx)
+        with pytest.raises(B.OasmError) as e:
+            B.oasm_open_stream(ctx)
+        assert e.value.code == B.OASM_ENOMEM
+        B.oasm_close_stream(ctx, s)
+        B.oasm_open_stream(ctx)
+    finally:
+        B.oasm_destroy(ctx)
+
+
+def test_dictionary_dna_reduced():
+    """Shape of the 1,024-pattern DNA dictionary at a size the oracle finishes fast."""
+    wl = W.dictionary_dna(n=1 << 21, n_pat=256, copies=20)
+    rows, st = run_gpu(wl.patterns, wl.ks, wl.texts[0])
+    assert canon(rows) == oracle_rows(wl.patterns, wl.ks, wl.texts[0])
+    assert st["kept"] == len(rows)
+
+
+def test_bytes_zipf_reduced():
+    wl = W.bytes_zipf(n=1 << 20, n_pat=200, copies=10)
+    rows, _ = run_gpu(wl.patterns, wl.ks, wl.texts[0])
+    assert canon(rows) == oracle_rows(wl.patterns, wl.ks, wl.texts[0])
+
+
+def test_many_texts_reduced():
+    wl = W.many_texts(n_texts=40, total=4e6, n_pat=64, copies=20)
+    ctx = B.oasm_create(wl.patterns, wl.ks, None, {"max_streams": 64})
+    try:
+        sids = []
+        for t in wl.texts:
+            s = B.oasm_open_stream(ctx)
+            B.oasm_feed(ctx, s, t)
+            B.oasm_end_stream(ctx, s)
+            sids.append(s)
+        B.oasm_step(ctx)
+        for s, t in zip(sids, wl.texts):
+            res = B.oasm_flush(ctx, s)
+            got = [(int(r["pattern_id"]), int(r["decided_at"]), int(r["k"]), int(r["start"]),
+                    int(r["len"])) for r in res]
+            assert canon(got) == oracle_rows(wl.patterns, wl.ks, t)
+    finally:
+        B.oasm_destroy(ctx)
+
+
+def test_autotune_then_search_matches_oracle():
+    import json
+
+    import torch
+    wl = W.dictionary_dna(n=1 << 21, n_pat=80, copies=20)
+    ctx = B.oasm_create(wl.patterns, wl.ks)
+    try:
+        t = torch.from_numpy(wl.texts[0]).cuda()
+        rep = json.loads(B.oasm_autotune(ctx, t))
+        assert rep["buckets"] and all(b["ms"] > 0 for b in rep["buckets"])
+        sid = B.oasm_open_stream(ctx)
+        B.oasm_feed_device(ctx, sid, t)
+        res = B.oasm_flush(ctx, sid, end_of_stream=True)
+        got = [(int(r["pattern_id"]), int(r["decided_at"]), int(r["k"]), int(r["start"]),
+                int(r["len"])) for r in res]
+        assert canon(got) == oracle_rows(wl.patterns, wl.ks, wl.texts[0])
+    finally:
+        B.oasm_destroy(ctx)
+
+
+def test_int_peak_microbenchmark_runs():
+    ops, ms = B.oasm_measure_int_peak(0)
+    assert ops > 1e12 and ms > 0

@@ -4,7 +4,7 @@
 * an edit distance found by breadth-first search over single-symbol edits,
   i.e. the definition of Sec. 3 ("minimum number of single-character edits")
   with no dynamic programming at all,
-* brute-force enumeration of every substring (Fully Naive, Sec. 4.1),
+* brute-force enumeration of every substring (Fully Naive, Sec. 5.1),
 * textbook special cases (K = 0 reduces to leftmost non-overlapping exact
   search, done here with ``bytes.find``),
 * invariants of the priority rules and of the validation step.
@@ -149,7 +149,7 @@ def test_lev_prefixes_equal_full_matrix_random():
 
 
 # --------------------------------------------------------------------------
-# Less Naive and the hit set against brute force (Fully Naive, Sec. 4.1)
+# Less Naive and the hit set against brute force (Fully Naive, Sec. 5.1)
 
 def fully_naive(p, K, t, levfn):
     """Every substring of every length, its distance, kept when <= K."""
@@ -376,6 +376,6 @@ def test_dictionary_is_independent_per_pattern():
 
 def test_oracle_rejects_bad_thresholds():
     with pytest.raises(ValueError):
-        oracle.oasm(b"ACGT", 4, b"ACGTACGT")  # K < l_p is required (Sec. 5.2)
+        oracle.oasm(b"ACGT", 4, b"ACGTACGT")  # K < l_p is required (Sec. 6.3)
     with pytest.raises(ValueError):
         oracle.hits(b"", 0, b"ACGT")
