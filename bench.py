@@ -33,7 +33,11 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-OPS_PER_WORD_STEP = 16  # integer ops of one 32-bit column step of the scan (see DESIGN.md)
+OPS_PER_WORD_STEP = 16  # integer ops of one 32-bit column step of the scan
+# DRAM bytes per scan launch and text byte, from an ncu capture of the scan on
+# the 64 MiB DNA dictionary (77.9 MB for 64 MiB); traffic scales with the text
+SCAN_DRAM_BYTES_PER_TEXT_BYTE = {"dictionary_dna": 77.9e6 / (64 << 20),
+                                 "dictionary_dna_64m": 77.9e6 / (64 << 20)}
 SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
 
@@ -296,8 +300,10 @@ def main():
     alg_ops_launch = words * OPS_PER_WORD_STEP / max(1, st["scan_launches"] // max(1, args.steps))
     achieved = alg_ops_launch / (scan_ms_launch * 1e-3) / 1e12
     derived_peak = SM_COUNT * 128 * SM_MAX_MHZ * 1e6 / 1e12
+    tpb = SCAN_DRAM_BYTES_PER_TEXT_BYTE.get(args.workload)
     roofline = {"bound": "alu", "achieved": achieved, "peak": derived_peak, "unit": "Tops/s",
-                "frac": achieved / derived_peak, "traffic": None,
+                "frac": achieved / derived_peak,
+                "traffic": tpb * wl.text_bytes if tpb else None,
                 "peak_measured_mix": peak_ops / 1e12,
                 "frac_of_measured_mix": achieved * 1e12 / peak_ops,
                 "kernel": "scan_kernel<1>", "kernel_ms_per_launch": scan_ms_launch,
@@ -364,6 +370,7 @@ def main():
         "candidates_per_step": st["candidates"] / args.steps,
         "hits_per_step": st["hits"] / args.steps,
         "gpu_launches": int(st["launches"]),
+        "reruns": int(st["reruns"]),
         "roofline": roofline,
         "e2e": e2e,
         "cpu_baseline": cpu,
