@@ -228,6 +228,45 @@ int oasm_autotune(oasm_ctx *ctx, const uint8_t *dsample, size_t n, char *report,
  * of that launch.  Used as the roofline peak of the scan. */
 int oasm_measure_int_peak(int device, double *ops_per_s, double *ms);
 
+/* ---- search without device allocation (no counterpart in the paper) ----
+ * For callers that cannot call cudaMalloc: code running inside a framework
+ * whose caching allocator already holds the device's memory, code under a
+ * hard per-process memory cap, or code that must not trigger the implicit
+ * synchronisation an allocation can cause.  This call uses only the
+ * caller's buffers and one fixed scratch array in the library's device image
+ * (OASM_NOALLOC_SCRATCH_BYTES, held by every GPU that loads the library until
+ * the process exits).
+ *
+ * It reports the "Less Naive" ends of Sec. 5.1 -- every end position e where
+ * min over starts i of lev(p, t[i..e]) <= K -- for up to
+ * OASM_NOALLOC_MAX_PATTERNS patterns over one device-resident text, with no
+ * priority filter and no streaming state: the same end positions and
+ * distances as an OASM_OUT_ENDS context, in no particular order.
+ *   pat/len/k  as for oasm_create (1..OASM_NOALLOC_MAX_PATTERNS patterns)
+ *   d_text, n  the text, device memory
+ *   d_out, cap caller's device array of cap oasm_end records
+ *   n_found    host pointer: the number of ends found (may exceed cap)
+ *   cuda_stream the stream to run on (NULL: the legacy default stream)
+ * Runs on the calling thread's current CUDA device and returns after the
+ * work has finished.  The first call on a device looks up the scratch
+ * array's device address; make that first call before any stream capture.
+ * Calls that overlap on the GPU share the scratch array and race.
+ * Returns OASM_OK, OASM_ETRUNC (more than cap ends: the first cap written,
+ * in no particular order), OASM_EINVAL (bad argument, or more than
+ * OASM_NOALLOC_MAX_PATTERNS patterns), OASM_ECUDA. */
+#define OASM_NOALLOC_MAX_PATTERNS 64
+#define OASM_NOALLOC_SCRATCH_BYTES (1024 + OASM_NOALLOC_MAX_PATTERNS * 4096)
+
+typedef struct {
+    uint32_t pattern_id;
+    uint32_t k;   /* min over starts of the distance of a substring ending here */
+    uint64_t end; /* 0-based end position */
+} oasm_end;
+
+int oasm_scan_ends_noalloc(const uint8_t *const *pat, const uint32_t *len, const uint32_t *k,
+                           uint32_t n_pat, const uint8_t *d_text, uint64_t n, oasm_end *d_out,
+                           uint64_t cap, uint64_t *n_found, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

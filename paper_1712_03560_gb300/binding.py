@@ -35,6 +35,7 @@ OUTPUT = {"filtered": 0, "ends": 1, "all_hits": 2}
 
 HIT_DTYPE = np.dtype([("pattern_id", "<u4"), ("k", "<u4"), ("start", "<u8"), ("len", "<u4"),
                       ("stream_id", "<u4"), ("decided_at", "<u8")])
+END_DTYPE = np.dtype([("pattern_id", "<u4"), ("k", "<u4"), ("end", "<u8")])
 
 
 class OasmError(RuntimeError):
@@ -77,7 +78,7 @@ EXPORTS = ["oasm_config_default", "oasm_rules_default", "oasm_create", "oasm_des
            "oasm_open_stream", "oasm_close_stream", "oasm_feed", "oasm_feed_device",
            "oasm_end_stream", "oasm_step", "oasm_flush", "oasm_ready", "oasm_get_stats", "oasm_reset_stats",
            "oasm_cuda_stream", "oasm_last_error", "oasm_strerror", "oasm_autotune",
-           "oasm_measure_int_peak"]
+           "oasm_measure_int_peak", "oasm_scan_ends_noalloc"]
 
 _lib = None
 _lock = threading.Lock()
@@ -118,6 +119,8 @@ def load(path: str | None = None):
             "oasm_autotune": ([vp, vp, ctypes.c_size_t, ctypes.c_char_p, ctypes.c_size_t], i32),
             "oasm_measure_int_peak": ([i32, ctypes.POINTER(ctypes.c_double),
                                        ctypes.POINTER(ctypes.c_double)], i32),
+            "oasm_scan_ends_noalloc": ([u8pp, ctypes.POINTER(u32), ctypes.POINTER(u32), u32, vp,
+                                        u64, vp, u64, ctypes.POINTER(u64), vp], i32),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -269,6 +272,31 @@ def oasm_measure_int_peak(device: int = 0):
     ops, ms = ctypes.c_double(), ctypes.c_double()
     _check(load().oasm_measure_int_peak(device, ctypes.byref(ops), ctypes.byref(ms)))
     return ops.value, ms.value
+
+
+def oasm_scan_ends_noalloc(patterns, ks, d_text, d_out, cap: int, n: int | None = None,
+                           stream: int = 0) -> int:
+    """Less Naive ends of up to 64 patterns over a device text, allocating no
+    device memory (for callers that cannot allocate: see include/oasm.h).
+
+    ``d_out`` is the caller's device buffer of ``cap`` records of
+    ``END_DTYPE`` (16 bytes each).  Returns the number of ends found, which
+    may exceed ``cap`` (then only ``cap`` were written)."""
+    lib = load()
+    pats = [_u8(p) for p in patterns]
+    m = len(pats)
+    ptrs = (ctypes.c_void_p * m)(*[p.ctypes.data for p in pats])
+    lens = (ctypes.c_uint32 * m)(*[p.size for p in pats])
+    kk = (ctypes.c_uint32 * m)(*[int(k) for k in ks])
+    if n is None:
+        n = d_text.numel()
+    found = ctypes.c_uint64(0)
+    rc = lib.oasm_scan_ends_noalloc(ptrs, lens, kk, m, _dev_ptr(d_text) if n else None, n,
+                                    _dev_ptr(d_out) if cap else None, cap, ctypes.byref(found),
+                                    stream or None)
+    if rc < 0 and rc != OASM_ETRUNC:
+        raise OasmError(rc, lib.oasm_strerror(rc).decode())
+    return found.value
 
 
 def oasm_strerror(code: int) -> str:
