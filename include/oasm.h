@@ -96,6 +96,11 @@ typedef struct {
     int32_t timing;            /* 1: time each kernel class with CUDA events */
     uint32_t flush_timeout_ms; /* bound on every host wait (default 600000) */
     void *cuda_stream;         /* cudaStream_t to run on; NULL = library-owned */
+    int32_t myers_only;        /* 1: every pattern on the Myers/Hyyro bit-vector scan;
+                                  0 (default): one-word patterns with K <= 2 use the
+                                  automaton scan where a class has >= 32 of them */
+    int32_t graphs;            /* 1: launch each step as a captured CUDA graph,
+                                  updated in place while its shape repeats */
 } oasm_config;
 
 /* One occurrence added to S (or, for the raw outputs, one hit/end). */
@@ -126,6 +131,7 @@ typedef struct {
     double copy_ms;          /* staging copies into the device text arena */
     double step_ms;          /* whole steps, first to last kernel */
     uint64_t scan_launches;  /* forward-scan kernel launches */
+    uint64_t graph_builds;   /* step graphs instantiated (cfg.graphs = 1) */
 } oasm_stats;
 
 /* Fills *cfg / *rules with the defaults described above. */
@@ -162,10 +168,28 @@ int oasm_open_stream(oasm_ctx *ctx, uint32_t *sid);
 /* Closes a stream and frees its slot; undelivered hits are dropped. */
 int oasm_close_stream(oasm_ctx *ctx, uint32_t sid);
 
+/* Batched forms for serving loops with many streams.
+ *   oasm_open_streams  opens up to n streams into sids[]; *n_opened receives
+ *                      how many (fewer than n when slots or the memory budget
+ *                      run out; that is not an error)
+ *   oasm_end_streams / oasm_close_streams  as the single-stream calls, for
+ *                      each id; stop at the first invalid id (OASM_EINVAL) */
+int oasm_open_streams(oasm_ctx *ctx, uint32_t n, uint32_t *sids, uint32_t *n_opened);
+int oasm_end_streams(oasm_ctx *ctx, uint32_t n, const uint32_t *sids);
+int oasm_close_streams(oasm_ctx *ctx, uint32_t n, const uint32_t *sids);
+
 /* Appends n bytes (host memory) to stream sid.  The bytes are copied into
  * pinned staging memory; `chunk` may be reused when the call returns.  No
  * device work is started until oasm_step / oasm_flush. */
 int oasm_feed(oasm_ctx *ctx, uint32_t sid, const uint8_t *chunk, size_t n);
+
+/* Appends many packets to many streams in one call (the ingest of a serving
+ * loop): packet j is buf[off[j] .. off[j] + len[j]) for stream sid[j], all
+ * host memory.  Packets of one stream are appended in array order.  The
+ * bytes are copied into pinned staging before the call returns.
+ * OASM_EINVAL if any sid is not open (nothing is appended then). */
+int oasm_feed_many(oasm_ctx *ctx, uint32_t n, const uint32_t *sid, const uint8_t *buf,
+                   const uint64_t *off, const uint32_t *len);
 
 /* Appends n bytes that are already in device memory.  The buffer is NOT
  * copied at this call: it must stay valid and unchanged until the next
@@ -193,9 +217,30 @@ int oasm_step(oasm_ctx *ctx);
 int oasm_flush(oasm_ctx *ctx, uint32_t sid, int end_of_stream, oasm_hit *out, size_t cap,
                size_t *n_out);
 
+/* Returns the queued hits of every stream at once: streams in id order,
+ * each stream's hits in canonical order (pattern_id, decided_at, k); no step
+ * is run.  OASM_ETRUNC when more than cap are queued (the rest stay). */
+int oasm_drain(oasm_ctx *ctx, oasm_hit *out, size_t cap, size_t *n_out);
+
 /* Number of decided hits of stream sid queued and not yet returned by
  * oasm_flush (no device work is started). */
 int oasm_ready(oasm_ctx *ctx, uint32_t sid, size_t *n);
+
+/* ---- stream checkpoint / migration -------------------------------------
+ * A stream's whole matching state is small and explicit: its position, the
+ * last T symbols it saw and, per pattern, the pending window (Algorithm 1's
+ * mem rows).  It can be saved and restored into a stream of another context
+ * built from the same patterns, thresholds and rules (checked by a
+ * fingerprint), e.g. to move a stream to another GPU or process.  Hits
+ * already decided are not part of the state: flush them first.
+ *   oasm_stream_state_size  bytes of a saved state for this context
+ *   oasm_save_stream        OASM_ESTATE if the stream has input no step has
+ *                           processed yet; OASM_ETRUNC if cap is too small
+ *   oasm_restore_stream     into an open stream with no pending input;
+ *                           OASM_EINVAL if the state does not fit the context */
+int oasm_stream_state_size(oasm_ctx *ctx, size_t *bytes);
+int oasm_save_stream(oasm_ctx *ctx, uint32_t sid, void *buf, size_t cap, size_t *n);
+int oasm_restore_stream(oasm_ctx *ctx, uint32_t sid, const void *buf, size_t n);
 
 /* Cumulative counters and (with cfg.timing = 1) per-kernel-class times. */
 int oasm_get_stats(oasm_ctx *ctx, oasm_stats *st);

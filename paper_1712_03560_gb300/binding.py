@@ -53,7 +53,8 @@ class oasm_config(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int32), ("max_streams", ctypes.c_uint32),
                 ("mem_budget", ctypes.c_uint64), ("region_bytes", ctypes.c_uint32),
                 ("tile_warps", ctypes.c_uint32), ("timing", ctypes.c_int32),
-                ("flush_timeout_ms", ctypes.c_uint32), ("cuda_stream", ctypes.c_void_p)]
+                ("flush_timeout_ms", ctypes.c_uint32), ("cuda_stream", ctypes.c_void_p),
+                ("myers_only", ctypes.c_int32), ("graphs", ctypes.c_int32)]
 
 
 class oasm_hit(ctypes.Structure):
@@ -71,14 +72,16 @@ class oasm_stats(ctypes.Structure):
                                                 "reruns")] + \
                [(n, ctypes.c_double) for n in ("scan_ms", "verify_ms", "order_ms", "filter_ms",
                                                "copy_ms", "step_ms")] + \
-               [("scan_launches", ctypes.c_uint64)]
+               [("scan_launches", ctypes.c_uint64), ("graph_builds", ctypes.c_uint64)]
 
 
 EXPORTS = ["oasm_config_default", "oasm_rules_default", "oasm_create", "oasm_destroy",
-           "oasm_open_stream", "oasm_close_stream", "oasm_feed", "oasm_feed_device",
-           "oasm_end_stream", "oasm_step", "oasm_flush", "oasm_ready", "oasm_get_stats", "oasm_reset_stats",
+           "oasm_open_stream", "oasm_close_stream", "oasm_open_streams", "oasm_end_streams",
+           "oasm_close_streams", "oasm_feed", "oasm_feed_many", "oasm_feed_device",
+           "oasm_end_stream", "oasm_step", "oasm_flush", "oasm_drain", "oasm_ready", "oasm_get_stats", "oasm_reset_stats",
            "oasm_cuda_stream", "oasm_last_error", "oasm_strerror", "oasm_autotune",
-           "oasm_measure_int_peak", "oasm_scan_ends_noalloc"]
+           "oasm_measure_int_peak", "oasm_scan_ends_noalloc", "oasm_stream_state_size",
+           "oasm_save_stream", "oasm_restore_stream"]
 
 _lib = None
 _lock = threading.Lock()
@@ -106,7 +109,12 @@ def load(path: str | None = None):
             "oasm_open_stream": ([vp, ctypes.POINTER(u32)], i32),
             "oasm_close_stream": ([vp, u32], i32),
             "oasm_feed": ([vp, u32, vp, ctypes.c_size_t], i32),
+            "oasm_open_streams": ([vp, u32, vp, ctypes.POINTER(u32)], i32),
+            "oasm_end_streams": ([vp, u32, vp], i32),
+            "oasm_close_streams": ([vp, u32, vp], i32),
             "oasm_feed_device": ([vp, u32, vp, ctypes.c_size_t], i32),
+            "oasm_feed_many": ([vp, u32, vp, vp, vp, vp], i32),
+            "oasm_drain": ([vp, vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)], i32),
             "oasm_end_stream": ([vp, u32], i32),
             "oasm_step": ([vp], i32),
             "oasm_flush": ([vp, u32, i32, vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)], i32),
@@ -119,6 +127,9 @@ def load(path: str | None = None):
             "oasm_autotune": ([vp, vp, ctypes.c_size_t, ctypes.c_char_p, ctypes.c_size_t], i32),
             "oasm_measure_int_peak": ([i32, ctypes.POINTER(ctypes.c_double),
                                        ctypes.POINTER(ctypes.c_double)], i32),
+            "oasm_stream_state_size": ([vp, ctypes.POINTER(ctypes.c_size_t)], i32),
+            "oasm_save_stream": ([vp, u32, vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)], i32),
+            "oasm_restore_stream": ([vp, u32, vp, ctypes.c_size_t], i32),
             "oasm_scan_ends_noalloc": ([u8pp, ctypes.POINTER(u32), ctypes.POINTER(u32), u32, vp,
                                         u64, vp, u64, ctypes.POINTER(u64), vp], i32),
         }
@@ -192,9 +203,40 @@ def oasm_close_stream(ctx, sid: int):
     return _check(load().oasm_close_stream(ctx, sid), ctx)
 
 
+def oasm_open_streams(ctx, n: int) -> np.ndarray:
+    """Up to n new stream ids (fewer when slots or memory run out)."""
+    sids = np.zeros(max(n, 1), dtype=np.uint32)
+    got = ctypes.c_uint32(0)
+    _check(load().oasm_open_streams(ctx, n, sids.ctypes.data, ctypes.byref(got)), ctx)
+    return sids[: got.value]
+
+
+def oasm_end_streams(ctx, sids):
+    sids = np.ascontiguousarray(sids, dtype=np.uint32)
+    return _check(load().oasm_end_streams(ctx, sids.size, sids.ctypes.data), ctx)
+
+
+def oasm_close_streams(ctx, sids):
+    sids = np.ascontiguousarray(sids, dtype=np.uint32)
+    return _check(load().oasm_close_streams(ctx, sids.size, sids.ctypes.data), ctx)
+
+
 def oasm_feed(ctx, sid: int, chunk):
     a = _u8(chunk)
     return _check(load().oasm_feed(ctx, sid, a.ctypes.data if a.size else None, a.size), ctx)
+
+
+def oasm_feed_many(ctx, sids, buf, offs, lens):
+    """Packets j = buf[offs[j] : offs[j] + lens[j]] for streams sids[j]."""
+    sids = np.ascontiguousarray(sids, dtype=np.uint32)
+    offs = np.ascontiguousarray(offs, dtype=np.uint64)
+    lens = np.ascontiguousarray(lens, dtype=np.uint32)
+    buf = _u8(buf)
+    n = sids.size
+    if n == 0:
+        return 0
+    return _check(load().oasm_feed_many(ctx, n, sids.ctypes.data, buf.ctypes.data,
+                                        offs.ctypes.data, lens.ctypes.data), ctx)
 
 
 def _dev_ptr(d):
@@ -219,6 +261,23 @@ def oasm_end_stream(ctx, sid: int):
 
 def oasm_step(ctx):
     return _check(load().oasm_step(ctx), ctx)
+
+
+def oasm_drain(ctx, cap: int = 1 << 16) -> np.ndarray:
+    """All queued hits of all streams (streams in id order, canonical order
+    within a stream)."""
+    lib = load()
+    parts = []
+    while True:
+        buf = np.zeros(cap, dtype=HIT_DTYPE)
+        n = ctypes.c_size_t(0)
+        rc = lib.oasm_drain(ctx, buf.ctypes.data, cap, ctypes.byref(n))
+        _check(rc, ctx, allow=(OASM_ETRUNC,))
+        parts.append(buf[: n.value])
+        if rc != OASM_ETRUNC:
+            break
+        cap *= 2
+    return np.concatenate(parts) if len(parts) > 1 else parts[0]
 
 
 def oasm_ready(ctx, sid: int) -> int:
@@ -297,6 +356,21 @@ def oasm_scan_ends_noalloc(patterns, ks, d_text, d_out, cap: int, n: int | None 
     if rc < 0 and rc != OASM_ETRUNC:
         raise OasmError(rc, lib.oasm_strerror(rc).decode())
     return found.value
+
+
+def oasm_save_stream(ctx, sid: int) -> bytes:
+    """The stream's matching state (position, stored tail, pending windows)."""
+    lib = load()
+    n = ctypes.c_size_t(0)
+    _check(lib.oasm_stream_state_size(ctx, ctypes.byref(n)), ctx)
+    buf = ctypes.create_string_buffer(n.value)
+    _check(lib.oasm_save_stream(ctx, sid, buf, n.value, ctypes.byref(n)), ctx)
+    return buf.raw[: n.value]
+
+
+def oasm_restore_stream(ctx, sid: int, state: bytes):
+    buf = ctypes.create_string_buffer(bytes(state), len(state))
+    return _check(load().oasm_restore_stream(ctx, sid, buf, len(state)), ctx)
 
 
 def oasm_strerror(code: int) -> str:

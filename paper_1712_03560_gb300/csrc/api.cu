@@ -16,6 +16,7 @@
 #include <chrono>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <thread>
@@ -30,7 +31,7 @@ namespace {
 constexpr size_t kFrontPad = 1024;   // arena bytes before the first work item
 constexpr size_t kEndPad = 2048;     // arena bytes after the last one
 constexpr size_t kChunk = 1 << 20;   // largest gather copy per block
-constexpr int kSortBlocks = 4 * 152;
+constexpr int kSortBlocks = 2 * 152;
 
 struct Piece {
   bool dev;
@@ -41,6 +42,7 @@ struct Piece {
 
 struct StreamRec {
   bool open = false;
+  bool clean = true;      // device windows of the slot are all empty
   int64_t pos = 0;        // symbols processed
   int32_t tail_len = 0;   // symbols of the stored tail
   bool eos_pending = false;
@@ -60,6 +62,7 @@ bool canon_less(const oasm_hit& a, const oasm_hit& b) {
 
 struct Bucket {
   int W = 0;
+  int algo = 0;           // 0: Myers/Hyyro bit-vectors; 1 + K: automaton for K <= 2
   int max_nseg = 1;
   int warps = 8;          // warps per scan block
   int chunk = 1024;       // text bytes per TMA buffer (dictionary mapping)
@@ -108,6 +111,8 @@ struct oasm_ctx {
   MemRow* d_mem = nullptr;
   size_t stream_bytes = 0;
   uint32_t n_open = 0;
+  size_t host_pending = 0;  // bytes in host staging not yet consumed by a step
+  bool debug = false;
 
   // host staging (pinned)
   uint8_t* h_stage = nullptr;
@@ -133,8 +138,11 @@ struct oasm_ctx {
   size_t h_out_cap = 0;
   cudaEvent_t ev[8] = {};
   cudaEvent_t done = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;  // the last captured step, updated in place
+  bool capturing = false;
 
   oasm_stats st{};
+  uint64_t fingerprint = 0;  // patterns, thresholds and rules (stream checkpoints)
 };
 
 namespace {
@@ -247,6 +255,7 @@ void free_ctx(oasm_ctx* c) {
   if (c->h_upload) cudaFreeHost(c->h_upload);
   if (c->h_out) cudaFreeHost(c->h_out);
   for (auto& e : c->ev) if (e) cudaEventDestroy(e);
+  if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
   if (c->done) cudaEventDestroy(c->done);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
@@ -282,16 +291,14 @@ int build_tables(oasm_ctx* ctx) {
   CK(cudaMemcpy(ctx->d_mem_off, ctx->mem_off.data(), size_t(n) * 4, cudaMemcpyHostToDevice));
 
   // forward lane groups per word-count class, patterns sorted by length so a
-  // group's lanes need similar warm-up
-  for (int W = 1; W <= kMaxW; ++W) {
-    std::vector<uint32_t> ids;
-    for (uint32_t p = 0; p < n; ++p)
-      if ((ctx->m[p] + 31) / 32 == W) ids.push_back(p);
-    if (ids.empty()) continue;
+  // group's lanes need similar warm-up.  One-word patterns with K <= 2 form
+  // automaton classes (one per K) when there are at least 32 of them.
+  auto add_bucket = [&](int W, int algo, std::vector<uint32_t> ids) -> int {
     std::stable_sort(ids.begin(), ids.end(),
-                     [&](uint32_t a, uint32_t b) { return ctx->m[a] < ctx->m[b]; });
+                     [&](uint32_t a0, uint32_t b0) { return ctx->m[a0] < ctx->m[b0]; });
     Bucket bk;
     bk.W = W;
+    bk.algo = algo;
     const size_t RW = size_t(32) * W;  // words per symbol row: [w][lane]
     std::vector<uint32_t> peq;
     for (size_t g0 = 0; g0 < ids.size(); g0 += kLaneGroup) {
@@ -340,6 +347,26 @@ int build_tables(oasm_ctx* ctx) {
     CK(cudaMalloc(&bk.d_peq, peq.size() * 4));
     CK(cudaMemcpy(bk.d_peq, peq.data(), peq.size() * 4, cudaMemcpyHostToDevice));
     ctx->buckets.push_back(bk);
+    return OASM_OK;
+  };
+  for (int W = 1; W <= kMaxW; ++W) {
+    std::vector<uint32_t> ids;
+    for (uint32_t p = 0; p < n; ++p)
+      if ((ctx->m[p] + 31) / 32 == W) ids.push_back(p);
+    if (W == 1 && !ctx->cfg.myers_only) {
+      for (int K = 0; K <= 2; ++K) {
+        std::vector<uint32_t> kid, rest;
+        for (uint32_t p : ids) (ctx->K[p] == K ? kid : rest).push_back(p);
+        if (kid.size() >= size_t(kLaneGroup)) {
+          int rc = add_bucket(1, 1 + K, kid);
+          if (rc) return rc;
+          ids.swap(rest);
+        }
+      }
+    }
+    if (ids.empty()) continue;
+    int rc = add_bucket(W, 0, ids);
+    if (rc) return rc;
   }
   return OASM_OK;
 }
@@ -486,17 +513,23 @@ int plan_step(oasm_ctx* ctx, StepPlan& pl) {
   return OASM_OK;
 }
 
-int run_step_once(oasm_ctx* ctx, StepPlan& pl, const WorkItem* d_items, const Region* d_regions,
-                  const CopyChunk* d_chunks, bool* overflow) {
+cudaError_t record_event(oasm_ctx* ctx, cudaEvent_t e, cudaStream_t s) {
+  return ctx->capturing ? cudaEventRecordWithFlags(e, s, cudaEventRecordExternal)
+                        : cudaEventRecord(e, s);
+}
+
+// Enqueues the device work of one step (directly, or into a stream capture).
+int enqueue_step(oasm_ctx* ctx, StepPlan& pl, const WorkItem* d_items, const Region* d_regions,
+                 const CopyChunk* d_chunks) {
   cudaStream_t s = ctx->stream;
   const uint32_t n_items = uint32_t(pl.items.size());
   const bool tm = ctx->cfg.timing != 0;
-  if (tm) CK(cudaEventRecord(ctx->ev[0], s));
+  if (tm) CK(record_event(ctx, ctx->ev[0], s));
   CK(cudaMemsetAsync(ctx->d_ctr, 0, sizeof(StepCounters), s));
   CK(cudaMemsetAsync(ctx->pair_pool.p, 0xff, size_t(n_items) * ctx->n_pat * sizeof(int32_t), s));
   CK(launch_gather(d_chunks, int(pl.chunks.size()), ctx->arena.p, s));
   ctx->st.launches += pl.chunks.empty() ? 0 : 1;
-  if (tm) CK(cudaEventRecord(ctx->ev[1], s));
+  if (tm) CK(record_event(ctx, ctx->ev[1], s));
   for (size_t bi = 0; bi < ctx->buckets.size(); ++bi) {
     const Bucket& b = ctx->buckets[bi];
     ScanArgs a{};
@@ -510,6 +543,7 @@ int run_step_once(oasm_ctx* ctx, StepPlan& pl, const WorkItem* d_items, const Re
     a.resv = b.max_nseg > 1 ? 256 : 32;
     a.dict = b.max_nseg == 1 ? 1 : 0;
     a.chunk = b.chunk;
+    a.algo = b.algo;
     a.items = d_items;
     a.arena = ctx->arena.p;
     a.cand = ctx->cand.p;
@@ -520,11 +554,11 @@ int run_step_once(oasm_ctx* ctx, StepPlan& pl, const WorkItem* d_items, const Re
     ctx->st.launches += 1;
     ctx->st.scan_launches += 1;
   }
-  if (tm) CK(cudaEventRecord(ctx->ev[2], s));
+  if (tm) CK(record_event(ctx, ctx->ev[2], s));
   StepParams P = make_params(ctx, d_items, n_items, pl.sb, pl.kb);
   CK(launch_verify(P, s));
   ctx->st.launches += 1;
-  if (tm) CK(cudaEventRecord(ctx->ev[3], s));
+  if (tm) CK(record_event(ctx, ctx->ev[3], s));
   unsigned long long* sorted = P.keys;
   if (ctx->rules.output == OASM_OUT_FILTERED) {
     int nl = 0;
@@ -532,12 +566,12 @@ int run_step_once(oasm_ctx* ctx, StepPlan& pl, const WorkItem* d_items, const Re
                 kKBits, pl.kb, ctx->d_hist, kSortBlocks};
     CK(launch_sort(sa, &sorted, nullptr, &nl, s));
     ctx->st.launches += uint64_t(nl);
-    if (tm) CK(cudaEventRecord(ctx->ev[4], s));
+    if (tm) CK(record_event(ctx, ctx->ev[4], s));
     CK(launch_filter(P, sorted, s));
     CK(launch_finalize(P, s));
     ctx->st.launches += 2;
   } else if (tm) {
-    CK(cudaEventRecord(ctx->ev[4], s));
+    CK(record_event(ctx, ctx->ev[4], s));
   }
   CK(launch_tails(P, s));
   ctx->st.launches += 1;
@@ -551,12 +585,65 @@ int run_step_once(oasm_ctx* ctx, StepPlan& pl, const WorkItem* d_items, const Re
     CK(launch_permute(ctx->out.p, vs, ctx->out_sorted.p, &ctx->d_ctr->n_out, P.cap_out, s));
     ctx->st.launches += uint64_t(nl) + 1;
   }
-  if (tm) CK(cudaEventRecord(ctx->ev[5], s));
+  if (tm) CK(record_event(ctx, ctx->ev[5], s));
   CK(cudaMemcpyAsync(ctx->h_ctr, ctx->d_ctr, sizeof(StepCounters), cudaMemcpyDeviceToHost, s));
+  return OASM_OK;
+}
+
+int run_step_once(oasm_ctx* ctx, StepPlan& pl, const WorkItem* d_items, const Region* d_regions,
+                  const CopyChunk* d_chunks, bool* overflow) {
+  cudaStream_t s = ctx->stream;
+  const bool tm = ctx->cfg.timing != 0;
+  int rc;
+  if (ctx->cfg.graphs) {
+    // capture the step, then update the cached executable graph in place when
+    // the step has the same shape (kernel arguments and grids may differ)
+    CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    ctx->capturing = true;
+    rc = enqueue_step(ctx, pl, d_items, d_regions, d_chunks);
+    ctx->capturing = false;
+    cudaGraph_t g = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(s, &g);
+    if (rc) {
+      if (g) cudaGraphDestroy(g);
+      return rc;
+    }
+    CK(ec);
+    bool updated = false;
+    if (ctx->graph_exec) {
+      cudaGraphExecUpdateResultInfo info;
+      updated = cudaGraphExecUpdate(ctx->graph_exec, g, &info) == cudaSuccess;
+      if (!updated) {
+        cudaGetLastError();
+        cudaGraphExecDestroy(ctx->graph_exec);
+        ctx->graph_exec = nullptr;
+      }
+    }
+    if (!updated) {
+      const cudaError_t ei = cudaGraphInstantiate(&ctx->graph_exec, g, 0);
+      if (ei != cudaSuccess) {
+        cudaGraphDestroy(g);
+        ctx->graph_exec = nullptr;
+        return fail(ctx, OASM_ECUDA, "cudaGraphInstantiate failed: %s", cudaGetErrorString(ei));
+      }
+      ctx->st.graph_builds += 1;
+    }
+    cudaGraphDestroy(g);
+    CK(cudaGraphLaunch(ctx->graph_exec, s));
+  } else {
+    if ((rc = enqueue_step(ctx, pl, d_items, d_regions, d_chunks))) return rc;
+  }
   CK(cudaEventRecord(ctx->done, s));
-  int rc = wait_event(ctx, ctx->done);
+  rc = wait_event(ctx, ctx->done);
+  const StepParams P = make_params(ctx, d_items, uint32_t(pl.items.size()), pl.sb, pl.kb);
   if (rc) return rc;
   const StepCounters c = *ctx->h_ctr;
+  if (ctx->debug)
+    fprintf(stderr,
+            "oasm step: items %zu flags 0x%x cand %llu/%zu hits %llu/%zu out %llu/%llu "
+            "windows %llu/%llu\n",
+            pl.items.size(), c.overflow, c.n_cand, ctx->cand.cap, c.n_hits,
+            (size_t)P.cap_hits, c.n_out, P.cap_out, c.n_pool, P.cap_pool);
   if (c.overflow & (1u << 16))
     return fail(ctx, OASM_ETIMEOUT, "a bounded wait for a TMA copy ran out in the scan");
   *overflow = c.overflow != 0;
@@ -664,7 +751,15 @@ int run_step(oasm_ctx* ctx) {
     const CopyChunk* d_chunks = reinterpret_cast<const CopyChunk*>(ctx->upload.p + o_c);
     bool over = true;
     for (int attempt = 0; over; ++attempt) {
-      if (attempt > 8) return fail(ctx, OASM_ENOMEM, "step buffers kept overflowing");
+      if (attempt > 16) {
+        const StepCounters c = *ctx->h_ctr;
+        return fail(ctx, OASM_ENOMEM,
+                    "step buffers kept overflowing (flags 0x%x; candidates %llu/%zu, hits "
+                    "%llu/%zu, records %llu/%zu, windows %llu/%zu)",
+                    c.overflow, c.n_cand, ctx->cand.cap, c.n_hits,
+                    std::min(ctx->keys.cap, ctx->keys_alt.cap), c.n_out, ctx->out.cap, c.n_pool,
+                    ctx->pool_hdr.cap);
+      }
       if ((rc = run_step_once(ctx, pl, d_items, d_regions, d_chunks, &over))) return rc;
     }
     // advance streams
@@ -675,20 +770,27 @@ int run_step(oasm_ctx* ctx) {
         Piece& pc = s.pieces.front();
         if (pc.n <= left) {
           left -= pc.n;
+          if (!pc.dev) ctx->host_pending -= pc.n;
           s.pieces.erase(s.pieces.begin());
         } else {
           pc.n -= left;
-          if (pc.dev) pc.dptr += left; else pc.host_off += left;
+          if (pc.dev) {
+            pc.dptr += left;
+          } else {
+            pc.host_off += left;
+            ctx->host_pending -= left;
+          }
           left = 0;
         }
       }
       s.pending -= pl.take[i];
       s.pos = pl.items[i].e_new;
       s.tail_len = int32_t(std::min<int64_t>(s.pos, ctx->T));
-      if (pl.items[i].eos) {
+      if (pl.items[i].eos) {  // every window of the stream was decided: slot is clean
         s.pos = 0;
         s.tail_len = 0;
         s.eos_pending = false;
+        s.clean = true;
       }
     }
     ctx->st.steps += 1;
@@ -703,14 +805,31 @@ int run_step(oasm_ctx* ctx) {
       ctx->st.word_steps += lanes * uint64_t(b.W) * pl.new_bytes;
     }
     // host staging is free again once no stream references it
-    bool any_host = false;
-    for (auto& s : ctx->streams)
-      for (auto& pc : s.pieces) any_host |= !pc.dev;
-    if (!any_host) ctx->h_stage_used = 0;
+    if (ctx->host_pending == 0) ctx->h_stage_used = 0;
     bool more = false;
     for (auto& s : ctx->streams) more |= s.open && (s.pending > 0 || s.eos_pending);
     if (!more) return OASM_OK;
   }
+}
+
+struct SavedHeader {
+  uint64_t magic;
+  uint64_t fingerprint;
+  int64_t pos;
+  uint32_t n_pat, mem_stride;
+  int32_t T, tail_len;
+};
+constexpr uint64_t kStateMagic = 0x4f41534d53543031ull;  // "OASMST01"
+
+uint64_t fnv1a(uint64_t h, const void* p, size_t n) {
+  const uint8_t* b = static_cast<const uint8_t*>(p);
+  for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * 1099511628211ull;
+  return h;
+}
+
+size_t state_bytes(const oasm_ctx* ctx) {
+  return sizeof(SavedHeader) + size_t(ctx->T) + size_t(ctx->n_pat) * sizeof(WinHdr) +
+         size_t(ctx->mem_stride) * sizeof(MemRow);
 }
 
 int check_sid(oasm_ctx* ctx, uint32_t sid) {
@@ -791,6 +910,7 @@ int oasm_create(const uint8_t* const* pat, const uint32_t* len, const uint32_t* 
   if (cfg) ctx->cfg = *cfg;
   if (ctx->cfg.max_streams == 0) ctx->cfg.max_streams = 64;
   ctx->rules = Rules{ru.replace, ru.order, ru.acc, ru.cmp, ru.output};
+  ctx->debug = getenv("OASM_DEBUG") != nullptr;
   ctx->device = ctx->cfg.device;
   auto bail = [&](int rc) {
     g_create_err = ctx->err.empty() ? oasm_strerror(rc) : ctx->err;
@@ -803,6 +923,15 @@ int oasm_create(const uint8_t* const* pat, const uint32_t* len, const uint32_t* 
     return bail(OASM_ECUDA);
   }
   cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device);
+  {
+    int max_smem = 0;
+    cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
+    if (prepare_scan_kernels(max_smem) != cudaSuccess) {
+      cudaGetLastError();
+      fail(ctx, OASM_ECUDA, "setting the scan kernels' shared-memory limit failed");
+      return bail(OASM_ECUDA);
+    }
+  }
   if (ctx->cfg.cuda_stream) {
     ctx->stream = static_cast<cudaStream_t>(ctx->cfg.cuda_stream);
   } else {
@@ -825,6 +954,17 @@ int oasm_create(const uint8_t* const* pat, const uint32_t* len, const uint32_t* 
   }
   int rc = build_tables(ctx);
   if (rc) return bail(rc);
+  {
+    uint64_t h = 1469598103934665603ull;
+    h = fnv1a(h, &n_pat, sizeof n_pat);
+    for (uint32_t p = 0; p < n_pat; ++p) {
+      h = fnv1a(h, &len[p], sizeof len[p]);
+      h = fnv1a(h, &k[p], sizeof k[p]);
+      h = fnv1a(h, pat[p], len[p]);
+    }
+    h = fnv1a(h, &ctx->rules, sizeof ctx->rules);
+    ctx->fingerprint = h;
+  }
   // stream slots: tail, window headers and level rows for every pattern
   const uint32_t S = ctx->cfg.max_streams;
   ctx->stream_bytes = size_t(ctx->T) + size_t(n_pat) * sizeof(WinHdr) +
@@ -840,6 +980,12 @@ int oasm_create(const uint8_t* const* pat, const uint32_t* len, const uint32_t* 
     cudaGetLastError();
     fail(ctx, OASM_ENOMEM, "stream state for %u streams does not fit", S);
     return bail(OASM_ENOMEM);
+  }
+  if (cudaMemset(ctx->d_hdr, 0, size_t(S) * n_pat * sizeof(WinHdr)) != cudaSuccess ||
+      cudaMemset(ctx->d_mem, 0, size_t(S) * ctx->mem_stride * sizeof(MemRow)) != cudaSuccess) {
+    cudaGetLastError();
+    fail(ctx, OASM_ECUDA, "clearing stream state failed");
+    return bail(OASM_ECUDA);
   }
   ctx->streams.resize(S);
   if (cudaMalloc(&ctx->d_ctr, sizeof(StepCounters)) != cudaSuccess ||
@@ -870,11 +1016,13 @@ int oasm_open_stream(oasm_ctx* ctx, uint32_t* sid) {
   for (uint32_t i = 0; i < ctx->streams.size(); ++i) {
     StreamRec& s = ctx->streams[i];
     if (s.open) continue;
-    CK(cudaSetDevice(ctx->device));
-    CK(cudaMemsetAsync(ctx->d_hdr + size_t(i) * ctx->n_pat, 0, size_t(ctx->n_pat) * sizeof(WinHdr),
-                       ctx->stream));
-    CK(cudaMemsetAsync(ctx->d_mem + size_t(i) * ctx->mem_stride, 0,
-                       size_t(ctx->mem_stride) * sizeof(MemRow), ctx->stream));
+    if (!s.clean) {  // closed before its end was processed: clear its windows
+      CK(cudaSetDevice(ctx->device));
+      CK(cudaMemsetAsync(ctx->d_hdr + size_t(i) * ctx->n_pat, 0,
+                         size_t(ctx->n_pat) * sizeof(WinHdr), ctx->stream));
+      CK(cudaMemsetAsync(ctx->d_mem + size_t(i) * ctx->mem_stride, 0,
+                         size_t(ctx->mem_stride) * sizeof(MemRow), ctx->stream));
+    }
     s = StreamRec();
     s.open = true;
     ++ctx->n_open;
@@ -887,12 +1035,45 @@ int oasm_open_stream(oasm_ctx* ctx, uint32_t* sid) {
 int oasm_close_stream(oasm_ctx* ctx, uint32_t sid) {
   int rc = check_sid(ctx, sid);
   if (rc) return rc;
-  ctx->streams[sid] = StreamRec();
+  StreamRec& s = ctx->streams[sid];
+  for (const Piece& pc : s.pieces)
+    if (!pc.dev) ctx->host_pending -= pc.n;
+  // a stream that never fed anything since its last end has empty windows
+  const bool clean = s.clean && s.pos == 0;
+  s = StreamRec();
+  s.clean = clean;
   --ctx->n_open;
-  bool any_host = false;
-  for (auto& s : ctx->streams)
-    for (auto& pc : s.pieces) any_host |= !pc.dev;
-  if (!any_host) ctx->h_stage_used = 0;
+  if (ctx->host_pending == 0) ctx->h_stage_used = 0;
+  return OASM_OK;
+}
+
+int oasm_open_streams(oasm_ctx* ctx, uint32_t n, uint32_t* sids, uint32_t* n_opened) {
+  if (!ctx || (n && !sids) || !n_opened) return OASM_EINVAL;
+  *n_opened = 0;
+  for (uint32_t j = 0; j < n; ++j) {
+    const int rc = oasm_open_stream(ctx, &sids[j]);
+    if (rc == OASM_EBUSY || rc == OASM_ENOMEM) break;
+    if (rc) return rc;
+    *n_opened = j + 1;
+  }
+  return OASM_OK;
+}
+
+int oasm_end_streams(oasm_ctx* ctx, uint32_t n, const uint32_t* sids) {
+  if (!ctx || (n && !sids)) return OASM_EINVAL;
+  for (uint32_t j = 0; j < n; ++j) {
+    const int rc = oasm_end_stream(ctx, sids[j]);
+    if (rc) return rc;
+  }
+  return OASM_OK;
+}
+
+int oasm_close_streams(oasm_ctx* ctx, uint32_t n, const uint32_t* sids) {
+  if (!ctx || (n && !sids)) return OASM_EINVAL;
+  for (uint32_t j = 0; j < n; ++j) {
+    const int rc = oasm_close_stream(ctx, sids[j]);
+    if (rc) return rc;
+  }
   return OASM_OK;
 }
 
@@ -912,7 +1093,47 @@ int oasm_feed(oasm_ctx* ctx, uint32_t sid, const uint8_t* chunk, size_t n) {
   memcpy(ctx->h_stage + ctx->h_stage_used, chunk, n);
   s.pieces.push_back(Piece{false, nullptr, ctx->h_stage_used, n});
   ctx->h_stage_used += n;
+  ctx->host_pending += n;
   s.pending += n;
+  s.clean = false;
+  return OASM_OK;
+}
+
+int oasm_feed_many(oasm_ctx* ctx, uint32_t n, const uint32_t* sid, const uint8_t* buf,
+                   const uint64_t* off, const uint32_t* len) {
+  if (!ctx) return OASM_EINVAL;
+  if (n == 0) return OASM_OK;
+  if (!sid || !buf || !off || !len) return fail(ctx, OASM_EINVAL, "null argument");
+  size_t total = 0;
+  for (uint32_t j = 0; j < n; ++j) {
+    if (sid[j] >= ctx->streams.size() || !ctx->streams[sid[j]].open)
+      return fail(ctx, OASM_EINVAL, "packet %u: stream %u is not open", j, sid[j]);
+    if (ctx->streams[sid[j]].eos_pending)
+      return fail(ctx, OASM_ESTATE, "packet %u: stream %u has a pending end", j, sid[j]);
+    total += len[j];
+  }
+  int rc;
+  if (ctx->h_stage_used + total > ctx->stage_limit && ctx->h_stage_used > 0) {
+    if ((rc = run_step(ctx))) return rc;
+  }
+  if ((rc = ensure_host(ctx, &ctx->h_stage, &ctx->h_stage_cap, ctx->h_stage_used + total,
+                        ctx->h_stage_used)))
+    return rc;
+  for (uint32_t j = 0; j < n; ++j) {
+    if (!len[j]) continue;
+    memcpy(ctx->h_stage + ctx->h_stage_used, buf + off[j], len[j]);
+    StreamRec& s = ctx->streams[sid[j]];
+    // consecutive packets of a stream are contiguous in staging: one piece
+    if (!s.pieces.empty() && !s.pieces.back().dev &&
+        s.pieces.back().host_off + s.pieces.back().n == ctx->h_stage_used)
+      s.pieces.back().n += len[j];
+    else
+      s.pieces.push_back(Piece{false, nullptr, ctx->h_stage_used, len[j]});
+    s.pending += len[j];
+    s.clean = false;
+    ctx->h_stage_used += len[j];
+    ctx->host_pending += len[j];
+  }
   return OASM_OK;
 }
 
@@ -925,6 +1146,7 @@ int oasm_feed_device(oasm_ctx* ctx, uint32_t sid, const uint8_t* dchunk, size_t 
   if (s.eos_pending) return fail(ctx, OASM_ESTATE, "stream %u has a pending end", sid);
   s.pieces.push_back(Piece{true, dchunk, 0, n});
   s.pending += n;
+  s.clean = false;
   return OASM_OK;
 }
 
@@ -976,11 +1198,95 @@ int oasm_flush(oasm_ctx* ctx, uint32_t sid, int end_of_stream, oasm_hit* out, si
   return OASM_ETRUNC;
 }
 
+int oasm_drain(oasm_ctx* ctx, oasm_hit* out, size_t cap, size_t* n_out) {
+  if (!ctx) return OASM_EINVAL;
+  if (n_out) *n_out = 0;
+  size_t got = 0;
+  for (uint32_t sid = 0; sid < ctx->streams.size(); ++sid) {
+    StreamRec& s = ctx->streams[sid];
+    if (!s.open || s.head == s.ready.size()) continue;
+    if (got == cap) {
+      if (n_out) *n_out = got;
+      return OASM_ETRUNC;
+    }
+    size_t n = 0;
+    const int rc = oasm_flush(ctx, sid, 0, out ? out + got : nullptr, cap - got, &n);
+    got += n;
+    if (rc == OASM_ETRUNC) {
+      if (n_out) *n_out = got;
+      return OASM_ETRUNC;
+    }
+    if (rc) return rc;
+  }
+  if (n_out) *n_out = got;
+  return OASM_OK;
+}
+
 int oasm_ready(oasm_ctx* ctx, uint32_t sid, size_t* n) {
   int rc = check_sid(ctx, sid);
   if (rc) return rc;
   if (!n) return OASM_EINVAL;
   *n = ctx->streams[sid].ready.size() - ctx->streams[sid].head;
+  return OASM_OK;
+}
+
+int oasm_stream_state_size(oasm_ctx* ctx, size_t* bytes) {
+  if (!ctx || !bytes) return OASM_EINVAL;
+  *bytes = state_bytes(ctx);
+  return OASM_OK;
+}
+
+int oasm_save_stream(oasm_ctx* ctx, uint32_t sid, void* buf, size_t cap, size_t* n) {
+  int rc = check_sid(ctx, sid);
+  if (rc) return rc;
+  const size_t need = state_bytes(ctx);
+  if (n) *n = need;
+  const StreamRec& s = ctx->streams[sid];
+  if (s.pending || s.eos_pending)
+    return fail(ctx, OASM_ESTATE, "stream %u has input no step has processed", sid);
+  if (!buf || cap < need) return OASM_ETRUNC;
+  CK(cudaSetDevice(ctx->device));
+  CK(cudaStreamSynchronize(ctx->stream));
+  SavedHeader hd{kStateMagic, ctx->fingerprint, s.pos, ctx->n_pat, ctx->mem_stride, ctx->T,
+                 s.tail_len};
+  uint8_t* o = static_cast<uint8_t*>(buf);
+  memcpy(o, &hd, sizeof hd);
+  o += sizeof hd;
+  CK(cudaMemcpy(o, ctx->d_tails + size_t(sid) * ctx->T, size_t(ctx->T), cudaMemcpyDeviceToHost));
+  o += ctx->T;
+  CK(cudaMemcpy(o, ctx->d_hdr + size_t(sid) * ctx->n_pat, size_t(ctx->n_pat) * sizeof(WinHdr),
+                cudaMemcpyDeviceToHost));
+  o += size_t(ctx->n_pat) * sizeof(WinHdr);
+  CK(cudaMemcpy(o, ctx->d_mem + size_t(sid) * ctx->mem_stride,
+                size_t(ctx->mem_stride) * sizeof(MemRow), cudaMemcpyDeviceToHost));
+  return OASM_OK;
+}
+
+int oasm_restore_stream(oasm_ctx* ctx, uint32_t sid, const void* buf, size_t n) {
+  int rc = check_sid(ctx, sid);
+  if (rc) return rc;
+  if (!buf || n != state_bytes(ctx)) return fail(ctx, OASM_EINVAL, "state size does not match");
+  SavedHeader hd;
+  memcpy(&hd, buf, sizeof hd);
+  if (hd.magic != kStateMagic || hd.fingerprint != ctx->fingerprint || hd.n_pat != ctx->n_pat ||
+      hd.mem_stride != ctx->mem_stride || hd.T != ctx->T || hd.tail_len < 0 ||
+      hd.tail_len > ctx->T || hd.pos < 0)
+    return fail(ctx, OASM_EINVAL, "state was saved by a context with other patterns or rules");
+  StreamRec& s = ctx->streams[sid];
+  if (s.pending || s.eos_pending)
+    return fail(ctx, OASM_ESTATE, "stream %u has pending input", sid);
+  CK(cudaSetDevice(ctx->device));
+  const uint8_t* p = static_cast<const uint8_t*>(buf) + sizeof hd;
+  CK(cudaMemcpy(ctx->d_tails + size_t(sid) * ctx->T, p, size_t(ctx->T), cudaMemcpyHostToDevice));
+  p += ctx->T;
+  CK(cudaMemcpy(ctx->d_hdr + size_t(sid) * ctx->n_pat, p, size_t(ctx->n_pat) * sizeof(WinHdr),
+                cudaMemcpyHostToDevice));
+  p += size_t(ctx->n_pat) * sizeof(WinHdr);
+  CK(cudaMemcpy(ctx->d_mem + size_t(sid) * ctx->mem_stride, p,
+                size_t(ctx->mem_stride) * sizeof(MemRow), cudaMemcpyHostToDevice));
+  s.pos = hd.pos;
+  s.tail_len = hd.tail_len;
+  s.clean = false;
   return OASM_OK;
 }
 
@@ -1054,6 +1360,7 @@ int oasm_autotune(oasm_ctx* ctx, const uint8_t* dsample, size_t n, char* report,
       a.resv = dict ? 32 : 256;
       a.dict = dict ? 1 : 0;
       a.chunk = co;
+      a.algo = b.algo;
       a.items = reinterpret_cast<const WorkItem*>(ctx->upload.p);
       a.arena = ctx->arena.p;
       a.cand = ctx->cand.p;
@@ -1101,9 +1408,10 @@ int oasm_autotune(oasm_ctx* ctx, const uint8_t* dsample, size_t n, char* report,
     b.region_scale = bs;
     char buf[256];
     snprintf(buf, sizeof buf,
-             "%s{\"W\":%d,\"groups\":%zu,\"dict\":%d,\"warps\":%d,\"chunk\":%d,"
-             "\"region_scale\":%.2f,\"ms\":%.4f,\"trials\":[",
-             bi ? "," : "", b.W, b.groups.size(), dict ? 1 : 0, bw, bc, bs, double(best));
+             "%s{\"W\":%d,\"algo\":%d,\"groups\":%zu,\"dict\":%d,\"warps\":%d,"
+             "\"chunk\":%d,\"region_scale\":%.2f,\"ms\":%.4f,\"trials\":[",
+             bi ? "," : "", b.W, b.algo, b.groups.size(), dict ? 1 : 0, bw, bc, bs,
+             double(best));
     js += buf;
     js += trials;
     js += "]}";

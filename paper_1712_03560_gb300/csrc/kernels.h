@@ -18,7 +18,7 @@ struct ScanArgs {
   int32_t resv;              // candidate slots a warp reserves at a time
   int32_t dict;              // 1: dictionary mapping (one pattern per lane, nseg = 1)
   int32_t chunk;             // text bytes per TMA buffer (dictionary mapping)
-  int32_t pad;
+  int32_t algo;              // 0: Myers/Hyyro bit-vectors; 1 + K: automaton for K <= 2 (W = 1)
   const WorkItem* items;
   const uint8_t* arena;
   Candidate* cand;
@@ -33,6 +33,9 @@ inline size_t scan_smem_bytes(int W, int warps, int chunk) {
 }
 
 cudaError_t launch_scan(const ScanArgs& a, cudaStream_t s);
+// Raises the dynamic shared-memory limit of every scan kernel (once per
+// context, outside any stream capture).
+cudaError_t prepare_scan_kernels(int max_smem_bytes);
 
 // Copies of stream bytes into the step's text arena.
 struct CopyChunk {

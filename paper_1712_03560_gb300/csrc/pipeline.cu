@@ -123,7 +123,9 @@ __device__ __forceinline__ void put_record(const StepParams& P, unsigned long lo
 
 __global__ void __launch_bounds__(256) verify_kernel(const StepParams P) {
   const unsigned long long n = min(P.ctr->n_cand, P.cap_cand);
-  if (P.ctr->overflow) return;
+  // stop only on an upstream overflow: the hit count must stay exact when this
+  // kernel's own output overflows, so the re-run can size the buffer at once
+  if (P.ctr->overflow & 1u) return;
   const unsigned lane = threadIdx.x & 31;
   const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
   for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x; base < n;
@@ -257,35 +259,15 @@ __global__ void __launch_bounds__(kSortThreads)
   for (unsigned long long i = b0 + threadIdx.x; i < b1; i += blockDim.x)
     atomicAdd(&h[(keys[i] >> shift) & 255u], 1u);
   __syncthreads();
-  hist[threadIdx.x * gridDim.x + blockIdx.x] = h[threadIdx.x];
+  hist[blockIdx.x * 256 + threadIdx.x] = h[threadIdx.x];  // block-major
 }
 
-// exclusive scan of hist[256 * nb] (digit-major) in one block of 1024 threads
-__global__ void __launch_bounds__(1024) rs_prefix(unsigned int* hist, int total) {
-  __shared__ unsigned int part[1024];
-  const int per = (total + 1023) / 1024;
-  const int b0 = threadIdx.x * per, b1 = min(total, b0 + per);
-  unsigned int s = 0;
-  for (int i = b0; i < b1; ++i) s += hist[i];
-  part[threadIdx.x] = s;
-  __syncthreads();
-  for (int d = 1; d < 1024; d <<= 1) {
-    const unsigned int t = threadIdx.x >= unsigned(d) ? part[threadIdx.x - d] : 0u;
-    __syncthreads();
-    part[threadIdx.x] += t;
-    __syncthreads();
-  }
-  unsigned int run = part[threadIdx.x] - s;
-  for (int i = b0; i < b1; ++i) {
-    const unsigned int v = hist[i];
-    hist[i] = run;
-    run += v;
-  }
-}
-
-// Stable scatter: a block walks its contiguous chunk in tiles of 256 keys;
-// inside a tile, ranks come from warp matching (lane order) and per-warp
-// digit counts (warp order); across tiles a running base per digit.
+// Stable scatter.  Each block first finds where its keys of each digit go:
+// all keys of smaller digits, plus the keys of its digit in earlier blocks
+// (thread d walks column d of the block-major histogram, coalesced across
+// threads).  It then walks its contiguous chunk in tiles of 256 keys; inside
+// a tile, ranks come from warp matching (lane order) and per-warp digit
+// counts (warp order); across tiles a running base per digit.
 __global__ void __launch_bounds__(kSortThreads)
     rs_scatter(const unsigned long long* __restrict__ in, unsigned long long* __restrict__ out,
                const uint32_t* __restrict__ vin, uint32_t* __restrict__ vout,
@@ -294,11 +276,33 @@ __global__ void __launch_bounds__(kSortThreads)
   __shared__ unsigned int wcnt[kSortWarps][256];
   __shared__ unsigned int woff[kSortWarps][256];
   __shared__ unsigned int base[256];
+  __shared__ unsigned int wsum[kSortWarps];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  base[threadIdx.x] = hist[threadIdx.x * gridDim.x + blockIdx.x];
+  const unsigned long long n = min(*count, cap);
+  if (n == 0) return;
+  {
+    const int d = threadIdx.x;
+    unsigned int tot = 0, pre = 0;
+    for (int b = 0; b < int(gridDim.x); ++b) {
+      const unsigned int v = hist[b * 256 + d];
+      tot += v;
+      if (b < int(blockIdx.x)) pre += v;
+    }
+    // exclusive scan of the digit totals across the block
+    unsigned int incl = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned int t = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += t;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    unsigned int wpre = 0;
+    for (int w = 0; w < warp; ++w) wpre += wsum[w];
+    base[d] = wpre + incl - tot + pre;
+  }
   for (int w = 0; w < kSortWarps; ++w) wcnt[w][threadIdx.x] = 0;
   __syncthreads();
-  const unsigned long long n = min(*count, cap);
   const unsigned long long chunk = (n + gridDim.x - 1) / gridDim.x;
   const unsigned long long b0 = chunk * blockIdx.x, b1 = min(n, b0 + chunk);
   const unsigned lt = (1u << lane) - 1u;
@@ -442,7 +446,7 @@ __device__ __forceinline__ uint32_t pair_of(uint64_t key, int sb) {
 
 __global__ void __launch_bounds__(128)
     filter_kernel(const StepParams P, const unsigned long long* __restrict__ S) {
-  if (P.ctr->overflow) return;
+  if (P.ctr->overflow & 3u) return;  // candidates or hits incomplete; keep counting records
   const unsigned long long n = min(P.ctr->n_hits, P.cap_hits);
   const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
   for (unsigned long long h = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; h < n;
@@ -615,9 +619,8 @@ cudaError_t launch_sort(const SortArgs& a, unsigned long long** keys_out, uint32
   int nl = 0;
   for (int shift = a.lo_bit; shift < a.hi_bit; shift += 8) {
     rs_hist<<<a.nblocks, kSortThreads, 0, s>>>(ka, a.count, a.cap, shift, a.hist);
-    rs_prefix<<<1, 1024, 0, s>>>(a.hist, 256 * a.nblocks);
     rs_scatter<<<a.nblocks, kSortThreads, 0, s>>>(ka, kb, va, vb, a.count, a.cap, shift, a.hist);
-    nl += 3;
+    nl += 2;
     std::swap(ka, kb);
     std::swap(va, vb);
   }

@@ -34,7 +34,9 @@
 //     double buffer by TMA bulk copies (cp.async.bulk + mbarrier); every lane
 //     reads the same symbol (one broadcast LDS.U8 per step).  Candidates are
 //     counted per 16-symbol block; a block with any is replayed from its
-//     saved state to find the exact end positions.
+//     saved state to find the exact end positions.  A warp that replays more
+//     than 3 of 64 blocks switches to recording every step (a funnel shift
+//     of the score sign into a mask) for the next 64 blocks.
 //   segment mapping: each lane reads its own sub-segment as 16-byte vectors
 //     from global memory, one vector ahead, and records candidates in a
 //     per-lane mask every step (candidates are frequent with one pattern).
@@ -315,6 +317,8 @@ __device__ void scan_dict(const ScanArgs& A, const char* peq, uint8_t* tbuf, uin
   int s = L.m - L.K - 1;
   Emitter em;
   int dead_at = -1;
+  bool record = false;  // warp-uniform: record every step instead of count + replay
+  int blocks = 0, replays = 0;
   for (int c = 0; c < nchunks; ++c) {
     const int buf = c & 1;
     const bool ok = mbar_wait(bar0 + 8 * buf, uint32_t((c >> 1) & 1));
@@ -327,6 +331,20 @@ __device__ void scan_dict(const ScanArgs& A, const char* peq, uint8_t* tbuf, uin
     for (int vv = 0; vv < nv; ++vv) {
       const int v = c * (CH >> 4) + vv;
       const uint8_t* tv = t + vv * 16;
+      if (record) {
+        uint32_t cm = 0;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const uint32_t sym = tv[j];
+          uint32_t eq[W];
+          load_eq<W>(peq, mad_lo(sym, 128u * W, lane_off), eq);
+          search_step<W>(Pv, Mv, s, eq);
+          cm = __funnelshift_l(uint32_t(s), cm, 1);
+        }
+        const uint32_t c16 = cm & block_mask(L.t_lo, L.t_hi, v);
+        if (__any_sync(kFull, c16 != 0)) em.put(A, lane, c16, L.spos + 16 * v, R.wi, L.pid, wi.base_pos);
+        continue;
+      }
       uint32_t Pv0[W], Mv0[W];
 #pragma unroll
       for (int w = 0; w < W; ++w) {
@@ -362,6 +380,12 @@ __device__ void scan_dict(const ScanArgs& A, const char* peq, uint8_t* tbuf, uin
           cm = __funnelshift_l(uint32_t(s), cm, 1);
         }
         em.put(A, lane, cm & vm, L.spos + 16 * v, R.wi, L.pid, wi.base_pos);
+        ++replays;
+      }
+      // candidates dense enough that replays cost more than recording: switch
+      if (++blocks == 64) {
+        record = replays > 3;
+        blocks = replays = 0;
       }
     }
     __syncwarp();
@@ -376,6 +400,133 @@ __device__ void scan_dict(const ScanArgs& A, const char* peq, uint8_t* tbuf, uin
     if (lane == 0) {
       atomicOr(&A.ctr->overflow, 1u << kTimeoutBit);
       // copies still in flight into this warp's buffers: bounded wait, then leave
+      for (int c = dead_at; c < dead_at + 2 && c < nchunks; ++c)
+        mbar_wait(bar0 + 8 * (c & 1), uint32_t((c >> 1) & 1));
+    }
+    __syncwarp();
+    return;
+  }
+  em.finish(A, lane);
+}
+
+// ---------------------------------- dictionary mapping, NFA for K <= 2
+// Bit-parallel simulation of the approximate-matching automaton (Wu and
+// Manber's row-wise formulation) for one-word patterns with K = KL errors at
+// most.  R_j, j = 0..KL, holds one bit per pattern prefix: bit (32 - m + i)
+// of R_j is set when p[0..i] matches a suffix of the text read so far with
+// at most j edits (top-aligned, so the full pattern is bit 31).  For symbol c
+// with match mask B:
+//   R'_0 = ((R_0 << 1) | E) & B
+//   R'_j = (((R_j << 1) | E) & B) | R_j-1 | (((R_j-1 | R'_j-1) << 1) | E)
+// (match, insertion, substitution, deletion; E marks the first pattern
+// position, reached from the always-active empty prefix).  Bit 31 of R'_K is
+// set exactly when D[e] <= K, the candidate test of the Myers scan, at
+// 1 + 3K logic operations per step instead of the recurrence's seven.
+template <int KL>
+__device__ __forceinline__ void nfa_step(uint32_t (&R)[KL + 1], uint32_t B, uint32_t E) {
+  uint32_t prev_old = R[0];
+  R[0] = ((R[0] << 1) | E) & B;
+#pragma unroll
+  for (int j = 1; j <= KL; ++j) {
+    const uint32_t old = R[j];
+    R[j] = (((old << 1) | E) & B) | prev_old | ((prev_old | R[j - 1]) << 1) | E;
+    prev_old = old;
+  }
+}
+
+template <int KL>
+__device__ void scan_dict_nfa(const ScanArgs& A, const char* peq, uint8_t* tbuf, uint32_t bar0,
+                              const LaneGroup& G, const Region& R, const WorkItem& wi, int lane) {
+  const LaneSetup L = lane_setup(A, G, R, wi, lane);
+  const int CH = A.chunk;
+  const int nbytes = L.nvec * 16;
+  const int nchunks = (nbytes + CH - 1) / CH;
+  const uint8_t* src = A.arena + L.ad_al;
+  const uint32_t tb = smem_u32(tbuf);
+  const uint32_t lane_off = uint32_t(lane) * 4u;
+  if (lane == 0) {
+    for (int c = 0; c < 2 && c < nchunks; ++c) {
+      const uint32_t n = uint32_t(min(CH, nbytes - c * CH));
+      mbar_expect_tx(bar0 + 8 * c, n);
+      tma_load_1d(tb + c * CH, src + size_t(c) * CH, n, bar0 + 8 * c);
+    }
+  }
+  const uint32_t E = (L.pid < 0) ? 0u : (1u << (32 - L.m));
+  uint32_t Rs[KL + 1];
+#pragma unroll
+  for (int j = 0; j <= KL; ++j) Rs[j] = (E == 0u) ? 0u : (((1u << j) - 1u) << (32 - L.m));
+  Emitter em;
+  int dead_at = -1;
+  bool record = false;
+  int blocks = 0, replays = 0;
+  for (int c = 0; c < nchunks; ++c) {
+    const int buf = c & 1;
+    const bool ok = mbar_wait(bar0 + 8 * buf, uint32_t((c >> 1) & 1));
+    if (__any_sync(kFull, !ok)) {
+      dead_at = c;
+      break;
+    }
+    const uint8_t* t = tbuf + buf * CH;
+    const int nv = min(CH, nbytes - c * CH) >> 4;
+    for (int vv = 0; vv < nv; ++vv) {
+      const int v = c * (CH >> 4) + vv;
+      const uint8_t* tv = t + vv * 16;
+      if (record) {
+        uint32_t cm = 0;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const uint32_t sym = tv[j];
+          const uint32_t B = *reinterpret_cast<const uint32_t*>(peq + mad_lo(sym, 128u, lane_off));
+          nfa_step<KL>(Rs, B, E);
+          cm = (cm << 1) | (Rs[KL] >> 31);
+        }
+        const uint32_t c16 = cm & block_mask(L.t_lo, L.t_hi, v);
+        if (__any_sync(kFull, c16 != 0)) em.put(A, lane, c16, L.spos + 16 * v, R.wi, L.pid, wi.base_pos);
+        continue;
+      }
+      uint32_t R0[KL + 1];
+#pragma unroll
+      for (int j = 0; j <= KL; ++j) R0[j] = Rs[j];
+      int cnt = 0;
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const uint32_t sym = tv[j];
+        const uint32_t B = *reinterpret_cast<const uint32_t*>(peq + mad_lo(sym, 128u, lane_off));
+        nfa_step<KL>(Rs, B, E);
+        cnt = add_top(cnt, Rs[KL]);  // counts steps with the full pattern reached
+      }
+      const uint32_t vm = block_mask(L.t_lo, L.t_hi, v);
+      if (__any_sync(kFull, cnt != 0 && vm != 0)) {
+        // rare: replay the block from its saved state, recording each step
+#pragma unroll
+        for (int j = 0; j <= KL; ++j) Rs[j] = R0[j];
+        uint32_t cm = 0;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const uint32_t sym = tv[j];
+          const uint32_t B = *reinterpret_cast<const uint32_t*>(peq + mad_lo(sym, 128u, lane_off));
+          nfa_step<KL>(Rs, B, E);
+          cm = (cm << 1) | (Rs[KL] >> 31);
+        }
+        em.put(A, lane, cm & vm, L.spos + 16 * v, R.wi, L.pid, wi.base_pos);
+        ++replays;
+      }
+      if (++blocks == 64) {
+        record = replays > 3;
+        blocks = replays = 0;
+      }
+    }
+    __syncwarp();
+    if (lane == 0 && c + 2 < nchunks) {
+      fence_proxy_async();
+      const uint32_t n = uint32_t(min(CH, nbytes - (c + 2) * CH));
+      mbar_expect_tx(bar0 + 8 * buf, n);
+      tma_load_1d(tb + buf * CH, src + size_t(c + 2) * CH, n, bar0 + 8 * buf);
+    }
+  }
+  if (dead_at >= 0) {
+    if (lane == 0) {
+      atomicOr(&A.ctr->overflow, 1u << kTimeoutBit);
       for (int c = dead_at; c < dead_at + 2 && c < nchunks; ++c)
         mbar_wait(bar0 + 8 * (c & 1), uint32_t((c >> 1) & 1));
     }
@@ -420,7 +571,7 @@ __device__ void scan_segments(const ScanArgs& A, const char* peq, const LaneGrou
   em.finish(A, lane);
 }
 
-template <int W, bool kDict>
+template <int W, bool kDict, int ALG>
 __global__ void __launch_bounds__(512) scan_kernel(const ScanArgs A) {
   extern __shared__ __align__(128) uint8_t smem[];
   constexpr uint32_t kPeqBytes = 256u * 128u * W;
@@ -455,30 +606,64 @@ __global__ void __launch_bounds__(512) scan_kernel(const ScanArgs A) {
   const Region R = A.regions[r];
   const WorkItem wi = A.items[R.wi];
   const char* peq = reinterpret_cast<const char*>(smem);
-  if (kDict)
+  if (kDict && ALG > 0)
+    scan_dict_nfa<(ALG > 0 ? ALG - 1 : 0)>(A, peq, tbase + size_t(warp) * 2 * A.chunk,
+                                           smem_u32(bars + 1 + 2 * warp), G, R, wi, lane);
+  else if (kDict)
     scan_dict<W>(A, peq, tbase + size_t(warp) * 2 * A.chunk, smem_u32(bars + 1 + 2 * warp), G, R,
                  wi, lane);
   else
     scan_segments<W>(A, peq, G, R, wi, lane);
 }
 
-template <int W, bool kDict>
+template <int W, bool kDict, int ALG = 0>
 cudaError_t launch_w(const ScanArgs& a, cudaStream_t st) {
   const size_t smem = scan_smem_bytes(W, a.warps, kDict ? a.chunk : 0);
-  cudaError_t e = cudaFuncSetAttribute(scan_kernel<W, kDict>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-  if (e != cudaSuccess) return e;
   const long long blocks_r = (a.n_regions + a.warps - 1) / a.warps;
   const long long grid = blocks_r * a.n_groups;
   if (grid <= 0) return cudaSuccess;
-  scan_kernel<W, kDict><<<unsigned(grid), a.warps * 32, smem, st>>>(a);
+  scan_kernel<W, kDict, ALG><<<unsigned(grid), a.warps * 32, smem, st>>>(a);
   return cudaGetLastError();
+}
+
+template <int W, bool kDict, int ALG = 0>
+cudaError_t allow_smem(int bytes) {
+  return cudaFuncSetAttribute(scan_kernel<W, kDict, ALG>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
 }  // namespace
 
+cudaError_t prepare_scan_kernels(int max_smem_bytes) {
+  cudaError_t e = cudaSuccess;
+  auto set = [&](cudaError_t r) {
+    if (e == cudaSuccess) e = r;
+  };
+  set(allow_smem<1, true>(max_smem_bytes));
+  set(allow_smem<1, false>(max_smem_bytes));
+  set(allow_smem<2, true>(max_smem_bytes));
+  set(allow_smem<2, false>(max_smem_bytes));
+  set(allow_smem<3, true>(max_smem_bytes));
+  set(allow_smem<3, false>(max_smem_bytes));
+  set(allow_smem<4, true>(max_smem_bytes));
+  set(allow_smem<4, false>(max_smem_bytes));
+  set(allow_smem<1, true, 1>(max_smem_bytes));
+  set(allow_smem<1, true, 2>(max_smem_bytes));
+  set(allow_smem<1, true, 3>(max_smem_bytes));
+  return e;
+}
+
 cudaError_t launch_scan(const ScanArgs& a, cudaStream_t s) {
   const bool d = a.dict != 0;
+  if (a.algo > 0) {  // automaton path: one-word patterns, dictionary mapping only
+    if (a.W != 1 || !d) return cudaErrorInvalidValue;
+    switch (a.algo) {
+      case 1: return launch_w<1, true, 1>(a, s);
+      case 2: return launch_w<1, true, 2>(a, s);
+      case 3: return launch_w<1, true, 3>(a, s);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   switch (a.W) {
     case 1: return d ? launch_w<1, true>(a, s) : launch_w<1, false>(a, s);
     case 2: return d ? launch_w<2, true>(a, s) : launch_w<2, false>(a, s);

@@ -122,16 +122,26 @@ def zipf_probs(s: float = 1.1, ranks: int = 256) -> np.ndarray:
     return w / w.sum()
 
 
-def zipf_bytes(rng: np.random.Generator, n: int, perm: np.ndarray, s: float = 1.1,
-               chunk: int = 1 << 24) -> np.ndarray:
-    """Bytes whose ranks follow Zipf(s) over 256 ranks, mapped by ``perm``."""
+def zipf_table(perm: np.ndarray, s: float = 1.1, cells: int = 1 << 20) -> np.ndarray:
+    """2^20 equally likely cells; cell i holds the byte of the rank whose CDF
+    interval contains (i + 0.5) / 2^20 (the smallest rank probability, ~3.5e-4
+    at s = 1.1, spans hundreds of cells)."""
     cdf = np.cumsum(zipf_probs(s, 256))
     cdf[-1] = 1.0
+    idx = np.searchsorted(cdf, (np.arange(cells) + 0.5) / cells, side="right").clip(0, 255)
+    return perm[idx]
+
+
+def zipf_bytes(rng: np.random.Generator, n: int, perm: np.ndarray, s: float = 1.1,
+               chunk: int = 1 << 26, table: np.ndarray | None = None) -> np.ndarray:
+    """Bytes whose ranks follow Zipf(s) over 256 ranks, mapped by ``perm``
+    (sampled by lookup in ``zipf_table``)."""
+    if table is None:
+        table = zipf_table(perm, s)
     out = np.empty(n, dtype=np.uint8)
     for a in range(0, n, chunk):
         b = min(n, a + chunk)
-        u = rng.random(b - a)
-        out[a:b] = perm[np.searchsorted(cdf, u, side="right").clip(0, 255)]
+        out[a:b] = table[rng.integers(0, table.size, size=b - a, dtype=np.uint32)]
     return out
 
 
@@ -187,8 +197,9 @@ def bytes_zipf(seed: int = 3, n: int = 1 << 30, n_pat: int = 4096, mlo: int = 16
     ms = ms.clip(mlo, mhi)
     kmax = np.minimum(8, ms // 4)
     ks = np.array([int(rng.integers(1, int(k) + 1)) for k in kmax], np.int32)
-    pats = [zipf_bytes(rng, int(m), perm, s) for m in ms]
-    text = zipf_bytes(rng, n, perm, s)
+    tab = zipf_table(perm, s)
+    pats = [zipf_bytes(rng, int(m), perm, s, table=tab) for m in ms]
+    text = zipf_bytes(rng, n, perm, s, table=tab)
     alpha = perm  # all 256 byte values
     for pid, p in enumerate(pats):
         for cp in edit_copies(rng, p, rng.integers(1, int(ks[pid]) + 1, size=copies), alpha):
@@ -218,53 +229,94 @@ def many_texts(seed: int = 4, n_texts: int = 10_000, total: float = 4e9, n_pat: 
 
 @dataclass
 class ServedTrace:
-    """Packet arrivals for online matching: time (s), stream id, payload."""
+    """Packet arrivals for online matching, sorted by time.
+
+    Packet j arrives at ``times[j]`` seconds for stream ``streams[j]`` with
+    payload ``payload[offs[j]:offs[j] + lens[j]]``; ``last[j]`` marks the last
+    packet of its stream (the connection closes after it)."""
     patterns: list
     ks: np.ndarray
     times: np.ndarray
     streams: np.ndarray
-    payloads: list
+    payload: np.ndarray
+    offs: np.ndarray
+    lens: np.ndarray
+    last: np.ndarray
     n_streams: int
     meta: dict = field(default_factory=dict)
+
+    @property
+    def n_packets(self) -> int:
+        return int(self.times.size)
+
+    def packet(self, j: int) -> np.ndarray:
+        return self.payload[self.offs[j]:self.offs[j] + self.lens[j]]
 
     def stream_texts(self) -> list:
         """Each stream's packets concatenated in arrival order."""
         parts = [[] for _ in range(self.n_streams)]
-        for sid, pl in zip(self.streams.tolist(), self.payloads):
-            parts[sid].append(pl)
+        for j, sid in enumerate(self.streams.tolist()):
+            parts[sid].append(self.packet(j))
         return [np.concatenate(p) if p else np.zeros(0, np.uint8) for p in parts]
 
 
 def served(seed: int = 5, n_streams: int = 4096, n_sig: int = 2000, mlo: int = 8, mhi: int = 64,
            K: int = 2, gbps: float = 10.0, duration: float = 0.01, plo: int = 64,
-           phi: int = 1500, planted_frac: float = 0.01, s: float = 1.1) -> ServedTrace:
+           phi: int = 1500, planted_frac: float = 0.01, s: float = 1.1,
+           life: float = 1.0, n_packets: int | None = None) -> ServedTrace:
+    """Poisson packet arrivals at ``gbps`` (aggregate) over ``duration`` s.
+
+    Each stream is active during a window of ``life * duration`` placed at a
+    uniform start; with ``life = 1`` every stream is active throughout and the
+    arrivals are a Poisson process.  ``n_packets`` fixes the packet count
+    instead (the duration then follows from the rate)."""
     rng = rng_for(seed)
     perm = rng.permutation(256).astype(np.uint8)
     ms = rng.integers(mlo, mhi + 1, size=n_sig)
-    pats = [zipf_bytes(rng, int(m), perm, s) for m in ms]
+    tab = zipf_table(perm, s)
+    pats = [zipf_bytes(rng, int(m), perm, s, table=tab) for m in ms]
     ks = np.full(n_sig, K, np.int32)
     mean_pkt = (plo + phi) / 2.0
     rate = gbps * 1e9 / 8.0 / mean_pkt  # packets per second
-    n_pkt = max(1, int(rng.poisson(rate * duration)))
-    gaps = rng.exponential(1.0 / rate, size=n_pkt)
-    times = np.cumsum(gaps)
+    if n_packets is not None:
+        n_pkt = int(n_packets)
+        duration = n_pkt / rate
+    else:
+        n_pkt = max(1, int(rng.poisson(rate * duration)))
     streams = rng.integers(0, n_streams, size=n_pkt).astype(np.int32)
-    sizes = rng.integers(plo, phi + 1, size=n_pkt)
-    payload = zipf_bytes(rng, int(sizes.sum()), perm, s)
-    offs = np.concatenate([[0], np.cumsum(sizes)])
-    payloads = [payload[offs[j]:offs[j + 1]].copy() for j in range(n_pkt)]
+    win = duration * life
+    starts = rng.uniform(0.0, max(duration - win, 0.0), size=n_streams)
+    times = starts[streams] + rng.uniform(0.0, win, size=n_pkt)
+    order = np.argsort(times, kind="stable")
+    times, streams = times[order], streams[order]
+    lens = rng.integers(plo, phi + 1, size=n_pkt).astype(np.uint32)
+    offs = np.concatenate([[0], np.cumsum(lens.astype(np.uint64))[:-1]]).astype(np.uint64)
+    payload = zipf_bytes(rng, int(lens.astype(np.int64).sum()), perm, s, table=tab)
+    # next packet of the same stream, for copies that straddle a packet boundary
+    nxt = np.full(n_pkt, -1, np.int64)
+    seen = {}
+    for j in range(n_pkt - 1, -1, -1):
+        sid = int(streams[j])
+        nxt[j] = seen.get(sid, -1)
+        seen[sid] = j
+    last = nxt < 0
     for j in np.nonzero(rng.random(n_pkt) < planted_frac)[0]:
         pid = int(rng.integers(0, n_sig))
         cp = edit_copy(rng, pats[pid], int(rng.integers(0, K + 1)), perm)
-        pl = payloads[j]
-        if cp.size <= pl.size:
-            # anchored at the packet end half of the time, so the copy can
-            # straddle into the stream's next packet when truncated below
-            if rng.random() < 0.5:
-                off = pl.size - int(rng.integers(1, cp.size + 1))
-                take = min(cp.size, pl.size - off)
-                pl[off:off + take] = cp[:take]
-            else:
-                plant(rng, pl, cp)
-    return ServedTrace(pats, ks, times, streams, payloads, n_streams,
-                       {"gbps": gbps, "duration": duration, "n_pkt": n_pkt})
+        o, ln = int(offs[j]), int(lens[j])
+        if cp.size > ln:
+            continue
+        if rng.random() < 0.5 and nxt[j] >= 0:
+            # the copy starts near the end of this packet and continues in the
+            # stream's next packet
+            head = int(rng.integers(1, cp.size + 1))
+            payload[o + ln - head:o + ln] = cp[:head]
+            rest = cp[head:]
+            k2 = int(nxt[j])
+            take = min(rest.size, int(lens[k2]))
+            payload[int(offs[k2]):int(offs[k2]) + take] = rest[:take]
+        else:
+            at = int(rng.integers(0, ln - cp.size + 1))
+            payload[o + at:o + at + cp.size] = cp
+    return ServedTrace(pats, ks, times, streams, payload, offs, lens, last, n_streams,
+                       {"gbps": gbps, "duration": duration, "n_pkt": n_pkt, "life": life})

@@ -283,3 +283,73 @@ def test_autotune_then_search_matches_oracle():
 def test_int_peak_microbenchmark_runs():
     ops, ms = B.oasm_measure_int_peak(0)
     assert ops > 1e12 and ms > 0
+
+
+@pytest.mark.parametrize("K", [0, 1, 2])
+def test_automaton_classes_equal_bit_vector_scan_and_oracle(K):
+    """One-word patterns with K <= 2 run on the automaton scan when a class
+    holds 32 or more of them; the Myers/Hyyro scan must give the same output."""
+    rng = np.random.default_rng(400 + K)
+    pats = [W.DNA[rng.integers(0, 4, size=int(rng.integers(max(K + 1, 3), 33)))] for _ in range(45)]
+    ks = [K] * len(pats)
+    text = W.DNA[rng.integers(0, 4, size=60000)]
+    for p in pats:
+        for cp in W.edit_copies(rng, p, rng.integers(0, K + 1, size=3), W.DNA):
+            W.plant(rng, text, cp)
+    auto, _ = run_gpu(pats, ks, text)
+    myers, _ = run_gpu(pats, ks, text, cfg={"myers_only": 1})
+    want = oracle_rows(pats, ks, text)
+    assert canon(auto) == canon(myers) == want
+    # also across feeds (state carried through the stored tail)
+    split, _ = run_gpu(pats, ks, text, splits=np.sort(rng.integers(0, text.size, size=7)))
+    assert canon(split) == want
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_stream_state_moves_to_another_context(seed):
+    """Save a stream mid-text, restore it into a new context, continue: the
+    union of both halves' hits equals the uninterrupted result (oracle)."""
+    rng = np.random.default_rng(600 + seed)
+    pats, ks, text = random_case(rng, 4, 40, 6, 70, 30000, kmax=4)
+    cut = int(rng.integers(1, text.size))
+    want = oracle_rows(pats, ks, text)
+    a = B.oasm_create(pats, ks)
+    b = B.oasm_create(pats, ks)
+    try:
+        sa = B.oasm_open_stream(a)
+        B.oasm_feed(a, sa, text[:cut])
+        first = B.oasm_flush(a, sa)
+        state = B.oasm_save_stream(a, sa)
+        B.oasm_close_stream(a, sa)
+        sb = B.oasm_open_stream(b)
+        B.oasm_restore_stream(b, sb, state)
+        B.oasm_feed(b, sb, text[cut:])
+        second = B.oasm_flush(b, sb, end_of_stream=True)
+        rows = [(int(r["pattern_id"]), int(r["decided_at"]), int(r["k"]), int(r["start"]),
+                 int(r["len"])) for r in np.concatenate([first, second])]
+        assert canon(rows) == want
+        # a state from another dictionary is refused
+        c = B.oasm_create(pats[:-1], ks[:-1])
+        try:
+            sc = B.oasm_open_stream(c)
+            with pytest.raises(B.OasmError):
+                B.oasm_restore_stream(c, sc, state)
+        finally:
+            B.oasm_destroy(c)
+    finally:
+        B.oasm_destroy(a)
+        B.oasm_destroy(b)
+
+
+def test_graph_launched_steps_equal_direct_launches():
+    """Steps launched as captured CUDA graphs (updated in place while the step
+    shape repeats) give the same output as direct launches."""
+    rng = np.random.default_rng(700)
+    pats, ks, text = random_case(rng, 4, 50, 5, 60, 64000, kmax=4)
+    splits = np.arange(4000, text.size, 4000)  # equal pieces: repeating step shapes
+    g, sg = run_gpu(pats, ks, text, splits=splits, cfg={"graphs": 1, "timing": 1})
+    d, sd = run_gpu(pats, ks, text, splits=splits)
+    assert canon(g) == canon(d) == oracle_rows(pats, ks, text)
+    assert 1 <= sg["graph_builds"] < sg["steps"]
+    assert sd["graph_builds"] == 0
+    assert sg["scan_ms"] > 0

@@ -1,0 +1,148 @@
+"""Serving loop: continuous batching over many streams with admission.
+
+CPU tests drive the scheduler against a fake library that records what it is
+asked to do.  The GPU tests replay a small trace through the CUDA library and
+check that every stream's hits equal the oracle's for that stream's packets
+concatenated, and equal the result of running the stream alone."""
+import numpy as np
+import pytest
+
+from paper_1712_03560_gb300 import serve
+from paper_1712_03560_gb300 import workloads as W
+
+
+class FakeLib:
+    """Stands in for the binding: slots, per-stream byte logs, no matching."""
+    OASM_EBUSY, OASM_ENOMEM = -3, -2
+
+    class OasmError(RuntimeError):
+        def __init__(self, code):
+            super().__init__(code)
+            self.code = code
+
+    def __init__(self, slots):
+        self.slots = slots
+        self.open = {}
+        self.log = []          # (event, ...) in call order
+        self.data = {}         # sid -> bytes fed in order (for the current occupant)
+        self.ended = set()
+        self.next_id = 0
+
+    def oasm_create(self, patterns, ks, rules, cfg):
+        return "ctx"
+
+    def oasm_destroy(self, ctx):
+        pass
+
+    def oasm_open_stream(self, ctx):
+        free = [s for s in range(self.slots) if s not in self.open]
+        if not free:
+            raise self.OasmError(self.OASM_EBUSY)
+        s = free[0]
+        self.open[s] = self.next_id
+        self.next_id += 1
+        self.data[s] = bytearray()
+        self.log.append(("open", s))
+        return s
+
+    def oasm_open_streams(self, ctx, n):
+        out = []
+        for _ in range(n):
+            try:
+                out.append(self.oasm_open_stream(ctx))
+            except self.OasmError:
+                break
+        return np.asarray(out, dtype=np.uint32)
+
+    def oasm_end_streams(self, ctx, sids):
+        for s in sids:
+            self.oasm_end_stream(ctx, int(s))
+
+    def oasm_close_streams(self, ctx, sids):
+        for s in sids:
+            self.oasm_close_stream(ctx, int(s))
+
+    def oasm_close_stream(self, ctx, s):
+        assert s in self.ended, "closed before its end was processed"
+        self.log.append(("close", s, bytes(self.data[s])))
+        del self.open[s]
+        self.ended.discard(s)
+
+    def oasm_feed_many(self, ctx, sids, buf, offs, lens):
+        for s, o, n in zip(sids.tolist(), offs.tolist(), lens.tolist()):
+            assert s in self.open and s not in self.ended
+            self.data[s] += bytes(buf[o:o + n])
+        self.log.append(("feed", len(sids)))
+
+    def oasm_end_stream(self, ctx, s):
+        self.ended.add(s)
+
+    def oasm_step(self, ctx):
+        self.log.append(("step",))
+
+    def oasm_drain(self, ctx):
+        from paper_1712_03560_gb300.binding import HIT_DTYPE
+        return np.zeros(0, dtype=HIT_DTYPE)
+
+
+@pytest.mark.parametrize("slots,budget", [(3, 1 << 30), (5, 3000), (64, 1 << 30), (2, 1500)])
+def test_scheduler_feeds_every_packet_once_in_stream_order(slots, budget):
+    tr = W.served(seed=3, n_streams=12, n_sig=4, gbps=1.0, duration=0.004, life=0.4)
+    lib = FakeLib(slots)
+    srv = serve.Server([b"AB"], [0], max_streams=slots, lib=lib, max_batch_bytes=budget)
+    res = srv.replay(tr, realtime=False)
+    texts = tr.stream_texts()
+    closed = [e for e in lib.log if e[0] == "close"]
+    # every stream that has packets was opened, got exactly its bytes in order, and closed
+    got = sorted(e[2] for e in closed)
+    want = sorted(bytes(t) for t in texts if t.size)
+    assert got == want
+    assert res["packets"] == tr.n_packets and res["fed_bytes"] == int(tr.lens.sum())
+    assert res["p50_ms"] is not None and res["p99_ms"] >= res["p50_ms"]
+    assert res["streams_admitted"] == sum(1 for t in texts if t.size)
+    # never more open streams than slots
+    live, peak = 0, 0
+    for e in lib.log:
+        live += {"open": 1, "close": -1}.get(e[0], 0)
+        peak = max(peak, live)
+    assert peak <= slots
+    if slots < 12:
+        assert res["max_waiting_streams"] > 0
+
+
+def test_scheduler_realtime_pacing_batches_arrivals():
+    tr = W.served(seed=4, n_streams=8, n_sig=4, gbps=0.05, duration=0.05)
+    lib = FakeLib(8)
+    srv = serve.Server([b"AB"], [0], max_streams=8, lib=lib)
+    res = srv.replay(tr, realtime=True)
+    assert res["wall_s"] >= tr.times[-1] * 0.9
+    assert res["steps"] >= 2
+    assert np.isfinite(res["p99_ms"])
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("slots,budget,realtime", [(4096, 1 << 30, False), (24, 20000, False),
+                                                   (64, 1 << 30, True)])
+def test_served_streams_match_oracle_alone_and_in_the_mix(slots, budget, realtime):
+    from parity_util import canon, oracle_rows
+    from paper_1712_03560_gb300 import binding as B
+    tr = W.served(seed=7, n_streams=48, n_sig=40, mlo=8, mhi=64, gbps=0.2, duration=0.05,
+                  life=0.5, planted_frac=0.05)
+    with serve.Server(tr.patterns, tr.ks, max_streams=slots, max_batch_bytes=budget) as srv:
+        res = srv.replay(tr, realtime=realtime, collect=True)
+    texts = tr.stream_texts()
+    assert res["steps"] >= (2 if budget < (1 << 30) or realtime else 1)
+    some = 0
+    for ext, t in enumerate(texts):
+        got = res["hits"].get(ext)
+        rows = [] if got is None else [(int(r["pattern_id"]), int(r["decided_at"]), int(r["k"]),
+                                        int(r["start"]), int(r["len"])) for r in got]
+        want = oracle_rows(tr.patterns, tr.ks, t)
+        assert canon(rows) == want, ext
+        some += len(want)
+        if ext < 6:  # the same stream alone
+            with B.Matcher(tr.patterns, tr.ks) as mt:
+                alone = mt.search(t)
+            assert canon([(int(r["pattern_id"]), int(r["decided_at"]), int(r["k"]),
+                           int(r["start"]), int(r["len"])) for r in alone]) == want
+    assert some > 0
