@@ -217,8 +217,10 @@ def run_served(args):
     sweep = []
     clocks = Clocks(0)
     with serve.Server(base.patterns, base.ks, max_streams=4096) as srv:
+        # warm-up: grow every step buffer to the sweep's sizes, then a paced pass
         for _ in range(max(1, args.warmup)):
-            srv.replay(W.served(seed=99, n_packets=2000, gbps=10.0), realtime=False)
+            srv.replay(W.served(seed=99, n_packets=20000, gbps=10.0), realtime=False)
+        srv.replay(W.served(seed=98, n_packets=20000, gbps=1.0), realtime=True)
         clocks.start()
         for g in SERVED_LOADS_GBPS:
             tr = W.served(seed=int(5 + 10 * g), n_packets=n_pkt, gbps=g)
@@ -226,7 +228,8 @@ def run_served(args):
             r["gcups"] = msum * r["bytes"] / r["wall_s"] / 1e9
             sweep.append({k: r[k] for k in ("offered_gbps", "achieved_gbps", "p50_ms", "p99_ms",
                                              "max_ms", "steps", "mean_batch_bytes",
-                                             "step_ms_p50", "gcups", "packets")})
+                                             "step_ms_p50", "step_ms_p99", "step_ms_max",
+                                             "gcups", "packets")})
         clk = clocks.stop()
     best = max(sweep, key=lambda x: x["achieved_gbps"])
     knee = max((x for x in sweep if x["achieved_gbps"] >= 0.9 * x["offered_gbps"]),

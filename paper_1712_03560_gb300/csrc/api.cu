@@ -497,6 +497,7 @@ int plan_step(oasm_ctx* ctx, StepPlan& pl) {
       total += std::max<int64_t>(0, w.e_new - lo);
     }
     const int64_t R = region_len(ctx, b, total);
+    const size_t first = pl.regions.size();
     for (uint32_t i = 0; i < pl.items.size(); ++i) {
       const WorkItem& w = pl.items[i];
       const int64_t lo = std::max<int64_t>(0, w.e_prev - 2 * b.kmax);
@@ -508,6 +509,10 @@ int plan_step(oasm_ctx* ctx, StepPlan& pl) {
         pl.regions.push_back(r);
       }
     }
+    // longest first: a block's warps get regions of similar length (a block
+    // holds its SM until its slowest warp ends) and long work starts early
+    std::stable_sort(pl.regions.begin() + first, pl.regions.end(),
+                     [](const Region& x, const Region& y) { return (x.b - x.a) > (y.b - y.a); });
   }
   pl.region_off.push_back(pl.regions.size());
   return OASM_OK;

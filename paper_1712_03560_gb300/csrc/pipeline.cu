@@ -247,6 +247,14 @@ __global__ void __launch_bounds__(256) verify_kernel(const StepParams P) {
 constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / 32;
 
+// Keys per block: an even split, but at least 1,024, so a small sort runs on
+// a few blocks and the rest leave at once (each active block reads the whole
+// histogram matrix to find its offsets).
+__device__ __forceinline__ unsigned long long sort_chunk(unsigned long long n) {
+  const unsigned long long even = (n + gridDim.x - 1) / gridDim.x;
+  return even > 1024ull ? even : 1024ull;
+}
+
 __global__ void __launch_bounds__(kSortThreads)
     rs_hist(const unsigned long long* __restrict__ keys, const unsigned long long* count,
             unsigned long long cap, int shift, unsigned int* hist) {
@@ -254,7 +262,7 @@ __global__ void __launch_bounds__(kSortThreads)
   h[threadIdx.x] = 0;
   __syncthreads();
   const unsigned long long n = min(*count, cap);
-  const unsigned long long chunk = (n + gridDim.x - 1) / gridDim.x;
+  const unsigned long long chunk = sort_chunk(n);
   const unsigned long long b0 = chunk * blockIdx.x, b1 = min(n, b0 + chunk);
   for (unsigned long long i = b0 + threadIdx.x; i < b1; i += blockDim.x)
     atomicAdd(&h[(keys[i] >> shift) & 255u], 1u);
@@ -279,7 +287,7 @@ __global__ void __launch_bounds__(kSortThreads)
   __shared__ unsigned int wsum[kSortWarps];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned long long n = min(*count, cap);
-  if (n == 0) return;
+  if (sort_chunk(n) * blockIdx.x >= n) return;  // no keys for this block
   {
     const int d = threadIdx.x;
     unsigned int tot = 0, pre = 0;
@@ -303,7 +311,7 @@ __global__ void __launch_bounds__(kSortThreads)
   }
   for (int w = 0; w < kSortWarps; ++w) wcnt[w][threadIdx.x] = 0;
   __syncthreads();
-  const unsigned long long chunk = (n + gridDim.x - 1) / gridDim.x;
+  const unsigned long long chunk = sort_chunk(n);
   const unsigned long long b0 = chunk * blockIdx.x, b1 = min(n, b0 + chunk);
   const unsigned lt = (1u << lane) - 1u;
   for (unsigned long long t0 = b0; t0 < b1; t0 += kSortThreads) {

@@ -31,13 +31,13 @@ import numpy as np
 
 class Server:
     def __init__(self, patterns, ks, max_streams: int = 4096, mem_budget: int = 0, rules=None,
-                 device: int = 0, max_batch_bytes: int = 8 << 20, lib=None):
+                 device: int = 0, max_batch_bytes: int = 8 << 20, graphs: bool = True, lib=None):
         if lib is None:
             from . import binding as lib
         self.B = lib
         self.ctx = lib.oasm_create(patterns, ks, rules,
                                    {"device": device, "max_streams": max_streams,
-                                    "mem_budget": mem_budget})
+                                    "mem_budget": mem_budget, "graphs": 1 if graphs else 0})
         self.max_batch_bytes = int(max_batch_bytes)
 
     def close(self):
@@ -166,6 +166,8 @@ class Server:
             "p99_ms": float(np.percentile(lat[ok], 99)) if ok.any() else None,
             "max_ms": float(lat[ok].max()) if ok.any() else None,
             "step_ms_p50": float(np.percentile(step_ms, 50)) if step_ms else None,
+            "step_ms_p99": float(np.percentile(step_ms, 99)) if step_ms else None,
+            "step_ms_max": float(max(step_ms)) if step_ms else None,
             "mean_batch_bytes": fed_bytes / max(1, steps),
             "streams_admitted": admitted, "max_waiting_streams": max_wait,
         }
