@@ -2,7 +2,8 @@
 """Benchmark of the OASM device path on GB300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload dictionary_dna|plain_dna|plain_dna_1g|bytes_zipf|many_texts]
+                    [--workload dictionary_dna|dictionary_dna_64m|plain_dna|plain_dna_1g|
+                     bytes_zipf|many_texts|many_texts_256m|served]
 
 One step = one pass of the whole path over the workload: open a stream, feed
 the text, end it and flush (stage, bit-parallel scan, anchored verification,
@@ -77,6 +78,9 @@ def make_workload(name: str, seed_offset: int):
     if name == "many_texts":
         return W.many_texts(seed=4 + 1000 * seed_offset), \
             "many_texts: 10000 DNA texts lognormal(median 1e5) ~4 GB x 512 DNA patterns m~U[12,48] K=3"
+    if name == "many_texts_256m":
+        return W.many_texts(seed=4 + 1000 * seed_offset, n_texts=640, total=2.56e8, copies=13), \
+            "many_texts_256m: 640 DNA texts lognormal(median 1e5) ~256 MB x 512 DNA patterns m~U[12,48] K=3"
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -285,31 +289,40 @@ def main():
         for bk in tuned["buckets"]:
             bk.pop("trials", None)
 
-    def step_device():
-        sids = []
-        for t in dtexts:
-            s = B.oasm_open_stream(ctx)
-            B.oasm_feed_device(ctx, s, t)
-            B.oasm_end_stream(ctx, s)
-            sids.append(s)
+    # host time per phase of a step (submit, device step, drain, close)
+    host_ms = {"submit": 0.0, "step": 0.0, "drain": 0.0, "close": 0.0}
+    drain_buf = [None]
+
+    def run_one(submit):
+        t0 = time.perf_counter()
+        sids = B.oasm_open_streams(ctx, len(wl.texts))
+        submit(sids.tolist())
+        B.oasm_end_streams(ctx, sids)
+        t1 = time.perf_counter()
         B.oasm_step(ctx)
-        n = len(B.oasm_drain(ctx))
-        for s in sids:
-            B.oasm_close_stream(ctx, s)
+        t2 = time.perf_counter()
+        out = B.oasm_drain(ctx, drain_buf[0])
+        n = len(out)
+        if drain_buf[0] is None or drain_buf[0].size < n:  # reused from the next step on
+            drain_buf[0] = np.empty(max(1024, n * 5 // 4), dtype=B.HIT_DTYPE)
+        t3 = time.perf_counter()
+        B.oasm_close_streams(ctx, sids)
+        t4 = time.perf_counter()
+        for k, a, b in (("submit", t0, t1), ("step", t1, t2), ("drain", t2, t3), ("close", t3, t4)):
+            host_ms[k] += (b - a) * 1e3
         return n
 
+    def step_device():
+        def submit(sids):
+            for s, t in zip(sids, dtexts):
+                B.oasm_feed_device(ctx, s, t)
+        return run_one(submit)
+
     def step_host(host_texts):
-        sids = []
-        for t in host_texts:
-            s = B.oasm_open_stream(ctx)
-            B.oasm_feed(ctx, s, t)
-            B.oasm_end_stream(ctx, s)
-            sids.append(s)
-        B.oasm_step(ctx)
-        n = len(B.oasm_drain(ctx))
-        for s in sids:
-            B.oasm_close_stream(ctx, s)
-        return n
+        def submit(sids):
+            for s, t in zip(sids, host_texts):
+                B.oasm_feed(ctx, s, t)
+        return run_one(submit)
 
     for _ in range(args.warmup):
         kept = step_device()
@@ -319,6 +332,8 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     B.oasm_reset_stats(ctx)
+    for k in host_ms:
+        host_ms[k] = 0.0
     clocks = Clocks(dev)
     clocks.start()
     time.sleep(0.25)
@@ -335,6 +350,7 @@ def main():
         dist.barrier()
     ms = ev0.elapsed_time(ev1)
     st = B.oasm_get_stats(ctx)
+    host_step_ms = {k: v / args.steps for k, v in host_ms.items()}
     if dist:
         t = torch.tensor([ms], device=f"cuda:{dev}")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -419,6 +435,7 @@ def main():
         "occurrences_per_step": int(kept),
         "kernel_ms": {k: st[k] / args.steps for k in ("copy_ms", "scan_ms", "verify_ms",
                                                         "order_ms", "filter_ms", "step_ms")},
+        "host_ms_per_step": host_step_ms,
         "candidates_per_step": st["candidates"] / args.steps,
         "hits_per_step": st["hits"] / args.steps,
         "gpu_launches": int(st["launches"]),

@@ -223,7 +223,9 @@ int oasm_flush(oasm_ctx *ctx, uint32_t sid, int end_of_stream, oasm_hit *out, si
 int oasm_drain(oasm_ctx *ctx, oasm_hit *out, size_t cap, size_t *n_out);
 
 /* Number of decided hits of stream sid queued and not yet returned by
- * oasm_flush (no device work is started). */
+ * oasm_flush (no device work is started).  sid = OASM_ALL_STREAMS gives the
+ * total over every open stream: the size oasm_drain needs. */
+#define OASM_ALL_STREAMS 0xFFFFFFFFu
 int oasm_ready(oasm_ctx *ctx, uint32_t sid, size_t *n);
 
 /* ---- stream checkpoint / migration -------------------------------------

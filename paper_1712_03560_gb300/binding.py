@@ -26,6 +26,7 @@ OASM_ETRUNC = -4
 OASM_ETIMEOUT = -5
 OASM_ECUDA = -6
 OASM_ESTATE = -7
+OASM_ALL_STREAMS = 0xFFFFFFFF  # oasm_ready: total over every open stream
 
 REPLACE = {"contained": 0, "same_end": 1, "never": 2}
 ORDER = {"per_start_length": 0, "per_start_best": 1}
@@ -263,21 +264,20 @@ def oasm_step(ctx):
     return _check(load().oasm_step(ctx), ctx)
 
 
-def oasm_drain(ctx, cap: int = 1 << 16) -> np.ndarray:
+def oasm_drain(ctx, out: np.ndarray | None = None) -> np.ndarray:
     """All queued hits of all streams (streams in id order, canonical order
-    within a stream)."""
+    within a stream).  With ``out`` (a HIT_DTYPE array), the hits are written
+    into it when it is large enough and a view of it is returned."""
     lib = load()
-    parts = []
-    while True:
-        buf = np.zeros(cap, dtype=HIT_DTYPE)
-        n = ctypes.c_size_t(0)
-        rc = lib.oasm_drain(ctx, buf.ctypes.data, cap, ctypes.byref(n))
-        _check(rc, ctx, allow=(OASM_ETRUNC,))
-        parts.append(buf[: n.value])
-        if rc != OASM_ETRUNC:
-            break
-        cap *= 2
-    return np.concatenate(parts) if len(parts) > 1 else parts[0]
+    total = oasm_ready(ctx, OASM_ALL_STREAMS)
+    if out is not None and out.dtype == HIT_DTYPE and out.size >= total and out.flags.c_contiguous:
+        buf = out[:total]
+    else:
+        buf = np.empty(total, dtype=HIT_DTYPE)
+    n = ctypes.c_size_t(0)
+    rc = lib.oasm_drain(ctx, buf.ctypes.data if total else None, total, ctypes.byref(n))
+    _check(rc, ctx)
+    return buf[: n.value]
 
 
 def oasm_ready(ctx, sid: int) -> int:

@@ -292,29 +292,54 @@ int build_tables(oasm_ctx* ctx) {
 
   // forward lane groups per word-count class, patterns sorted by length so a
   // group's lanes need similar warm-up.  One-word patterns with K <= 2 form
-  // automaton classes (one per K) when there are at least 32 of them.
+  // automaton classes (one per K) when there are at least 32 of them; their
+  // lanes are packed with up to kMaxSlots patterns whose lengths sum to <= 32
+  // (first-fit over lengths in decreasing order).
   auto add_bucket = [&](int W, int algo, std::vector<uint32_t> ids) -> int {
-    std::stable_sort(ids.begin(), ids.end(),
-                     [&](uint32_t a0, uint32_t b0) { return ctx->m[a0] < ctx->m[b0]; });
     Bucket bk;
     bk.W = W;
     bk.algo = algo;
+    std::vector<std::vector<uint32_t>> lanes;  // patterns of each lane
+    if (algo > 0) {
+      std::stable_sort(ids.begin(), ids.end(),
+                       [&](uint32_t a0, uint32_t b0) { return ctx->m[a0] > ctx->m[b0]; });
+      std::vector<int> used;
+      for (uint32_t p : ids) {
+        size_t l = 0;
+        while (l < lanes.size() &&
+               !(used[l] + ctx->m[p] <= 32 && lanes[l].size() < size_t(kMaxSlots)))
+          ++l;
+        if (l == lanes.size()) {
+          lanes.emplace_back();
+          used.push_back(0);
+        }
+        lanes[l].push_back(p);
+        used[l] += ctx->m[p];
+      }
+    } else {
+      std::stable_sort(ids.begin(), ids.end(),
+                       [&](uint32_t a0, uint32_t b0) { return ctx->m[a0] < ctx->m[b0]; });
+      for (uint32_t p : ids) lanes.push_back({p});
+    }
     const size_t RW = size_t(32) * W;  // words per symbol row: [w][lane]
     std::vector<uint32_t> peq;
-    for (size_t g0 = 0; g0 < ids.size(); g0 += kLaneGroup) {
-      const int np = int(std::min<size_t>(kLaneGroup, ids.size() - g0));
-      // a class with 32 or more patterns runs one pattern per lane (idle lanes
-      // in its last group); a smaller one spreads each pattern over lanes
+    for (size_t g0 = 0; g0 < lanes.size(); g0 += kLaneGroup) {
+      const int np = int(std::min<size_t>(kLaneGroup, lanes.size() - g0));
+      // a class with 32 or more patterns runs one lane word per lane (idle
+      // lanes in its last group); a smaller one spreads each pattern over lanes
       const int nseg = ids.size() >= size_t(kLaneGroup) ? 1 : std::max(1, kLaneGroup / np);
       LaneGroup G;
       memset(&G, 0, sizeof G);
       G.nseg = nseg;
       G.W = W;
       G.ov = 1;
+      G.nslot = 1;
       const size_t base = peq.size();
       peq.resize(base + size_t(256) * RW, 0u);
       for (int l = 0; l < kLaneGroup; ++l) {
         const int pi = l / nseg, sg = l % nseg;
+        for (int q = 0; q < kMaxSlots; ++q) G.lastbit[q][l] = 31;
+        for (int q = 0; q + 1 < kMaxSlots; ++q) G.xpat[q][l] = -1;
         if (pi >= np) {
           G.pat[l] = -1;
           G.m[l] = uint8_t(32 * W);
@@ -322,19 +347,30 @@ int build_tables(oasm_ctx* ctx) {
           G.seg[l] = 0;
           continue;
         }
-        const uint32_t p = ids[g0 + pi];
-        const auto& s = ctx->pats[p];
-        const int m = int(s.size());
-        G.pat[l] = int32_t(p);
-        G.m[l] = uint8_t(m);
-        G.K[l] = ctx->K[p];
+        const auto& lp = lanes[g0 + pi];
+        G.nslot = std::max<int>(G.nslot, int(lp.size()));
+        G.pat[l] = int32_t(lp[0]);
         G.seg[l] = uint8_t(sg);
-        G.ov = std::max(G.ov, m + ctx->K[p] - 1);
-        bk.kmax = std::max<int>(bk.kmax, ctx->K[p]);
-        const int off0 = 32 * W - m;  // top-aligned
-        for (int j = 0; j < m; ++j) {
-          const int bit = off0 + j;
-          peq[base + size_t(s[j]) * RW + size_t(bit >> 5) * 32 + l] |= 1u << (bit & 31);
+        G.K[l] = ctx->K[lp[0]];
+        int off = (algo > 0) ? 0 : 32 * W - ctx->m[lp[0]];  // Myers lanes are top-aligned
+        for (size_t q = 0; q < lp.size(); ++q) {
+          const uint32_t p = lp[q];
+          const auto& s = ctx->pats[p];
+          const int m = int(s.size());
+          if (q > 0) G.xpat[q - 1][l] = int32_t(p);
+          G.m[l] = std::max<uint8_t>(G.m[l], uint8_t(m));
+          G.ov = std::max(G.ov, m + ctx->K[p] - 1);
+          bk.kmax = std::max<int>(bk.kmax, ctx->K[p]);
+          for (int j = 0; j < m; ++j) {
+            const int bit = off + j;
+            peq[base + size_t(s[j]) * RW + size_t(bit >> 5) * 32 + l] |= 1u << (bit & 31);
+          }
+          if (algo > 0) {
+            G.first[l] |= 1u << off;
+            G.last[l] |= 1u << (off + m - 1);
+            G.lastbit[q][l] = uint8_t(off + m - 1);
+          }
+          off += m;
         }
       }
       bk.ov_max = std::max(bk.ov_max, G.ov);
@@ -1228,6 +1264,13 @@ int oasm_drain(oasm_ctx* ctx, oasm_hit* out, size_t cap, size_t* n_out) {
 }
 
 int oasm_ready(oasm_ctx* ctx, uint32_t sid, size_t* n) {
+  if (ctx && n && sid == OASM_ALL_STREAMS) {
+    size_t tot = 0;
+    for (const StreamRec& s : ctx->streams)
+      if (s.open) tot += s.ready.size() - s.head;
+    *n = tot;
+    return OASM_OK;
+  }
   int rc = check_sid(ctx, sid);
   if (rc) return rc;
   if (!n) return OASM_EINVAL;

@@ -43,18 +43,29 @@ struct Region {
   int64_t a, b;
 };
 
-// 32 lanes of the forward scan.  Lane l searches pattern pat[l] over
-// sub-segment seg[l] of the warp's region (nseg sub-segments).
+// Lanes of the automaton classes pack up to kMaxSlots short patterns of one
+// K into their 32-bit word (slot q holds one pattern in a contiguous range
+// of bits); every other lane holds one pattern.
+constexpr int kMaxSlots = 4;
+
+// 32 lanes of the forward scan.  Lane l searches pattern pat[l] (and, in a
+// packed automaton lane, the patterns of slots 1..nslot-1) over sub-segment
+// seg[l] of the warp's region (nseg sub-segments).
 struct LaneGroup {
-  int32_t pat[kLaneGroup];   // pattern id, -1 for an idle lane
-  uint8_t m[kLaneGroup];
-  uint8_t K[kLaneGroup];
+  int32_t pat[kLaneGroup];   // pattern id of slot 0, -1 for an idle lane
+  uint8_t m[kLaneGroup];     // longest pattern of the lane
+  uint8_t K[kLaneGroup];     // threshold (one K per automaton lane)
   uint8_t seg[kLaneGroup];
   uint8_t pad0[kLaneGroup];
   int32_t nseg;              // sub-segments per region
   int32_t ov;                // warm-up symbols: max over lanes of m + K - 1
   int32_t W;                 // 32-bit words per lane
-  int32_t pad1;
+  int32_t nslot;             // slots per lane in this group (1 unless packed)
+  // automaton lanes only
+  uint32_t first[kLaneGroup];                // bit of each slot's first symbol
+  uint32_t last[kLaneGroup];                 // bit of each slot's last symbol
+  int32_t xpat[kMaxSlots - 1][kLaneGroup];   // pattern ids of slots 1.., -1 empty
+  uint8_t lastbit[kMaxSlots][kLaneGroup];    // index of each slot's last bit
 };
 
 // Candidate end found by the forward scan: min over starts of the distance of

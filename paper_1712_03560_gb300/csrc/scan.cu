@@ -412,16 +412,19 @@ __device__ void scan_dict(const ScanArgs& A, const char* peq, uint8_t* tbuf, uin
 // ---------------------------------- dictionary mapping, NFA for K <= 2
 // Bit-parallel simulation of the approximate-matching automaton (Wu and
 // Manber's row-wise formulation) for one-word patterns with K = KL errors at
-// most.  R_j, j = 0..KL, holds one bit per pattern prefix: bit (32 - m + i)
-// of R_j is set when p[0..i] matches a suffix of the text read so far with
-// at most j edits (top-aligned, so the full pattern is bit 31).  For symbol c
-// with match mask B:
+// most.  R_j, j = 0..KL, holds one bit per pattern prefix: bit f + i of R_j
+// (f = the pattern's first bit) is set when p[0..i] matches a suffix of the
+// text read so far with at most j edits.  For symbol c with match mask B:
 //   R'_0 = ((R_0 << 1) | E) & B
 //   R'_j = (((R_j << 1) | E) & B) | R_j-1 | (((R_j-1 | R'_j-1) << 1) | E)
 // (match, insertion, substitution, deletion; E marks the first pattern
-// position, reached from the always-active empty prefix).  Bit 31 of R'_K is
-// set exactly when D[e] <= K, the candidate test of the Myers scan, at
-// 1 + 3K logic operations per step instead of the recurrence's seven.
+// position, reached from the always-active empty prefix).  The last bit of
+// R'_K is set exactly when D[e] <= K, the candidate test of the Myers scan.
+//
+// Several short patterns share one lane word: each left shift carries the
+// last bit of one pattern into the first bit of the next, and every shifted
+// term is OR-ed with E, which sets that first bit anyway, so the patterns do
+// not interact.  Lane masks: E = the first bits, LAST = the last bits.
 template <int KL>
 __device__ __forceinline__ void nfa_step(uint32_t (&R)[KL + 1], uint32_t B, uint32_t E) {
   uint32_t prev_old = R[0];
@@ -432,6 +435,14 @@ __device__ __forceinline__ void nfa_step(uint32_t (&R)[KL + 1], uint32_t B, uint
     R[j] = (((old << 1) | E) & B) | prev_old | ((prev_old | R[j - 1]) << 1) | E;
     prev_old = old;
   }
+}
+
+// Appends this step's candidate bit of every slot to the slots' step masks.
+__device__ __forceinline__ void record_slots(uint32_t (&cm)[kMaxSlots], uint32_t r,
+                                             const uint32_t (&sh)[kMaxSlots], int ns) {
+#pragma unroll
+  for (int q = 0; q < kMaxSlots; ++q)
+    if (q < ns) cm[q] = __funnelshift_l(r << sh[q], cm[q], 1);
 }
 
 template <int KL>
@@ -451,10 +462,21 @@ __device__ void scan_dict_nfa(const ScanArgs& A, const char* peq, uint8_t* tbuf,
       tma_load_1d(tb + c * CH, src + size_t(c) * CH, n, bar0 + 8 * c);
     }
   }
-  const uint32_t E = (L.pid < 0) ? 0u : (1u << (32 - L.m));
+  const int ns = G.nslot;  // block-uniform
+  const uint32_t E = (L.pid < 0) ? 0u : G.first[lane];
+  const uint32_t LAST = (L.pid < 0) ? 0u : G.last[lane];
+  int pids[kMaxSlots];
+  uint32_t sh[kMaxSlots];
+#pragma unroll
+  for (int q = 0; q < kMaxSlots; ++q) {
+    pids[q] = (q == 0) ? L.pid : (L.pid < 0 ? -1 : G.xpat[q > 0 ? q - 1 : 0][lane]);
+    sh[q] = 31u - G.lastbit[q][lane];
+  }
+  // before the first symbol, prefixes of up to j symbols are within j edits
+  // (deletions): bits f..f+j-1 of R_j for every slot (slots are > K bits wide)
   uint32_t Rs[KL + 1];
 #pragma unroll
-  for (int j = 0; j <= KL; ++j) Rs[j] = (E == 0u) ? 0u : (((1u << j) - 1u) << (32 - L.m));
+  for (int j = 0; j <= KL; ++j) Rs[j] = E * ((1u << j) - 1u);
   Emitter em;
   int dead_at = -1;
   bool record = false;
@@ -471,49 +493,60 @@ __device__ void scan_dict_nfa(const ScanArgs& A, const char* peq, uint8_t* tbuf,
     for (int vv = 0; vv < nv; ++vv) {
       const int v = c * (CH >> 4) + vv;
       const uint8_t* tv = t + vv * 16;
-      if (record) {
-        uint32_t cm = 0;
+      uint32_t cm[kMaxSlots];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const uint32_t sym = tv[j];
-          const uint32_t B = *reinterpret_cast<const uint32_t*>(peq + mad_lo(sym, 128u, lane_off));
-          nfa_step<KL>(Rs, B, E);
-          cm = (cm << 1) | (Rs[KL] >> 31);
-        }
-        const uint32_t c16 = cm & block_mask(L.t_lo, L.t_hi, v);
-        if (__any_sync(kFull, c16 != 0)) em.put(A, lane, c16, L.spos + 16 * v, R.wi, L.pid, wi.base_pos);
-        continue;
-      }
-      uint32_t R0[KL + 1];
-#pragma unroll
-      for (int j = 0; j <= KL; ++j) R0[j] = Rs[j];
-      int cnt = 0;
-#pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const uint32_t sym = tv[j];
-        const uint32_t B = *reinterpret_cast<const uint32_t*>(peq + mad_lo(sym, 128u, lane_off));
-        nfa_step<KL>(Rs, B, E);
-        cnt = add_top(cnt, Rs[KL]);  // counts steps with the full pattern reached
-      }
+      for (int q = 0; q < kMaxSlots; ++q) cm[q] = 0u;
+      bool emit = false;
       const uint32_t vm = block_mask(L.t_lo, L.t_hi, v);
-      if (__any_sync(kFull, cnt != 0 && vm != 0)) {
-        // rare: replay the block from its saved state, recording each step
-#pragma unroll
-        for (int j = 0; j <= KL; ++j) Rs[j] = R0[j];
-        uint32_t cm = 0;
+      if (record) {
+        uint32_t any = 0;
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
           const uint32_t sym = tv[j];
           const uint32_t B = *reinterpret_cast<const uint32_t*>(peq + mad_lo(sym, 128u, lane_off));
           nfa_step<KL>(Rs, B, E);
-          cm = (cm << 1) | (Rs[KL] >> 31);
+          any |= Rs[KL] & LAST;
+          record_slots(cm, Rs[KL], sh, ns);
         }
-        em.put(A, lane, cm & vm, L.spos + 16 * v, R.wi, L.pid, wi.base_pos);
-        ++replays;
+        emit = __any_sync(kFull, any != 0 && vm != 0);
+      } else {
+        uint32_t R0[KL + 1];
+#pragma unroll
+        for (int j = 0; j <= KL; ++j) R0[j] = Rs[j];
+        uint32_t any = 0;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const uint32_t sym = tv[j];
+          const uint32_t B = *reinterpret_cast<const uint32_t*>(peq + mad_lo(sym, 128u, lane_off));
+          nfa_step<KL>(Rs, B, E);
+          any |= Rs[KL] & LAST;  // some slot reached its full pattern
+        }
+        if (__any_sync(kFull, any != 0 && vm != 0)) {
+          // rare: replay the block from its saved state, recording each step
+#pragma unroll
+          for (int j = 0; j <= KL; ++j) Rs[j] = R0[j];
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const uint32_t sym = tv[j];
+            const uint32_t B =
+                *reinterpret_cast<const uint32_t*>(peq + mad_lo(sym, 128u, lane_off));
+            nfa_step<KL>(Rs, B, E);
+            record_slots(cm, Rs[KL], sh, ns);
+          }
+          emit = true;
+          ++replays;
+        }
+        if (++blocks == 64) {
+          record = replays > 3;
+          blocks = replays = 0;
+        }
       }
-      if (++blocks == 64) {
-        record = replays > 3;
-        blocks = replays = 0;
+      if (emit) {
+#pragma unroll
+        for (int q = 0; q < kMaxSlots; ++q)
+          if (q < ns)
+            em.put(A, lane, pids[q] >= 0 ? (cm[q] & vm) : 0u, L.spos + 16 * v, R.wi, pids[q],
+                   wi.base_pos);
       }
     }
     __syncwarp();

@@ -305,6 +305,47 @@ def test_automaton_classes_equal_bit_vector_scan_and_oracle(K):
     assert canon(split) == want
 
 
+@pytest.mark.parametrize("K,alpha", [(0, 2), (1, 2), (2, 4), (1, 256), (2, 2)])
+def test_packed_automaton_lanes(K, alpha):
+    """Automaton lanes hold up to four patterns whose lengths sum to at most
+    32 bits.  Lanes of one to four slots, exactly full words, dense
+    candidates (binary alphabet: the per-step recording mode) and sparse ones
+    must all give the oracle's output, equal to the one-pattern-per-lane
+    bit-vector scan, in one feed and across feeds."""
+    rng = np.random.default_rng(700 + 10 * K + alpha)
+    lens = [8] * 40 + [max(K + 1, 3)] * 10 + [16] * 6 + [24] * 6
+    lens += [int(x) for x in rng.integers(K + 1, 33, size=40)]
+    alphabet = np.arange(alpha, dtype=np.uint8)
+    pats = [alphabet[rng.integers(0, alpha, size=m)] for m in lens]
+    ks = [K] * len(pats)
+    text = alphabet[rng.integers(0, alpha, size=12000 if alpha == 2 else 40000)]
+    for p in pats[::3]:
+        for cp in W.edit_copies(rng, p, rng.integers(0, K + 1, size=2), alphabet):
+            W.plant(rng, text, cp)
+    auto, st_auto = run_gpu(pats, ks, text)
+    myers, st_myers = run_gpu(pats, ks, text, cfg={"myers_only": 1})
+    want = oracle_rows(pats, ks, text)
+    assert len(want) > 0
+    assert canon(auto) == canon(myers) == want
+    split, _ = run_gpu(pats, ks, text, splits=np.sort(rng.integers(0, text.size, size=5)))
+    assert canon(split) == want
+    # packing runs fewer lane words than one pattern per lane
+    assert st_auto["word_steps"] < st_myers["word_steps"]
+
+
+def test_packing_fills_lanes_with_four_short_patterns():
+    """128 patterns of length 8 with K = 1 pack four to a lane: one lane
+    group (32 lanes) instead of four."""
+    rng = np.random.default_rng(77)
+    pats = [W.DNA[rng.integers(0, 4, size=8)] for _ in range(128)]
+    ks = [1] * 128
+    text = W.DNA[rng.integers(0, 4, size=20000)]
+    auto, st_auto = run_gpu(pats, ks, text)
+    myers, st_myers = run_gpu(pats, ks, text, cfg={"myers_only": 1})
+    assert canon(auto) == canon(myers) == oracle_rows(pats, ks, text)
+    assert st_myers["word_steps"] == 4 * st_auto["word_steps"]
+
+
 @pytest.mark.parametrize("seed", range(3))
 def test_stream_state_moves_to_another_context(seed):
     """Save a stream mid-text, restore it into a new context, continue: the
