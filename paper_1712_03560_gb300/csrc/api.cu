@@ -19,6 +19,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <string>
+#include <mutex>
 #include <thread>
 #include <vector>
 
@@ -40,6 +41,46 @@ struct Piece {
   size_t n;
 };
 
+// Vector storage that leaves new elements uninitialised: decided records are
+// copied in right after the resize, so zero-filling them first would be a
+// wasted pass over memory.
+template <class T>
+struct NoInitAlloc : std::allocator<T> {
+  template <class U>
+  struct rebind {
+    using other = NoInitAlloc<U>;
+  };
+  NoInitAlloc() = default;
+  template <class U>
+  NoInitAlloc(const NoInitAlloc<U>&) noexcept {}
+  template <class U>
+  void construct(U* p) noexcept {
+    ::new (static_cast<void*>(p)) U;
+  }
+  template <class U, class... Args>
+  void construct(U* p, Args&&... args) {
+    ::new (static_cast<void*>(p)) U(std::forward<Args>(args)...);
+  }
+};
+using HitVec = std::vector<oasm_hit, NoInitAlloc<oasm_hit>>;
+
+// Runs f(lo, hi) over [0, n) split into contiguous parts on up to `threads`
+// host threads (one part when n is small).
+template <class F>
+void parallel_parts(size_t n, size_t min_per_part, F f) {
+  unsigned hw = std::thread::hardware_concurrency();
+  size_t parts = std::min<size_t>(hw ? std::min(hw, 16u) : 1u, n / std::max<size_t>(1, min_per_part));
+  if (parts <= 1) {
+    f(size_t(0), n);
+    return;
+  }
+  std::vector<std::thread> th;
+  th.reserve(parts);
+  for (size_t t = 0; t < parts; ++t)
+    th.emplace_back(f, n * t / parts, n * (t + 1) / parts);
+  for (auto& x : th) x.join();
+}
+
 struct StreamRec {
   bool open = false;
   bool clean = true;      // device windows of the slot are all empty
@@ -48,7 +89,7 @@ struct StreamRec {
   bool eos_pending = false;
   std::vector<Piece> pieces;
   size_t pending = 0;
-  std::vector<oasm_hit> ready;  // decided hits; [head, end) not yet returned
+  HitVec ready;                 // decided hits; [head, end) not yet returned
   size_t head = 0;
   std::vector<size_t> runs;     // starts of canonically sorted runs in `ready`
 };
@@ -733,16 +774,51 @@ int run_step_once(oasm_ctx* ctx, StepPlan& pl, const WorkItem* d_items, const Re
       ctx->h_out_cap = n;
     }
     CK(cudaMemcpy(ctx->h_out, ctx->out_sorted.p, n * sizeof(DevHit), cudaMemcpyDeviceToHost));
-    // sorted by work item first: one contiguous, already canonical run per stream
+    // sorted by work item first: one contiguous, already canonical run per
+    // stream.  Run starts are found and the runs copied into the streams'
+    // queues on several host threads when the output is large.
     const oasm_hit* recs = reinterpret_cast<const oasm_hit*>(ctx->h_out);
-    for (size_t i = 0; i < n;) {
-      size_t j = i + 1;
-      while (j < n && recs[j].stream_id == recs[i].stream_id) ++j;
-      StreamRec& sr = ctx->streams[recs[i].stream_id];
-      sr.runs.push_back(sr.ready.size());
-      sr.ready.insert(sr.ready.end(), recs + i, recs + j);
-      i = j;
+    std::vector<size_t> starts;
+    {
+      std::mutex mu;
+      std::vector<std::pair<size_t, std::vector<size_t>>> found;
+      parallel_parts(n, size_t(1) << 20, [&](size_t lo, size_t hi) {
+        std::vector<size_t> v;
+        for (size_t i = lo; i < hi; ++i)
+          if (i == 0 || recs[i].stream_id != recs[i - 1].stream_id) v.push_back(i);
+        std::lock_guard<std::mutex> g(mu);
+        found.emplace_back(lo, std::move(v));
+      });
+      std::sort(found.begin(), found.end(),
+                [](const auto& a, const auto& b) { return a.first < b.first; });
+      for (auto& f : found) starts.insert(starts.end(), f.second.begin(), f.second.end());
     }
+    const size_t nr = starts.size();
+    std::vector<oasm_hit*> dst(nr);
+    for (size_t r = 0; r < nr; ++r) {
+      const size_t b = starts[r], e = (r + 1 < nr) ? starts[r + 1] : n;
+      StreamRec& sr = ctx->streams[recs[b].stream_id];
+      const size_t old = sr.ready.size();
+      sr.runs.push_back(old);
+      sr.ready.resize(old + (e - b));
+      dst[r] = sr.ready.data() + old;
+    }
+    // copy the runs in parts of about equal record counts
+    const size_t T = std::max<size_t>(1, std::min<size_t>(16, n >> 20));
+    std::vector<size_t> cut(T + 1, nr);
+    cut[0] = 0;
+    for (size_t t = 1, r = 0; t < T; ++t) {
+      const size_t want = n * t / T;
+      while (r < nr && starts[r] < want) ++r;
+      cut[t] = r;
+    }
+    parallel_parts(T, 1, [&](size_t t0, size_t t1) {
+      for (size_t t = t0; t < t1; ++t)
+        for (size_t r = cut[t]; r < cut[t + 1]; ++r) {
+          const size_t b = starts[r], e = (r + 1 < nr) ? starts[r + 1] : n;
+          memcpy(dst[r], recs + b, (e - b) * sizeof(oasm_hit));
+        }
+    });
   }
   return OASM_OK;
 }
@@ -1203,6 +1279,20 @@ int oasm_step(oasm_ctx* ctx) {
   return run_step(ctx);
 }
 
+// Merges the canonically sorted runs that several steps left in a stream's
+// queue into one run.
+static void merge_runs(StreamRec& s) {
+  if (s.runs.size() <= 1) return;
+  size_t lo = s.head;
+  for (size_t r = 1; r < s.runs.size(); ++r) {
+    const size_t mid = std::max(s.runs[r], lo);
+    const size_t hi = (r + 1 < s.runs.size()) ? s.runs[r + 1] : s.ready.size();
+    std::inplace_merge(s.ready.begin() + lo, s.ready.begin() + mid, s.ready.begin() + hi,
+                       canon_less);
+  }
+  s.runs.assign(1, s.head);
+}
+
 int oasm_flush(oasm_ctx* ctx, uint32_t sid, int end_of_stream, oasm_hit* out, size_t cap,
                size_t* n_out) {
   int rc = check_sid(ctx, sid);
@@ -1214,16 +1304,7 @@ int oasm_flush(oasm_ctx* ctx, uint32_t sid, int end_of_stream, oasm_hit* out, si
     if ((rc = run_step(ctx))) return rc;
   }
   StreamRec& s = ctx->streams[sid];
-  if (s.runs.size() > 1) {  // merge the sorted runs of several steps
-    size_t lo = s.head;
-    for (size_t r = 1; r < s.runs.size(); ++r) {
-      const size_t mid = std::max(s.runs[r], lo);
-      const size_t hi = (r + 1 < s.runs.size()) ? s.runs[r + 1] : s.ready.size();
-      std::inplace_merge(s.ready.begin() + lo, s.ready.begin() + mid, s.ready.begin() + hi,
-                         canon_less);
-    }
-    s.runs.assign(1, s.head);
-  }
+  merge_runs(s);
   const size_t avail = s.ready.size() - s.head;
   const size_t n = std::min(cap, avail);
   if (n && !out) return fail(ctx, OASM_EINVAL, "null output array");
@@ -1242,25 +1323,58 @@ int oasm_flush(oasm_ctx* ctx, uint32_t sid, int end_of_stream, oasm_hit* out, si
 int oasm_drain(oasm_ctx* ctx, oasm_hit* out, size_t cap, size_t* n_out) {
   if (!ctx) return OASM_EINVAL;
   if (n_out) *n_out = 0;
+  // plan: streams in id order, each stream's queue already one canonical run
+  struct Copy {
+    uint32_t sid;
+    size_t off, n;
+  };
+  std::vector<Copy> plan;
   size_t got = 0;
+  bool trunc = false;
   for (uint32_t sid = 0; sid < ctx->streams.size(); ++sid) {
     StreamRec& s = ctx->streams[sid];
     if (!s.open || s.head == s.ready.size()) continue;
     if (got == cap) {
-      if (n_out) *n_out = got;
-      return OASM_ETRUNC;
+      trunc = true;
+      break;
     }
-    size_t n = 0;
-    const int rc = oasm_flush(ctx, sid, 0, out ? out + got : nullptr, cap - got, &n);
-    got += n;
-    if (rc == OASM_ETRUNC) {
-      if (n_out) *n_out = got;
-      return OASM_ETRUNC;
+    merge_runs(s);
+    const size_t avail = s.ready.size() - s.head;
+    const size_t take = std::min(avail, cap - got);
+    plan.push_back(Copy{sid, got, take});
+    got += take;
+    if (take < avail) {
+      trunc = true;
+      break;
     }
-    if (rc) return rc;
+  }
+  if (got && !out) return fail(ctx, OASM_EINVAL, "null output array");
+  // copy in parts of about equal record counts on several host threads
+  const size_t T = std::max<size_t>(1, std::min<size_t>(16, got >> 20));
+  std::vector<size_t> cut(T + 1, plan.size());
+  cut[0] = 0;
+  for (size_t t = 1, c = 0; t < T; ++t) {
+    while (c < plan.size() && plan[c].off < got * t / T) ++c;
+    cut[t] = c;
+  }
+  parallel_parts(T, 1, [&](size_t t0, size_t t1) {
+    for (size_t t = t0; t < t1; ++t)
+      for (size_t c = cut[t]; c < cut[t + 1]; ++c) {
+        const StreamRec& s = ctx->streams[plan[c].sid];
+        memcpy(out + plan[c].off, s.ready.data() + s.head, plan[c].n * sizeof(oasm_hit));
+      }
+  });
+  for (const Copy& c : plan) {
+    StreamRec& s = ctx->streams[c.sid];
+    s.head += c.n;
+    if (s.head == s.ready.size()) {
+      s.ready.clear();
+      s.runs.clear();
+      s.head = 0;
+    }
   }
   if (n_out) *n_out = got;
-  return OASM_OK;
+  return trunc ? OASM_ETRUNC : OASM_OK;
 }
 
 int oasm_ready(oasm_ctx* ctx, uint32_t sid, size_t* n) {
