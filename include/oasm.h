@@ -101,6 +101,10 @@ typedef struct {
                                   automaton scan where a class has >= 32 of them */
     int32_t graphs;            /* 1: launch each step as a captured CUDA graph,
                                   updated in place while its shape repeats */
+    uint32_t groups_per_warp;  /* lane groups (32 patterns each) a scan warp runs
+                                  together in one-word classes: 1 or 2; 0 = the
+                                  tuned value (1 until oasm_autotune picks) */
+    uint32_t reserved;         /* must be 0 */
 } oasm_config;
 
 /* One occurrence added to S (or, for the raw outputs, one hit/end). */

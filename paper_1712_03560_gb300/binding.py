@@ -55,7 +55,8 @@ class oasm_config(ctypes.Structure):
                 ("mem_budget", ctypes.c_uint64), ("region_bytes", ctypes.c_uint32),
                 ("tile_warps", ctypes.c_uint32), ("timing", ctypes.c_int32),
                 ("flush_timeout_ms", ctypes.c_uint32), ("cuda_stream", ctypes.c_void_p),
-                ("myers_only", ctypes.c_int32), ("graphs", ctypes.c_int32)]
+                ("myers_only", ctypes.c_int32), ("graphs", ctypes.c_int32),
+                ("groups_per_warp", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
 class oasm_hit(ctypes.Structure):

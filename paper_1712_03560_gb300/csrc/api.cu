@@ -107,6 +107,7 @@ struct Bucket {
   int max_nseg = 1;
   int warps = 8;          // warps per scan block
   int chunk = 1024;       // text bytes per TMA buffer (dictionary mapping)
+  int gpw = 1;            // lane groups per warp (dictionary mapping, W = 1)
   double region_scale = 1.0;
   int kmax = 0;
   int ov_max = 1;
@@ -485,13 +486,23 @@ StepParams make_params(oasm_ctx* ctx, const WorkItem* d_items, uint32_t n_items,
 }
 
 // Region length (symbols of reported ends per warp) for a bucket.
+// Lane groups per warp for a bucket: the configured value where the kernel
+// has that form (one-word class, dictionary mapping), else the tuned one.
+int bucket_gpw(const oasm_ctx* ctx, const Bucket& b) {
+  if (b.W != 1 || b.max_nseg != 1) return 1;
+  const uint32_t c = ctx->cfg.groups_per_warp;
+  return c == 1 || c == 2 ? int(c) : b.gpw;
+}
+
 int64_t region_len(oasm_ctx* ctx, const Bucket& b, int64_t total_ends) {
   if (ctx->cfg.region_bytes) {
     int64_t r = int64_t(ctx->cfg.region_bytes) * b.max_nseg;
     return std::max<int64_t>(16 * b.max_nseg, (r + 15) & ~int64_t(15));
   }
   const double target_warps = double(ctx->num_sms) * 48.0 * 4.0;
-  double r = double(total_ends) * double(b.groups.size()) / target_warps * b.region_scale;
+  const int gpw = bucket_gpw(ctx, b);
+  const double warps_per_region = double((b.groups.size() + gpw - 1) / gpw);
+  double r = double(total_ends) * warps_per_region / target_warps * b.region_scale;
   const double lane_min = std::max(64.0, 4.0 * b.ov_max);
   r = std::max(r, lane_min * b.max_nseg);
   r = std::min(r, double(int64_t(1) << 24));
@@ -626,6 +637,7 @@ int enqueue_step(oasm_ctx* ctx, StepPlan& pl, const WorkItem* d_items, const Reg
     a.dict = b.max_nseg == 1 ? 1 : 0;
     a.chunk = b.chunk;
     a.algo = b.algo;
+    a.gpw = bucket_gpw(ctx, b);
     a.items = d_items;
     a.arena = ctx->arena.p;
     a.cand = ctx->cand.p;
@@ -1020,6 +1032,10 @@ int oasm_create(const uint8_t* const* pat, const uint32_t* len, const uint32_t* 
   if (ru.replace < 0 || ru.replace > 2 || ru.order < 0 || ru.order > 1 || ru.acc < 0 ||
       ru.acc > 1 || ru.cmp < 0 || ru.cmp > 1 || ru.output < 0 || ru.output > 2) {
     g_create_err = "rules field out of range";
+    return OASM_EINVAL;
+  }
+  if (cfg && (cfg->groups_per_warp > 2 || cfg->reserved != 0)) {
+    g_create_err = "config: groups_per_warp must be 0, 1 or 2 and reserved 0";
     return OASM_EINVAL;
   }
   oasm_ctx* ctx = new oasm_ctx();
@@ -1493,12 +1509,17 @@ int oasm_autotune(oasm_ctx* ctx, const uint8_t* dsample, size_t n, char* report,
     const bool dict = b.max_nseg == 1;
     std::string trials;
     // times one scan launch of the sample for the bucket's current settings
-    auto time_cfg = [&](int wo, int co, double so, float* out_ms) -> int {
-      if (scan_smem_bytes(b.W, wo, dict ? co : 0) > size_t(max_smem)) {
+    // two groups per warp exist for one-word classes in the dictionary mapping;
+    // a configured value is kept
+    const int g_lo = bucket_gpw(ctx, b) == 2 && ctx->cfg.groups_per_warp ? 2 : 1;
+    const int g_hi = (dict && b.W == 1 && ctx->cfg.groups_per_warp != 1) ? 2 : 1;
+    auto time_cfg = [&](int go, int wo, int co, double so, float* out_ms) -> int {
+      if (scan_smem_bytes(b.W, wo, dict ? co : 0, go) > size_t(max_smem)) {
         *out_ms = 1e30f;
         return OASM_OK;
       }
       b.region_scale = so;
+      b.gpw = go;
       const int64_t R = region_len(ctx, b, int64_t(n));
       std::vector<Region> regs;
       for (int64_t a0 = 0; a0 < int64_t(n); a0 += R)
@@ -1523,6 +1544,7 @@ int oasm_autotune(oasm_ctx* ctx, const uint8_t* dsample, size_t n, char* report,
       a.dict = dict ? 1 : 0;
       a.chunk = co;
       a.algo = b.algo;
+      a.gpw = go;
       a.items = reinterpret_cast<const WorkItem*>(ctx->upload.p);
       a.arena = ctx->arena.p;
       a.cand = ctx->cand.p;
@@ -1541,38 +1563,40 @@ int oasm_autotune(oasm_ctx* ctx, const uint8_t* dsample, size_t n, char* report,
       }
       ctx->st.launches += 3;
       char tb[96];
-      snprintf(tb, sizeof tb, "%s[%d,%d,%.2f,%.4f]", trials.empty() ? "" : ",", wo, co, so,
+      snprintf(tb, sizeof tb, "%s[%d,%d,%d,%.2f,%.4f]", trials.empty() ? "" : ",", go, wo, co, so,
                double(tbest));
       trials += tb;
       *out_ms = tbest;
       return OASM_OK;
     };
     float best = 1e30f;
-    int bw = b.warps, bc = b.chunk;
+    int bg = 1, bw = b.warps, bc = b.chunk;
     double bs = 1.0;
-    // phase 1: warps per block at the default geometry
-    for (int wo : warp_opts) {
-      float ms;
-      if ((rc = time_cfg(wo, dict ? 1024 : 512, 1.0, &ms))) return rc;
-      if (ms < best) { best = ms; bw = wo; bc = dict ? 1024 : 512; bs = 1.0; }
-    }
+    // phase 1: lane groups per warp x warps per block at the default geometry
+    for (int go = g_lo; go <= g_hi; ++go)
+      for (int wo : warp_opts) {
+        float ms;
+        if ((rc = time_cfg(go, wo, dict ? 1024 : 512, 1.0, &ms))) return rc;
+        if (ms < best) { best = ms; bg = go; bw = wo; bc = dict ? 1024 : 512; bs = 1.0; }
+      }
     // phase 2: text buffer size x region length for the winner
     for (int co : chunk_opts) {
       if (!dict && co != chunk_opts[0]) continue;  // the segment mapping stages no text
       for (double so : scale_opts) {
         float ms;
-        if ((rc = time_cfg(bw, co, so, &ms))) return rc;
+        if ((rc = time_cfg(bg, bw, co, so, &ms))) return rc;
         if (ms < best) { best = ms; bc = co; bs = so; }
       }
     }
+    b.gpw = bg;
     b.warps = bw;
     b.chunk = bc;
     b.region_scale = bs;
     char buf[256];
     snprintf(buf, sizeof buf,
-             "%s{\"W\":%d,\"algo\":%d,\"groups\":%zu,\"dict\":%d,\"warps\":%d,"
+             "%s{\"W\":%d,\"algo\":%d,\"groups\":%zu,\"dict\":%d,\"gpw\":%d,\"warps\":%d,"
              "\"chunk\":%d,\"region_scale\":%.2f,\"ms\":%.4f,\"trials\":[",
-             bi ? "," : "", b.W, b.algo, b.groups.size(), dict ? 1 : 0, bw, bc, bs,
+             bi ? "," : "", b.W, b.algo, b.groups.size(), dict ? 1 : 0, bg, bw, bc, bs,
              double(best));
     js += buf;
     js += trials;

@@ -19,6 +19,8 @@ struct ScanArgs {
   int32_t dict;              // 1: dictionary mapping (one pattern per lane, nseg = 1)
   int32_t chunk;             // text bytes per TMA buffer (dictionary mapping)
   int32_t algo;              // 0: Myers/Hyyro bit-vectors; 1 + K: automaton for K <= 2 (W = 1)
+  int32_t gpw;               // lane groups per warp: 1, or 2 (dictionary mapping, W = 1)
+  int32_t pad;
   const WorkItem* items;
   const uint8_t* arena;
   Candidate* cand;
@@ -26,10 +28,11 @@ struct ScanArgs {
   StepCounters* ctr;
 };
 
-// Shared memory of one scan block: the group's Peq table (256 rows of W x 32
-// words), two text buffers per warp (dictionary mapping) and the mbarriers.
-inline size_t scan_smem_bytes(int W, int warps, int chunk) {
-  return size_t(256) * 128 * W + size_t(warps) * 2 * chunk + size_t(1 + 2 * warps) * 8;
+// Shared memory of one scan block: the Peq tables of its gpw lane groups (256
+// rows of W x 32 words each), two text buffers per warp (dictionary mapping)
+// and the mbarriers.
+inline size_t scan_smem_bytes(int W, int warps, int chunk, int gpw = 1) {
+  return size_t(256) * 128 * W * gpw + size_t(warps) * 2 * chunk + size_t(1 + 2 * warps) * 8;
 }
 
 cudaError_t launch_scan(const ScanArgs& a, cudaStream_t s);

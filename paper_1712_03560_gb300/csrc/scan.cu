@@ -262,13 +262,15 @@ struct LaneSetup {
   int t_lo, t_hi;   // report window in steps
 };
 
+// ov: warm-up symbols before the region (at least the group's l_p + K - 1).
 __device__ __forceinline__ LaneSetup lane_setup(const ScanArgs& A, const LaneGroup& G,
-                                                const Region& R, const WorkItem& wi, int lane) {
+                                                const Region& R, const WorkItem& wi, int lane,
+                                                int ov) {
   LaneSetup L;
   L.pid = G.pat[lane];
   L.m = G.m[lane];
   L.K = G.K[lane];
-  const int nseg = G.nseg, ov = G.ov;
+  const int nseg = G.nseg;
   // lane sub-segment [a, b) of reported ends; Ls is a multiple of 16 so every
   // lane of the warp shares the same vector alignment and trip count
   const int64_t len = R.b - R.a;
@@ -290,17 +292,28 @@ __device__ __forceinline__ LaneSetup lane_setup(const ScanArgs& A, const LaneGro
   return L;
 }
 
-// ------------------------------------------------- dictionary mapping
-template <int W>
-__device__ void scan_dict(const ScanArgs& A, const char* peq, uint8_t* tbuf, uint32_t bar0,
-                          const LaneGroup& G, const Region& R, const WorkItem& wi, int lane) {
-  const LaneSetup L = lane_setup(A, G, R, wi, lane);
+// The lane groups a warp scans together (dictionary mapping): GPW groups share
+// the warp's region, its text buffer and each step's symbol and Peq address;
+// their tables sit kPeqBytes apart in shared memory.  A group past the end of
+// the class (odd count) is idle: no lane reports.
+template <int GPW>
+struct GroupSet {
+  const LaneGroup* g[GPW];
+  bool valid[GPW];
+  int ov;  // common warm-up: the largest over the valid groups
+};
+
+// Streams the warp's text through its double buffer and calls body(tv, v)
+// for each 16-symbol block v (tv = the block's 16 symbols in shared memory).
+// Returns false when a bounded wait for a TMA copy ran out (the warp has then
+// raised the timeout bit and waited for its copies in flight).
+template <class Body>
+__device__ __forceinline__ bool stream_blocks(const ScanArgs& A, uint8_t* tbuf, uint32_t bar0,
+                                              const uint8_t* src, int nbytes, int lane,
+                                              Body&& body) {
   const int CH = A.chunk;
-  const int nbytes = L.nvec * 16;
   const int nchunks = (nbytes + CH - 1) / CH;
-  const uint8_t* src = A.arena + L.ad_al;
   const uint32_t tb = smem_u32(tbuf);
-  const uint32_t lane_off = uint32_t(lane) * 4u;
   if (lane == 0) {
     for (int c = 0; c < 2 && c < nchunks; ++c) {
       const uint32_t n = uint32_t(min(CH, nbytes - c * CH));
@@ -308,17 +321,7 @@ __device__ void scan_dict(const ScanArgs& A, const char* peq, uint8_t* tbuf, uin
       tma_load_1d(tb + c * CH, src + size_t(c) * CH, n, bar0 + 8 * c);
     }
   }
-  uint32_t Pv[W], Mv[W];
-#pragma unroll
-  for (int w = 0; w < W; ++w) {
-    Pv[w] = 0xffffffffu;
-    Mv[w] = 0u;
-  }
-  int s = L.m - L.K - 1;
-  Emitter em;
   int dead_at = -1;
-  bool record = false;  // warp-uniform: record every step instead of count + replay
-  int blocks = 0, replays = 0;
   for (int c = 0; c < nchunks; ++c) {
     const int buf = c & 1;
     const bool ok = mbar_wait(bar0 + 8 * buf, uint32_t((c >> 1) & 1));
@@ -328,66 +331,7 @@ __device__ void scan_dict(const ScanArgs& A, const char* peq, uint8_t* tbuf, uin
     }
     const uint8_t* t = tbuf + buf * CH;
     const int nv = min(CH, nbytes - c * CH) >> 4;
-    for (int vv = 0; vv < nv; ++vv) {
-      const int v = c * (CH >> 4) + vv;
-      const uint8_t* tv = t + vv * 16;
-      if (record) {
-        uint32_t cm = 0;
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const uint32_t sym = tv[j];
-          uint32_t eq[W];
-          load_eq<W>(peq, mad_lo(sym, 128u * W, lane_off), eq);
-          search_step<W>(Pv, Mv, s, eq);
-          cm = __funnelshift_l(uint32_t(s), cm, 1);
-        }
-        const uint32_t c16 = cm & block_mask(L.t_lo, L.t_hi, v);
-        if (__any_sync(kFull, c16 != 0)) em.put(A, lane, c16, L.spos + 16 * v, R.wi, L.pid, wi.base_pos);
-        continue;
-      }
-      uint32_t Pv0[W], Mv0[W];
-#pragma unroll
-      for (int w = 0; w < W; ++w) {
-        Pv0[w] = Pv[w];
-        Mv0[w] = Mv[w];
-      }
-      const int s0 = s;
-      int cnt = 0;
-#pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const uint32_t sym = tv[j];
-        uint32_t eq[W];
-        load_eq<W>(peq, mad_lo(sym, 128u * W, lane_off), eq);
-        search_step<W>(Pv, Mv, s, eq);
-        cnt = add_top(cnt, uint32_t(s));  // counts steps with s < 0
-      }
-      const uint32_t vm = block_mask(L.t_lo, L.t_hi, v);
-      if (__any_sync(kFull, cnt != 0 && vm != 0)) {
-        // rare: replay the block from its saved state, recording each step
-#pragma unroll
-        for (int w = 0; w < W; ++w) {
-          Pv[w] = Pv0[w];
-          Mv[w] = Mv0[w];
-        }
-        s = s0;
-        uint32_t cm = 0;
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const uint32_t sym = tv[j];
-          uint32_t eq[W];
-          load_eq<W>(peq, mad_lo(sym, 128u * W, lane_off), eq);
-          search_step<W>(Pv, Mv, s, eq);
-          cm = __funnelshift_l(uint32_t(s), cm, 1);
-        }
-        em.put(A, lane, cm & vm, L.spos + 16 * v, R.wi, L.pid, wi.base_pos);
-        ++replays;
-      }
-      // candidates dense enough that replays cost more than recording: switch
-      if (++blocks == 64) {
-        record = replays > 3;
-        blocks = replays = 0;
-      }
-    }
+    for (int vv = 0; vv < nv; ++vv) body(t + vv * 16, c * (CH >> 4) + vv);
     __syncwarp();
     if (lane == 0 && c + 2 < nchunks) {
       fence_proxy_async();  // our reads of this buffer precede the async write
@@ -404,9 +348,121 @@ __device__ void scan_dict(const ScanArgs& A, const char* peq, uint8_t* tbuf, uin
         mbar_wait(bar0 + 8 * (c & 1), uint32_t((c >> 1) & 1));
     }
     __syncwarp();
-    return;
+    return false;
   }
-  em.finish(A, lane);
+  return true;
+}
+
+// ------------------------------------------------- dictionary mapping
+template <int W, int GPW>
+__device__ void scan_dict(const ScanArgs& A, const char* peq, uint8_t* tbuf, uint32_t bar0,
+                          const GroupSet<GPW>& GS, const Region& R, const WorkItem& wi, int lane) {
+  constexpr uint32_t kPeqBytes = 256u * 128u * W;
+  LaneSetup L[GPW];
+#pragma unroll
+  for (int v = 0; v < GPW; ++v) {
+    L[v] = lane_setup(A, *GS.g[v], R, wi, lane, GS.ov);
+    if (!GS.valid[v]) L[v].pid = -1, L[v].t_lo = L[v].t_hi = 0;
+  }
+  const uint32_t lane_off = uint32_t(lane) * 4u;
+  uint32_t Pv[GPW][W], Mv[GPW][W];
+  int s[GPW];
+#pragma unroll
+  for (int v = 0; v < GPW; ++v) {
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+      Pv[v][w] = 0xffffffffu;
+      Mv[v][w] = 0u;
+    }
+    s[v] = L[v].m - L[v].K - 1;
+  }
+  Emitter em;
+  bool record = false;  // warp-uniform: record every step instead of count + replay
+  int blocks = 0, replays = 0;
+  auto step_all = [&](uint32_t sym) {
+    const uint32_t addr = mad_lo(sym, 128u * W, lane_off);
+#pragma unroll
+    for (int v = 0; v < GPW; ++v) {
+      uint32_t eq[W];
+      load_eq<W>(peq + v * kPeqBytes, addr, eq);
+      search_step<W>(Pv[v], Mv[v], s[v], eq);
+    }
+  };
+  const bool ok = stream_blocks(A, tbuf, bar0, A.arena + L[0].ad_al, L[0].nvec * 16, lane,
+                                [&](const uint8_t* tv, int v) {
+    uint32_t vm[GPW];
+#pragma unroll
+    for (int g = 0; g < GPW; ++g) vm[g] = block_mask(L[g].t_lo, L[g].t_hi, v);
+    uint32_t cm[GPW];
+#pragma unroll
+    for (int g = 0; g < GPW; ++g) cm[g] = 0u;
+    bool emit;
+    if (record) {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        step_all(tv[j]);
+#pragma unroll
+        for (int g = 0; g < GPW; ++g) cm[g] = __funnelshift_l(uint32_t(s[g]), cm[g], 1);
+      }
+      bool any = false;
+#pragma unroll
+      for (int g = 0; g < GPW; ++g) any |= (cm[g] & vm[g]) != 0;
+      emit = __any_sync(kFull, any);
+    } else {
+      uint32_t Pv0[GPW][W], Mv0[GPW][W];
+      int s0[GPW], cnt[GPW];
+#pragma unroll
+      for (int g = 0; g < GPW; ++g) {
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+          Pv0[g][w] = Pv[g][w];
+          Mv0[g][w] = Mv[g][w];
+        }
+        s0[g] = s[g];
+        cnt[g] = 0;
+      }
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        step_all(tv[j]);
+#pragma unroll
+        for (int g = 0; g < GPW; ++g) cnt[g] = add_top(cnt[g], uint32_t(s[g]));  // steps with s < 0
+      }
+      bool any = false;
+#pragma unroll
+      for (int g = 0; g < GPW; ++g) any |= cnt[g] != 0 && vm[g] != 0;
+      emit = __any_sync(kFull, any);
+      if (emit) {
+        // rare: replay the block from its saved state, recording each step
+#pragma unroll
+        for (int g = 0; g < GPW; ++g) {
+#pragma unroll
+          for (int w = 0; w < W; ++w) {
+            Pv[g][w] = Pv0[g][w];
+            Mv[g][w] = Mv0[g][w];
+          }
+          s[g] = s0[g];
+        }
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          step_all(tv[j]);
+#pragma unroll
+          for (int g = 0; g < GPW; ++g) cm[g] = __funnelshift_l(uint32_t(s[g]), cm[g], 1);
+        }
+        ++replays;
+      }
+      // candidates dense enough that replays cost more than recording: switch
+      if (++blocks == 64) {
+        record = replays > 3;
+        blocks = replays = 0;
+      }
+    }
+    if (emit) {
+#pragma unroll
+      for (int g = 0; g < GPW; ++g)
+        em.put(A, lane, cm[g] & vm[g], L[0].spos + 16 * v, R.wi, L[g].pid, wi.base_pos);
+    }
+  });
+  if (ok) em.finish(A, lane);
 }
 
 // ---------------------------------- dictionary mapping, NFA for K <= 2
@@ -437,6 +493,21 @@ __device__ __forceinline__ void nfa_step(uint32_t (&R)[KL + 1], uint32_t B, uint
   }
 }
 
+// The same step for lanes that hold one pattern in bits [0, m): every R_j is
+// zero below bit 0 trivially, so (x << 1) | E equals x * 2 + E (no carry
+// reaches bit 0) and each shift-or is one multiply-add.
+template <int KL>
+__device__ __forceinline__ void nfa_step_single(uint32_t (&R)[KL + 1], uint32_t B, uint32_t E) {
+  uint32_t prev_old = R[0];
+  R[0] = mad_lo(R[0], 2u, E) & B;
+#pragma unroll
+  for (int j = 1; j <= KL; ++j) {
+    const uint32_t old = R[j];
+    R[j] = (mad_lo(old, 2u, E) & B) | prev_old | mad_lo(prev_old | R[j - 1], 2u, E);
+    prev_old = old;
+  }
+}
+
 // Appends this step's candidate bit of every slot to the slots' step masks.
 __device__ __forceinline__ void record_slots(uint32_t (&cm)[kMaxSlots], uint32_t r,
                                              const uint32_t (&sh)[kMaxSlots], int ns) {
@@ -445,135 +516,139 @@ __device__ __forceinline__ void record_slots(uint32_t (&cm)[kMaxSlots], uint32_t
     if (q < ns) cm[q] = __funnelshift_l(r << sh[q], cm[q], 1);
 }
 
-template <int KL>
+template <int KL, bool SINGLE, int GPW>
 __device__ void scan_dict_nfa(const ScanArgs& A, const char* peq, uint8_t* tbuf, uint32_t bar0,
-                              const LaneGroup& G, const Region& R, const WorkItem& wi, int lane) {
-  const LaneSetup L = lane_setup(A, G, R, wi, lane);
-  const int CH = A.chunk;
-  const int nbytes = L.nvec * 16;
-  const int nchunks = (nbytes + CH - 1) / CH;
-  const uint8_t* src = A.arena + L.ad_al;
-  const uint32_t tb = smem_u32(tbuf);
+                              const GroupSet<GPW>& GS, const Region& R, const WorkItem& wi,
+                              int lane) {
+  constexpr uint32_t kPeqBytes = 256u * 128u;
+  LaneSetup L[GPW];
+  int ns[GPW];
+  uint32_t E[GPW], LAST[GPW];
+  uint32_t Rs[GPW][KL + 1];
+#pragma unroll
+  for (int g = 0; g < GPW; ++g) {
+    const LaneGroup& G = *GS.g[g];
+    L[g] = lane_setup(A, G, R, wi, lane, GS.ov);
+    if (!GS.valid[g]) L[g].pid = -1, L[g].t_lo = L[g].t_hi = 0;
+    ns[g] = G.nslot;  // block-uniform
+    E[g] = (L[g].pid < 0) ? 0u : G.first[lane];
+    LAST[g] = (L[g].pid < 0) ? 0u : G.last[lane];
+    // before the first symbol, prefixes of up to j symbols are within j edits
+    // (deletions): bits f..f+j-1 of R_j for every slot (slots are > K bits wide)
+#pragma unroll
+    for (int j = 0; j <= KL; ++j) Rs[g][j] = E[g] * ((1u << j) - 1u);
+  }
   const uint32_t lane_off = uint32_t(lane) * 4u;
-  if (lane == 0) {
-    for (int c = 0; c < 2 && c < nchunks; ++c) {
-      const uint32_t n = uint32_t(min(CH, nbytes - c * CH));
-      mbar_expect_tx(bar0 + 8 * c, n);
-      tma_load_1d(tb + c * CH, src + size_t(c) * CH, n, bar0 + 8 * c);
+  auto step_all = [&](uint32_t sym) {
+    const uint32_t addr = mad_lo(sym, 128u, lane_off);
+#pragma unroll
+    for (int g = 0; g < GPW; ++g) {
+      const uint32_t B = *reinterpret_cast<const uint32_t*>(peq + g * kPeqBytes + addr);
+      if (SINGLE)
+        nfa_step_single<KL>(Rs[g], B, E[g]);
+      else
+        nfa_step<KL>(Rs[g], B, E[g]);
     }
-  }
-  const int ns = G.nslot;  // block-uniform
-  const uint32_t E = (L.pid < 0) ? 0u : G.first[lane];
-  const uint32_t LAST = (L.pid < 0) ? 0u : G.last[lane];
-  int pids[kMaxSlots];
-  uint32_t sh[kMaxSlots];
+  };
+  // per-slot step masks of group g, recorded while replaying or recording
+  auto record_group = [&](uint32_t (&cm)[kMaxSlots], int g) {
+    const LaneGroup& G = *GS.g[g];
+    uint32_t sh[kMaxSlots];
 #pragma unroll
-  for (int q = 0; q < kMaxSlots; ++q) {
-    pids[q] = (q == 0) ? L.pid : (L.pid < 0 ? -1 : G.xpat[q > 0 ? q - 1 : 0][lane]);
-    sh[q] = 31u - G.lastbit[q][lane];
-  }
-  // before the first symbol, prefixes of up to j symbols are within j edits
-  // (deletions): bits f..f+j-1 of R_j for every slot (slots are > K bits wide)
-  uint32_t Rs[KL + 1];
-#pragma unroll
-  for (int j = 0; j <= KL; ++j) Rs[j] = E * ((1u << j) - 1u);
+    for (int q = 0; q < kMaxSlots; ++q) sh[q] = 31u - G.lastbit[q][lane];
+    record_slots(cm, Rs[g][KL], sh, ns[g]);
+  };
   Emitter em;
-  int dead_at = -1;
   bool record = false;
   int blocks = 0, replays = 0;
-  for (int c = 0; c < nchunks; ++c) {
-    const int buf = c & 1;
-    const bool ok = mbar_wait(bar0 + 8 * buf, uint32_t((c >> 1) & 1));
-    if (__any_sync(kFull, !ok)) {
-      dead_at = c;
-      break;
-    }
-    const uint8_t* t = tbuf + buf * CH;
-    const int nv = min(CH, nbytes - c * CH) >> 4;
-    for (int vv = 0; vv < nv; ++vv) {
-      const int v = c * (CH >> 4) + vv;
-      const uint8_t* tv = t + vv * 16;
-      uint32_t cm[kMaxSlots];
+  const bool ok = stream_blocks(A, tbuf, bar0, A.arena + L[0].ad_al, L[0].nvec * 16, lane,
+                                [&](const uint8_t* tv, int v) {
+    uint32_t vm[GPW];
 #pragma unroll
-      for (int q = 0; q < kMaxSlots; ++q) cm[q] = 0u;
-      bool emit = false;
-      const uint32_t vm = block_mask(L.t_lo, L.t_hi, v);
-      if (record) {
-        uint32_t any = 0;
+    for (int g = 0; g < GPW; ++g) vm[g] = block_mask(L[g].t_lo, L[g].t_hi, v);
+    uint32_t cm[GPW][kMaxSlots];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const uint32_t sym = tv[j];
-          const uint32_t B = *reinterpret_cast<const uint32_t*>(peq + mad_lo(sym, 128u, lane_off));
-          nfa_step<KL>(Rs, B, E);
-          any |= Rs[KL] & LAST;
-          record_slots(cm, Rs[KL], sh, ns);
-        }
-        emit = __any_sync(kFull, any != 0 && vm != 0);
-      } else {
-        uint32_t R0[KL + 1];
+    for (int g = 0; g < GPW; ++g)
 #pragma unroll
-        for (int j = 0; j <= KL; ++j) R0[j] = Rs[j];
-        uint32_t any = 0;
+      for (int q = 0; q < kMaxSlots; ++q) cm[g][q] = 0u;
+    bool emit;
+    if (record) {
+      uint32_t any[GPW];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const uint32_t sym = tv[j];
-          const uint32_t B = *reinterpret_cast<const uint32_t*>(peq + mad_lo(sym, 128u, lane_off));
-          nfa_step<KL>(Rs, B, E);
-          any |= Rs[KL] & LAST;  // some slot reached its full pattern
-        }
-        if (__any_sync(kFull, any != 0 && vm != 0)) {
-          // rare: replay the block from its saved state, recording each step
+      for (int g = 0; g < GPW; ++g) any[g] = 0u;
 #pragma unroll
-          for (int j = 0; j <= KL; ++j) Rs[j] = R0[j];
+      for (int j = 0; j < 16; ++j) {
+        step_all(tv[j]);
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const uint32_t sym = tv[j];
-            const uint32_t B =
-                *reinterpret_cast<const uint32_t*>(peq + mad_lo(sym, 128u, lane_off));
-            nfa_step<KL>(Rs, B, E);
-            record_slots(cm, Rs[KL], sh, ns);
-          }
-          emit = true;
-          ++replays;
-        }
-        if (++blocks == 64) {
-          record = replays > 3;
-          blocks = replays = 0;
+        for (int g = 0; g < GPW; ++g) {
+          any[g] |= Rs[g][KL] & LAST[g];
+          record_group(cm[g], g);
         }
       }
+      bool hit = false;
+#pragma unroll
+      for (int g = 0; g < GPW; ++g) hit |= any[g] != 0 && vm[g] != 0;
+      emit = __any_sync(kFull, hit);
+    } else {
+      uint32_t R0[GPW][KL + 1], any[GPW];
+#pragma unroll
+      for (int g = 0; g < GPW; ++g) {
+#pragma unroll
+        for (int j = 0; j <= KL; ++j) R0[g][j] = Rs[g][j];
+        any[g] = 0u;
+      }
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        step_all(tv[j]);
+#pragma unroll
+        for (int g = 0; g < GPW; ++g) any[g] |= Rs[g][KL] & LAST[g];  // a slot reached its end
+      }
+      bool hit = false;
+#pragma unroll
+      for (int g = 0; g < GPW; ++g) hit |= any[g] != 0 && vm[g] != 0;
+      emit = __any_sync(kFull, hit);
       if (emit) {
+        // rare: replay the block from its saved state, recording each step
 #pragma unroll
-        for (int q = 0; q < kMaxSlots; ++q)
-          if (q < ns)
-            em.put(A, lane, pids[q] >= 0 ? (cm[q] & vm) : 0u, L.spos + 16 * v, R.wi, pids[q],
-                   wi.base_pos);
+        for (int g = 0; g < GPW; ++g)
+#pragma unroll
+          for (int j = 0; j <= KL; ++j) Rs[g][j] = R0[g][j];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          step_all(tv[j]);
+#pragma unroll
+          for (int g = 0; g < GPW; ++g) record_group(cm[g], g);
+        }
+        ++replays;
+      }
+      if (++blocks == 64) {
+        record = replays > 3;
+        blocks = replays = 0;
       }
     }
-    __syncwarp();
-    if (lane == 0 && c + 2 < nchunks) {
-      fence_proxy_async();
-      const uint32_t n = uint32_t(min(CH, nbytes - (c + 2) * CH));
-      mbar_expect_tx(bar0 + 8 * buf, n);
-      tma_load_1d(tb + buf * CH, src + size_t(c + 2) * CH, n, bar0 + 8 * buf);
+    if (emit) {
+#pragma unroll
+      for (int g = 0; g < GPW; ++g) {
+        const LaneGroup& G = *GS.g[g];
+#pragma unroll
+        for (int q = 0; q < kMaxSlots; ++q) {
+          if (q < ns[g]) {
+            const int pid = (q == 0) ? L[g].pid : (L[g].pid < 0 ? -1 : G.xpat[q > 0 ? q - 1 : 0][lane]);
+            em.put(A, lane, pid >= 0 ? (cm[g][q] & vm[g]) : 0u, L[0].spos + 16 * v, R.wi, pid,
+                   wi.base_pos);
+          }
+        }
+      }
     }
-  }
-  if (dead_at >= 0) {
-    if (lane == 0) {
-      atomicOr(&A.ctr->overflow, 1u << kTimeoutBit);
-      for (int c = dead_at; c < dead_at + 2 && c < nchunks; ++c)
-        mbar_wait(bar0 + 8 * (c & 1), uint32_t((c >> 1) & 1));
-    }
-    __syncwarp();
-    return;
-  }
-  em.finish(A, lane);
+  });
+  if (ok) em.finish(A, lane);
 }
 
 // ---------------------------------------------------- segment mapping
 template <int W>
 __device__ void scan_segments(const ScanArgs& A, const char* peq, const LaneGroup& G,
                               const Region& R, const WorkItem& wi, int lane) {
-  const LaneSetup L = lane_setup(A, G, R, wi, lane);
+  const LaneSetup L = lane_setup(A, G, R, wi, lane, G.ov);
   const uint32_t lane_off = uint32_t(lane) * 4u;
   uint32_t Pv[W], Mv[W];
 #pragma unroll
@@ -604,15 +679,19 @@ __device__ void scan_segments(const ScanArgs& A, const char* peq, const LaneGrou
   em.finish(A, lane);
 }
 
-template <int W, bool kDict, int ALG>
+// GPW lane groups per warp (dictionary mapping, W = 1 only): blocks of the
+// grid walk the class's groups GPW at a time.
+template <int W, bool kDict, int ALG, int GPW>
 __global__ void __launch_bounds__(512) scan_kernel(const ScanArgs A) {
   extern __shared__ __align__(128) uint8_t smem[];
   constexpr uint32_t kPeqBytes = 256u * 128u * W;
-  const int g = blockIdx.x % A.n_groups;
-  const int rb = blockIdx.x / A.n_groups;
+  const int ngb = (A.n_groups + GPW - 1) / GPW;
+  const int g0 = (blockIdx.x % ngb) * GPW;
+  const int rb = blockIdx.x / ngb;
+  const int nvalid = min(GPW, A.n_groups - g0);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // layout: Peq | text double buffers (dictionary) | mbarriers
-  uint8_t* tbase = smem + kPeqBytes;
+  // layout: GPW Peq tables | text double buffers (dictionary) | mbarriers
+  uint8_t* tbase = smem + size_t(kPeqBytes) * GPW;
   uint64_t* bars = reinterpret_cast<uint64_t*>(tbase + (kDict ? size_t(A.warps) * 2 * A.chunk : 0));
   const uint32_t bar_peq = smem_u32(bars);
   if (threadIdx.x == 0) mbar_init(bar_peq, 1);
@@ -623,10 +702,13 @@ __global__ void __launch_bounds__(512) scan_kernel(const ScanArgs A) {
   fence_mbar_init();
   __syncthreads();
   if (threadIdx.x == 0) {
-    const uint8_t* src = reinterpret_cast<const uint8_t*>(A.peq) + size_t(g) * kPeqBytes;
-    mbar_expect_tx(bar_peq, kPeqBytes);
-    for (uint32_t o = 0; o < kPeqBytes; o += 32768u)
-      tma_load_1d(smem_u32(smem + o), src + o, min(32768u, kPeqBytes - o), bar_peq);
+    mbar_expect_tx(bar_peq, kPeqBytes * uint32_t(nvalid));
+    for (int v = 0; v < nvalid; ++v) {
+      const uint8_t* src = reinterpret_cast<const uint8_t*>(A.peq) + size_t(g0 + v) * kPeqBytes;
+      for (uint32_t o = 0; o < kPeqBytes; o += 32768u)
+        tma_load_1d(smem_u32(smem + size_t(v) * kPeqBytes + o), src + o,
+                    min(32768u, kPeqBytes - o), bar_peq);
+    }
   }
   const bool peq_ok = mbar_wait(bar_peq, 0);
   if (!peq_ok) {
@@ -635,33 +717,50 @@ __global__ void __launch_bounds__(512) scan_kernel(const ScanArgs A) {
   }
   const int r = rb * A.warps + warp;
   if (r >= A.n_regions) return;  // the whole warp leaves together
-  const LaneGroup& G = A.groups[g];
   const Region R = A.regions[r];
   const WorkItem wi = A.items[R.wi];
   const char* peq = reinterpret_cast<const char*>(smem);
-  if (kDict && ALG > 0)
-    scan_dict_nfa<(ALG > 0 ? ALG - 1 : 0)>(A, peq, tbase + size_t(warp) * 2 * A.chunk,
-                                           smem_u32(bars + 1 + 2 * warp), G, R, wi, lane);
-  else if (kDict)
-    scan_dict<W>(A, peq, tbase + size_t(warp) * 2 * A.chunk, smem_u32(bars + 1 + 2 * warp), G, R,
-                 wi, lane);
-  else
-    scan_segments<W>(A, peq, G, R, wi, lane);
+  if constexpr (kDict) {
+    GroupSet<GPW> GS;
+    GS.ov = 1;
+    bool single = true;  // every valid group holds one pattern per lane
+#pragma unroll
+    for (int v = 0; v < GPW; ++v) {
+      GS.valid[v] = v < nvalid;
+      GS.g[v] = &A.groups[g0 + (GS.valid[v] ? v : 0)];
+      if (GS.valid[v]) {
+        GS.ov = max(GS.ov, GS.g[v]->ov);
+        single = single && GS.g[v]->nslot == 1;
+      }
+    }
+    uint8_t* tb = tbase + size_t(warp) * 2 * A.chunk;
+    const uint32_t bar0 = smem_u32(bars + 1 + 2 * warp);
+    if constexpr (ALG > 0) {
+      if (single)
+        scan_dict_nfa<ALG - 1, true, GPW>(A, peq, tb, bar0, GS, R, wi, lane);
+      else
+        scan_dict_nfa<ALG - 1, false, GPW>(A, peq, tb, bar0, GS, R, wi, lane);
+    } else {
+      scan_dict<W, GPW>(A, peq, tb, bar0, GS, R, wi, lane);
+    }
+  } else {
+    scan_segments<W>(A, peq, A.groups[g0], R, wi, lane);
+  }
 }
 
-template <int W, bool kDict, int ALG = 0>
+template <int W, bool kDict, int ALG = 0, int GPW = 1>
 cudaError_t launch_w(const ScanArgs& a, cudaStream_t st) {
-  const size_t smem = scan_smem_bytes(W, a.warps, kDict ? a.chunk : 0);
+  const size_t smem = scan_smem_bytes(W, a.warps, kDict ? a.chunk : 0, GPW);
   const long long blocks_r = (a.n_regions + a.warps - 1) / a.warps;
-  const long long grid = blocks_r * a.n_groups;
+  const long long grid = blocks_r * ((a.n_groups + GPW - 1) / GPW);
   if (grid <= 0) return cudaSuccess;
-  scan_kernel<W, kDict, ALG><<<unsigned(grid), a.warps * 32, smem, st>>>(a);
+  scan_kernel<W, kDict, ALG, GPW><<<unsigned(grid), a.warps * 32, smem, st>>>(a);
   return cudaGetLastError();
 }
 
-template <int W, bool kDict, int ALG = 0>
+template <int W, bool kDict, int ALG = 0, int GPW = 1>
 cudaError_t allow_smem(int bytes) {
-  return cudaFuncSetAttribute(scan_kernel<W, kDict, ALG>,
+  return cudaFuncSetAttribute(scan_kernel<W, kDict, ALG, GPW>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
@@ -683,11 +782,26 @@ cudaError_t prepare_scan_kernels(int max_smem_bytes) {
   set(allow_smem<1, true, 1>(max_smem_bytes));
   set(allow_smem<1, true, 2>(max_smem_bytes));
   set(allow_smem<1, true, 3>(max_smem_bytes));
+  set(allow_smem<1, true, 0, 2>(max_smem_bytes));
+  set(allow_smem<1, true, 1, 2>(max_smem_bytes));
+  set(allow_smem<1, true, 2, 2>(max_smem_bytes));
+  set(allow_smem<1, true, 3, 2>(max_smem_bytes));
   return e;
 }
 
 cudaError_t launch_scan(const ScanArgs& a, cudaStream_t s) {
   const bool d = a.dict != 0;
+  if (a.gpw == 2) {  // two lane groups per warp: one-word classes, dictionary mapping
+    if (a.W != 1 || !d) return cudaErrorInvalidValue;
+    switch (a.algo) {
+      case 0: return launch_w<1, true, 0, 2>(a, s);
+      case 1: return launch_w<1, true, 1, 2>(a, s);
+      case 2: return launch_w<1, true, 2, 2>(a, s);
+      case 3: return launch_w<1, true, 3, 2>(a, s);
+      default: return cudaErrorInvalidValue;
+    }
+  }
+  if (a.gpw != 1) return cudaErrorInvalidValue;
   if (a.algo > 0) {  // automaton path: one-word patterns, dictionary mapping only
     if (a.W != 1 || !d) return cudaErrorInvalidValue;
     switch (a.algo) {

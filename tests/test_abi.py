@@ -35,8 +35,8 @@ def test_library_exports_every_declared_symbol():
 def test_struct_sizes_match_header():
     assert ctypes.sizeof(B.oasm_hit) == 32
     assert ctypes.sizeof(B.oasm_rules) == 20
-    # oasm_config: 4+4+8+4+4+4+4+8+4+4
-    assert ctypes.sizeof(B.oasm_config) == 48
+    # oasm_config: 4+4+8+4+4+4+4+8+4+4+4+4
+    assert ctypes.sizeof(B.oasm_config) == 56
 
 
 @pytest.mark.parametrize("lens,ks", [([0], [0]), ([129], [1]), ([8], [8]), ([20], [16]), ([], [])])

@@ -280,6 +280,48 @@ def test_autotune_then_search_matches_oracle():
         B.oasm_destroy(ctx)
 
 
+@pytest.mark.parametrize("gpw", [1, 2])
+def test_two_lane_groups_per_warp(gpw):
+    """One-word classes scanned with one or two lane groups per warp: odd
+    group counts (an idle second group), packed and one-pattern automaton
+    groups sharing a warp, and the Myers/Hyyro class, against the oracle, in
+    one feed and across feeds."""
+    rng = np.random.default_rng(900 + gpw)
+    lens, ks = [], []
+    for m in rng.integers(8, 14, size=70).tolist() + rng.integers(20, 33, size=40).tolist():
+        lens.append(m); ks.append(1)
+    for m in rng.integers(20, 33, size=33).tolist():
+        lens.append(m); ks.append(2)
+    for m in rng.integers(12, 33, size=150).tolist():
+        lens.append(m); ks.append(3)
+    pats = [W.DNA[rng.integers(0, 4, size=m)] for m in lens]
+    text = W.DNA[rng.integers(0, 4, size=50000)]
+    for p, k in zip(pats[::2], ks[::2]):
+        for cp in W.edit_copies(rng, p, rng.integers(0, k + 1, size=2), W.DNA):
+            W.plant(rng, text, cp)
+    want = oracle_rows(pats, ks, text)
+    rows, _ = run_gpu(pats, ks, text, cfg={"groups_per_warp": gpw})
+    assert canon(rows) == want
+    split, _ = run_gpu(pats, ks, text, cfg={"groups_per_warp": gpw},
+                       splits=np.sort(rng.integers(0, text.size, size=6)))
+    assert canon(split) == want
+
+
+def test_autotune_picks_groups_per_warp():
+    import json
+
+    import torch
+    wl = W.dictionary_dna(n=1 << 21, n_pat=200, copies=10)
+    ctx = B.oasm_create(wl.patterns, wl.ks)
+    try:
+        rep = json.loads(B.oasm_autotune(ctx, torch.from_numpy(wl.texts[0]).cuda()))
+        for b in rep["buckets"]:
+            assert b["gpw"] in ((1, 2) if b["W"] == 1 and b["dict"] else (1,))
+            assert {t[0] for t in b["trials"]} <= {1, 2}
+    finally:
+        B.oasm_destroy(ctx)
+
+
 def test_int_peak_microbenchmark_runs():
     ops, ms = B.oasm_measure_int_peak(0)
     assert ops > 1e12 and ms > 0
