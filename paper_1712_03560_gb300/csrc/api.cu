@@ -81,6 +81,31 @@ void parallel_parts(size_t n, size_t min_per_part, F f) {
   for (auto& x : th) x.join();
 }
 
+// Copies the pieces (dst, src, records) on up to 16 host threads, each
+// thread taking an equal share of the bytes (pieces are cut where needed).
+struct CopyTask {
+  oasm_hit* dst;
+  const oasm_hit* src;
+  size_t n;
+};
+void parallel_copy(const std::vector<CopyTask>& tasks) {
+  size_t total = 0;
+  for (const CopyTask& t : tasks) total += t.n;
+  const size_t T = std::max<size_t>(1, std::min<size_t>(16, total >> 18));
+  parallel_parts(T, 1, [&](size_t t0, size_t t1) {
+    for (size_t t = t0; t < t1; ++t) {
+      const size_t lo = total * t / T, hi = total * (t + 1) / T;  // this share of records
+      size_t pos = 0;
+      for (const CopyTask& c : tasks) {
+        const size_t a = std::max(lo, pos), b = std::min(hi, pos + c.n);
+        if (a < b) memcpy(c.dst + (a - pos), c.src + (a - pos), (b - a) * sizeof(oasm_hit));
+        pos += c.n;
+        if (pos >= hi) break;
+      }
+    }
+  });
+}
+
 struct StreamRec {
   bool open = false;
   bool clean = true;      // device windows of the slot are all empty
@@ -419,6 +444,12 @@ int build_tables(oasm_ctx* ctx) {
       bk.max_nseg = std::max(bk.max_nseg, nseg);
       bk.groups.push_back(G);
     }
+    // untuned default: the Myers/Hyyro one-word scan runs two groups per warp
+    // (measured faster) unless an odd, small group count would leave much of
+    // the last warp idle; the automaton runs one
+    const size_t ng = bk.groups.size();
+    bk.gpw = (algo == 0 && W == 1 && bk.max_nseg == 1 && ng >= 2 && (ng % 2 == 0 || ng >= 7))
+                 ? 2 : 1;
     CK(cudaMalloc(&bk.d_groups, bk.groups.size() * sizeof(LaneGroup)));
     CK(cudaMemcpy(bk.d_groups, bk.groups.data(), bk.groups.size() * sizeof(LaneGroup),
                   cudaMemcpyHostToDevice));
@@ -815,22 +846,12 @@ int run_step_once(oasm_ctx* ctx, StepPlan& pl, const WorkItem* d_items, const Re
       sr.ready.resize(old + (e - b));
       dst[r] = sr.ready.data() + old;
     }
-    // copy the runs in parts of about equal record counts
-    const size_t T = std::max<size_t>(1, std::min<size_t>(16, n >> 20));
-    std::vector<size_t> cut(T + 1, nr);
-    cut[0] = 0;
-    for (size_t t = 1, r = 0; t < T; ++t) {
-      const size_t want = n * t / T;
-      while (r < nr && starts[r] < want) ++r;
-      cut[t] = r;
+    std::vector<CopyTask> tasks(nr);
+    for (size_t r = 0; r < nr; ++r) {
+      const size_t b = starts[r], e = (r + 1 < nr) ? starts[r + 1] : n;
+      tasks[r] = CopyTask{dst[r], recs + b, e - b};
     }
-    parallel_parts(T, 1, [&](size_t t0, size_t t1) {
-      for (size_t t = t0; t < t1; ++t)
-        for (size_t r = cut[t]; r < cut[t + 1]; ++r) {
-          const size_t b = starts[r], e = (r + 1 < nr) ? starts[r + 1] : n;
-          memcpy(dst[r], recs + b, (e - b) * sizeof(oasm_hit));
-        }
-    });
+    parallel_copy(tasks);
   }
   return OASM_OK;
 }
@@ -1324,7 +1345,7 @@ int oasm_flush(oasm_ctx* ctx, uint32_t sid, int end_of_stream, oasm_hit* out, si
   const size_t avail = s.ready.size() - s.head;
   const size_t n = std::min(cap, avail);
   if (n && !out) return fail(ctx, OASM_EINVAL, "null output array");
-  if (n) memcpy(out, s.ready.data() + s.head, n * sizeof(oasm_hit));
+  if (n) parallel_copy({CopyTask{out, s.ready.data() + s.head, n}});
   s.head += n;
   if (n_out) *n_out = n;
   if (s.head == s.ready.size()) {
@@ -1365,21 +1386,13 @@ int oasm_drain(oasm_ctx* ctx, oasm_hit* out, size_t cap, size_t* n_out) {
     }
   }
   if (got && !out) return fail(ctx, OASM_EINVAL, "null output array");
-  // copy in parts of about equal record counts on several host threads
-  const size_t T = std::max<size_t>(1, std::min<size_t>(16, got >> 20));
-  std::vector<size_t> cut(T + 1, plan.size());
-  cut[0] = 0;
-  for (size_t t = 1, c = 0; t < T; ++t) {
-    while (c < plan.size() && plan[c].off < got * t / T) ++c;
-    cut[t] = c;
+  std::vector<CopyTask> tasks;
+  tasks.reserve(plan.size());
+  for (const Copy& c : plan) {
+    const StreamRec& s = ctx->streams[c.sid];
+    tasks.push_back(CopyTask{out + c.off, s.ready.data() + s.head, c.n});
   }
-  parallel_parts(T, 1, [&](size_t t0, size_t t1) {
-    for (size_t t = t0; t < t1; ++t)
-      for (size_t c = cut[t]; c < cut[t + 1]; ++c) {
-        const StreamRec& s = ctx->streams[plan[c].sid];
-        memcpy(out + plan[c].off, s.ready.data() + s.head, plan[c].n * sizeof(oasm_hit));
-      }
-  });
+  parallel_copy(tasks);
   for (const Copy& c : plan) {
     StreamRec& s = ctx->streams[c.sid];
     s.head += c.n;
