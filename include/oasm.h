@@ -104,7 +104,13 @@ typedef struct {
     uint32_t groups_per_warp;  /* lane groups (32 patterns each) a scan warp runs
                                   together in one-word classes: 1 or 2; 0 = the
                                   tuned value (1 until oasm_autotune picks) */
-    uint32_t reserved;         /* must be 0 */
+    uint32_t prefilter_piece;  /* 0 (default): every pattern on the forward scan.
+                                  4..128: a pattern whose K + 1 pieces are all at
+                                  least this many symbols long (l_p / (K + 1) >= it)
+                                  is searched by the exact piece filter instead:
+                                  exact matches of its pieces propose the ends that
+                                  verification checks (pays off where pieces rarely
+                                  match at random, e.g. long byte signatures) */
 } oasm_config;
 
 /* One occurrence added to S (or, for the raw outputs, one hit/end). */

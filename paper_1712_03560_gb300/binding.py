@@ -56,7 +56,7 @@ class oasm_config(ctypes.Structure):
                 ("tile_warps", ctypes.c_uint32), ("timing", ctypes.c_int32),
                 ("flush_timeout_ms", ctypes.c_uint32), ("cuda_stream", ctypes.c_void_p),
                 ("myers_only", ctypes.c_int32), ("graphs", ctypes.c_int32),
-                ("groups_per_warp", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("groups_per_warp", ctypes.c_uint32), ("prefilter_piece", ctypes.c_uint32)]
 
 
 class oasm_hit(ctypes.Structure):
@@ -159,7 +159,10 @@ def oasm_rules_make(replace="contained", order="per_start_length", acc="sum", cm
 def oasm_config_make(**kw) -> oasm_config:
     cfg = oasm_config()
     load().oasm_config_default(ctypes.byref(cfg))
+    names = {f[0] for f in oasm_config._fields_}
     for k, v in kw.items():
+        if k not in names:
+            raise KeyError(f"oasm_config has no field {k!r}")
         setattr(cfg, k, v)
     return cfg
 

@@ -170,6 +170,14 @@ struct oasm_ctx {
   uint32_t* d_mem_off = nullptr;
   uint32_t* d_peq_rev = nullptr;
   std::vector<Bucket> buckets;
+  // piece filter (cfg.prefilter_piece): tables of the patterns it serves
+  uint32_t n_pref_pat = 0;
+  PrefSlot* d_pdir = nullptr;
+  uint32_t pdir_bits = 0, pmax_probe = 0;
+  PrefEntry* d_pent = nullptr;
+  uint8_t* d_pbytes = nullptr;
+  uint32_t* d_poff = nullptr;
+  DevArray<unsigned long long> pset;  // (end, pattern) set, capacity a power of two
 
   // streams
   std::vector<StreamRec> streams;
@@ -254,6 +262,15 @@ int ensure(oasm_ctx* ctx, DevArray<T>& a, size_t n, const char* what) {
   return OASM_OK;
 }
 
+// A power-of-two capacity of at least n (the piece filter's open-addressing set).
+template <class T>
+int ensure_pow2(oasm_ctx* ctx, DevArray<T>& a, size_t n, const char* what) {
+  if (a.p && a.cap >= n) return OASM_OK;
+  size_t want = 1024;
+  while (want < n || want < 2 * a.cap) want <<= 1;
+  return ensure(ctx, a, want, what);
+}
+
 int ensure_host(oasm_ctx* ctx, uint8_t** p, size_t* cap, size_t n, size_t keep) {
   if (*cap >= n && *p) return OASM_OK;
   size_t want = std::max<size_t>(n, *cap + *cap / 2);
@@ -311,6 +328,7 @@ void free_ctx(oasm_ctx* c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   auto f = [](void* p) { if (p) cudaFree(p); };
   f(c->d_m); f(c->d_K); f(c->d_mem_off); f(c->d_peq_rev);
+  f(c->d_pdir); f(c->d_pent); f(c->d_pbytes); f(c->d_poff); f(c->pset.p);
   for (auto& b : c->buckets) { f(b.d_groups); f(b.d_peq); }
   f(c->d_tails); f(c->d_hdr); f(c->d_mem);
   f(c->arena.p); f(c->dstage.p); f(c->upload.p); f(c->cand.p); f(c->keys.p);
@@ -329,6 +347,69 @@ void free_ctx(oasm_ctx* c) {
 }
 
 // --------------------------------------------------------------- tables
+// Piece filter tables: each selected pattern is cut into K + 1 pieces (the
+// first m mod (K + 1) one symbol longer); the directory maps a piece's first
+// four bytes (little-endian) to its run of entries, by open addressing with
+// the same multiplicative hash as the kernel.
+int build_prefilter(oasm_ctx* ctx, const std::vector<char>& pref) {
+  const uint32_t n = ctx->n_pat;
+  std::vector<std::pair<uint32_t, PrefEntry>> ents;
+  std::vector<uint8_t> bytes;
+  std::vector<uint32_t> poff(n, 0);
+  for (uint32_t p = 0; p < n; ++p) {
+    poff[p] = uint32_t(bytes.size());
+    bytes.insert(bytes.end(), ctx->pats[p].begin(), ctx->pats[p].end());
+    if (!pref[p]) continue;
+    ctx->n_pref_pat += 1;
+    const int m = ctx->m[p], parts = ctx->K[p] + 1;
+    int off = 0;
+    for (int j = 0; j < parts; ++j) {
+      const int q = m / parts + (j < m % parts ? 1 : 0);
+      const uint8_t* b = ctx->pats[p].data() + off;
+      const uint32_t key = uint32_t(b[0]) | (uint32_t(b[1]) << 8) | (uint32_t(b[2]) << 16) |
+                           (uint32_t(b[3]) << 24);
+      ents.push_back({key, PrefEntry{p, uint16_t(off), uint16_t(q)}});
+      off += q;
+    }
+  }
+  if (ents.empty()) return OASM_OK;
+  std::stable_sort(ents.begin(), ents.end(),
+                   [](const auto& a, const auto& b) { return a.first < b.first; });
+  size_t distinct = 0;
+  for (size_t i = 0; i < ents.size(); ++i) distinct += (i == 0 || ents[i].first != ents[i - 1].first);
+  uint32_t bits = 10;
+  while ((size_t(1) << bits) < 2 * distinct) ++bits;
+  std::vector<PrefSlot> dir(size_t(1) << bits, PrefSlot{0, 0, 0, 0});
+  const uint32_t mask = (1u << bits) - 1u;
+  uint32_t max_probe = 0;
+  for (size_t i = 0; i < ents.size();) {
+    size_t j = i;
+    while (j < ents.size() && ents[j].first == ents[i].first) ++j;
+    const uint32_t key = ents[i].first;
+    uint32_t h = (key * 0x9E3779B1u) >> (32u - bits), pr = 0;
+    while (dir[h].count != 0) {
+      h = (h + 1) & mask;
+      ++pr;
+    }
+    dir[h] = PrefSlot{key, uint32_t(i), uint32_t(j - i), 0};
+    max_probe = std::max(max_probe, pr);
+    i = j;
+  }
+  std::vector<PrefEntry> ev;
+  for (const auto& e : ents) ev.push_back(e.second);
+  CK(cudaMalloc(&ctx->d_pdir, dir.size() * sizeof(PrefSlot)));
+  CK(cudaMemcpy(ctx->d_pdir, dir.data(), dir.size() * sizeof(PrefSlot), cudaMemcpyHostToDevice));
+  CK(cudaMalloc(&ctx->d_pent, ev.size() * sizeof(PrefEntry)));
+  CK(cudaMemcpy(ctx->d_pent, ev.data(), ev.size() * sizeof(PrefEntry), cudaMemcpyHostToDevice));
+  CK(cudaMalloc(&ctx->d_pbytes, bytes.size()));
+  CK(cudaMemcpy(ctx->d_pbytes, bytes.data(), bytes.size(), cudaMemcpyHostToDevice));
+  CK(cudaMalloc(&ctx->d_poff, size_t(n) * 4));
+  CK(cudaMemcpy(ctx->d_poff, poff.data(), size_t(n) * 4, cudaMemcpyHostToDevice));
+  ctx->pdir_bits = bits;
+  ctx->pmax_probe = max_probe;
+  return OASM_OK;
+}
+
 int build_tables(oasm_ctx* ctx) {
   const uint32_t n = ctx->n_pat;
   // reversed, bottom-aligned Peq (verification pass): [p][256][4]
@@ -458,10 +539,19 @@ int build_tables(oasm_ctx* ctx) {
     ctx->buckets.push_back(bk);
     return OASM_OK;
   };
+  // patterns whose K + 1 pieces are all at least cfg.prefilter_piece symbols
+  // long go to the piece filter instead of the forward scan
+  std::vector<char> pref(n, 0);
+  if (ctx->cfg.prefilter_piece) {
+    for (uint32_t p = 0; p < n; ++p)
+      pref[p] = ctx->m[p] / (ctx->K[p] + 1u) >= ctx->cfg.prefilter_piece;
+    int rc = build_prefilter(ctx, pref);
+    if (rc) return rc;
+  }
   for (int W = 1; W <= kMaxW; ++W) {
     std::vector<uint32_t> ids;
     for (uint32_t p = 0; p < n; ++p)
-      if ((ctx->m[p] + 31) / 32 == W) ids.push_back(p);
+      if ((ctx->m[p] + 31) / 32 == W && !pref[p]) ids.push_back(p);
     if (W == 1 && !ctx->cfg.myers_only) {
       for (int K = 0; K <= 2; ++K) {
         std::vector<uint32_t> kid, rest;
@@ -554,6 +644,8 @@ struct StepPlan {
   uint64_t new_bytes = 0;
 };
 
+constexpr int64_t kPrefSeg = 4096;  // start positions per piece-filter block
+
 int plan_step(oasm_ctx* ctx, StepPlan& pl) {
   const int T = ctx->T;
   size_t off = kFrontPad;
@@ -634,6 +726,23 @@ int plan_step(oasm_ctx* ctx, StepPlan& pl) {
                      [](const Region& x, const Region& y) { return (x.b - x.a) > (y.b - y.a); });
   }
   pl.region_off.push_back(pl.regions.size());
+  // piece filter: start positions x with t[x .. x + 3] in the text, in
+  // segments of kPrefSeg (every piece of an occurrence whose end is reported
+  // this step starts at or after base_pos, inside the stored tail)
+  if (ctx->n_pref_pat) {
+    for (uint32_t i = 0; i < pl.items.size(); ++i) {
+      const WorkItem& w = pl.items[i];
+      const int64_t x_end = w.e_new - 3;  // exclusive
+      for (int64_t a = w.base_pos; a < x_end; a += kPrefSeg) {
+        Region r{};
+        r.wi = i;
+        r.a = a;
+        r.b = std::min(x_end, a + kPrefSeg);
+        pl.regions.push_back(r);
+      }
+    }
+  }
+  pl.region_off.push_back(pl.regions.size());
   return OASM_OK;
 }
 
@@ -679,8 +788,27 @@ int enqueue_step(oasm_ctx* ctx, StepPlan& pl, const WorkItem* d_items, const Reg
     ctx->st.launches += 1;
     ctx->st.scan_launches += 1;
   }
-  if (tm) CK(record_event(ctx, ctx->ev[2], s));
   StepParams P = make_params(ctx, d_items, n_items, pl.sb, pl.kb);
+  if (ctx->n_pref_pat) {
+    const size_t nb = ctx->buckets.size();
+    PrefArgs f{};
+    f.dir = ctx->d_pdir;
+    f.dir_bits = ctx->pdir_bits;
+    f.max_probe = ctx->pmax_probe;
+    f.ent = ctx->d_pent;
+    f.pbytes = ctx->d_pbytes;
+    f.poff = ctx->d_poff;
+    f.segs = d_regions + pl.region_off[nb];
+    f.n_segs = int(pl.region_off[nb + 1] - pl.region_off[nb]);
+    f.set = ctx->pset.p;
+    f.set_mask = ctx->pset.cap - 1;
+    if (f.n_segs > 0) {
+      CK(cudaMemsetAsync(ctx->pset.p, 0xff, ctx->pset.cap * sizeof(unsigned long long), s));
+      CK(launch_prefilter(P, f, s));
+      ctx->st.launches += 1;
+    }
+  }
+  if (tm) CK(record_event(ctx, ctx->ev[2], s));
   CK(launch_verify(P, s));
   ctx->st.launches += 1;
   if (tm) CK(record_event(ctx, ctx->ev[3], s));
@@ -783,6 +911,8 @@ int run_step_once(oasm_ctx* ctx, StepPlan& pl, const WorkItem* d_items, const Re
     }
     if ((c.overflow & 4u) || c.n_out > P.cap_out)
       if ((rc = ensure_out(ctx, size_t(c.n_out * 5 / 4 + 1024)))) return rc;
+    if (c.overflow & 32u)  // the piece filter's set filled up: room for 4x its inserts
+      if ((rc = ensure_pow2(ctx, ctx->pset, size_t(c.n_pref) * 4, "piece filter set"))) return rc;
     if ((c.overflow & 8u) || c.n_pool > P.cap_pool) {
       const size_t want = size_t(c.n_pool * 5 / 4 + 1024);
       if ((rc = ensure(ctx, ctx->pool_hdr, want, "window pool"))) return rc;
@@ -880,6 +1010,9 @@ int run_step(oasm_ctx* ctx) {
       if ((rc = ensure(ctx, ctx->keys_alt, h0, "hit keys"))) return rc;
     }
     if (!ctx->out.p && (rc = ensure_out(ctx, 1 << 16))) return rc;
+    if (ctx->n_pref_pat && !ctx->pset.p &&
+        (rc = ensure_pow2(ctx, ctx->pset, size_t(1) << 20, "piece filter set")))
+      return rc;
     if (!ctx->pool_hdr.p) {
       if ((rc = ensure(ctx, ctx->pool_hdr, 1 << 14, "window pool"))) return rc;
       if ((rc = ensure(ctx, ctx->pool_mem, size_t(1 << 14) * (kMaxK + 1), "window pool"))) return rc;
@@ -1055,8 +1188,13 @@ int oasm_create(const uint8_t* const* pat, const uint32_t* len, const uint32_t* 
     g_create_err = "rules field out of range";
     return OASM_EINVAL;
   }
-  if (cfg && (cfg->groups_per_warp > 2 || cfg->reserved != 0)) {
-    g_create_err = "config: groups_per_warp must be 0, 1 or 2 and reserved 0";
+  if (cfg && (cfg->groups_per_warp > 2 ||
+              (cfg->prefilter_piece != 0 && (cfg->prefilter_piece < 4 || cfg->prefilter_piece > 128)))) {
+    g_create_err = "config: groups_per_warp must be 0, 1 or 2; prefilter_piece 0 or 4..128";
+    return OASM_EINVAL;
+  }
+  if (cfg && cfg->prefilter_piece && n_pat >= (1u << 24)) {
+    g_create_err = "config: the piece filter takes fewer than 2^24 patterns";
     return OASM_EINVAL;
   }
   oasm_ctx* ctx = new oasm_ctx();

@@ -49,6 +49,23 @@ struct CopyChunk {
 };
 cudaError_t launch_gather(const CopyChunk* chunks, int n, uint8_t* arena, cudaStream_t s);
 
+// Piece filter over segments of the step's text: exact matches of pattern
+// pieces propose candidate ends, deduplicated through an open-addressing set.
+struct PrefArgs {
+  const PrefSlot* dir;
+  uint32_t dir_bits;             // directory size 2^dir_bits
+  uint32_t max_probe;            // longest probe sequence in the directory
+  const PrefEntry* ent;
+  const uint8_t* pbytes;         // all patterns' bytes
+  const uint32_t* poff;          // [n_pat] first byte of each pattern in pbytes
+  const Region* segs;            // text segments [a, b) of start positions
+  int32_t n_segs;
+  int32_t pad;
+  unsigned long long* set;       // (end, pattern) keys; all ones = empty
+  unsigned long long set_mask;   // capacity - 1 (a power of two)
+};
+cudaError_t launch_prefilter(const StepParams& p, const PrefArgs& f, cudaStream_t s);
+
 cudaError_t launch_verify(const StepParams& p, cudaStream_t s);
 
 // Stable LSD radix sort (8-bit digits) of keys by bits [lo_bit, hi_bit),

@@ -110,8 +110,26 @@ struct StepCounters {
   unsigned long long n_out;
   unsigned long long n_pool;
   unsigned long long word_steps;
-  unsigned int overflow;     // bit 0 candidates, 1 hits, 2 outputs, 3 pool
+  unsigned int overflow;     // bit 0 candidates, 1 hits, 2 outputs, 3 pool,
+                             // 5 the prefilter's candidate set (with bit 0)
   unsigned int pad;
+  unsigned long long n_pref;  // distinct (pattern, end) pairs the prefilter proposed
+};
+
+// Piece filter (exact pigeonhole prefilter).  A pattern with K errors split
+// into K + 1 disjoint pieces keeps at least one piece unedited in any
+// occurrence; the filter finds exact piece matches through their first four
+// bytes and proposes the 2K + 1 ends each one allows.
+struct PrefEntry {           // one piece, entries sorted by their 4-byte key
+  uint32_t pat;
+  uint16_t off;              // first symbol of the piece in the pattern
+  uint16_t q;                // piece length (>= 4)
+};
+struct PrefSlot {            // directory: open addressing on the 4-byte key
+  uint32_t key;
+  uint32_t start;            // first entry with this key
+  uint32_t count;            // 0 = empty slot
+  uint32_t pad;
 };
 
 struct Rules {

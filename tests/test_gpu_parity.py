@@ -322,6 +322,72 @@ def test_autotune_picks_groups_per_warp():
         B.oasm_destroy(ctx)
 
 
+@pytest.mark.parametrize("seed", range(3))
+def test_piece_filter_equals_scan_and_oracle(seed):
+    """Patterns whose K + 1 pieces are at least 4 symbols long go through the
+    exact piece filter (cfg.prefilter_piece = 4); shorter ones stay on the
+    scan.  Byte patterns over a skewed (Zipf) text with edited planted copies:
+    the output equals the oracle's and the scan-only output, in one feed and
+    across feeds, for several streams at once."""
+    rng = np.random.default_rng(1000 + seed)
+    table = W.zipf_table(np.random.default_rng(seed).permutation(256).astype(np.uint8))
+    pats, ks = [], []
+    for _ in range(60):
+        m = int(rng.integers(6, 70))
+        k = int(rng.integers(0, min(4, m // 3) + 1))
+        pats.append(table[rng.integers(0, table.size, size=m)].astype(np.uint8))
+        ks.append(k)
+    for m in (8, 9, 10, 11):  # pieces of 2-3 symbols: these stay on the scan
+        pats.append(table[rng.integers(0, table.size, size=m)].astype(np.uint8))
+        ks.append(2)
+    texts = []
+    for _ in range(3):
+        t = table[rng.integers(0, table.size, size=int(rng.integers(20000, 60000)))].astype(np.uint8)
+        for p, k in zip(pats, ks):
+            for cp in W.edit_copies(rng, p, rng.integers(0, k + 1, size=2), np.arange(256, dtype=np.uint8)):
+                W.plant(rng, t, cp)
+        texts.append(t)
+    on_filter = sum(len(p) // (k + 1) >= 4 for p, k in zip(pats, ks))
+    assert 20 <= on_filter < len(pats)
+    for t in texts:
+        want = oracle_rows(pats, ks, t)
+        assert len(want) > 0
+        got, _ = run_gpu(pats, ks, t, cfg={"prefilter_piece": 4})
+        scan, _ = run_gpu(pats, ks, t)
+        assert canon(got) == canon(scan) == want
+    split, _ = run_gpu(pats, ks, texts[0], cfg={"prefilter_piece": 4},
+                       splits=np.sort(rng.integers(0, texts[0].size, size=8)))
+    assert canon(split) == oracle_rows(pats, ks, texts[0])
+    # several streams in one step
+    ctx = B.oasm_create(pats, ks, None, {"prefilter_piece": 4, "max_streams": 8})
+    try:
+        sids = [B.oasm_open_stream(ctx) for _ in texts]
+        for s_, t in zip(sids, texts):
+            B.oasm_feed(ctx, s_, t)
+            B.oasm_end_stream(ctx, s_)
+        B.oasm_step(ctx)
+        for s_, t in zip(sids, texts):
+            res = B.oasm_flush(ctx, s_)
+            rows = [(int(r["pattern_id"]), int(r["decided_at"]), int(r["k"]), int(r["start"]),
+                     int(r["len"])) for r in res]
+            assert canon(rows) == oracle_rows(pats, ks, t)
+    finally:
+        B.oasm_destroy(ctx)
+
+
+def test_piece_filter_set_grows_on_repetitive_text():
+    """A text of one repeated symbol makes every piece match everywhere: the
+    filter's (end, pattern) set overflows, grows and the step re-runs; pieces
+    of 5 and 8 symbols, K = 0..3."""
+    pats = [np.full(m, 65, np.uint8) for m in (16, 17, 20, 24, 32, 40)]
+    ks = [0, 1, 2, 3, 2, 3]
+    text = np.full(120000, 65, np.uint8)
+    text[::997] = 66
+    got, st = run_gpu(pats, ks, text, cfg={"prefilter_piece": 4})
+    assert st["reruns"] >= 1
+    assert canon(got) == oracle_rows(pats, ks, text)
+
+
 def test_int_peak_microbenchmark_runs():
     ops, ms = B.oasm_measure_int_peak(0)
     assert ops > 1e12 and ms > 0
