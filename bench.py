@@ -56,6 +56,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--served-packets", type=int, default=200000)
+    ap.add_argument("--prefilter", type=int, default=0,
+                    help="cfg.prefilter_piece: patterns whose K+1 pieces are at least this "
+                         "long use the exact piece filter instead of the scan (0 = off)")
     return ap.parse_args()
 
 
@@ -212,6 +215,11 @@ def run_reference(args):
 SERVED_LOADS_GBPS = (0.5, 1.0, 2.0, 3.0, 4.0, 6.0, 10.0, 25.0, 100.0, 400.0)
 
 
+def on_filter(m: int, k: int, piece: int) -> bool:
+    """Whether cfg.prefilter_piece = piece routes a pattern to the piece filter."""
+    return piece > 0 and m // (k + 1) >= piece
+
+
 def measured_hbm_gbs():
     """HBM copy bandwidth measured on this GPU pool (the driver's file), else
     the fallback figure."""
@@ -241,7 +249,8 @@ def run_served(args):
             "that matched the packet")
     sweep = []
     clocks = Clocks(0)
-    with serve.Server(base.patterns, base.ks, max_streams=4096, timing=True) as srv:
+    with serve.Server(base.patterns, base.ks, max_streams=4096, timing=True,
+                      prefilter_piece=args.prefilter) as srv:
         # warm-up: grow every step buffer to the sweep's sizes, then a paced pass
         for _ in range(max(1, args.warmup)):
             srv.replay(W.served(seed=99, n_packets=20000, gbps=10.0), realtime=False)
@@ -268,7 +277,8 @@ def run_served(args):
     best = max(sweep, key=lambda x: x["achieved_gbps"])
     # roofline of the scan over the steps of the best load point (library events)
     peak_ops, _ = B_peak()
-    words = sum((p.size + 31) // 32 for p in base.patterns) * st_best["text_bytes"]
+    words = sum((p.size + 31) // 32 for p, k in zip(base.patterns, base.ks)
+                if not on_filter(p.size, int(k), args.prefilter)) * st_best["text_bytes"]
     scan_ms = st_best["scan_ms"]
     achieved = words * OPS_PER_WORD_STEP / max(scan_ms * 1e-3, 1e-12) / 1e12
     derived_peak = SM_COUNT * 128 * SM_MAX_MHZ * 1e6 / 1e12
@@ -278,7 +288,8 @@ def run_served(args):
                 "kernel": "scan_kernel (all classes of a step)",
                 "kernel_ms_per_launch": scan_ms / max(1, st_best["scan_launches"]),
                 "ops_per_word_step": OPS_PER_WORD_STEP,
-                "scan_share_of_device_step": scan_ms / max(st_best["step_ms"], 1e-12)}
+                "scan_share_of_device_step": scan_ms / max(st_best["step_ms"], 1e-12),
+                "prefilter_share_of_device_step": st_best["prefilter_ms"] / max(st_best["step_ms"], 1e-12)}
     cpu = None
     if not args.no_cpu:
         wl, _ = make_workload("served", 0)
@@ -290,6 +301,7 @@ def run_served(args):
             "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "u32", "data": "synthetic",
             "config": {"workload": desc, "streams": 4096, "signatures": len(base.patterns),
+                       "prefilter_piece": args.prefilter,
                        "packets_per_load": n_pkt, "l2": "per-step text is small; L2-resident"},
             "served": {"sweep": sweep, "sustained_gbps": best["achieved_gbps"],
                        "knee_offered_gbps": knee["offered_gbps"] if knee else None,
@@ -333,7 +345,8 @@ def main():
 
     wl, desc = make_workload(args.workload, rank)
     ctx = B.oasm_create(wl.patterns, wl.ks, None,
-                        {"device": dev, "timing": 1, "max_streams": max(64, len(wl.texts))})
+                        {"device": dev, "timing": 1, "max_streams": max(64, len(wl.texts)),
+                         "prefilter_piece": args.prefilter})
     stream = torch.cuda.ExternalStream(B.oasm_cuda_stream(ctx), device=dev)
     dtexts = [torch.from_numpy(t).to(f"cuda:{dev}") for t in wl.texts]
     torch.cuda.synchronize()
@@ -419,7 +432,8 @@ def main():
     # ---- roofline of the dominant kernel (the forward scan), measured live
     peak_ops, _ = B.oasm_measure_int_peak(dev)
     scan_ms_launch = st["scan_ms"] / max(1, st["scan_launches"])
-    words = sum((p.size + 31) // 32 for p in wl.patterns) * wl.text_bytes
+    words = sum((p.size + 31) // 32 for p, k in zip(wl.patterns, wl.ks)
+                if not on_filter(p.size, int(k), args.prefilter)) * wl.text_bytes
     alg_ops_launch = words * OPS_PER_WORD_STEP / max(1, st["scan_launches"] // max(1, args.steps))
     achieved = alg_ops_launch / (scan_ms_launch * 1e-3) / 1e12
     derived_peak = SM_COUNT * 128 * SM_MAX_MHZ * 1e6 / 1e12
@@ -493,11 +507,21 @@ def main():
         "config": {"workload": desc, "text_bytes": int(wl.text_bytes),
                    "patterns": len(wl.patterns), "l2": "inputs larger than L2 (text > 129 MB)"
                    if wl.text_bytes > (129 << 20) else "input smaller than L2",
-                   "parallelism": f"replicas x{world}", "autotune": tuned},
+                   "parallelism": f"replicas x{world}", "autotune": tuned,
+                   "prefilter_piece": args.prefilter},
         "text_gbps": text_gbps,
         "occurrences_per_step": int(kept),
-        "kernel_ms": {k: st[k] / args.steps for k in ("copy_ms", "scan_ms", "verify_ms",
-                                                        "order_ms", "filter_ms", "step_ms")},
+        "kernel_ms": {k: st[k] / args.steps for k in ("copy_ms", "scan_ms", "prefilter_ms",
+                                                        "verify_ms", "order_ms", "filter_ms",
+                                                        "step_ms")},
+        "prefilter": None if not args.prefilter else {
+            "piece": args.prefilter,
+            "patterns": sum(on_filter(p.size, int(k), args.prefilter) for p, k in zip(wl.patterns, wl.ks)),
+            "candidates_per_step": st["prefilter_candidates"] / args.steps,
+            # one pass over the text: bytes read per second against the HBM copy peak
+            "text_gbs": wl.text_bytes * args.steps / max(st["prefilter_ms"] * 1e-3, 1e-12) / 1e9,
+            "hbm_frac": wl.text_bytes * args.steps / max(st["prefilter_ms"] * 1e-3, 1e-12) / 1e9
+                        / measured_hbm_gbs()[0]},
         "host_ms_per_step": host_step_ms,
         "candidates_per_step": st["candidates"] / args.steps,
         "hits_per_step": st["hits"] / args.steps,

@@ -142,6 +142,8 @@ typedef struct {
     double step_ms;          /* whole steps, first to last kernel */
     uint64_t scan_launches;  /* forward-scan kernel launches */
     uint64_t graph_builds;   /* step graphs instantiated (cfg.graphs = 1) */
+    double prefilter_ms;     /* with timing=1: the piece filter (cfg.prefilter_piece) */
+    uint64_t prefilter_candidates; /* distinct (pattern, end) pairs it proposed */
 } oasm_stats;
 
 /* Fills *cfg / *rules with the defaults described above. */

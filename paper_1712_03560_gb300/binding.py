@@ -74,7 +74,8 @@ class oasm_stats(ctypes.Structure):
                                                 "reruns")] + \
                [(n, ctypes.c_double) for n in ("scan_ms", "verify_ms", "order_ms", "filter_ms",
                                                "copy_ms", "step_ms")] + \
-               [("scan_launches", ctypes.c_uint64), ("graph_builds", ctypes.c_uint64)]
+               [("scan_launches", ctypes.c_uint64), ("graph_builds", ctypes.c_uint64),
+                ("prefilter_ms", ctypes.c_double), ("prefilter_candidates", ctypes.c_uint64)]
 
 
 EXPORTS = ["oasm_config_default", "oasm_rules_default", "oasm_create", "oasm_destroy",

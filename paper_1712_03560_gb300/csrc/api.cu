@@ -211,7 +211,7 @@ struct oasm_ctx {
   size_t h_upload_cap = 0;
   DevHit* h_out = nullptr;
   size_t h_out_cap = 0;
-  cudaEvent_t ev[8] = {};
+  cudaEvent_t ev[9] = {};  // 0-5 step phases, 6-7 autotune, 8 piece filter start
   cudaEvent_t done = nullptr;
   cudaGraphExec_t graph_exec = nullptr;  // the last captured step, updated in place
   bool capturing = false;
@@ -803,6 +803,7 @@ int enqueue_step(oasm_ctx* ctx, StepPlan& pl, const WorkItem* d_items, const Reg
     f.set = ctx->pset.p;
     f.set_mask = ctx->pset.cap - 1;
     if (f.n_segs > 0) {
+      if (tm) CK(record_event(ctx, ctx->ev[8], s));
       CK(cudaMemsetAsync(ctx->pset.p, 0xff, ctx->pset.cap * sizeof(unsigned long long), s));
       CK(launch_prefilter(P, f, s));
       ctx->st.launches += 1;
@@ -924,13 +925,21 @@ int run_step_once(oasm_ctx* ctx, StepPlan& pl, const WorkItem* d_items, const Re
   if (tm) {
     float ms = 0;
     cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]); ctx->st.copy_ms += ms;
-    cudaEventElapsedTime(&ms, ctx->ev[1], ctx->ev[2]); ctx->st.scan_ms += ms;
+    const size_t nb = ctx->buckets.size();
+    const bool pf = ctx->n_pref_pat && pl.region_off[nb + 1] > pl.region_off[nb];
+    if (pf) {
+      cudaEventElapsedTime(&ms, ctx->ev[1], ctx->ev[8]); ctx->st.scan_ms += ms;
+      cudaEventElapsedTime(&ms, ctx->ev[8], ctx->ev[2]); ctx->st.prefilter_ms += ms;
+    } else {
+      cudaEventElapsedTime(&ms, ctx->ev[1], ctx->ev[2]); ctx->st.scan_ms += ms;
+    }
     cudaEventElapsedTime(&ms, ctx->ev[2], ctx->ev[3]); ctx->st.verify_ms += ms;
     cudaEventElapsedTime(&ms, ctx->ev[3], ctx->ev[4]); ctx->st.order_ms += ms;
     cudaEventElapsedTime(&ms, ctx->ev[4], ctx->ev[5]); ctx->st.filter_ms += ms;
     cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[5]); ctx->st.step_ms += ms;
   }
   ctx->st.candidates += c.n_cand;
+  ctx->st.prefilter_candidates += c.n_pref;
   ctx->st.hits += c.n_hits;
   ctx->st.kept += c.n_out;
   // records -> streams

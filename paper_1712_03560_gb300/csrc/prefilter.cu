@@ -42,21 +42,30 @@ __device__ __forceinline__ uint32_t dir_hash(uint32_t key, uint32_t bits) {
   return (key * 0x9E3779B1u) >> (32u - bits);
 }
 
+// Adds 1 for every calling thread of the warp with one atomic per warp (the
+// threads that reach this call together); returns this thread's old value.
+__device__ __forceinline__ unsigned long long warp_add1(unsigned long long* ctr) {
+  const unsigned act = __activemask();
+  const int lane = int(threadIdx.x & 31u);
+  const int leader = __ffs(act) - 1;
+  const int rank = __popc(act & ((1u << lane) - 1u));
+  unsigned long long base = 0;
+  if (lane == leader) base = atomicAdd(ctr, (unsigned long long)__popc(act));
+  base = __shfl_sync(act, base, leader);
+  return base + unsigned(rank);
+}
+
 // Inserts key; true if it was not in the set yet.  Sets the overflow bits
 // when no free slot turns up within the probe bound.
-__device__ bool set_insert(const PrefArgs& F, StepCounters* ctr, unsigned long long key) {
+__device__ bool set_insert(const PrefArgs& F, unsigned long long key, bool* full) {
   unsigned long long h = mix64(key) & F.set_mask;
   for (int i = 0; i < kSetProbes; ++i) {
     const unsigned long long prev = atomicCAS(&F.set[h], kEmpty, key);
-    if (prev == kEmpty) {
-      const unsigned long long n = atomicAdd(&ctr->n_pref, 1ull);
-      if (n + 1 > (F.set_mask + 1) / 2) atomicOr(&ctr->overflow, kSetOverflow | kCandOverflow);
-      return true;
-    }
+    if (prev == kEmpty) return true;
     if (prev == key) return false;
     h = (h + 1) & F.set_mask;
   }
-  atomicOr(&ctr->overflow, kSetOverflow | kCandOverflow);
+  *full = true;
   return false;
 }
 
@@ -90,8 +99,14 @@ __global__ void __launch_bounds__(256) prefilter_kernel(const StepParams P, cons
             const int64_t hi = min(ec + K, w.e_new - 1);
             for (int64_t e = lo; e <= hi; ++e) {
               const unsigned long long arena_off = w.arena_base + uint64_t(e - w.base_pos);
-              if (!set_insert(F, P.ctr, (arena_off << 24) | pe.pat)) continue;
-              const unsigned long long o = atomicAdd(&P.ctr->n_cand, 1ull);
+              bool full = false;
+              const bool fresh = set_insert(F, (arena_off << 24) | pe.pat, &full);
+              if (full) atomicOr(&P.ctr->overflow, kSetOverflow | kCandOverflow);
+              if (!fresh) continue;
+              // the set stays at most half full (short probe runs)
+              if (warp_add1(&P.ctr->n_pref) + 1 > (F.set_mask + 1) / 2)
+                atomicOr(&P.ctr->overflow, kSetOverflow | kCandOverflow);
+              const unsigned long long o = warp_add1(&P.ctr->n_cand);
               if (o < P.cap_cand) {
                 Candidate c;
                 c.wi = R.wi;
