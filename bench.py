@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--served-packets", type=int, default=200000)
+    ap.add_argument("--served-batch-mb", type=float, default=8.0,
+                    help="byte budget of one serving step (MiB)")
     ap.add_argument("--prefilter", type=int, default=0,
                     help="cfg.prefilter_piece: patterns whose K+1 pieces are at least this "
                          "long use the exact piece filter instead of the scan (0 = off)")
@@ -250,7 +252,8 @@ def run_served(args):
     sweep = []
     clocks = Clocks(0)
     with serve.Server(base.patterns, base.ks, max_streams=4096, timing=True,
-                      prefilter_piece=args.prefilter) as srv:
+                      prefilter_piece=args.prefilter,
+                      max_batch_bytes=int(args.served_batch_mb * (1 << 20))) as srv:
         # warm-up: grow every step buffer to the sweep's sizes, then a paced pass
         for _ in range(max(1, args.warmup)):
             srv.replay(W.served(seed=99, n_packets=20000, gbps=10.0), realtime=False)
@@ -261,10 +264,9 @@ def run_served(args):
         for g in SERVED_LOADS_GBPS:
             tr = W.served(seed=int(5 + 10 * g), n_packets=n_pkt, gbps=g)
             st0 = srv.stats()
-            r = srv.replay(tr, realtime=True, collect=True)
+            r = srv.replay(tr, realtime=True)
             st1 = srv.stats()
             r["gcups"] = msum * r["bytes"] / r["wall_s"] / 1e9
-            r["kept"] = int(sum(v.size for v in r.pop("hits").values()))
             if not sweep or r["achieved_gbps"] > max(x["achieved_gbps"] for x in sweep):
                 st_best = {k: st1[k] - st0[k] for k in st1}
                 kept_best = r["kept"]
@@ -302,6 +304,7 @@ def run_served(args):
             "dtype": "u32", "data": "synthetic",
             "config": {"workload": desc, "streams": 4096, "signatures": len(base.patterns),
                        "prefilter_piece": args.prefilter,
+                       "step_budget_bytes": int(args.served_batch_mb * (1 << 20)),
                        "packets_per_load": n_pkt, "l2": "per-step text is small; L2-resident"},
             "served": {"sweep": sweep, "sustained_gbps": best["achieved_gbps"],
                        "knee_offered_gbps": knee["offered_gbps"] if knee else None,

@@ -84,8 +84,10 @@ class Server:
         waiting = collections.deque()                    # external ids waiting for a slot
         held = collections.defaultdict(list)             # packets of waiting streams
         done_at = np.full(n, np.nan)
+        csum = np.cumsum(lens)                          # bytes of packets [0, q]
         hits = collections.defaultdict(list) if collect else None
         steps = 0
+        kept = 0
         fed_bytes = 0
         max_wait = 0
         admitted = 0
@@ -99,20 +101,24 @@ class Server:
             else:
                 j = n
             # admit waiting streams first (slots freed by the last step)
-            batch = []
+            parts = []
             if waiting:
                 for sid in self._admit_many(len(waiting)):
                     ext = waiting.popleft()
                     sid_of[ext] = sid
                     ext_of[sid] = ext
                     admitted += 1
-                    batch.extend(held.pop(ext, []))
+                    got = held.pop(ext, None)
+                    if got:
+                        parts.append(np.asarray(got, dtype=np.int64))
             # newly arrived packets, within the byte budget
-            budget = self.max_batch_bytes - int(lens[batch].sum()) if batch else self.max_batch_bytes
+            used = int(sum(int(lens[p].sum()) for p in parts))
+            budget = self.max_batch_bytes - used
             k = i
             if j > i:
-                csum = np.cumsum(lens[i:j])
-                k = i + max(1, int(np.searchsorted(csum, budget, side="right")))
+                before = int(csum[i - 1]) if i else 0
+                k = int(np.searchsorted(csum, before + budget, side="right"))
+                k = min(j, max(i + 1, k))
             if k > i:
                 exts = streams[i:k]
                 # streams seen for the first time: admit now or queue (in arrival order)
@@ -130,12 +136,13 @@ class Server:
                         sid_of[ext] = -3  # waiting
                 qs = np.arange(i, k)
                 live = sid_of[exts] >= 0
-                batch.extend(qs[live].tolist())
+                parts.append(qs[live])
                 for q in qs[~live].tolist():
                     held[int(streams[q])].append(q)
             i = k
             max_wait = max(max_wait, len(waiting))
-            if not batch:
+            batch = np.concatenate(parts) if parts else np.zeros(0, np.int64)
+            if batch.size == 0:
                 if i < n and realtime:
                     gap = times[i] - (time.perf_counter() - t0)
                     if gap > 2e-3:
@@ -143,7 +150,6 @@ class Server:
                 elif waiting and not ext_of:
                     raise RuntimeError("no stream can be admitted under the memory budget")
                 continue
-            batch = np.asarray(batch, dtype=np.int64)
             sids = sid_of[streams[batch]].astype(np.uint32)
             B.oasm_feed_many(self.ctx, sids, tr.payload, offs[batch], lens[batch].astype(np.uint32))
             ending = sids[last[batch]].astype(np.int64).tolist()
@@ -156,6 +162,7 @@ class Server:
             step_ms.append((te - ts) * 1e3)
             done_at[batch] = te - t0
             steps += 1
+            kept += int(out.size)
             fed_bytes += int(lens[batch].sum())
             if collect and out.size:
                 for s in np.unique(out["stream_id"]):
@@ -171,7 +178,7 @@ class Server:
             "packets": int(n), "bytes": int(lens.sum()), "fed_bytes": fed_bytes,
             "offered_gbps": float(tr.meta.get("gbps", 0.0)),
             "achieved_gbps": lens.sum() * 8 / wall / 1e9,
-            "wall_s": wall, "steps": steps,
+            "wall_s": wall, "steps": steps, "kept": kept,
             "p50_ms": float(np.percentile(lat[ok], 50)) if ok.any() else None,
             "p99_ms": float(np.percentile(lat[ok], 99)) if ok.any() else None,
             "max_ms": float(lat[ok].max()) if ok.any() else None,
