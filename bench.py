@@ -318,6 +318,10 @@ def run_served(args):
                     "note": "the served value is measured end to end (wall clock, host packets in, "
                             "host hits out)"},
             "gpu_launches": int(st_all["launches"]),
+            "library_ms_per_step_at_best": {
+                k: st_best[k] / max(1, st_best["steps"])
+                for k in ("step_ms", "scan_ms", "prefilter_ms", "host_plan_ms", "host_launch_ms",
+                          "host_wait_ms", "host_post_ms")},
             "roofline": roofline,
             "cpu_baseline": cpu,
             "clocks": clk}
@@ -526,6 +530,9 @@ def main():
             "hbm_frac": wl.text_bytes * args.steps / max(st["prefilter_ms"] * 1e-3, 1e-12) / 1e9
                         / measured_hbm_gbs()[0]},
         "host_ms_per_step": host_step_ms,
+        "library_host_ms_per_step": {k: st[k] / args.steps for k in
+                                     ("host_plan_ms", "host_launch_ms", "host_wait_ms",
+                                      "host_post_ms")},
         "candidates_per_step": st["candidates"] / args.steps,
         "hits_per_step": st["hits"] / args.steps,
         "gpu_launches": int(st["launches"]),

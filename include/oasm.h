@@ -144,6 +144,11 @@ typedef struct {
     uint64_t graph_builds;   /* step graphs instantiated (cfg.graphs = 1) */
     double prefilter_ms;     /* with timing=1: the piece filter (cfg.prefilter_piece) */
     uint64_t prefilter_candidates; /* distinct (pattern, end) pairs it proposed */
+    double host_plan_ms;     /* host time: planning a step and preparing its upload */
+    double host_launch_ms;   /* host time: enqueueing (or capturing and updating) a step */
+    double host_wait_ms;     /* host time waiting for the device to finish a step */
+    double host_post_ms;     /* host time after a step: counters, records into the
+                                stream queues, stream bookkeeping */
 } oasm_stats;
 
 /* Fills *cfg / *rules with the defaults described above. */

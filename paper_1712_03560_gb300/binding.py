@@ -75,7 +75,9 @@ class oasm_stats(ctypes.Structure):
                [(n, ctypes.c_double) for n in ("scan_ms", "verify_ms", "order_ms", "filter_ms",
                                                "copy_ms", "step_ms")] + \
                [("scan_launches", ctypes.c_uint64), ("graph_builds", ctypes.c_uint64),
-                ("prefilter_ms", ctypes.c_double), ("prefilter_candidates", ctypes.c_uint64)]
+                ("prefilter_ms", ctypes.c_double), ("prefilter_candidates", ctypes.c_uint64),
+                ("host_plan_ms", ctypes.c_double), ("host_launch_ms", ctypes.c_double),
+                ("host_wait_ms", ctypes.c_double), ("host_post_ms", ctypes.c_double)]
 
 
 EXPORTS = ["oasm_config_default", "oasm_rules_default", "oasm_create", "oasm_destroy",

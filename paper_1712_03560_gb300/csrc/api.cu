@@ -844,8 +844,13 @@ int enqueue_step(oasm_ctx* ctx, StepPlan& pl, const WorkItem* d_items, const Reg
   return OASM_OK;
 }
 
+double ms_since(std::chrono::steady_clock::time_point t0) {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
+
 int run_step_once(oasm_ctx* ctx, StepPlan& pl, const WorkItem* d_items, const Region* d_regions,
                   const CopyChunk* d_chunks, bool* overflow) {
+  const auto t_launch = std::chrono::steady_clock::now();
   cudaStream_t s = ctx->stream;
   const bool tm = ctx->cfg.timing != 0;
   int rc;
@@ -888,7 +893,16 @@ int run_step_once(oasm_ctx* ctx, StepPlan& pl, const WorkItem* d_items, const Re
     if ((rc = enqueue_step(ctx, pl, d_items, d_regions, d_chunks))) return rc;
   }
   CK(cudaEventRecord(ctx->done, s));
+  ctx->st.host_launch_ms += ms_since(t_launch);
+  const auto t_wait = std::chrono::steady_clock::now();
   rc = wait_event(ctx, ctx->done);
+  ctx->st.host_wait_ms += ms_since(t_wait);
+  const auto t_post = std::chrono::steady_clock::now();
+  struct PostTimer {  // host work after the device finished, to every return
+    oasm_ctx* c;
+    std::chrono::steady_clock::time_point t;
+    ~PostTimer() { c->st.host_post_ms += ms_since(t); }
+  } post_timer{ctx, t_post};
   const StepParams P = make_params(ctx, d_items, uint32_t(pl.items.size()), pl.sb, pl.kb);
   if (rc) return rc;
   const StepCounters c = *ctx->h_ctr;
@@ -1003,6 +1017,7 @@ int run_step(oasm_ctx* ctx) {
     if (ctx->h_stage_used &&
         (rc = ensure(ctx, ctx->dstage, ctx->h_stage_used, "staging")))
       return rc;
+    const auto t_plan = std::chrono::steady_clock::now();
     StepPlan pl;
     if ((rc = plan_step(ctx, pl))) return rc;
     if (pl.items.empty()) return OASM_OK;
@@ -1041,6 +1056,7 @@ int run_step(oasm_ctx* ctx) {
     const WorkItem* d_items = reinterpret_cast<const WorkItem*>(ctx->upload.p);
     const Region* d_regions = reinterpret_cast<const Region*>(ctx->upload.p + o_r);
     const CopyChunk* d_chunks = reinterpret_cast<const CopyChunk*>(ctx->upload.p + o_c);
+    ctx->st.host_plan_ms += ms_since(t_plan);
     bool over = true;
     for (int attempt = 0; over; ++attempt) {
       if (attempt > 16) {
@@ -1055,6 +1071,7 @@ int run_step(oasm_ctx* ctx) {
       if ((rc = run_step_once(ctx, pl, d_items, d_regions, d_chunks, &over))) return rc;
     }
     // advance streams
+    const auto t_adv = std::chrono::steady_clock::now();
     for (size_t i = 0; i < pl.items.size(); ++i) {
       StreamRec& s = ctx->streams[pl.sids[i]];
       size_t left = pl.take[i];
@@ -1098,6 +1115,7 @@ int run_step(oasm_ctx* ctx) {
     }
     // host staging is free again once no stream references it
     if (ctx->host_pending == 0) ctx->h_stage_used = 0;
+    ctx->st.host_post_ms += ms_since(t_adv);
     bool more = false;
     for (auto& s : ctx->streams) more |= s.open && (s.pending > 0 || s.eos_pending);
     if (!more) return OASM_OK;
