@@ -3,7 +3,7 @@
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                     [--workload dictionary_dna|dictionary_dna_64m|plain_dna|plain_dna_1g|
-                     bytes_zipf|many_texts|many_texts_256m|served]
+                     bytes_zipf|bytes_zipf_256m|many_texts|many_texts_256m|served]
 
 One step = one pass of the whole path over the workload: open a stream, feed
 the text, end it and flush (stage, bit-parallel scan, anchored verification,
@@ -76,6 +76,9 @@ def make_workload(name: str, seed_offset: int):
     if name == "dictionary_dna_64m":
         return W.dictionary_dna(seed=2 + 1000 * seed_offset, n=64 << 20, copies=250), \
             "dictionary_dna_64m: 1024 DNA patterns m~U[8,32] K=floor(m/10), 64 MiB iid DNA text, 250 planted copies/pattern"
+    if name == "bytes_zipf_256m":
+        return W.bytes_zipf(seed=3 + 1000 * seed_offset, n=256 << 20, copies=125), \
+            "bytes_zipf_256m: 4096 byte patterns m log-uniform [16,128], K~U[1,min(8,m/4)], 256 MiB Zipf(1.1) text, 125 copies/pattern"
     if name == "plain_dna":
         return W.plain_dna(seed=1 + 1000 * seed_offset), \
             "plain_dna: 1 DNA pattern m=8 K=2, 1e6 iid DNA symbols, 200 planted copies"
