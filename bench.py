@@ -280,7 +280,7 @@ def run_served(args):
             sweep.append({k: r[k] for k in ("offered_gbps", "achieved_gbps", "p50_ms", "p99_ms",
                                              "max_ms", "steps", "mean_batch_bytes",
                                              "step_ms_p50", "step_ms_p99", "step_ms_max",
-                                             "gcups", "packets")})
+                                             "gcups", "packets", "phase_ms_per_step")})
         clk = clocks.stop()
         st_all = srv.stats()
     best = max(sweep, key=lambda x: x["achieved_gbps"])

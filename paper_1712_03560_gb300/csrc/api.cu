@@ -1438,21 +1438,42 @@ int oasm_feed_many(oasm_ctx* ctx, uint32_t n, const uint32_t* sid, const uint8_t
   if ((rc = ensure_host(ctx, &ctx->h_stage, &ctx->h_stage_cap, ctx->h_stage_used + total,
                         ctx->h_stage_used)))
     return rc;
+  // staging layout: the packets of one stream side by side in call order
+  // (streams in order of first appearance), so each stream gets one piece
+  // per call; the byte copies run on several host threads when large
+  std::vector<uint32_t> order;              // streams in order of first appearance
+  std::vector<uint64_t> base(ctx->streams.size(), ~0ull);
   for (uint32_t j = 0; j < n; ++j) {
     if (!len[j]) continue;
-    memcpy(ctx->h_stage + ctx->h_stage_used, buf + off[j], len[j]);
-    StreamRec& s = ctx->streams[sid[j]];
-    // consecutive packets of a stream are contiguous in staging: one piece
-    if (!s.pieces.empty() && !s.pieces.back().dev &&
-        s.pieces.back().host_off + s.pieces.back().n == ctx->h_stage_used)
-      s.pieces.back().n += len[j];
-    else
-      s.pieces.push_back(Piece{false, nullptr, ctx->h_stage_used, len[j]});
-    s.pending += len[j];
-    s.clean = false;
-    ctx->h_stage_used += len[j];
-    ctx->host_pending += len[j];
+    if (base[sid[j]] == ~0ull) {
+      base[sid[j]] = 0;
+      order.push_back(sid[j]);
+    }
+    base[sid[j]] += len[j];  // bytes of the stream in this call
   }
+  size_t at = ctx->h_stage_used;
+  for (uint32_t sd : order) {
+    const uint64_t bytes = base[sd];
+    base[sd] = at;
+    StreamRec& s = ctx->streams[sd];
+    s.pieces.push_back(Piece{false, nullptr, at, size_t(bytes)});
+    s.pending += bytes;
+    s.clean = false;
+    at += bytes;
+  }
+  std::vector<uint64_t> dst(n);
+  for (uint32_t j = 0; j < n; ++j) {
+    if (!len[j]) continue;
+    dst[j] = base[sid[j]];
+    base[sid[j]] += len[j];
+  }
+  parallel_parts(n, total > (size_t(4) << 20) ? std::max<size_t>(1, n / 16) : n + 1,
+                 [&](size_t lo, size_t hi) {
+                   for (size_t j = lo; j < hi; ++j)
+                     if (len[j]) memcpy(ctx->h_stage + dst[j], buf + off[j], len[j]);
+                 });
+  ctx->h_stage_used = at;
+  ctx->host_pending += total;
   return OASM_OK;
 }
 

@@ -92,10 +92,12 @@ class Server:
         max_wait = 0
         admitted = 0
         step_ms = []
+        phase = {"schedule": 0.0, "feed": 0.0, "step_drain": 0.0, "close": 0.0}
         t0 = time.perf_counter()
         i = 0
         while i < n or waiting or held:
-            now = time.perf_counter() - t0
+            t_it = time.perf_counter()
+            now = t_it - t0
             if realtime:
                 j = int(np.searchsorted(times, now, side="right"))
             else:
@@ -151,6 +153,7 @@ class Server:
                     raise RuntimeError("no stream can be admitted under the memory budget")
                 continue
             sids = sid_of[streams[batch]].astype(np.uint32)
+            tf = time.perf_counter()
             B.oasm_feed_many(self.ctx, sids, tr.payload, offs[batch], lens[batch].astype(np.uint32))
             ending = sids[last[batch]].astype(np.int64).tolist()
             if ending:
@@ -159,6 +162,9 @@ class Server:
             B.oasm_step(self.ctx)
             out = B.oasm_drain(self.ctx)
             te = time.perf_counter()
+            phase["schedule"] += tf - t_it
+            phase["feed"] += ts - tf
+            phase["step_drain"] += te - ts
             step_ms.append((te - ts) * 1e3)
             done_at[batch] = te - t0
             steps += 1
@@ -171,6 +177,7 @@ class Server:
                 B.oasm_close_streams(self.ctx, ending)
                 for s in ending:
                     sid_of[ext_of.pop(s)] = -2
+            phase["close"] += time.perf_counter() - te
         wall = time.perf_counter() - t0
         lat = (done_at - times) * 1e3
         ok = ~np.isnan(lat)
@@ -186,6 +193,7 @@ class Server:
             "step_ms_p99": float(np.percentile(step_ms, 99)) if step_ms else None,
             "step_ms_max": float(max(step_ms)) if step_ms else None,
             "mean_batch_bytes": fed_bytes / max(1, steps),
+            "phase_ms_per_step": {k: v * 1e3 / max(1, steps) for k, v in phase.items()},
             "streams_admitted": admitted, "max_waiting_streams": max_wait,
         }
         if collect:
