@@ -174,6 +174,8 @@ struct oasm_ctx {
   uint32_t n_pref_pat = 0;
   PrefSlot* d_pdir = nullptr;
   uint32_t pdir_bits = 0, pmax_probe = 0;
+  uint32_t* d_pbloom = nullptr;
+  uint32_t pbloom_bits = 0;
   PrefEntry* d_pent = nullptr;
   uint8_t* d_pbytes = nullptr;
   uint32_t* d_poff = nullptr;
@@ -328,7 +330,7 @@ void free_ctx(oasm_ctx* c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   auto f = [](void* p) { if (p) cudaFree(p); };
   f(c->d_m); f(c->d_K); f(c->d_mem_off); f(c->d_peq_rev);
-  f(c->d_pdir); f(c->d_pent); f(c->d_pbytes); f(c->d_poff); f(c->pset.p);
+  f(c->d_pdir); f(c->d_pent); f(c->d_pbytes); f(c->d_poff); f(c->pset.p); f(c->d_pbloom);
   for (auto& b : c->buckets) { f(b.d_groups); f(b.d_peq); }
   f(c->d_tails); f(c->d_hdr); f(c->d_mem);
   f(c->arena.p); f(c->dstage.p); f(c->upload.p); f(c->cand.p); f(c->keys.p);
@@ -407,6 +409,23 @@ int build_prefilter(oasm_ctx* ctx, const std::vector<char>& pref) {
   CK(cudaMemcpy(ctx->d_poff, poff.data(), size_t(n) * 4, cudaMemcpyHostToDevice));
   ctx->pdir_bits = bits;
   ctx->pmax_probe = max_probe;
+  // Bloom bits over the distinct prefixes (two hash bits each), at most 64 KiB
+  // so that two filter blocks fit an SM: a start whose key misses a bit has
+  // no piece and skips the directory
+  uint32_t bb = 12;
+  while (bb < 19 && (size_t(1) << bb) < 16 * distinct) ++bb;
+  std::vector<uint32_t> bloom((size_t(1) << bb) / 32, 0u);
+  for (size_t i = 0; i < ents.size(); ++i) {
+    if (i && ents[i].first == ents[i - 1].first) continue;
+    const uint32_t key = ents[i].first;
+    const uint32_t b1 = (key * 0x9E3779B1u) >> (32u - bb);
+    const uint32_t b2 = ((key ^ (key >> 15)) * 0x2C1B3C6Du) >> (32u - bb);
+    bloom[b1 >> 5] |= 1u << (b1 & 31);
+    bloom[b2 >> 5] |= 1u << (b2 & 31);
+  }
+  CK(cudaMalloc(&ctx->d_pbloom, bloom.size() * 4));
+  CK(cudaMemcpy(ctx->d_pbloom, bloom.data(), bloom.size() * 4, cudaMemcpyHostToDevice));
+  ctx->pbloom_bits = bb;
   return OASM_OK;
 }
 
@@ -644,7 +663,7 @@ struct StepPlan {
   uint64_t new_bytes = 0;
 };
 
-constexpr int64_t kPrefSeg = 4096;  // start positions per piece-filter block
+constexpr int64_t kPrefSeg = kPrefSegMax;  // start positions per piece-filter segment
 
 int plan_step(oasm_ctx* ctx, StepPlan& pl) {
   const int T = ctx->T;
@@ -802,6 +821,9 @@ int enqueue_step(oasm_ctx* ctx, StepPlan& pl, const WorkItem* d_items, const Reg
     f.n_segs = int(pl.region_off[nb + 1] - pl.region_off[nb]);
     f.set = ctx->pset.p;
     f.set_mask = ctx->pset.cap - 1;
+    f.bloom = ctx->d_pbloom;
+    f.bloom_bits = ctx->pbloom_bits;
+    f.grid = ctx->num_sms * 2;
     if (f.n_segs > 0) {
       if (tm) CK(record_event(ctx, ctx->ev[8], s));
       CK(cudaMemsetAsync(ctx->pset.p, 0xff, ctx->pset.cap * sizeof(unsigned long long), s));
@@ -1245,7 +1267,8 @@ int oasm_create(const uint8_t* const* pat, const uint32_t* len, const uint32_t* 
   {
     int max_smem = 0;
     cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
-    if (prepare_scan_kernels(max_smem) != cudaSuccess) {
+    if (prepare_scan_kernels(max_smem) != cudaSuccess ||
+        prepare_prefilter_kernel(64 << 10) != cudaSuccess) {
       cudaGetLastError();
       fail(ctx, OASM_ECUDA, "setting the scan kernels' shared-memory limit failed");
       return bail(OASM_ECUDA);

@@ -63,8 +63,13 @@ struct PrefArgs {
   int32_t pad;
   unsigned long long* set;       // (end, pattern) keys; all ones = empty
   unsigned long long set_mask;   // capacity - 1 (a power of two)
+  const uint32_t* bloom;         // 2^bloom_bits bits: two hash bits per piece prefix
+  uint32_t bloom_bits;
+  int32_t grid;                  // resident blocks (each walks many segments)
 };
+constexpr int kPrefSegMax = 4096;  // start positions per segment
 cudaError_t launch_prefilter(const StepParams& p, const PrefArgs& f, cudaStream_t s);
+cudaError_t prepare_prefilter_kernel(int max_smem_bytes);
 
 cudaError_t launch_verify(const StepParams& p, cudaStream_t s);
 

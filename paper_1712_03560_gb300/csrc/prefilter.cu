@@ -69,59 +69,103 @@ __device__ bool set_insert(const PrefArgs& F, unsigned long long key, bool* full
   return false;
 }
 
+__device__ __forceinline__ uint32_t bloom_h2(uint32_t key, uint32_t bits) {
+  return ((key ^ (key >> 15)) * 0x2C1B3C6Du) >> (32u - bits);
+}
+
+// Proposes the ends of the piece matches at start x (text at t); j0/j1 =
+// the directory entries whose piece starts with t's four bytes.
+__device__ void piece_matches(const StepParams& P, const PrefArgs& F, const WorkItem& w,
+                              uint32_t wi, int64_t x, const uint8_t* t, uint32_t j0, uint32_t j1) {
+  for (uint32_t j = j0; j < j1; ++j) {
+    const PrefEntry pe = F.ent[j];
+    if (x + pe.q > w.e_new) continue;
+    const uint8_t* pp = F.pbytes + F.poff[pe.pat] + pe.off;
+    bool eq = true;
+    for (int i = 4; i < pe.q && eq; ++i) eq = pp[i] == t[i];
+    if (!eq) continue;
+    const int m = P.m[pe.pat], K = P.K[pe.pat];
+    const int64_t ec = x - pe.off + m - 1;
+    const int64_t lo = max(ec - K, max(int64_t(0), w.e_prev - 2 * int64_t(K)));
+    const int64_t hi = min(ec + K, w.e_new - 1);
+    for (int64_t e = lo; e <= hi; ++e) {
+      const unsigned long long arena_off = w.arena_base + uint64_t(e - w.base_pos);
+      bool full = false;
+      const bool fresh = set_insert(F, (arena_off << 24) | pe.pat, &full);
+      if (full) atomicOr(&P.ctr->overflow, kSetOverflow | kCandOverflow);
+      if (!fresh) continue;
+      // the set stays at most half full (short probe runs)
+      if (warp_add1(&P.ctr->n_pref) + 1 > (F.set_mask + 1) / 2)
+        atomicOr(&P.ctr->overflow, kSetOverflow | kCandOverflow);
+      const unsigned long long o = warp_add1(&P.ctr->n_cand);
+      if (o < P.cap_cand) {
+        Candidate c;
+        c.wi = wi;
+        c.pat = pe.pat;
+        c.e_rel = uint64_t(e - w.base_pos);
+        P.cand[o] = c;
+      } else {
+        atomicOr(&P.ctr->overflow, kCandOverflow);
+      }
+    }
+  }
+}
+
+// Resident blocks walk the segments.  Per segment: (1) the segment's bytes
+// are staged in shared memory; (2) every thread tests its starts' 4-byte keys
+// against the Bloom bits (shared memory) and probes the directory only on a
+// pass, queueing starts whose key is in the directory; (3) the block works
+// through the queue, so the rare matches do not leave most of a warp idle.
 __global__ void __launch_bounds__(256) prefilter_kernel(const StepParams P, const PrefArgs F) {
+  extern __shared__ __align__(16) uint32_t bloom_s[];
+  __shared__ __align__(16) uint8_t stage[kPrefSegMax + 64];
+  __shared__ uint32_t qx[kPrefSegMax];   // queued starts (relative to the segment)
+  __shared__ uint32_t qs[kPrefSegMax];   // their directory slots
+  __shared__ unsigned qn;
   if (F.dir_bits == 0) return;
+  const uint32_t nbw = (1u << F.bloom_bits) >> 5;
+  for (uint32_t i = threadIdx.x; i < nbw; i += blockDim.x) bloom_s[i] = F.bloom[i];
+  const uint32_t dmask = (1u << F.dir_bits) - 1u;
   for (int sg = blockIdx.x; sg < F.n_segs; sg += gridDim.x) {
     const Region R = F.segs[sg];
     const WorkItem w = P.items[R.wi];
     const uint8_t* base = P.arena + w.arena_base;  // text position w.base_pos
-    for (int64_t x = R.a + threadIdx.x; x < R.b; x += blockDim.x) {
-      // segments end 4 symbols before e_new: t[x .. x + 3] is text
-      const uint8_t* t = base + (x - w.base_pos);
-      const uint32_t key = uint32_t(t[0]) | (uint32_t(t[1]) << 8) | (uint32_t(t[2]) << 16) |
-                           (uint32_t(t[3]) << 24);
+    const uint8_t* src = base + (R.a - w.base_pos);
+    const int nx = int(R.b - R.a);                  // starts; bytes needed nx + 3
+    // aligned 16-byte copies (the arena is padded on both sides)
+    const uintptr_t s0 = reinterpret_cast<uintptr_t>(src) & ~uintptr_t(15);
+    const int shift = int(reinterpret_cast<uintptr_t>(src) - s0);
+    const int nv = (shift + nx + 3 + 15) >> 4;
+    __syncthreads();  // previous segment's queue and stage are done
+    for (int v = threadIdx.x; v < nv; v += blockDim.x)
+      reinterpret_cast<uint4*>(stage)[v] = reinterpret_cast<const uint4*>(s0)[v];
+    if (threadIdx.x == 0) qn = 0;
+    __syncthreads();
+    const uint32_t* st32 = reinterpret_cast<const uint32_t*>(stage);
+    for (int xr = threadIdx.x; xr < nx; xr += blockDim.x) {
+      const int o = shift + xr;
+      const uint32_t key = __funnelshift_r(st32[o >> 2], st32[(o >> 2) + 1], (o & 3) * 8);
+      const uint32_t b1 = dir_hash(key, F.bloom_bits), b2 = bloom_h2(key, F.bloom_bits);
+      if (!((bloom_s[b1 >> 5] >> (b1 & 31)) & (bloom_s[b2 >> 5] >> (b2 & 31)) & 1u)) continue;
       uint32_t h = dir_hash(key, F.dir_bits);
-      const uint32_t mask = (1u << F.dir_bits) - 1u;
       for (uint32_t pr = 0; pr <= F.max_probe; ++pr) {
         const PrefSlot sl = F.dir[h];
         if (sl.count == 0) break;
         if (sl.key == key) {
-          for (uint32_t j = sl.start; j < sl.start + sl.count; ++j) {
-            const PrefEntry pe = F.ent[j];
-            if (x + pe.q > w.e_new) continue;
-            const uint8_t* pp = F.pbytes + F.poff[pe.pat] + pe.off;
-            bool eq = true;
-            for (int i = 4; i < pe.q && eq; ++i) eq = pp[i] == t[i];
-            if (!eq) continue;
-            const int m = P.m[pe.pat], K = P.K[pe.pat];
-            const int64_t ec = x - pe.off + m - 1;
-            const int64_t lo = max(ec - K, max(int64_t(0), w.e_prev - 2 * int64_t(K)));
-            const int64_t hi = min(ec + K, w.e_new - 1);
-            for (int64_t e = lo; e <= hi; ++e) {
-              const unsigned long long arena_off = w.arena_base + uint64_t(e - w.base_pos);
-              bool full = false;
-              const bool fresh = set_insert(F, (arena_off << 24) | pe.pat, &full);
-              if (full) atomicOr(&P.ctr->overflow, kSetOverflow | kCandOverflow);
-              if (!fresh) continue;
-              // the set stays at most half full (short probe runs)
-              if (warp_add1(&P.ctr->n_pref) + 1 > (F.set_mask + 1) / 2)
-                atomicOr(&P.ctr->overflow, kSetOverflow | kCandOverflow);
-              const unsigned long long o = warp_add1(&P.ctr->n_cand);
-              if (o < P.cap_cand) {
-                Candidate c;
-                c.wi = R.wi;
-                c.pat = pe.pat;
-                c.e_rel = uint64_t(e - w.base_pos);
-                P.cand[o] = c;
-              } else {
-                atomicOr(&P.ctr->overflow, kCandOverflow);
-              }
-            }
-          }
+          const unsigned q = atomicAdd(&qn, 1u);  // at most one per start: q < kPrefSegMax
+          qx[q] = uint32_t(xr);
+          qs[q] = h;
           break;
         }
-        h = (h + 1) & mask;
+        h = (h + 1) & dmask;
       }
+    }
+    __syncthreads();
+    const unsigned nq = qn;
+    for (unsigned i = threadIdx.x; i < nq; i += blockDim.x) {
+      const int64_t x = R.a + qx[i];
+      const PrefSlot sl = F.dir[qs[i]];
+      piece_matches(P, F, w, R.wi, x, base + (x - w.base_pos), sl.start, sl.start + sl.count);
     }
   }
 }
@@ -130,9 +174,15 @@ __global__ void __launch_bounds__(256) prefilter_kernel(const StepParams P, cons
 
 cudaError_t launch_prefilter(const StepParams& p, const PrefArgs& f, cudaStream_t s) {
   if (f.n_segs <= 0 || f.dir_bits == 0) return cudaSuccess;
-  const int grid = f.n_segs < 152 * 8 ? f.n_segs : 152 * 8;
-  prefilter_kernel<<<grid, 256, 0, s>>>(p, f);
+  const int grid = f.n_segs < f.grid ? f.n_segs : f.grid;
+  const size_t smem = size_t(1) << (f.bloom_bits - 3);
+  prefilter_kernel<<<grid, 256, smem, s>>>(p, f);
   return cudaGetLastError();
+}
+
+cudaError_t prepare_prefilter_kernel(int max_smem_bytes) {
+  return cudaFuncSetAttribute(prefilter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              max_smem_bytes);
 }
 
 }  // namespace oasm
