@@ -73,10 +73,20 @@ __device__ __forceinline__ uint32_t bloom_h2(uint32_t key, uint32_t bits) {
   return ((key ^ (key >> 15)) * 0x2C1B3C6Du) >> (32u - bits);
 }
 
+// Block-local candidate buffer: proposals are collected in shared memory and
+// written with one global reservation per segment (a global counter bumped
+// per candidate serialises at the L2).
+constexpr int kCandBuf = 512;
+struct CandBuf {
+  Candidate c[kCandBuf];
+  unsigned n;        // proposals this segment (may exceed kCandBuf)
+};
+
 // Proposes the ends of the piece matches at start x (text at t); j0/j1 =
 // the directory entries whose piece starts with t's four bytes.
 __device__ void piece_matches(const StepParams& P, const PrefArgs& F, const WorkItem& w,
-                              uint32_t wi, int64_t x, const uint8_t* t, uint32_t j0, uint32_t j1) {
+                              uint32_t wi, int64_t x, const uint8_t* t, uint32_t j0, uint32_t j1,
+                              CandBuf& cb) {
   for (uint32_t j = j0; j < j1; ++j) {
     const PrefEntry pe = F.ent[j];
     if (x + pe.q > w.e_new) continue;
@@ -94,18 +104,19 @@ __device__ void piece_matches(const StepParams& P, const PrefArgs& F, const Work
       const bool fresh = set_insert(F, (arena_off << 24) | pe.pat, &full);
       if (full) atomicOr(&P.ctr->overflow, kSetOverflow | kCandOverflow);
       if (!fresh) continue;
-      // the set stays at most half full (short probe runs)
-      if (warp_add1(&P.ctr->n_pref) + 1 > (F.set_mask + 1) / 2)
-        atomicOr(&P.ctr->overflow, kSetOverflow | kCandOverflow);
-      const unsigned long long o = warp_add1(&P.ctr->n_cand);
-      if (o < P.cap_cand) {
-        Candidate c;
-        c.wi = wi;
-        c.pat = pe.pat;
-        c.e_rel = uint64_t(e - w.base_pos);
-        P.cand[o] = c;
-      } else {
-        atomicOr(&P.ctr->overflow, kCandOverflow);
+      Candidate c;
+      c.wi = wi;
+      c.pat = pe.pat;
+      c.e_rel = uint64_t(e - w.base_pos);
+      const unsigned slot = atomicAdd(&cb.n, 1u);
+      if (slot < unsigned(kCandBuf)) {
+        cb.c[slot] = c;
+      } else {  // buffer full: this one goes straight to global memory
+        const unsigned long long o = warp_add1(&P.ctr->n_cand);
+        if (o < P.cap_cand)
+          P.cand[o] = c;
+        else
+          atomicOr(&P.ctr->overflow, kCandOverflow);
       }
     }
   }
@@ -122,6 +133,8 @@ __global__ void __launch_bounds__(256) prefilter_kernel(const StepParams P, cons
   __shared__ uint32_t qx[kPrefSegMax];   // queued starts (relative to the segment)
   __shared__ uint32_t qs[kPrefSegMax];   // their directory slots
   __shared__ unsigned qn;
+  __shared__ CandBuf cb;
+  __shared__ unsigned long long cbase;
   if (F.dir_bits == 0) return;
   const uint32_t nbw = (1u << F.bloom_bits) >> 5;
   for (uint32_t i = threadIdx.x; i < nbw; i += blockDim.x) bloom_s[i] = F.bloom[i];
@@ -139,7 +152,10 @@ __global__ void __launch_bounds__(256) prefilter_kernel(const StepParams P, cons
     __syncthreads();  // previous segment's queue and stage are done
     for (int v = threadIdx.x; v < nv; v += blockDim.x)
       reinterpret_cast<uint4*>(stage)[v] = reinterpret_cast<const uint4*>(s0)[v];
-    if (threadIdx.x == 0) qn = 0;
+    if (threadIdx.x == 0) {
+      qn = 0;
+      cb.n = 0;
+    }
     __syncthreads();
     const uint32_t* st32 = reinterpret_cast<const uint32_t*>(stage);
     for (int xr = threadIdx.x; xr < nx; xr += blockDim.x) {
@@ -165,7 +181,24 @@ __global__ void __launch_bounds__(256) prefilter_kernel(const StepParams P, cons
     for (unsigned i = threadIdx.x; i < nq; i += blockDim.x) {
       const int64_t x = R.a + qx[i];
       const PrefSlot sl = F.dir[qs[i]];
-      piece_matches(P, F, w, R.wi, x, base + (x - w.base_pos), sl.start, sl.start + sl.count);
+      piece_matches(P, F, w, R.wi, x, base + (x - w.base_pos), sl.start, sl.start + sl.count, cb);
+    }
+    __syncthreads();
+    // one reservation for the segment's buffered candidates; every proposal
+    // of the segment (buffered or not) counts towards the set's fill
+    const unsigned nb = min(cb.n, unsigned(kCandBuf));
+    if (threadIdx.x == 0 && cb.n) {
+      cbase = nb ? atomicAdd(&P.ctr->n_cand, (unsigned long long)nb) : 0ull;
+      const unsigned long long filled = atomicAdd(&P.ctr->n_pref, (unsigned long long)cb.n) + cb.n;
+      if (filled > (F.set_mask + 1) / 2) atomicOr(&P.ctr->overflow, kSetOverflow | kCandOverflow);
+    }
+    __syncthreads();
+    for (unsigned i = threadIdx.x; i < nb; i += blockDim.x) {
+      const unsigned long long o = cbase + i;
+      if (o < P.cap_cand)
+        P.cand[o] = cb.c[i];
+      else
+        atomicOr(&P.ctr->overflow, kCandOverflow);
     }
   }
 }
