@@ -64,3 +64,25 @@ def test_strerror_and_null_safety():
     cfg = B.oasm_config()
     assert lib.oasm_config_default(ctypes.byref(cfg)) == 0
     assert cfg.max_streams == 64 and cfg.flush_timeout_ms > 0
+
+
+@pytest.mark.parametrize("field,value", [("groups_per_warp", 3), ("prefilter_piece", 2),
+                                         ("prefilter_piece", 129)])
+def test_create_rejects_bad_config(field, value):
+    """Config fields out of range are rejected on the host, before any device work."""
+    lib = B.load()
+    pats = [b"ACGTACGTACGT"]
+    ptrs = (ctypes.c_void_p * 1)(ctypes.cast(ctypes.c_char_p(pats[0]), ctypes.c_void_p))
+    L = (ctypes.c_uint32 * 1)(12)
+    K = (ctypes.c_uint32 * 1)(1)
+    cfg = B.oasm_config_make(**{field: value})
+    ctx = ctypes.c_void_p()
+    rc = lib.oasm_create(ptrs, L, K, 1, None, ctypes.byref(cfg), ctypes.byref(ctx))
+    assert rc == B.OASM_EINVAL
+    assert not ctx.value
+    assert b"config" in lib.oasm_last_error(None)
+
+
+def test_config_maker_rejects_unknown_fields():
+    with pytest.raises(KeyError):
+        B.oasm_config_make(prefilter=4)
