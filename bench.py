@@ -224,9 +224,29 @@ def run_reference(args):
 SERVED_LOADS_GBPS = (0.5, 1.0, 2.0, 3.0, 4.0, 6.0, 10.0, 25.0, 100.0, 400.0)
 
 
-def on_filter(m: int, k: int, piece: int) -> bool:
-    """Whether cfg.prefilter_piece = piece routes a pattern to the piece filter."""
-    return piece > 0 and m // (k + 1) >= piece
+def filter_mask(patterns, ks, piece: int) -> list:
+    """Which patterns cfg.prefilter_piece = piece routes to the piece filter
+    (the library's rule: a fixed minimum piece length, or with piece = 1 the
+    expected piece matches under the pattern set's symbol frequencies)."""
+    if piece == 0:
+        return [False] * len(patterns)
+    if piece >= 4:
+        return [p.size // (int(k) + 1) >= piece for p, k in zip(patterns, ks)]
+    cnt = np.bincount(np.concatenate(patterns), minlength=256).astype(np.float64)
+    f = cnt / cnt.sum()
+    out = []
+    for p, k in zip(patterns, ks):
+        m, parts = p.size, int(k) + 1
+        if m // parts < 4:
+            out.append(False)
+            continue
+        s, off = 0.0, 0
+        for j in range(parts):
+            q = m // parts + (1 if j < m % parts else 0)
+            s += float(np.prod(f[p[off:off + q]]))
+            off += q
+        out.append((2 * int(k) + 1) * s < (1.0 / 4500.0) * ((m + 31) // 32))
+    return out
 
 
 def measured_hbm_gbs():
@@ -286,8 +306,9 @@ def run_served(args):
     best = max(sweep, key=lambda x: x["achieved_gbps"])
     # roofline of the scan over the steps of the best load point (library events)
     peak_ops, _ = B_peak()
-    words = sum((p.size + 31) // 32 for p, k in zip(base.patterns, base.ks)
-                if not on_filter(p.size, int(k), args.prefilter)) * st_best["text_bytes"]
+    fm = filter_mask(base.patterns, base.ks, args.prefilter)
+    words = sum((p.size + 31) // 32 for p, on in zip(base.patterns, fm) if not on) \
+        * st_best["text_bytes"]
     scan_ms = st_best["scan_ms"]
     achieved_alg = words * OPS_PER_WORD_STEP / max(scan_ms * 1e-3, 1e-12) / 1e12
     achieved = st_best["word_steps"] * OPS_PER_WORD_STEP / max(scan_ms * 1e-3, 1e-12) / 1e12
@@ -449,8 +470,8 @@ def main():
     # ---- roofline of the dominant kernel (the forward scan), measured live
     peak_ops, _ = B.oasm_measure_int_peak(dev)
     scan_ms_launch = st["scan_ms"] / max(1, st["scan_launches"])
-    words = sum((p.size + 31) // 32 for p, k in zip(wl.patterns, wl.ks)
-                if not on_filter(p.size, int(k), args.prefilter)) * wl.text_bytes
+    fm = filter_mask(wl.patterns, wl.ks, args.prefilter)
+    words = sum((p.size + 31) // 32 for p, on in zip(wl.patterns, fm) if not on) * wl.text_bytes
     launches_step = max(1, st["scan_launches"] // max(1, args.steps))
     alg_ops_launch = words * OPS_PER_WORD_STEP / launches_step
     achieved_alg = alg_ops_launch / (scan_ms_launch * 1e-3) / 1e12
@@ -538,13 +559,14 @@ def main():
                                                         "verify_ms", "order_ms", "filter_ms",
                                                         "step_ms")},
         "prefilter": None if not args.prefilter else {
-            "piece": args.prefilter,
-            "patterns": sum(on_filter(p.size, int(k), args.prefilter) for p, k in zip(wl.patterns, wl.ks)),
+            "piece": args.prefilter if args.prefilter >= 4 else "auto",
+            "patterns": int(sum(fm)),
             "candidates_per_step": st["prefilter_candidates"] / args.steps,
             # one pass over the text: bytes read per second against the HBM copy peak
-            "text_gbs": wl.text_bytes * args.steps / max(st["prefilter_ms"] * 1e-3, 1e-12) / 1e9,
-            "hbm_frac": wl.text_bytes * args.steps / max(st["prefilter_ms"] * 1e-3, 1e-12) / 1e9
-                        / measured_hbm_gbs()[0]},
+            "text_gbs": None if st["prefilter_ms"] <= 0 else
+            wl.text_bytes * args.steps / (st["prefilter_ms"] * 1e-3) / 1e9,
+            "hbm_frac": None if st["prefilter_ms"] <= 0 else
+            wl.text_bytes * args.steps / (st["prefilter_ms"] * 1e-3) / 1e9 / measured_hbm_gbs()[0]},
         "host_ms_per_step": host_step_ms,
         "library_host_ms_per_step": {k: st[k] / args.steps for k in
                                      ("host_plan_ms", "host_launch_ms", "host_wait_ms",

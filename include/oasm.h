@@ -110,7 +110,10 @@ typedef struct {
                                   is searched by the exact piece filter instead:
                                   exact matches of its pieces propose the ends that
                                   verification checks (pays off where pieces rarely
-                                  match at random, e.g. long byte signatures) */
+                                  match at random, e.g. long byte signatures).
+                                  1: automatic, per pattern, from the expected
+                                  number of piece matches (symbol frequencies of
+                                  the pattern set) against the scan's cost */
 } oasm_config;
 
 /* One occurrence added to S (or, for the raw outputs, one hit/end). */

@@ -349,6 +349,13 @@ void free_ctx(oasm_ctx* c) {
 }
 
 // --------------------------------------------------------------- tables
+// Automatic piece-filter choice: a filter proposal (set insert, candidate,
+// verification) costs about as much as 4,500 scan word-steps (measured on a
+// GB300: DNA texts with K = 3, Zipf bytes with K up to 8), so a pattern goes
+// to the filter when it expects fewer than 1 / 4,500 proposals per text
+// position and scan word.
+constexpr double kAutoProposalsPerWord = 1.0 / 4500.0;
+
 // Piece filter tables: each selected pattern is cut into K + 1 pieces (the
 // first m mod (K + 1) one symbol longer); the directory maps a piece's first
 // four bytes (little-endian) to its run of entries, by open addressing with
@@ -558,12 +565,40 @@ int build_tables(oasm_ctx* ctx) {
     ctx->buckets.push_back(bk);
     return OASM_OK;
   };
-  // patterns whose K + 1 pieces are all at least cfg.prefilter_piece symbols
-  // long go to the piece filter instead of the forward scan
+  // patterns for the piece filter instead of the forward scan:
+  //   prefilter_piece >= 4: every pattern whose K + 1 pieces are all at least
+  //     that many symbols long;
+  //   prefilter_piece == 1 (automatic): a pattern with pieces of 4 or more
+  //     symbols whose expected proposals per text position, (2K + 1) times the
+  //     sum over its pieces of the product of their symbols' frequencies,
+  //     stay under kAutoProposalsPerWord per word the scan would run.  The
+  //     frequencies are those of all pattern bytes together (the patterns
+  //     stand in for the text, which is not known yet).
   std::vector<char> pref(n, 0);
-  if (ctx->cfg.prefilter_piece) {
+  if (ctx->cfg.prefilter_piece >= 4) {
     for (uint32_t p = 0; p < n; ++p)
       pref[p] = ctx->m[p] / (ctx->K[p] + 1u) >= ctx->cfg.prefilter_piece;
+  } else if (ctx->cfg.prefilter_piece == 1) {
+    double cnt[256] = {0};
+    double tot = 0;
+    for (uint32_t p = 0; p < n; ++p)
+      for (uint8_t c : ctx->pats[p]) cnt[c] += 1, tot += 1;
+    for (uint32_t p = 0; p < n; ++p) {
+      const int m = ctx->m[p], parts = ctx->K[p] + 1;
+      if (m / parts < 4) continue;
+      double sum = 0;
+      int off = 0;
+      for (int j = 0; j < parts; ++j) {
+        const int q = m / parts + (j < m % parts ? 1 : 0);
+        double pr = 1;
+        for (int i = 0; i < q; ++i) pr *= cnt[ctx->pats[p][off + i]] / tot;
+        sum += pr;
+        off += q;
+      }
+      pref[p] = double(2 * ctx->K[p] + 1) * sum < kAutoProposalsPerWord * ((m + 31) / 32);
+    }
+  }
+  if (ctx->cfg.prefilter_piece) {
     int rc = build_prefilter(ctx, pref);
     if (rc) return rc;
   }
@@ -1238,8 +1273,8 @@ int oasm_create(const uint8_t* const* pat, const uint32_t* len, const uint32_t* 
     return OASM_EINVAL;
   }
   if (cfg && (cfg->groups_per_warp > 2 ||
-              (cfg->prefilter_piece != 0 && (cfg->prefilter_piece < 4 || cfg->prefilter_piece > 128)))) {
-    g_create_err = "config: groups_per_warp must be 0, 1 or 2; prefilter_piece 0 or 4..128";
+              (cfg->prefilter_piece > 1 && (cfg->prefilter_piece < 4 || cfg->prefilter_piece > 128)))) {
+    g_create_err = "config: groups_per_warp must be 0, 1 or 2; prefilter_piece 0, 1 or 4..128";
     return OASM_EINVAL;
   }
   if (cfg && cfg->prefilter_piece && n_pat >= (1u << 24)) {

@@ -375,6 +375,26 @@ def test_piece_filter_equals_scan_and_oracle(seed):
         B.oasm_destroy(ctx)
 
 
+@pytest.mark.parametrize("workload", ["dna", "zipf"])
+def test_piece_filter_automatic_choice(workload):
+    """prefilter_piece = 1: the library picks per pattern between the scan and
+    the piece filter; the output equals the oracle's and the scan-only one."""
+    rng = np.random.default_rng(77 if workload == "dna" else 78)
+    if workload == "dna":
+        wl = W.dictionary_dna(seed=21, n=300_000, n_pat=120, copies=6)
+        pats, ks, text = wl.patterns, wl.ks, wl.texts[0]
+    else:
+        wl = W.bytes_zipf(seed=22, n=300_000, n_pat=150, copies=4)
+        pats, ks, text = wl.patterns, wl.ks, wl.texts[0]
+    want = oracle_rows(pats, ks, text)
+    got, _ = run_gpu(pats, ks, text, cfg={"prefilter_piece": 1})
+    assert len(want) > 0
+    assert canon(got) == want
+    split, _ = run_gpu(pats, ks, text, cfg={"prefilter_piece": 1},
+                       splits=np.sort(rng.integers(0, text.size, size=4)))
+    assert canon(split) == want
+
+
 def test_piece_filter_set_grows_on_repetitive_text():
     """A text of one repeated symbol makes every piece match everywhere: the
     filter's (end, pattern) set overflows, grows and the step re-runs; pieces
