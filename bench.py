@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-alt", action="store_true",
+                    help="skip the extra measurement with the automatic piece filter")
     ap.add_argument("--served-packets", type=int, default=200000)
     ap.add_argument("--served-batch-mb", type=float, default=32.0,
                     help="byte budget of one serving step (MiB)")
@@ -533,7 +535,7 @@ def main():
             from paper_1712_03560_gb300 import binding as B2
             sub_pats = [wl.patterns[i] for i in idx]
             sub_ks = [int(wl.ks[i]) for i in idx]
-            with B2.Matcher(sub_pats, sub_ks) as mt:
+            with B2.Matcher(sub_pats, sub_ks, prefilter_piece=args.prefilter) as mt:
                 g = mt.search(torch.from_numpy(np.ascontiguousarray(text)).to(f"cuda:{dev}"),
                               device=True)
             got = sorted((int(r["pattern_id"]), int(r["decided_at"]), int(r["k"]),
@@ -542,6 +544,70 @@ def main():
                            int(r["start"]), int(r["len"])) for r in ores)
             parity = {"patterns": len(idx), "text_symbols": int(text.size),
                       "occurrences": len(want), "equal": got == want}
+
+    # ---- the same workload with the automatic piece filter (prefilter_piece = 1):
+    # patterns whose pieces rarely match go to the exact filter, the rest stay
+    # on the scan; device-resident inputs, timed like the main value
+    alt = None
+    if args.prefilter == 0 and not args.no_alt and world == 1:
+        B.oasm_destroy(ctx)
+        ctx = None
+        ctx2 = B.oasm_create(wl.patterns, wl.ks, None,
+                             {"device": dev, "timing": 1, "max_streams": max(64, len(wl.texts)),
+                              "prefilter_piece": 1})
+        try:
+            stream2 = torch.cuda.ExternalStream(B.oasm_cuda_stream(ctx2), device=dev)
+            if not args.no_autotune:
+                big = max(dtexts, key=lambda t: t.numel())
+                B.oasm_autotune(ctx2, big[: min(big.numel(), 32 << 20)])
+            last = [None]
+
+            def step2():
+                sids = B.oasm_open_streams(ctx2, len(dtexts))
+                for sd, t in zip(sids.tolist(), dtexts):
+                    B.oasm_feed_device(ctx2, sd, t)
+                B.oasm_end_streams(ctx2, sids)
+                B.oasm_step(ctx2)
+                last[0] = B.oasm_drain(ctx2)
+                B.oasm_close_streams(ctx2, sids)
+            for _ in range(args.warmup):
+                step2()
+            torch.cuda.synchronize()
+            B.oasm_reset_stats(ctx2)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream2)
+            for _ in range(args.steps):
+                step2()
+            e1.record(stream2)
+            e1.synchronize()
+            ms2 = e0.elapsed_time(e1)
+            st2 = B.oasm_get_stats(ctx2)
+            fm2 = filter_mask(wl.patterns, wl.ks, 1)
+            par2 = None
+            if parity is not None and len(wl.texts) == 1:
+                # the sampled patterns' rows of the full output against the oracle
+                sel = set(int(i) for i in idx)
+                full = text.size == wl.texts[0].size
+                lim = {i: text.size - wl.patterns[i].size - int(wl.ks[i]) for i in sel}
+                out2 = last[0]
+                pos = {int(i): j for j, i in enumerate(idx)}
+                got2 = sorted((pos[int(r["pattern_id"])], int(r["decided_at"]), int(r["k"]),
+                               int(r["start"]), int(r["len"])) for r in out2
+                              if int(r["pattern_id"]) in sel and
+                              (full or int(r["decided_at"]) <= lim[int(r["pattern_id"])]))
+                want2 = sorted(w for w in want if full or w[1] <= lim[int(idx[w[0]])])
+                par2 = {"patterns": len(idx), "occurrences": len(want2), "equal": got2 == want2}
+            alt = {"path": "automatic piece filter + scan (prefilter_piece = 1)",
+                   "value": cells_step * args.steps / (ms2 * 1e-3) / 1e9, "unit": "GCUPS",
+                   "ms_per_step": ms2 / args.steps,
+                   "patterns_on_filter": int(sum(fm2)),
+                   "kernel_ms": {k: st2[k] / args.steps for k in ("scan_ms", "prefilter_ms",
+                                                                  "verify_ms", "order_ms",
+                                                                  "filter_ms", "step_ms")},
+                   "parity_sample": par2}
+        finally:
+            B.oasm_destroy(ctx2)
 
     line = {
         "metric": "GCUPS", "value": value, "unit": "GCUPS", "n_gpus": world,
@@ -579,6 +645,7 @@ def main():
         "e2e": e2e,
         "cpu_baseline": cpu,
         "parity_sample": parity,
+        "with_piece_filter": alt,
         "clocks": clk,
     }
     print(json.dumps(line), flush=True)
