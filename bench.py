@@ -62,11 +62,12 @@ def parse():
                     help="byte budget of one serving step (MiB)")
     ap.add_argument("--prefilter", type=int, default=None,
                     help="cfg.prefilter_piece: patterns whose K+1 pieces are at least this "
-                         "long use the exact piece filter instead of the scan (0 = off; "
-                         "default 4 for the served signatures, 0 elsewhere)")
+                         "long use the exact piece filter instead of the scan (0 = off, "
+                         "1 = automatic per pattern; default 1 for the served signatures, "
+                         "0 elsewhere)")
     a = ap.parse_args()
     if a.prefilter is None:
-        a.prefilter = 4 if a.workload == "served" else 0
+        a.prefilter = 1 if a.workload == "served" else 0
     return a
 
 
