@@ -1467,7 +1467,14 @@ int oasm_feed(oasm_ctx* ctx, uint32_t sid, const uint8_t* chunk, size_t n) {
   if ((rc = ensure_host(ctx, &ctx->h_stage, &ctx->h_stage_cap, ctx->h_stage_used + n,
                         ctx->h_stage_used)))
     return rc;
-  memcpy(ctx->h_stage + ctx->h_stage_used, chunk, n);
+  {  // large chunks are copied into pinned staging on several host threads
+    uint8_t* dst = ctx->h_stage + ctx->h_stage_used;
+    const size_t parts = n > (size_t(4) << 20) ? 16 : 1;
+    parallel_parts(parts, 1, [&](size_t t0, size_t t1) {
+      const size_t lo = n * t0 / parts, hi = n * t1 / parts;
+      memcpy(dst + lo, chunk + lo, hi - lo);
+    });
+  }
   s.pieces.push_back(Piece{false, nullptr, ctx->h_stage_used, n});
   ctx->h_stage_used += n;
   ctx->host_pending += n;

@@ -189,6 +189,21 @@ def test_raw_outputs_less_naive_and_all_hits():
     assert len(kept) <= len(ends) <= len(allh)
 
 
+@pytest.mark.parametrize("piece", [1, 4])
+def test_raw_outputs_through_the_piece_filter(piece):
+    """Less Naive ends and the full hit set of Eq. 2 with patterns on the piece
+    filter: the filter's candidates are a superset of the scan's, so the raw
+    outputs must still equal the oracle's."""
+    rng = np.random.default_rng(19 + piece)
+    pats, ks, text = random_case(rng, 256, 24, 12, 60, 20000, kmax=3)
+    cfg = {"prefilter_piece": piece}
+    ends, _ = run_gpu(pats, ks, text, {"output": "ends"}, cfg=cfg)
+    assert canon(ends) == oracle_rows(pats, ks, text, mode="ends")
+    allh, _ = run_gpu(pats, ks, text, {"output": "all_hits"}, cfg=cfg)
+    assert canon(allh) == oracle_rows(pats, ks, text, mode="hits")
+    assert len(allh) > 0
+
+
 def test_small_buffers_regrow_and_rerun():
     """A step whose device buffers overflow is re-run after they grow."""
     rng = np.random.default_rng(21)
