@@ -11,15 +11,19 @@
 // their work, the host grows the buffer and re-runs the step from the same
 // (unchanged) state.
 #include <cuda_runtime.h>
+#include <unistd.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
+#include <condition_variable>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
-#include <string>
+#include <functional>
 #include <mutex>
+#include <string>
 #include <thread>
 #include <vector>
 
@@ -64,21 +68,92 @@ struct NoInitAlloc : std::allocator<T> {
 };
 using HitVec = std::vector<oasm_hit, NoInitAlloc<oasm_hit>>;
 
-// Runs f(lo, hi) over [0, n) split into contiguous parts on up to `threads`
-// host threads (one part when n is small).
+// A small pool of host threads, started on first use and kept for the life of
+// the process: the host-side copies of a step fan out to it without paying a
+// thread start per call.  One job runs at a time (callers are serialised).
+class HostPool {
+ public:
+  static HostPool& get() {
+    static HostPool pool;
+    return pool;
+  }
+  // the caller works too; a forked child has no workers (threads do not
+  // survive fork) and runs every part itself
+  size_t size() const { return getpid() == pid_ ? workers_.size() + 1 : 1; }
+  // Runs job(i) for i in [0, n) and returns when all have finished.
+  void run(size_t n, const std::function<void(size_t)>& job) {
+    std::lock_guard<std::mutex> one(job_mu_);
+    {
+      std::lock_guard<std::mutex> g(mu_);
+      job_ = &job;
+      n_ = n;
+      next_.store(0);
+      busy_ = workers_.size();
+      ++gen_;
+    }
+    cv_.notify_all();
+    work();
+    std::unique_lock<std::mutex> g(mu_);
+    done_cv_.wait(g, [&] { return busy_ == 0; });
+    job_ = nullptr;
+  }
+  ~HostPool() {
+    if (getpid() != pid_) return;  // a forked child: the workers are not ours
+    {
+      std::lock_guard<std::mutex> g(mu_);
+      stop_ = true;
+      ++gen_;
+    }
+    cv_.notify_all();
+    for (auto& t : workers_) t.join();
+  }
+
+ private:
+  HostPool() : pid_(getpid()) {
+    unsigned hw = std::thread::hardware_concurrency();
+    const unsigned n = hw ? std::min(hw, 16u) : 1u;
+    for (unsigned i = 1; i < n; ++i) workers_.emplace_back([this] { loop(); });
+  }
+  void work() {
+    for (size_t i; (i = next_.fetch_add(1)) < n_;) (*job_)(i);
+  }
+  void loop() {
+    uint64_t seen = 0;
+    while (true) {
+      {
+        std::unique_lock<std::mutex> g(mu_);
+        cv_.wait(g, [&] { return gen_ != seen; });
+        seen = gen_;
+        if (stop_) return;
+      }
+      work();
+      std::lock_guard<std::mutex> g(mu_);
+      if (--busy_ == 0) done_cv_.notify_one();
+    }
+  }
+  std::vector<std::thread> workers_;
+  std::mutex mu_, job_mu_;
+  std::condition_variable cv_, done_cv_;
+  const std::function<void(size_t)>* job_ = nullptr;
+  size_t n_ = 0, busy_ = 0;
+  std::atomic<size_t> next_{0};
+  uint64_t gen_ = 0;
+  bool stop_ = false;
+  pid_t pid_;
+};
+
+// Runs f(lo, hi) over [0, n) split into contiguous parts on the host pool
+// (one part, on the caller, when n is small).
 template <class F>
 void parallel_parts(size_t n, size_t min_per_part, F f) {
-  unsigned hw = std::thread::hardware_concurrency();
-  size_t parts = std::min<size_t>(hw ? std::min(hw, 16u) : 1u, n / std::max<size_t>(1, min_per_part));
+  HostPool& pool = HostPool::get();
+  size_t parts = std::min<size_t>(std::min<size_t>(pool.size(), 16), n / std::max<size_t>(1, min_per_part));
   if (parts <= 1) {
     f(size_t(0), n);
     return;
   }
-  std::vector<std::thread> th;
-  th.reserve(parts);
-  for (size_t t = 0; t < parts; ++t)
-    th.emplace_back(f, n * t / parts, n * (t + 1) / parts);
-  for (auto& x : th) x.join();
+  const std::function<void(size_t)> job = [&](size_t t) { f(n * t / parts, n * (t + 1) / parts); };
+  pool.run(parts, job);
 }
 
 // Copies the pieces (dst, src, records) on up to 16 host threads, each
