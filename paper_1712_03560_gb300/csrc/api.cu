@@ -1492,7 +1492,13 @@ int oasm_close_stream(oasm_ctx* ctx, uint32_t sid) {
     if (!pc.dev) ctx->host_pending -= pc.n;
   // a stream that never fed anything since its last end has empty windows
   const bool clean = s.clean && s.pos == 0;
+  // the slot keeps its queue's storage for the next stream it serves (no new
+  // pages to touch when large outputs repeat)
+  HitVec keep;
+  keep.swap(s.ready);
+  keep.clear();
   s = StreamRec();
+  s.ready.swap(keep);
   s.clean = clean;
   --ctx->n_open;
   if (ctx->host_pending == 0) ctx->h_stage_used = 0;
