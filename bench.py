@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--no-alt", action="store_true",
                     help="skip the extra measurement with the automatic piece filter")
     ap.add_argument("--served-packets", type=int, default=200000)
+    ap.add_argument("--served-engine", default="native", choices=["native", "python"],
+                    help="serving loop: inside the library (oasm_replay) or in Python")
     ap.add_argument("--served-batch-mb", type=float, default=32.0,
                     help="byte budget of one serving step (MiB)")
     ap.add_argument("--prefilter", type=int, default=None,
@@ -286,24 +288,27 @@ def run_served(args):
                       max_batch_bytes=int(args.served_batch_mb * (1 << 20))) as srv:
         # warm-up: grow every step buffer to the sweep's sizes, then a paced pass
         for _ in range(max(1, args.warmup)):
-            srv.replay(W.served(seed=99, n_packets=20000, gbps=10.0), realtime=False)
-        srv.replay(W.served(seed=98, n_packets=20000, gbps=1.0), realtime=True)
+            srv.replay(W.served(seed=99, n_packets=20000, gbps=10.0), realtime=False,
+                       engine=args.served_engine)
+        srv.replay(W.served(seed=98, n_packets=20000, gbps=1.0), realtime=True,
+                   engine=args.served_engine)
         clocks.start()
         srv.reset_stats()
         st_best, kept_best = None, 0
         for g in SERVED_LOADS_GBPS:
             tr = W.served(seed=int(5 + 10 * g), n_packets=n_pkt, gbps=g)
             st0 = srv.stats()
-            r = srv.replay(tr, realtime=True)
+            r = srv.replay(tr, realtime=True, engine=args.served_engine)
             st1 = srv.stats()
             r["gcups"] = msum * r["bytes"] / r["wall_s"] / 1e9
             if not sweep or r["achieved_gbps"] > max(x["achieved_gbps"] for x in sweep):
                 st_best = {k: st1[k] - st0[k] for k in st1}
                 kept_best = r["kept"]
-            sweep.append({k: r[k] for k in ("offered_gbps", "achieved_gbps", "p50_ms", "p99_ms",
-                                             "max_ms", "steps", "mean_batch_bytes",
-                                             "step_ms_p50", "step_ms_p99", "step_ms_max",
-                                             "gcups", "packets", "phase_ms_per_step")})
+            sweep.append({k: r.get(k) for k in ("offered_gbps", "achieved_gbps", "p50_ms",
+                                                 "p99_ms", "max_ms", "steps", "mean_batch_bytes",
+                                                 "step_ms_p50", "step_ms_p99", "step_ms_mean",
+                                                 "step_ms_max", "gcups", "packets",
+                                                 "phase_ms_per_step")})
         clk = clocks.stop()
         st_all = srv.stats()
     best = max(sweep, key=lambda x: x["achieved_gbps"])
@@ -339,6 +344,7 @@ def run_served(args):
             "config": {"workload": desc, "streams": 4096, "signatures": len(base.patterns),
                        "prefilter_piece": args.prefilter,
                        "step_budget_bytes": int(args.served_batch_mb * (1 << 20)),
+                       "engine": args.served_engine,
                        "packets_per_load": n_pkt, "l2": "per-step text is small; L2-resident"},
             "served": {"sweep": sweep, "sustained_gbps": best["achieved_gbps"],
                        "knee_offered_gbps": knee["offered_gbps"] if knee else None,

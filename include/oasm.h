@@ -242,6 +242,55 @@ int oasm_flush(oasm_ctx *ctx, uint32_t sid, int end_of_stream, oasm_hit *out, si
  * is run.  OASM_ETRUNC when more than cap are queued (the rest stay). */
 int oasm_drain(oasm_ctx *ctx, oasm_hit *out, size_t cap, size_t *n_out);
 
+/* ------------------------------------------------------------ serving loop
+ * A packet trace for oasm_replay: packet q arrives at t[q] seconds (sorted)
+ * on external stream stream[q] (< n_streams) with payload
+ * payload[off[q] .. off[q] + len[q]); last[q] = 1 marks the last packet of
+ * its stream.  All arrays are the caller's and are only read. */
+typedef struct {
+    const double *t;
+    const uint32_t *stream;
+    const uint64_t *off;
+    const uint32_t *len;
+    const uint8_t *last;
+    const uint8_t *payload;
+    uint64_t n_packets;
+    uint32_t n_streams;
+    uint32_t reserved;
+} oasm_trace;
+
+typedef struct {
+    uint64_t steps;              /* batched steps run */
+    uint64_t packets;            /* packets fed */
+    uint64_t bytes;              /* payload bytes fed */
+    uint64_t kept;               /* hits drained (all streams) */
+    uint64_t n_out;              /* hits written to the caller's array */
+    uint64_t streams_admitted;
+    uint64_t max_waiting_streams;
+    double wall_s;               /* first arrival window to last drain */
+    double step_s_sum;           /* feed + step + drain, summed over steps */
+    double step_s_max;
+} oasm_replay_stats;
+
+/* Online matching of many concurrent streams (the paper's online setting,
+ * Sec. 1 and 4, served with continuous batching): replays the trace against
+ * the clock (realtime != 0; otherwise every packet is present at the start).
+ * Each step takes the packets that have arrived, up to max_batch_bytes (at
+ * least one packet), feeds them with oasm_feed_many, runs oasm_step and
+ * drains every stream's decided hits with oasm_drain.  A stream is opened at
+ * its first packet when a slot and the memory budget allow it, else it waits
+ * (FIFO, packets held in order); the step that ingests its last packet ends
+ * it, and its slot is freed after the drain.
+ *   done_at   optional [n_packets]: seconds from the start of the replay to
+ *             the end of the step that matched each packet
+ *   out/out_cap  optional array for the drained hits, stream_id = the
+ *             external stream id; more than out_cap hits: OASM_ETRUNC (the
+ *             replay still completes and rs->kept counts them all)
+ * OASM_EINVAL for a malformed trace, OASM_ENOMEM when no stream fits the
+ * memory budget, and every error of the calls it makes. */
+int oasm_replay(oasm_ctx *ctx, const oasm_trace *trace, int realtime, uint64_t max_batch_bytes,
+                double *done_at, oasm_hit *out, size_t out_cap, oasm_replay_stats *rs);
+
 /* Number of decided hits of stream sid queued and not yet returned by
  * oasm_flush (no device work is started).  sid = OASM_ALL_STREAMS gives the
  * total over every open stream: the size oasm_drain needs. */

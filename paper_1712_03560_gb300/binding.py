@@ -80,13 +80,26 @@ class oasm_stats(ctypes.Structure):
                 ("host_wait_ms", ctypes.c_double), ("host_post_ms", ctypes.c_double)]
 
 
+class oasm_trace(ctypes.Structure):
+    _fields_ = [("t", ctypes.c_void_p), ("stream", ctypes.c_void_p), ("off", ctypes.c_void_p),
+                ("len", ctypes.c_void_p), ("last", ctypes.c_void_p), ("payload", ctypes.c_void_p),
+                ("n_packets", ctypes.c_uint64), ("n_streams", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
+
+
+class oasm_replay_stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in ("steps", "packets", "bytes", "kept", "n_out",
+                                                "streams_admitted", "max_waiting_streams")] + \
+               [(n, ctypes.c_double) for n in ("wall_s", "step_s_sum", "step_s_max")]
+
+
 EXPORTS = ["oasm_config_default", "oasm_rules_default", "oasm_create", "oasm_destroy",
            "oasm_open_stream", "oasm_close_stream", "oasm_open_streams", "oasm_end_streams",
            "oasm_close_streams", "oasm_feed", "oasm_feed_many", "oasm_feed_device",
            "oasm_end_stream", "oasm_step", "oasm_flush", "oasm_drain", "oasm_ready", "oasm_get_stats", "oasm_reset_stats",
            "oasm_cuda_stream", "oasm_last_error", "oasm_strerror", "oasm_autotune",
            "oasm_measure_int_peak", "oasm_scan_ends_noalloc", "oasm_stream_state_size",
-           "oasm_save_stream", "oasm_restore_stream"]
+           "oasm_save_stream", "oasm_restore_stream", "oasm_replay"]
 
 _lib = None
 _lock = threading.Lock()
@@ -137,6 +150,8 @@ def load(path: str | None = None):
             "oasm_restore_stream": ([vp, u32, vp, ctypes.c_size_t], i32),
             "oasm_scan_ends_noalloc": ([u8pp, ctypes.POINTER(u32), ctypes.POINTER(u32), u32, vp,
                                         u64, vp, u64, ctypes.POINTER(u64), vp], i32),
+            "oasm_replay": ([vp, ctypes.POINTER(oasm_trace), i32, u64, vp, vp, ctypes.c_size_t,
+                             ctypes.POINTER(oasm_replay_stats)], i32),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -386,6 +401,40 @@ def oasm_strerror(code: int) -> str:
 
 def oasm_last_error(ctx=None) -> str:
     return load().oasm_last_error(ctx).decode()
+
+
+def oasm_replay(ctx, times, streams, offs, lens, last, payload, n_streams: int,
+                realtime: bool = True, max_batch_bytes: int = 32 << 20, collect: bool = False,
+                out_cap: int | None = None):
+    """Runs the native serving loop over a packet trace.  Returns (done_at,
+    hits, stats): done_at[q] = seconds from the start to the end of the step
+    that matched packet q (NaN if never fed), hits = the drained records
+    (external stream ids) when ``collect``, stats = the loop's counters."""
+    t = np.ascontiguousarray(times, dtype=np.float64)
+    st_ = np.ascontiguousarray(streams, dtype=np.uint32)
+    of = np.ascontiguousarray(offs, dtype=np.uint64)
+    ln = np.ascontiguousarray(lens, dtype=np.uint32)
+    la = np.ascontiguousarray(last, dtype=np.uint8)
+    pay = _u8(payload)
+    n = t.size
+    tr = oasm_trace(t.ctypes.data, st_.ctypes.data, of.ctypes.data, ln.ctypes.data,
+                    la.ctypes.data, pay.ctypes.data, n, int(n_streams), 0)
+    done = np.full(n, np.nan)
+    cap = 0
+    out = None
+    if collect:
+        cap = int(out_cap) if out_cap is not None else max(1 << 16, n * 4)
+        out = np.empty(cap, dtype=HIT_DTYPE)
+    rs = oasm_replay_stats()
+    rc = load().oasm_replay(ctx, ctypes.byref(tr), 1 if realtime else 0, int(max_batch_bytes),
+                            done.ctypes.data, out.ctypes.data if out is not None else None, cap,
+                            ctypes.byref(rs))
+    _check(rc, ctx, allow=(OASM_ETRUNC,))
+    stats = {f[0]: getattr(rs, f[0]) for f in oasm_replay_stats._fields_}
+    if rc == OASM_ETRUNC:
+        raise OasmError(rc, f"replay kept {stats['kept']} hits, more than out_cap={cap}")
+    hits = out[: rs.n_out] if out is not None else None
+    return done, hits, stats
 
 
 class Matcher:

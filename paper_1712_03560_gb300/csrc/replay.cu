@@ -1,0 +1,196 @@
+// replay.cu -- native serving loop over the public C ABI (host code only).
+//
+// Replays a packet trace against the clock with continuous batching: every
+// step takes the packets that have arrived (up to a byte budget), hands them
+// over in one oasm_feed_many, runs oasm_step and drains every stream's decided
+// hits with one oasm_drain.  Packets that arrive while a step runs go to the
+// next step.  A stream is admitted at its first packet when a slot (and the
+// memory budget) allow it; otherwise it waits, its packets held in arrival
+// order, and is admitted in FIFO order when a closing stream frees a slot.
+// The step that ingests a stream's last packet also ends it; its slot is
+// freed after the drain.  The same scheduler is written in Python in
+// serve.py (tested there against a fake library); this one removes the
+// interpreter from the loop.
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <deque>
+#include <thread>
+#include <vector>
+
+#include "oasm.h"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+double seconds_since(Clock::time_point t0) {
+  return std::chrono::duration<double>(Clock::now() - t0).count();
+}
+
+}  // namespace
+
+extern "C" {
+
+int oasm_replay(oasm_ctx* ctx, const oasm_trace* tr, int realtime, uint64_t max_batch_bytes,
+                double* done_at, oasm_hit* out, size_t out_cap, oasm_replay_stats* rs) {
+  if (!ctx || !tr || !rs || (tr->n_packets && (!tr->t || !tr->stream || !tr->off || !tr->len ||
+                                                !tr->last || !tr->payload)))
+    return OASM_EINVAL;
+  if (max_batch_bytes == 0) return OASM_EINVAL;
+  const uint64_t n = tr->n_packets;
+  for (uint64_t q = 0; q < n; ++q)
+    if (tr->stream[q] >= tr->n_streams || (q && tr->t[q] < tr->t[q - 1])) return OASM_EINVAL;
+  memset(rs, 0, sizeof *rs);
+  // sid_of[ext]: -1 not seen, -2 closed, -3 waiting, >= 0 library stream id
+  std::vector<int64_t> sid_of(tr->n_streams, -1);
+  std::vector<uint32_t> ext_of;  // library sid -> external id
+  std::deque<uint32_t> waiting;
+  std::vector<std::vector<uint64_t>> held(tr->n_streams);
+  uint64_t n_held = 0;
+  std::vector<uint64_t> csum(n + 1, 0);  // bytes of packets [0, q)
+  for (uint64_t q = 0; q < n; ++q) csum[q + 1] = csum[q] + tr->len[q];
+  std::vector<uint64_t> batch;
+  std::vector<uint32_t> b_sid, b_len, ending, fresh, got;
+  std::vector<uint64_t> b_off;
+  std::vector<oasm_hit> drained;
+  size_t n_out = 0;
+  uint64_t open_now = 0;
+  int rc = OASM_OK;
+  const Clock::time_point t0 = Clock::now();
+  uint64_t i = 0;
+  auto admit = [&](size_t k) -> int {  // up to k new library streams into got
+    got.assign(k, 0);
+    uint32_t opened = 0;
+    if (k) {
+      const int r = oasm_open_streams(ctx, uint32_t(k), got.data(), &opened);
+      if (r) return r;
+    }
+    got.resize(opened);
+    return OASM_OK;
+  };
+  while (i < n || !waiting.empty() || n_held) {
+    const double now = seconds_since(t0);
+    const uint64_t j =
+        realtime ? uint64_t(std::upper_bound(tr->t, tr->t + n, now) - tr->t) : n;
+    batch.clear();
+    // waiting streams first (slots freed by the last step)
+    if (!waiting.empty()) {
+      if ((rc = admit(waiting.size()))) return rc;
+      for (uint32_t sd : got) {
+        const uint32_t ext = waiting.front();
+        waiting.pop_front();
+        sid_of[ext] = sd;
+        if (ext_of.size() <= sd) ext_of.resize(sd + 1);
+        ext_of[sd] = ext;
+        ++open_now;
+        rs->streams_admitted += 1;
+        batch.insert(batch.end(), held[ext].begin(), held[ext].end());
+        n_held -= held[ext].size();
+        held[ext].clear();
+        held[ext].shrink_to_fit();
+      }
+    }
+    uint64_t used = 0;
+    for (uint64_t q : batch) used += tr->len[q];
+    const uint64_t budget = max_batch_bytes > used ? max_batch_bytes - used : 0;
+    uint64_t k = i;
+    if (j > i) {
+      k = uint64_t(std::upper_bound(csum.begin() + i + 1, csum.begin() + j + 1, csum[i] + budget) -
+                   csum.begin()) - 1;
+      k = std::min(j, std::max(i + 1, k));
+    }
+    if (k > i) {
+      // streams seen for the first time: admit now, in arrival order, or queue
+      fresh.clear();
+      for (uint64_t q = i; q < k; ++q) {
+        const uint32_t ext = tr->stream[q];
+        if (sid_of[ext] == -1 || sid_of[ext] == -2) {  // new (or reused) external id
+          sid_of[ext] = -3;  // pending admission below
+          fresh.push_back(ext);
+        }
+      }
+      if (!fresh.empty()) {
+        if ((rc = admit(waiting.empty() ? fresh.size() : 0))) return rc;  // FIFO behind waiters
+        size_t a = 0;
+        for (; a < got.size(); ++a) {
+          const uint32_t ext = fresh[a];
+          sid_of[ext] = got[a];
+          if (ext_of.size() <= got[a]) ext_of.resize(got[a] + 1);
+          ext_of[got[a]] = ext;
+          ++open_now;
+          rs->streams_admitted += 1;
+        }
+        for (; a < fresh.size(); ++a) waiting.push_back(fresh[a]);
+      }
+      for (uint64_t q = i; q < k; ++q) {
+        const uint32_t ext = tr->stream[q];
+        if (sid_of[ext] >= 0) {
+          batch.push_back(q);
+        } else {
+          held[ext].push_back(q);
+          ++n_held;
+        }
+      }
+    }
+    i = k;
+    rs->max_waiting_streams = std::max<uint64_t>(rs->max_waiting_streams, waiting.size());
+    if (batch.empty()) {
+      if (i < n && realtime) {
+        const double gap = tr->t[i] - seconds_since(t0);
+        if (gap > 2e-3) std::this_thread::sleep_for(std::chrono::duration<double>(gap - 1e-3));
+      } else if (!waiting.empty() && open_now == 0) {
+        return OASM_ENOMEM;  // no stream can be admitted under the memory budget
+      }
+      continue;
+    }
+    b_sid.resize(batch.size());
+    b_off.resize(batch.size());
+    b_len.resize(batch.size());
+    ending.clear();
+    uint64_t bytes = 0;
+    for (size_t b = 0; b < batch.size(); ++b) {
+      const uint64_t q = batch[b];
+      b_sid[b] = uint32_t(sid_of[tr->stream[q]]);
+      b_off[b] = tr->off[q];
+      b_len[b] = tr->len[q];
+      bytes += tr->len[q];
+      if (tr->last[q]) ending.push_back(b_sid[b]);
+    }
+    const double ts = seconds_since(t0);
+    if ((rc = oasm_feed_many(ctx, uint32_t(batch.size()), b_sid.data(), tr->payload, b_off.data(),
+                             b_len.data())))
+      return rc;
+    if (!ending.empty() && (rc = oasm_end_streams(ctx, uint32_t(ending.size()), ending.data())))
+      return rc;
+    if ((rc = oasm_step(ctx))) return rc;
+    size_t nr = 0;
+    if ((rc = oasm_ready(ctx, OASM_ALL_STREAMS, &nr))) return rc;
+    drained.resize(nr);
+    size_t nd = 0;
+    if ((rc = oasm_drain(ctx, nr ? drained.data() : nullptr, nr, &nd))) return rc;
+    const double te = seconds_since(t0);
+    for (size_t r = 0; r < nd; ++r) {
+      drained[r].stream_id = ext_of[drained[r].stream_id];  // external stream ids
+      if (out && n_out < out_cap) out[n_out++] = drained[r];
+    }
+    rs->kept += nd;
+    if (done_at)
+      for (uint64_t q : batch) done_at[q] = te;
+    rs->steps += 1;
+    rs->packets += batch.size();
+    rs->bytes += bytes;
+    rs->step_s_sum += te - ts;
+    rs->step_s_max = std::max(rs->step_s_max, te - ts);
+    if (!ending.empty()) {  // their last decisions are drained: free the slots
+      if ((rc = oasm_close_streams(ctx, uint32_t(ending.size()), ending.data()))) return rc;
+      for (uint32_t sd : ending) sid_of[ext_of[sd]] = -2;
+      open_now -= ending.size();
+    }
+  }
+  rs->wall_s = seconds_since(t0);
+  rs->n_out = n_out;
+  return rs->kept > n_out && out ? OASM_ETRUNC : OASM_OK;
+}
+
+}  // extern "C"

@@ -65,13 +65,17 @@ class Server:
         """Up to n new library stream ids (fewer when slots or memory run out)."""
         return self.B.oasm_open_streams(self.ctx, n).tolist() if n else []
 
-    def replay(self, tr, realtime: bool = True, collect: bool = False) -> dict:
+    def replay(self, tr, realtime: bool = True, collect: bool = False,
+               engine: str = "python") -> dict:
         """Replays a ``workloads.ServedTrace``; returns latency/throughput stats.
 
         With ``realtime`` the packets become visible at their arrival times;
         otherwise all of them are present at the start (pure throughput).
         With ``collect`` the hits of each stream are returned under ``hits``
-        (one structured array per external stream id)."""
+        (one structured array per external stream id).  ``engine="native"``
+        runs the same scheduler inside the library (``oasm_replay``)."""
+        if engine == "native":
+            return self._replay_native(tr, realtime, collect)
         B = self.B
         n = tr.n_packets
         times = np.asarray(tr.times, dtype=np.float64)
@@ -198,4 +202,42 @@ class Server:
         }
         if collect:
             res["hits"] = {e: np.concatenate(v) for e, v in hits.items()}
+        return res
+
+    def _replay_native(self, tr, realtime: bool, collect: bool) -> dict:
+        times = np.asarray(tr.times, dtype=np.float64)
+        lens = np.asarray(tr.lens, dtype=np.int64)
+        done, hits, st = self.B.oasm_replay(self.ctx, times, tr.streams, tr.offs, tr.lens,
+                                            tr.last, tr.payload, tr.n_streams,
+                                            realtime=realtime,
+                                            max_batch_bytes=self.max_batch_bytes,
+                                            collect=collect)
+        lat = (done - times) * 1e3
+        ok = ~np.isnan(lat)
+        steps = int(st["steps"])
+        res = {
+            "packets": int(times.size), "bytes": int(lens.sum()), "fed_bytes": int(st["bytes"]),
+            "offered_gbps": float(tr.meta.get("gbps", 0.0)),
+            "achieved_gbps": lens.sum() * 8 / max(st["wall_s"], 1e-12) / 1e9,
+            "wall_s": float(st["wall_s"]), "steps": steps, "kept": int(st["kept"]),
+            "p50_ms": float(np.percentile(lat[ok], 50)) if ok.any() else None,
+            "p99_ms": float(np.percentile(lat[ok], 99)) if ok.any() else None,
+            "max_ms": float(lat[ok].max()) if ok.any() else None,
+            "step_ms_mean": st["step_s_sum"] * 1e3 / max(1, steps),
+            "step_ms_max": st["step_s_max"] * 1e3,
+            "mean_batch_bytes": st["bytes"] / max(1, steps),
+            "streams_admitted": int(st["streams_admitted"]),
+            "max_waiting_streams": int(st["max_waiting_streams"]),
+            "engine": "native",
+        }
+        if collect:
+            out = {}
+            if hits is not None and hits.size:
+                order = np.argsort(hits["stream_id"], kind="stable")
+                h = hits[order]
+                ids, starts = np.unique(h["stream_id"], return_index=True)
+                bounds = list(starts[1:]) + [h.size]
+                for e, a, b in zip(ids.tolist(), starts.tolist(), bounds):
+                    out[int(e)] = h[a:b]
+            res["hits"] = out
         return res
