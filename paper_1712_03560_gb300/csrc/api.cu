@@ -23,6 +23,7 @@
 #include <cstring>
 #include <functional>
 #include <mutex>
+#include <queue>
 #include <string>
 #include <thread>
 #include <vector>
@@ -258,6 +259,8 @@ struct oasm_ctx {
 
   // streams
   std::vector<StreamRec> streams;
+  // free slots, lowest first (a stream takes the lowest free slot)
+  std::priority_queue<uint32_t, std::vector<uint32_t>, std::greater<uint32_t>> free_slots;
   uint8_t* d_tails = nullptr;
   WinHdr* d_hdr = nullptr;
   MemRow* d_mem = nullptr;
@@ -1440,6 +1443,7 @@ int oasm_create(const uint8_t* const* pat, const uint32_t* len, const uint32_t* 
     return bail(OASM_ECUDA);
   }
   ctx->streams.resize(S);
+  for (uint32_t i = 0; i < S; ++i) ctx->free_slots.push(i);
   if (cudaMalloc(&ctx->d_ctr, sizeof(StepCounters)) != cudaSuccess ||
       cudaHostAlloc(&ctx->h_ctr, sizeof(StepCounters), cudaHostAllocDefault) != cudaSuccess ||
       cudaMalloc(&ctx->d_hist, size_t(256) * kSortBlocks * 4) != cudaSuccess) {
@@ -1465,23 +1469,27 @@ int oasm_open_stream(oasm_ctx* ctx, uint32_t* sid) {
   if (ctx->cfg.mem_budget &&
       (uint64_t(ctx->n_open) + 1) * ctx->stream_bytes > ctx->cfg.mem_budget)
     return fail(ctx, OASM_ENOMEM, "admitting another stream would exceed the memory budget");
-  for (uint32_t i = 0; i < ctx->streams.size(); ++i) {
-    StreamRec& s = ctx->streams[i];
-    if (s.open) continue;
-    if (!s.clean) {  // closed before its end was processed: clear its windows
-      CK(cudaSetDevice(ctx->device));
-      CK(cudaMemsetAsync(ctx->d_hdr + size_t(i) * ctx->n_pat, 0,
-                         size_t(ctx->n_pat) * sizeof(WinHdr), ctx->stream));
-      CK(cudaMemsetAsync(ctx->d_mem + size_t(i) * ctx->mem_stride, 0,
-                         size_t(ctx->mem_stride) * sizeof(MemRow), ctx->stream));
-    }
-    s = StreamRec();
-    s.open = true;
-    ++ctx->n_open;
-    *sid = i;
-    return OASM_OK;
+  if (ctx->free_slots.empty())
+    return fail(ctx, OASM_EBUSY, "all %zu stream slots are in use", ctx->streams.size());
+  const uint32_t i = ctx->free_slots.top();
+  StreamRec& s = ctx->streams[i];
+  if (!s.clean) {  // closed before its end was processed: clear its windows
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaMemsetAsync(ctx->d_hdr + size_t(i) * ctx->n_pat, 0,
+                       size_t(ctx->n_pat) * sizeof(WinHdr), ctx->stream));
+    CK(cudaMemsetAsync(ctx->d_mem + size_t(i) * ctx->mem_stride, 0,
+                       size_t(ctx->mem_stride) * sizeof(MemRow), ctx->stream));
   }
-  return fail(ctx, OASM_EBUSY, "all %zu stream slots are in use", ctx->streams.size());
+  ctx->free_slots.pop();
+  HitVec keep;  // the slot's queue storage, kept from its last stream
+  keep.swap(s.ready);
+  keep.clear();
+  s = StreamRec();
+  s.ready.swap(keep);
+  s.open = true;
+  ++ctx->n_open;
+  *sid = i;
+  return OASM_OK;
 }
 
 int oasm_close_stream(oasm_ctx* ctx, uint32_t sid) {
@@ -1501,6 +1509,7 @@ int oasm_close_stream(oasm_ctx* ctx, uint32_t sid) {
   s.ready.swap(keep);
   s.clean = clean;
   --ctx->n_open;
+  ctx->free_slots.push(sid);
   if (ctx->host_pending == 0) ctx->h_stage_used = 0;
   return OASM_OK;
 }
