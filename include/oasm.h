@@ -242,6 +242,18 @@ int oasm_flush(oasm_ctx *ctx, uint32_t sid, int end_of_stream, oasm_hit *out, si
  * is run.  OASM_ETRUNC when more than cap are queued (the rest stay). */
 int oasm_drain(oasm_ctx *ctx, oasm_hit *out, size_t cap, size_t *n_out);
 
+/* Zero-copy input.  oasm_register_host pins [ptr, ptr + bytes) of the
+ * caller's host memory and maps it for the device.  An oasm_feed_many whose
+ * packets all lie in one registered range then copies nothing at the call:
+ * the step's gather kernel reads the packets straight from host memory over
+ * the CPU-GPU link.  The caller must not modify or free the range while
+ * input from it is waiting for a step.  oasm_unregister_host (ptr as
+ * registered) returns OASM_ESTATE while such input is pending; ranges still
+ * registered are released by oasm_destroy.  OASM_EINVAL for an overlapping
+ * range, OASM_ECUDA when the driver refuses the registration. */
+int oasm_register_host(oasm_ctx *ctx, const void *ptr, size_t bytes);
+int oasm_unregister_host(oasm_ctx *ctx, const void *ptr);
+
 /* ------------------------------------------------------------ serving loop
  * A packet trace for oasm_replay: packet q arrives at t[q] seconds (sorted)
  * on external stream stream[q] (< n_streams) with payload

@@ -99,7 +99,8 @@ EXPORTS = ["oasm_config_default", "oasm_rules_default", "oasm_create", "oasm_des
            "oasm_end_stream", "oasm_step", "oasm_flush", "oasm_drain", "oasm_ready", "oasm_get_stats", "oasm_reset_stats",
            "oasm_cuda_stream", "oasm_last_error", "oasm_strerror", "oasm_autotune",
            "oasm_measure_int_peak", "oasm_scan_ends_noalloc", "oasm_stream_state_size",
-           "oasm_save_stream", "oasm_restore_stream", "oasm_replay"]
+           "oasm_save_stream", "oasm_restore_stream", "oasm_replay", "oasm_register_host",
+           "oasm_unregister_host"]
 
 _lib = None
 _lock = threading.Lock()
@@ -152,6 +153,8 @@ def load(path: str | None = None):
                                         u64, vp, u64, ctypes.POINTER(u64), vp], i32),
             "oasm_replay": ([vp, ctypes.POINTER(oasm_trace), i32, u64, vp, vp, ctypes.c_size_t,
                              ctypes.POINTER(oasm_replay_stats)], i32),
+            "oasm_register_host": ([vp, vp, ctypes.c_size_t], i32),
+            "oasm_unregister_host": ([vp, vp], i32),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -401,6 +404,18 @@ def oasm_strerror(code: int) -> str:
 
 def oasm_last_error(ctx=None) -> str:
     return load().oasm_last_error(ctx).decode()
+
+
+def oasm_register_host(ctx, buf: np.ndarray):
+    """Pins and maps a host array for zero-copy feeds; keep ``buf`` alive and
+    unchanged until oasm_unregister_host."""
+    if not (isinstance(buf, np.ndarray) and buf.flags.c_contiguous and buf.nbytes):
+        raise ValueError("need a non-empty C-contiguous numpy array")
+    return _check(load().oasm_register_host(ctx, buf.ctypes.data, buf.nbytes), ctx)
+
+
+def oasm_unregister_host(ctx, buf: np.ndarray):
+    return _check(load().oasm_unregister_host(ctx, buf.ctypes.data), ctx)
 
 
 def oasm_replay(ctx, times, streams, offs, lens, last, payload, n_streams: int,

@@ -259,6 +259,14 @@ struct oasm_ctx {
 
   // streams
   std::vector<StreamRec> streams;
+  // host ranges registered for zero-copy feeds (read by the gather kernel
+  // over the CPU-GPU link instead of through pinned staging)
+  struct HostRange {
+    const uint8_t* host;
+    size_t bytes;
+    const uint8_t* dev;
+  };
+  std::vector<HostRange> host_ranges;
   // free slots, lowest first (a stream takes the lowest free slot)
   std::priority_queue<uint32_t, std::vector<uint32_t>, std::greater<uint32_t>> free_slots;
   uint8_t* d_tails = nullptr;
@@ -415,6 +423,7 @@ void free_ctx(oasm_ctx* c) {
   f(c->keys_alt.p); f(c->out.p); f(c->pool_hdr.p); f(c->pool_mem.p); f(c->pair_pool.p);
   f(c->out_sorted.p); f(c->okeys.p); f(c->okeys_alt.p); f(c->ovals.p); f(c->ovals_alt.p);
   f(c->d_ctr); f(c->d_hist);
+  for (const auto& r : c->host_ranges) cudaHostUnregister(const_cast<uint8_t*>(r.host));
   if (c->h_ctr) cudaFreeHost(c->h_ctr);
   if (c->h_stage) cudaFreeHost(c->h_stage);
   if (c->h_upload) cudaFreeHost(c->h_upload);
@@ -1573,6 +1582,69 @@ int oasm_feed(oasm_ctx* ctx, uint32_t sid, const uint8_t* chunk, size_t n) {
   return OASM_OK;
 }
 
+// The registered range that holds every packet of a feed_many call, or null.
+static const oasm_ctx::HostRange* find_host_range(const oasm_ctx* ctx, const uint8_t* buf,
+                                                  uint32_t n, const uint64_t* off,
+                                                  const uint32_t* len) {
+  if (ctx->host_ranges.empty()) return nullptr;
+  uint64_t lo = ~0ull, hi = 0;
+  for (uint32_t j = 0; j < n; ++j) {
+    if (!len[j]) continue;
+    lo = std::min<uint64_t>(lo, off[j]);
+    hi = std::max<uint64_t>(hi, off[j] + len[j]);
+  }
+  if (lo > hi) return nullptr;
+  for (const auto& r : ctx->host_ranges)
+    if (buf + lo >= r.host && buf + hi <= r.host + r.bytes) return &r;
+  return nullptr;
+}
+
+int oasm_register_host(oasm_ctx* ctx, const void* ptr, size_t bytes) {
+  if (!ctx || !ptr || !bytes) return OASM_EINVAL;
+  CK(cudaSetDevice(ctx->device));
+  const uint8_t* h = static_cast<const uint8_t*>(ptr);
+  for (const auto& r : ctx->host_ranges)
+    if (h < r.host + r.bytes && r.host < h + bytes)
+      return fail(ctx, OASM_EINVAL, "range overlaps a registered range");
+  cudaError_t e = cudaHostRegister(const_cast<void*>(ptr), bytes,
+                                   cudaHostRegisterMapped | cudaHostRegisterReadOnly);
+  if (e != cudaSuccess) {  // read-only registration is not supported everywhere
+    cudaGetLastError();
+    e = cudaHostRegister(const_cast<void*>(ptr), bytes, cudaHostRegisterMapped);
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, OASM_ECUDA, "cudaHostRegister failed: %s", cudaGetErrorString(e));
+  }
+  void* dev = nullptr;
+  e = cudaHostGetDevicePointer(&dev, const_cast<void*>(ptr), 0);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    cudaHostUnregister(const_cast<void*>(ptr));
+    return fail(ctx, OASM_ECUDA, "cudaHostGetDevicePointer failed: %s", cudaGetErrorString(e));
+  }
+  ctx->host_ranges.push_back({h, bytes, static_cast<const uint8_t*>(dev)});
+  return OASM_OK;
+}
+
+int oasm_unregister_host(oasm_ctx* ctx, const void* ptr) {
+  if (!ctx || !ptr) return OASM_EINVAL;
+  for (size_t i = 0; i < ctx->host_ranges.size(); ++i) {
+    const auto r = ctx->host_ranges[i];
+    if (r.host != ptr) continue;
+    for (const StreamRec& s : ctx->streams)
+      for (const Piece& pc : s.pieces)
+        if (pc.dev && pc.dptr >= r.dev && pc.dptr < r.dev + r.bytes)
+          return fail(ctx, OASM_ESTATE, "input from the range is still waiting for a step");
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaStreamSynchronize(ctx->stream));
+    cudaHostUnregister(const_cast<uint8_t*>(r.host));
+    ctx->host_ranges.erase(ctx->host_ranges.begin() + long(i));
+    return OASM_OK;
+  }
+  return fail(ctx, OASM_EINVAL, "pointer was not registered");
+}
+
 int oasm_feed_many(oasm_ctx* ctx, uint32_t n, const uint32_t* sid, const uint8_t* buf,
                    const uint64_t* off, const uint32_t* len) {
   if (!ctx) return OASM_EINVAL;
@@ -1587,6 +1659,22 @@ int oasm_feed_many(oasm_ctx* ctx, uint32_t n, const uint32_t* sid, const uint8_t
     total += len[j];
   }
   int rc;
+  // zero copy: packets inside one registered range become device pieces that
+  // the gather kernel reads straight from host memory
+  if (const oasm_ctx::HostRange* hr = find_host_range(ctx, buf, n, off, len)) {
+    for (uint32_t j = 0; j < n; ++j) {
+      if (!len[j]) continue;
+      const uint8_t* dp = hr->dev + ((buf + off[j]) - hr->host);
+      StreamRec& s = ctx->streams[sid[j]];
+      if (!s.pieces.empty() && s.pieces.back().dev && s.pieces.back().dptr + s.pieces.back().n == dp)
+        s.pieces.back().n += len[j];  // adjacent in memory: one piece
+      else
+        s.pieces.push_back(Piece{true, dp, 0, len[j]});
+      s.pending += len[j];
+      s.clean = false;
+    }
+    return OASM_OK;
+  }
   if (ctx->h_stage_used + total > ctx->stage_limit && ctx->h_stage_used > 0) {
     if ((rc = run_step(ctx))) return rc;
   }

@@ -66,14 +66,26 @@ class Server:
         return self.B.oasm_open_streams(self.ctx, n).tolist() if n else []
 
     def replay(self, tr, realtime: bool = True, collect: bool = False,
-               engine: str = "python") -> dict:
+               engine: str = "python", zero_copy: bool = False) -> dict:
         """Replays a ``workloads.ServedTrace``; returns latency/throughput stats.
 
         With ``realtime`` the packets become visible at their arrival times;
         otherwise all of them are present at the start (pure throughput).
         With ``collect`` the hits of each stream are returned under ``hits``
         (one structured array per external stream id).  ``engine="native"``
-        runs the same scheduler inside the library (``oasm_replay``)."""
+        runs the same scheduler inside the library (``oasm_replay``).  With
+        ``zero_copy`` the trace's payload is registered with the library for
+        the replay, and the device reads packets straight from it."""
+        if zero_copy:
+            payload = np.ascontiguousarray(tr.payload, dtype=np.uint8)
+            self.B.oasm_register_host(self.ctx, payload)
+            try:
+                if payload is not tr.payload:
+                    import dataclasses
+                    tr = dataclasses.replace(tr, payload=payload)
+                return self.replay(tr, realtime, collect, engine, zero_copy=False)
+            finally:
+                self.B.oasm_unregister_host(self.ctx, payload)
         if engine == "native":
             return self._replay_native(tr, realtime, collect)
         B = self.B

@@ -423,6 +423,55 @@ def test_piece_filter_set_grows_on_repetitive_text():
     assert canon(got) == oracle_rows(pats, ks, text)
 
 
+def test_zero_copy_feed_from_registered_host_memory():
+    """Packets fed from a registered host range are read by the device in
+    place (no staging copy); the output equals the oracle's, and the range
+    cannot be unregistered while its input waits for a step."""
+    rng = np.random.default_rng(31)
+    pats, ks, _ = random_case(rng, 4, 20, 6, 40, 10, kmax=3)
+    texts = [random_case(rng, 4, 1, 6, 8, int(rng.integers(3000, 9000)))[2] for _ in range(5)]
+    for t in texts:
+        for p, k in zip(pats[:6], ks[:6]):
+            W.plant(rng, t, W.edit_copy(rng, p, k, W.DNA))
+    # interleave the texts as packets of 1..700 bytes in one buffer
+    buf, pk = [], []
+    pos = [0] * len(texts)
+    off = 0
+    while any(p_ < t.size for p_, t in zip(pos, texts)):
+        for i, t in enumerate(texts):
+            if pos[i] < t.size:
+                n = int(min(rng.integers(1, 700), t.size - pos[i]))
+                buf.append(t[pos[i]:pos[i] + n])
+                pk.append((i, off, n))
+                pos[i] += n
+                off += n
+    payload = np.ascontiguousarray(np.concatenate(buf))
+    ctx = B.oasm_create(pats, ks, None, {"max_streams": 8})
+    try:
+        B.oasm_register_host(ctx, payload)
+        sids = [B.oasm_open_stream(ctx) for _ in texts]
+        half = len(pk) // 2
+        for part in (pk[:half], pk[half:]):
+            B.oasm_feed_many(ctx, np.array([sids[i] for i, _, _ in part], np.uint32), payload,
+                             np.array([o for _, o, _ in part], np.uint64),
+                             np.array([n for _, _, n in part], np.uint32))
+            with pytest.raises(B.OasmError) as ei:
+                B.oasm_unregister_host(ctx, payload)
+            assert ei.value.code == B.OASM_ESTATE
+            B.oasm_step(ctx)
+        for s_ in sids:
+            B.oasm_end_stream(ctx, s_)
+        B.oasm_step(ctx)
+        B.oasm_unregister_host(ctx, payload)
+        for s_, t in zip(sids, texts):
+            res = B.oasm_flush(ctx, s_)
+            rows = [(int(r["pattern_id"]), int(r["decided_at"]), int(r["k"]), int(r["start"]),
+                     int(r["len"])) for r in res]
+            assert canon(rows) == oracle_rows(pats, ks, t)
+    finally:
+        B.oasm_destroy(ctx)
+
+
 def test_int_peak_microbenchmark_runs():
     ops, ms = B.oasm_measure_int_peak(0)
     assert ops > 1e12 and ms > 0

@@ -125,14 +125,16 @@ def test_scheduler_realtime_pacing_batches_arrivals():
                          [(4096, 1 << 30, False, "python"), (24, 20000, False, "python"),
                           (64, 1 << 30, True, "python"), (4096, 1 << 30, False, "native"),
                           (24, 20000, False, "native"), (64, 1 << 30, True, "native"),
-                          (5, 3000, False, "native")])
+                          (5, 3000, False, "native"), (4096, 1 << 30, False, "native+zc"),
+                          (24, 20000, True, "python+zc")])
 def test_served_streams_match_oracle_alone_and_in_the_mix(slots, budget, realtime, engine):
     from parity_util import canon, oracle_rows
     from paper_1712_03560_gb300 import binding as B
     tr = W.served(seed=7, n_streams=48, n_sig=40, mlo=8, mhi=64, gbps=0.2, duration=0.05,
                   life=0.5, planted_frac=0.05)
     with serve.Server(tr.patterns, tr.ks, max_streams=slots, max_batch_bytes=budget) as srv:
-        res = srv.replay(tr, realtime=realtime, collect=True, engine=engine)
+        res = srv.replay(tr, realtime=realtime, collect=True, engine=engine.split("+")[0],
+                         zero_copy=engine.endswith("+zc"))
     texts = tr.stream_texts()
     assert res["steps"] >= (2 if budget < (1 << 30) or realtime else 1)
     assert res["packets"] == tr.n_packets and res["fed_bytes"] == int(tr.lens.sum())
