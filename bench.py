@@ -60,9 +60,9 @@ def parse():
     ap.add_argument("--served-packets", type=int, default=200000)
     ap.add_argument("--served-engine", default="native", choices=["native", "python"],
                     help="serving loop: inside the library (oasm_replay) or in Python")
-    ap.add_argument("--served-staging", action="store_true",
-                    help="copy packets through pinned staging instead of registering the "
-                         "trace payload for zero-copy feeds")
+    ap.add_argument("--served-zero-copy", action="store_true",
+                    help="register each trace's payload for zero-copy feeds instead of "
+                         "copying packets through pinned staging")
     ap.add_argument("--served-batch-mb", type=float, default=32.0,
                     help="byte budget of one serving step (MiB)")
     ap.add_argument("--prefilter", type=int, default=None,
@@ -302,7 +302,7 @@ def run_served(args):
             tr = W.served(seed=int(5 + 10 * g), n_packets=n_pkt, gbps=g)
             st0 = srv.stats()
             r = srv.replay(tr, realtime=True, engine=args.served_engine,
-                           zero_copy=not args.served_staging)
+                           zero_copy=args.served_zero_copy)
             st1 = srv.stats()
             r["gcups"] = msum * r["bytes"] / r["wall_s"] / 1e9
             if not sweep or r["achieved_gbps"] > max(x["achieved_gbps"] for x in sweep):
@@ -349,7 +349,7 @@ def run_served(args):
                        "prefilter_piece": args.prefilter,
                        "step_budget_bytes": int(args.served_batch_mb * (1 << 20)),
                        "engine": args.served_engine,
-                       "zero_copy": not args.served_staging,
+                       "zero_copy": args.served_zero_copy,
                        "packets_per_load": n_pkt, "l2": "per-step text is small; L2-resident"},
             "served": {"sweep": sweep, "sustained_gbps": best["achieved_gbps"],
                        "knee_offered_gbps": knee["offered_gbps"] if knee else None,
