@@ -226,6 +226,19 @@ int oasm_end_stream(oasm_ctx *ctx, uint32_t sid);
  * on the device and its decided hits are queued on their streams. */
 int oasm_step(oasm_ctx *ctx);
 
+/* oasm_step in two halves, so that host work can overlap the device.
+ * oasm_step_begin plans one step over the input pending now and launches it;
+ * it returns once the step's host bytes are on the device (the host may then
+ * feed more input, open and end streams, and drain earlier hits).
+ * oasm_step_end waits for that step and queues its decided hits.  A call
+ * that needs a quiet context (oasm_step, oasm_flush, oasm_close_stream,
+ * oasm_save_stream, oasm_restore_stream, oasm_autotune) finishes a step in
+ * flight first.  oasm_step_begin returns OASM_ESTATE if a step is already in
+ * flight; with no pending input it launches nothing and oasm_step_end is a
+ * no-op. */
+int oasm_step_begin(oasm_ctx *ctx);
+int oasm_step_end(oasm_ctx *ctx);
+
 /* Returns the hits of stream sid decided so far and not yet returned, in
  * canonical order (pattern_id, decided_at, k).  If the stream has input or
  * an end that no step has processed yet, a step is run first.  With

@@ -100,7 +100,7 @@ EXPORTS = ["oasm_config_default", "oasm_rules_default", "oasm_create", "oasm_des
            "oasm_cuda_stream", "oasm_last_error", "oasm_strerror", "oasm_autotune",
            "oasm_measure_int_peak", "oasm_scan_ends_noalloc", "oasm_stream_state_size",
            "oasm_save_stream", "oasm_restore_stream", "oasm_replay", "oasm_register_host",
-           "oasm_unregister_host"]
+           "oasm_unregister_host", "oasm_step_begin", "oasm_step_end"]
 
 _lib = None
 _lock = threading.Lock()
@@ -136,6 +136,8 @@ def load(path: str | None = None):
             "oasm_drain": ([vp, vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)], i32),
             "oasm_end_stream": ([vp, u32], i32),
             "oasm_step": ([vp], i32),
+            "oasm_step_begin": ([vp], i32),
+            "oasm_step_end": ([vp], i32),
             "oasm_flush": ([vp, u32, i32, vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)], i32),
             "oasm_ready": ([vp, u32, ctypes.POINTER(ctypes.c_size_t)], i32),
             "oasm_get_stats": ([vp, ctypes.POINTER(oasm_stats)], i32),
@@ -287,6 +289,14 @@ def oasm_end_stream(ctx, sid: int):
 
 def oasm_step(ctx):
     return _check(load().oasm_step(ctx), ctx)
+
+
+def oasm_step_begin(ctx):
+    return _check(load().oasm_step_begin(ctx), ctx)
+
+
+def oasm_step_end(ctx):
+    return _check(load().oasm_step_end(ctx), ctx)
 
 
 def oasm_drain(ctx, out: np.ndarray | None = None) -> np.ndarray:

@@ -42,9 +42,11 @@ constexpr int kSortBlocks = 2 * 152;
 struct Piece {
   bool dev;
   const uint8_t* dptr;  // device pointer (dev) or nullptr
-  size_t host_off;      // offset into the pinned staging buffer (host pieces)
+  size_t host_off;      // offset into its pinned staging buffer (host pieces)
   size_t n;
+  int sb = 0;           // staging buffer (host pieces)
 };
+
 
 // Vector storage that leaves new elements uninitialised: decided records are
 // copied in right after the resize, so zero-filling them first would be a
@@ -225,6 +227,39 @@ struct DevArray {
 
 }  // namespace
 
+struct StepPlan {
+  std::vector<WorkItem> items;
+  std::vector<uint32_t> sids;
+  std::vector<size_t> take;
+  std::vector<Region> regions;       // all buckets, concatenated
+  std::vector<size_t> region_off;    // per bucket
+  std::vector<CopyChunk> chunks;
+  size_t arena_bytes = 0;
+  int sb = 1, kb = 10;
+  uint64_t new_bytes = 0;
+};
+
+// Pinned host staging for fed bytes, with its device copy.  Two of them
+// alternate: bytes fed while a step is in flight go to the buffer that step
+// does not read, and a buffer is reused from its start once every piece in
+// it has been consumed.
+struct Stage {
+  uint8_t* h = nullptr;
+  size_t cap = 0, used = 0;
+  size_t pending = 0;    // bytes of pieces still waiting for a step
+  size_t copied = 0;     // bytes [0, copied) already on the device
+  DevArray<uint8_t> d;
+};
+
+// A step launched by oasm_step_begin and not yet finished.
+struct Flight {
+  bool on = false;
+  StepPlan pl;
+  const WorkItem* d_items = nullptr;
+  const Region* d_regions = nullptr;
+  const CopyChunk* d_chunks = nullptr;
+};
+
 struct oasm_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -274,16 +309,16 @@ struct oasm_ctx {
   MemRow* d_mem = nullptr;
   size_t stream_bytes = 0;
   uint32_t n_open = 0;
-  size_t host_pending = 0;  // bytes in host staging not yet consumed by a step
+  Flight flight;
   bool debug = false;
 
   // host staging (pinned)
-  uint8_t* h_stage = nullptr;
-  size_t h_stage_cap = 0, h_stage_used = 0;
+  Stage stage[2];
+  int cur_stage = 0;         // the buffer new host bytes go to
   size_t stage_limit = size_t(2) << 30;
 
   // step buffers
-  DevArray<uint8_t> arena, dstage, upload;
+  DevArray<uint8_t> arena, upload;
   DevArray<Candidate> cand;
   DevArray<unsigned long long> keys, keys_alt;
   DevArray<DevHit> out, out_sorted;
@@ -301,6 +336,7 @@ struct oasm_ctx {
   size_t h_out_cap = 0;
   cudaEvent_t ev[9] = {};  // 0-5 step phases, 6-7 autotune, 8 piece filter start
   cudaEvent_t done = nullptr;
+  cudaEvent_t staged = nullptr;  // host staging copies of the step in flight done
   cudaGraphExec_t graph_exec = nullptr;  // the last captured step, updated in place
   bool capturing = false;
 
@@ -419,18 +455,20 @@ void free_ctx(oasm_ctx* c) {
   f(c->d_pdir); f(c->d_pent); f(c->d_pbytes); f(c->d_poff); f(c->pset.p); f(c->d_pbloom);
   for (auto& b : c->buckets) { f(b.d_groups); f(b.d_peq); }
   f(c->d_tails); f(c->d_hdr); f(c->d_mem);
-  f(c->arena.p); f(c->dstage.p); f(c->upload.p); f(c->cand.p); f(c->keys.p);
+  f(c->arena.p); f(c->upload.p); f(c->stage[0].d.p); f(c->stage[1].d.p); f(c->cand.p); f(c->keys.p);
   f(c->keys_alt.p); f(c->out.p); f(c->pool_hdr.p); f(c->pool_mem.p); f(c->pair_pool.p);
   f(c->out_sorted.p); f(c->okeys.p); f(c->okeys_alt.p); f(c->ovals.p); f(c->ovals_alt.p);
   f(c->d_ctr); f(c->d_hist);
   for (const auto& r : c->host_ranges) cudaHostUnregister(const_cast<uint8_t*>(r.host));
   if (c->h_ctr) cudaFreeHost(c->h_ctr);
-  if (c->h_stage) cudaFreeHost(c->h_stage);
+  for (auto& sg : c->stage)
+    if (sg.h) cudaFreeHost(sg.h);
   if (c->h_upload) cudaFreeHost(c->h_upload);
   if (c->h_out) cudaFreeHost(c->h_out);
   for (auto& e : c->ev) if (e) cudaEventDestroy(e);
   if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
   if (c->done) cudaEventDestroy(c->done);
+  if (c->staged) cudaEventDestroy(c->staged);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
 }
@@ -773,17 +811,6 @@ int64_t region_len(oasm_ctx* ctx, const Bucket& b, int64_t total_ends) {
   return std::max<int64_t>(q, (ri + q - 1) / q * q);
 }
 
-struct StepPlan {
-  std::vector<WorkItem> items;
-  std::vector<uint32_t> sids;
-  std::vector<size_t> take;
-  std::vector<Region> regions;       // all buckets, concatenated
-  std::vector<size_t> region_off;    // per bucket
-  std::vector<CopyChunk> chunks;
-  size_t arena_bytes = 0;
-  int sb = 1, kb = 10;
-  uint64_t new_bytes = 0;
-};
 
 constexpr int64_t kPrefSeg = kPrefSegMax;  // start positions per piece-filter segment
 
@@ -817,7 +844,7 @@ int plan_step(oasm_ctx* ctx, StepPlan& pl) {
     for (const Piece& pc : s.pieces) {
       if (left <= 0) break;
       const size_t n = size_t(std::min<int64_t>(left, int64_t(pc.n)));
-      const uint8_t* src = pc.dev ? pc.dptr : ctx->dstage.p + pc.host_off;
+      const uint8_t* src = pc.dev ? pc.dptr : ctx->stage[pc.sb].d.p + pc.host_off;
       for (size_t o = 0; o < n; o += kChunk) {
         CopyChunk ch{src + o, dst + o, uint32_t(std::min(kChunk, n - o)), 0};
         pl.chunks.push_back(ch);
@@ -992,11 +1019,12 @@ double ms_since(std::chrono::steady_clock::time_point t0) {
   return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
 }
 
-int run_step_once(oasm_ctx* ctx, StepPlan& pl, const WorkItem* d_items, const Region* d_regions,
-                  const CopyChunk* d_chunks, bool* overflow) {
+// Launches one step's device work (as a graph or directly) and records the
+// completion event; returns without waiting.
+int launch_step(oasm_ctx* ctx, StepPlan& pl, const WorkItem* d_items, const Region* d_regions,
+                const CopyChunk* d_chunks) {
   const auto t_launch = std::chrono::steady_clock::now();
   cudaStream_t s = ctx->stream;
-  const bool tm = ctx->cfg.timing != 0;
   int rc;
   if (ctx->cfg.graphs) {
     // capture the step, then update the cached executable graph in place when
@@ -1038,6 +1066,15 @@ int run_step_once(oasm_ctx* ctx, StepPlan& pl, const WorkItem* d_items, const Re
   }
   CK(cudaEventRecord(ctx->done, s));
   ctx->st.host_launch_ms += ms_since(t_launch);
+  return OASM_OK;
+}
+
+// Waits for the launched step, then either grows the buffers that overflowed
+// (*overflow: the caller re-launches from unchanged state) or books the
+// step's timings and moves its records into the streams' queues.
+int finish_step(oasm_ctx* ctx, StepPlan& pl, const WorkItem* d_items, bool* overflow) {
+  const bool tm = ctx->cfg.timing != 0;
+  int rc;
   const auto t_wait = std::chrono::steady_clock::now();
   rc = wait_event(ctx, ctx->done);
   ctx->st.host_wait_ms += ms_since(t_wait);
@@ -1153,113 +1190,172 @@ int run_step_once(oasm_ctx* ctx, StepPlan& pl, const WorkItem* d_items, const Re
   return OASM_OK;
 }
 
-int run_step(oasm_ctx* ctx) {
+// A staging buffer whose pieces have all been consumed is reused from its start.
+void release_stages(oasm_ctx* ctx) {
+  for (Stage& sg : ctx->stage)
+    if (sg.pending == 0) sg.used = sg.copied = 0;
+}
+
+// Plans a step over the pending input, brings host bytes to the device and
+// launches the device work; returns without waiting (ctx->flight).  With no
+// pending input nothing is launched.
+int step_begin(oasm_ctx* ctx) {
+  if (ctx->flight.on) return fail(ctx, OASM_ESTATE, "a step is already in flight");
   CK(cudaSetDevice(ctx->device));
-  while (true) {
-    int rc;
-    // device staging of host bytes first: host pieces are gathered from it
-    if (ctx->h_stage_used &&
-        (rc = ensure(ctx, ctx->dstage, ctx->h_stage_used, "staging")))
-      return rc;
-    const auto t_plan = std::chrono::steady_clock::now();
-    StepPlan pl;
-    if ((rc = plan_step(ctx, pl))) return rc;
-    if (pl.items.empty()) return OASM_OK;
-    if (ctx->h_stage_used)
-      CK(cudaMemcpyAsync(ctx->dstage.p, ctx->h_stage, ctx->h_stage_used, cudaMemcpyHostToDevice,
-                         ctx->stream));
-    if ((rc = ensure(ctx, ctx->arena, pl.arena_bytes, "text arena"))) return rc;
-    if ((rc = ensure(ctx, ctx->pair_pool, pl.items.size() * size_t(ctx->n_pat), "pair table")))
-      return rc;
-    if (!ctx->cand.p && (rc = ensure(ctx, ctx->cand, std::max<size_t>(1 << 16, pl.new_bytes / 64), "candidates"))) return rc;
-    if (!ctx->keys.p) {
-      const size_t h0 = std::max<size_t>(1 << 16, pl.new_bytes / 64);
-      if ((rc = ensure(ctx, ctx->keys, h0, "hit keys"))) return rc;
-      if ((rc = ensure(ctx, ctx->keys_alt, h0, "hit keys"))) return rc;
+  int rc;
+  const auto t_plan = std::chrono::steady_clock::now();
+  Flight& f = ctx->flight;
+  f.pl = StepPlan();
+  StepPlan& pl = f.pl;
+  // device copies of the staging buffers first: plan_step takes their addresses
+  for (Stage& sg : ctx->stage)
+    if (sg.used && (!sg.d.p || sg.d.cap < sg.used)) {
+      if ((rc = ensure(ctx, sg.d, sg.used, "staging"))) return rc;
+      sg.copied = 0;  // a new device buffer: copy everything again
     }
-    if (!ctx->out.p && (rc = ensure_out(ctx, 1 << 16))) return rc;
-    if (ctx->n_pref_pat && !ctx->pset.p &&
-        (rc = ensure_pow2(ctx, ctx->pset, size_t(1) << 20, "piece filter set")))
+  if ((rc = plan_step(ctx, pl))) return rc;
+  if (pl.items.empty()) return OASM_OK;
+  bool copies = false;
+  for (Stage& sg : ctx->stage)
+    if (sg.used > sg.copied) {
+      CK(cudaMemcpyAsync(sg.d.p + sg.copied, sg.h + sg.copied, sg.used - sg.copied,
+                         cudaMemcpyHostToDevice, ctx->stream));
+      sg.copied = sg.used;
+      copies = true;
+    }
+  if ((rc = ensure(ctx, ctx->arena, pl.arena_bytes, "text arena"))) return rc;
+  if ((rc = ensure(ctx, ctx->pair_pool, pl.items.size() * size_t(ctx->n_pat), "pair table")))
+    return rc;
+  if (!ctx->cand.p && (rc = ensure(ctx, ctx->cand, std::max<size_t>(1 << 16, pl.new_bytes / 64), "candidates"))) return rc;
+  if (!ctx->keys.p) {
+    const size_t h0 = std::max<size_t>(1 << 16, pl.new_bytes / 64);
+    if ((rc = ensure(ctx, ctx->keys, h0, "hit keys"))) return rc;
+    if ((rc = ensure(ctx, ctx->keys_alt, h0, "hit keys"))) return rc;
+  }
+  if (!ctx->out.p && (rc = ensure_out(ctx, 1 << 16))) return rc;
+  if (ctx->n_pref_pat && !ctx->pset.p &&
+      (rc = ensure_pow2(ctx, ctx->pset, size_t(1) << 20, "piece filter set")))
+    return rc;
+  if (!ctx->pool_hdr.p) {
+    if ((rc = ensure(ctx, ctx->pool_hdr, 1 << 14, "window pool"))) return rc;
+    if ((rc = ensure(ctx, ctx->pool_mem, size_t(1 << 14) * (kMaxK + 1), "window pool"))) return rc;
+  }
+  // one upload: items | regions | chunks
+  const size_t bi = pl.items.size() * sizeof(WorkItem);
+  const size_t br = pl.regions.size() * sizeof(Region);
+  const size_t bc = pl.chunks.size() * sizeof(CopyChunk);
+  const size_t o_r = (bi + 255) & ~size_t(255), o_c = (o_r + br + 255) & ~size_t(255);
+  const size_t total = o_c + bc + 256;
+  if ((rc = ensure_host(ctx, &ctx->h_upload, &ctx->h_upload_cap, total, 0))) return rc;
+  if ((rc = ensure(ctx, ctx->upload, total, "step upload"))) return rc;
+  memcpy(ctx->h_upload, pl.items.data(), bi);
+  memcpy(ctx->h_upload + o_r, pl.regions.data(), br);
+  memcpy(ctx->h_upload + o_c, pl.chunks.data(), bc);
+  CK(cudaMemcpyAsync(ctx->upload.p, ctx->h_upload, total, cudaMemcpyHostToDevice, ctx->stream));
+  f.d_items = reinterpret_cast<const WorkItem*>(ctx->upload.p);
+  f.d_regions = reinterpret_cast<const Region*>(ctx->upload.p + o_r);
+  f.d_chunks = reinterpret_cast<const CopyChunk*>(ctx->upload.p + o_c);
+  // the host staging copies must be done before bytes fed while this step
+  // runs may move a staging buffer (a growing buffer is reallocated)
+  if (copies) {
+    CK(cudaEventRecord(ctx->staged, ctx->stream));
+  }
+  ctx->st.host_plan_ms += ms_since(t_plan);
+  if ((rc = launch_step(ctx, pl, f.d_items, f.d_regions, f.d_chunks))) return rc;
+  if (copies && (rc = wait_event(ctx, ctx->staged))) return rc;
+  f.on = true;
+  // new host bytes go to the other buffer while this one is consumed
+  ctx->cur_stage ^= 1;
+  return OASM_OK;
+}
+
+// Finishes the step in flight: waits, re-runs it after growing any buffer
+// that overflowed, moves its records into the stream queues and advances
+// the streams past the bytes it consumed.
+int step_end(oasm_ctx* ctx) {
+  Flight& f = ctx->flight;
+  if (!f.on) return OASM_OK;
+  CK(cudaSetDevice(ctx->device));
+  StepPlan& pl = f.pl;
+  int rc;
+  bool over = true;
+  for (int attempt = 0; over; ++attempt) {
+    if (attempt > 16) {
+      f.on = false;
+      const StepCounters c = *ctx->h_ctr;
+      return fail(ctx, OASM_ENOMEM,
+                  "step buffers kept overflowing (flags 0x%x; candidates %llu/%zu, hits "
+                  "%llu/%zu, records %llu/%zu, windows %llu/%zu)",
+                  c.overflow, c.n_cand, ctx->cand.cap, c.n_hits,
+                  std::min(ctx->keys.cap, ctx->keys_alt.cap), c.n_out, ctx->out.cap, c.n_pool,
+                  ctx->pool_hdr.cap);
+    }
+    if (attempt > 0 && (rc = launch_step(ctx, pl, f.d_items, f.d_regions, f.d_chunks))) {
+      f.on = false;
       return rc;
-    if (!ctx->pool_hdr.p) {
-      if ((rc = ensure(ctx, ctx->pool_hdr, 1 << 14, "window pool"))) return rc;
-      if ((rc = ensure(ctx, ctx->pool_mem, size_t(1 << 14) * (kMaxK + 1), "window pool"))) return rc;
     }
-    // one upload: items | regions | chunks
-    const size_t bi = pl.items.size() * sizeof(WorkItem);
-    const size_t br = pl.regions.size() * sizeof(Region);
-    const size_t bc = pl.chunks.size() * sizeof(CopyChunk);
-    const size_t o_r = (bi + 255) & ~size_t(255), o_c = (o_r + br + 255) & ~size_t(255);
-    const size_t total = o_c + bc + 256;
-    if ((rc = ensure_host(ctx, &ctx->h_upload, &ctx->h_upload_cap, total, 0))) return rc;
-    if ((rc = ensure(ctx, ctx->upload, total, "step upload"))) return rc;
-    memcpy(ctx->h_upload, pl.items.data(), bi);
-    memcpy(ctx->h_upload + o_r, pl.regions.data(), br);
-    memcpy(ctx->h_upload + o_c, pl.chunks.data(), bc);
-    CK(cudaMemcpyAsync(ctx->upload.p, ctx->h_upload, total, cudaMemcpyHostToDevice, ctx->stream));
-    const WorkItem* d_items = reinterpret_cast<const WorkItem*>(ctx->upload.p);
-    const Region* d_regions = reinterpret_cast<const Region*>(ctx->upload.p + o_r);
-    const CopyChunk* d_chunks = reinterpret_cast<const CopyChunk*>(ctx->upload.p + o_c);
-    ctx->st.host_plan_ms += ms_since(t_plan);
-    bool over = true;
-    for (int attempt = 0; over; ++attempt) {
-      if (attempt > 16) {
-        const StepCounters c = *ctx->h_ctr;
-        return fail(ctx, OASM_ENOMEM,
-                    "step buffers kept overflowing (flags 0x%x; candidates %llu/%zu, hits "
-                    "%llu/%zu, records %llu/%zu, windows %llu/%zu)",
-                    c.overflow, c.n_cand, ctx->cand.cap, c.n_hits,
-                    std::min(ctx->keys.cap, ctx->keys_alt.cap), c.n_out, ctx->out.cap, c.n_pool,
-                    ctx->pool_hdr.cap);
-      }
-      if ((rc = run_step_once(ctx, pl, d_items, d_regions, d_chunks, &over))) return rc;
+    if ((rc = finish_step(ctx, pl, f.d_items, &over))) {
+      f.on = false;
+      return rc;
     }
-    // advance streams
-    const auto t_adv = std::chrono::steady_clock::now();
-    for (size_t i = 0; i < pl.items.size(); ++i) {
-      StreamRec& s = ctx->streams[pl.sids[i]];
-      size_t left = pl.take[i];
-      while (left > 0 && !s.pieces.empty()) {
-        Piece& pc = s.pieces.front();
-        if (pc.n <= left) {
-          left -= pc.n;
-          if (!pc.dev) ctx->host_pending -= pc.n;
-          s.pieces.erase(s.pieces.begin());
+  }
+  f.on = false;
+  // advance streams
+  const auto t_adv = std::chrono::steady_clock::now();
+  for (size_t i = 0; i < pl.items.size(); ++i) {
+    StreamRec& s = ctx->streams[pl.sids[i]];
+    size_t left = pl.take[i];
+    while (left > 0 && !s.pieces.empty()) {
+      Piece& pc = s.pieces.front();
+      if (pc.n <= left) {
+        left -= pc.n;
+        if (!pc.dev) ctx->stage[pc.sb].pending -= pc.n;
+        s.pieces.erase(s.pieces.begin());
+      } else {
+        pc.n -= left;
+        if (pc.dev) {
+          pc.dptr += left;
         } else {
-          pc.n -= left;
-          if (pc.dev) {
-            pc.dptr += left;
-          } else {
-            pc.host_off += left;
-            ctx->host_pending -= left;
-          }
-          left = 0;
+          pc.host_off += left;
+          ctx->stage[pc.sb].pending -= left;
         }
-      }
-      s.pending -= pl.take[i];
-      s.pos = pl.items[i].e_new;
-      s.tail_len = int32_t(std::min<int64_t>(s.pos, ctx->T));
-      if (pl.items[i].eos) {  // every window of the stream was decided: slot is clean
-        s.pos = 0;
-        s.tail_len = 0;
-        s.eos_pending = false;
-        s.clean = true;
+        left = 0;
       }
     }
-    ctx->st.steps += 1;
-    ctx->st.text_bytes += pl.new_bytes;
-    uint64_t msum = 0;
-    for (uint32_t p = 0; p < ctx->n_pat; ++p) msum += ctx->m[p];
-    ctx->st.cells += msum * pl.new_bytes;
-    for (const Bucket& b : ctx->buckets) {
-      uint64_t lanes = 0;
-      for (const auto& g : b.groups)
-        for (int l = 0; l < kLaneGroup; l += g.nseg) lanes += g.pat[l] >= 0 ? 1 : 0;
-      ctx->st.word_steps += lanes * uint64_t(b.W) * pl.new_bytes;
+    s.pending -= pl.take[i];
+    s.pos = pl.items[i].e_new;
+    s.tail_len = int32_t(std::min<int64_t>(s.pos, ctx->T));
+    if (pl.items[i].eos) {  // every window of the stream was decided: slot is clean
+      s.pos = 0;
+      s.tail_len = 0;
+      s.eos_pending = false;
+      s.clean = true;
     }
-    // host staging is free again once no stream references it
-    if (ctx->host_pending == 0) ctx->h_stage_used = 0;
-    ctx->st.host_post_ms += ms_since(t_adv);
+  }
+  ctx->st.steps += 1;
+  ctx->st.text_bytes += pl.new_bytes;
+  uint64_t msum = 0;
+  for (uint32_t p = 0; p < ctx->n_pat; ++p) msum += ctx->m[p];
+  ctx->st.cells += msum * pl.new_bytes;
+  for (const Bucket& b : ctx->buckets) {
+    uint64_t lanes = 0;
+    for (const auto& g : b.groups)
+      for (int l = 0; l < kLaneGroup; l += g.nseg) lanes += g.pat[l] >= 0 ? 1 : 0;
+    ctx->st.word_steps += lanes * uint64_t(b.W) * pl.new_bytes;
+  }
+  release_stages(ctx);
+  ctx->st.host_post_ms += ms_since(t_adv);
+  return OASM_OK;
+}
+
+// Runs steps until no stream has input left (finishing a step in flight first).
+int run_step(oasm_ctx* ctx) {
+  int rc;
+  if ((rc = step_end(ctx))) return rc;
+  while (true) {
+    if ((rc = step_begin(ctx))) return rc;
+    if (!ctx->flight.on) return OASM_OK;
+    if ((rc = step_end(ctx))) return rc;
     bool more = false;
     for (auto& s : ctx->streams) more |= s.open && (s.pending > 0 || s.eos_pending);
     if (!more) return OASM_OK;
@@ -1462,7 +1558,8 @@ int oasm_create(const uint8_t* const* pat, const uint32_t* len, const uint32_t* 
   }
   for (auto& e : ctx->ev)
     if (cudaEventCreate(&e) != cudaSuccess) return bail(fail(ctx, OASM_ECUDA, "event"));
-  if (cudaEventCreateWithFlags(&ctx->done, cudaEventDisableTiming) != cudaSuccess)
+  if (cudaEventCreateWithFlags(&ctx->done, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->staged, cudaEventDisableTiming) != cudaSuccess)
     return bail(fail(ctx, OASM_ECUDA, "event"));
   *out = ctx;
   return OASM_OK;
@@ -1504,9 +1601,13 @@ int oasm_open_stream(oasm_ctx* ctx, uint32_t* sid) {
 int oasm_close_stream(oasm_ctx* ctx, uint32_t sid) {
   int rc = check_sid(ctx, sid);
   if (rc) return rc;
+  if (ctx->flight.on &&
+      std::binary_search(ctx->flight.pl.sids.begin(), ctx->flight.pl.sids.end(), sid) &&
+      (rc = step_end(ctx)))  // the stream is part of the step in flight
+    return rc;
   StreamRec& s = ctx->streams[sid];
   for (const Piece& pc : s.pieces)
-    if (!pc.dev) ctx->host_pending -= pc.n;
+    if (!pc.dev) ctx->stage[pc.sb].pending -= pc.n;
   // a stream that never fed anything since its last end has empty windows
   const bool clean = s.clean && s.pos == 0;
   // the slot keeps its queue's storage for the next stream it serves (no new
@@ -1519,7 +1620,7 @@ int oasm_close_stream(oasm_ctx* ctx, uint32_t sid) {
   s.clean = clean;
   --ctx->n_open;
   ctx->free_slots.push(sid);
-  if (ctx->host_pending == 0) ctx->h_stage_used = 0;
+  release_stages(ctx);
   return OASM_OK;
 }
 
@@ -1560,23 +1661,23 @@ int oasm_feed(oasm_ctx* ctx, uint32_t sid, const uint8_t* chunk, size_t n) {
   if (!chunk) return fail(ctx, OASM_EINVAL, "null chunk");
   StreamRec& s = ctx->streams[sid];
   if (s.eos_pending) return fail(ctx, OASM_ESTATE, "stream %u has a pending end", sid);
-  if (ctx->h_stage_used + n > ctx->stage_limit && ctx->h_stage_used > 0) {
+  Stage* sg = &ctx->stage[ctx->cur_stage];
+  if (sg->used + n > ctx->stage_limit && sg->used > 0) {
     if ((rc = run_step(ctx))) return rc;
+    sg = &ctx->stage[ctx->cur_stage];
   }
-  if ((rc = ensure_host(ctx, &ctx->h_stage, &ctx->h_stage_cap, ctx->h_stage_used + n,
-                        ctx->h_stage_used)))
-    return rc;
+  if ((rc = ensure_host(ctx, &sg->h, &sg->cap, sg->used + n, sg->used))) return rc;
   {  // large chunks are copied into pinned staging on several host threads
-    uint8_t* dst = ctx->h_stage + ctx->h_stage_used;
+    uint8_t* dst = sg->h + sg->used;
     const size_t parts = n > (size_t(4) << 20) ? 16 : 1;
     parallel_parts(parts, 1, [&](size_t t0, size_t t1) {
       const size_t lo = n * t0 / parts, hi = n * t1 / parts;
       memcpy(dst + lo, chunk + lo, hi - lo);
     });
   }
-  s.pieces.push_back(Piece{false, nullptr, ctx->h_stage_used, n});
-  ctx->h_stage_used += n;
-  ctx->host_pending += n;
+  s.pieces.push_back(Piece{false, nullptr, sg->used, n, ctx->cur_stage});
+  sg->used += n;
+  sg->pending += n;
   s.pending += n;
   s.clean = false;
   return OASM_OK;
@@ -1675,12 +1776,12 @@ int oasm_feed_many(oasm_ctx* ctx, uint32_t n, const uint32_t* sid, const uint8_t
     }
     return OASM_OK;
   }
-  if (ctx->h_stage_used + total > ctx->stage_limit && ctx->h_stage_used > 0) {
+  Stage* sg = &ctx->stage[ctx->cur_stage];
+  if (sg->used + total > ctx->stage_limit && sg->used > 0) {
     if ((rc = run_step(ctx))) return rc;
+    sg = &ctx->stage[ctx->cur_stage];
   }
-  if ((rc = ensure_host(ctx, &ctx->h_stage, &ctx->h_stage_cap, ctx->h_stage_used + total,
-                        ctx->h_stage_used)))
-    return rc;
+  if ((rc = ensure_host(ctx, &sg->h, &sg->cap, sg->used + total, sg->used))) return rc;
   // staging layout: the packets of one stream side by side in call order
   // (streams in order of first appearance), so each stream gets one piece
   // per call; the byte copies run on several host threads when large
@@ -1694,12 +1795,12 @@ int oasm_feed_many(oasm_ctx* ctx, uint32_t n, const uint32_t* sid, const uint8_t
     }
     base[sid[j]] += len[j];  // bytes of the stream in this call
   }
-  size_t at = ctx->h_stage_used;
+  size_t at = sg->used;
   for (uint32_t sd : order) {
     const uint64_t bytes = base[sd];
     base[sd] = at;
     StreamRec& s = ctx->streams[sd];
-    s.pieces.push_back(Piece{false, nullptr, at, size_t(bytes)});
+    s.pieces.push_back(Piece{false, nullptr, at, size_t(bytes), ctx->cur_stage});
     s.pending += bytes;
     s.clean = false;
     at += bytes;
@@ -1713,10 +1814,10 @@ int oasm_feed_many(oasm_ctx* ctx, uint32_t n, const uint32_t* sid, const uint8_t
   parallel_parts(n, total > (size_t(4) << 20) ? std::max<size_t>(1, n / 16) : n + 1,
                  [&](size_t lo, size_t hi) {
                    for (size_t j = lo; j < hi; ++j)
-                     if (len[j]) memcpy(ctx->h_stage + dst[j], buf + off[j], len[j]);
+                     if (len[j]) memcpy(sg->h + dst[j], buf + off[j], len[j]);
                  });
-  ctx->h_stage_used = at;
-  ctx->host_pending += total;
+  sg->used = at;
+  sg->pending += total;
   return OASM_OK;
 }
 
@@ -1743,6 +1844,16 @@ int oasm_end_stream(oasm_ctx* ctx, uint32_t sid) {
 int oasm_step(oasm_ctx* ctx) {
   if (!ctx) return OASM_EINVAL;
   return run_step(ctx);
+}
+
+int oasm_step_begin(oasm_ctx* ctx) {
+  if (!ctx) return OASM_EINVAL;
+  return step_begin(ctx);
+}
+
+int oasm_step_end(oasm_ctx* ctx) {
+  if (!ctx) return OASM_EINVAL;
+  return step_end(ctx);
 }
 
 // Merges the canonically sorted runs that several steps left in a stream's
@@ -1859,6 +1970,7 @@ int oasm_stream_state_size(oasm_ctx* ctx, size_t* bytes) {
 int oasm_save_stream(oasm_ctx* ctx, uint32_t sid, void* buf, size_t cap, size_t* n) {
   int rc = check_sid(ctx, sid);
   if (rc) return rc;
+  if ((rc = step_end(ctx))) return rc;
   const size_t need = state_bytes(ctx);
   if (n) *n = need;
   const StreamRec& s = ctx->streams[sid];
@@ -1885,6 +1997,7 @@ int oasm_save_stream(oasm_ctx* ctx, uint32_t sid, void* buf, size_t cap, size_t*
 int oasm_restore_stream(oasm_ctx* ctx, uint32_t sid, const void* buf, size_t n) {
   int rc = check_sid(ctx, sid);
   if (rc) return rc;
+  if ((rc = step_end(ctx))) return rc;
   if (!buf || n != state_bytes(ctx)) return fail(ctx, OASM_EINVAL, "state size does not match");
   SavedHeader hd;
   memcpy(&hd, buf, sizeof hd);
@@ -1929,6 +2042,7 @@ int oasm_autotune(oasm_ctx* ctx, const uint8_t* dsample, size_t n, char* report,
   if (!ctx || !dsample || n < 4096) return OASM_EINVAL;
   CK(cudaSetDevice(ctx->device));
   int rc;
+  if ((rc = step_end(ctx))) return rc;
   // a synthetic work item over the sample, laid out like a step's arena
   const size_t need = kFrontPad + n + kEndPad;
   if ((rc = ensure(ctx, ctx->arena, need, "text arena"))) return rc;

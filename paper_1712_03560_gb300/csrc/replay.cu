@@ -69,7 +69,13 @@ int oasm_replay(oasm_ctx* ctx, const oasm_trace* tr, int realtime, uint64_t max_
     got.resize(opened);
     return OASM_OK;
   };
-  while (i < n || !waiting.empty() || n_held) {
+  // steps are pipelined: step k + 1's packets are fed and launched while the
+  // host hands out step k's results (oasm_step_begin / oasm_step_end)
+  bool inflight = false;
+  std::vector<uint64_t> prev_batch;
+  std::vector<uint32_t> prev_ending;
+  double prev_start = 0;
+  while (i < n || !waiting.empty() || n_held || inflight) {
     const double now = seconds_since(t0);
     const uint64_t j =
         realtime ? uint64_t(std::upper_bound(tr->t, tr->t + n, now) - tr->t) : n;
@@ -135,7 +141,7 @@ int oasm_replay(oasm_ctx* ctx, const oasm_trace* tr, int realtime, uint64_t max_
     }
     i = k;
     rs->max_waiting_streams = std::max<uint64_t>(rs->max_waiting_streams, waiting.size());
-    if (batch.empty()) {
+    if (batch.empty() && !inflight) {
       if (i < n && realtime) {
         const double gap = tr->t[i] - seconds_since(t0);
         if (gap > 2e-3) std::this_thread::sleep_for(std::chrono::duration<double>(gap - 1e-3));
@@ -144,48 +150,74 @@ int oasm_replay(oasm_ctx* ctx, const oasm_trace* tr, int realtime, uint64_t max_
       }
       continue;
     }
-    b_sid.resize(batch.size());
-    b_off.resize(batch.size());
-    b_len.resize(batch.size());
-    ending.clear();
+    // (1) this step's packets go in while the previous step runs on the device
     uint64_t bytes = 0;
-    for (size_t b = 0; b < batch.size(); ++b) {
-      const uint64_t q = batch[b];
-      b_sid[b] = uint32_t(sid_of[tr->stream[q]]);
-      b_off[b] = tr->off[q];
-      b_len[b] = tr->len[q];
-      bytes += tr->len[q];
-      if (tr->last[q]) ending.push_back(b_sid[b]);
+    ending.clear();
+    if (!batch.empty()) {
+      b_sid.resize(batch.size());
+      b_off.resize(batch.size());
+      b_len.resize(batch.size());
+      for (size_t b = 0; b < batch.size(); ++b) {
+        const uint64_t q = batch[b];
+        b_sid[b] = uint32_t(sid_of[tr->stream[q]]);
+        b_off[b] = tr->off[q];
+        b_len[b] = tr->len[q];
+        bytes += tr->len[q];
+        if (tr->last[q]) ending.push_back(b_sid[b]);
+      }
+      if ((rc = oasm_feed_many(ctx, uint32_t(batch.size()), b_sid.data(), tr->payload,
+                               b_off.data(), b_len.data())))
+        return rc;
+      if (!ending.empty() && (rc = oasm_end_streams(ctx, uint32_t(ending.size()), ending.data())))
+        return rc;
     }
+    // (2) finish the previous step: its hits are queued now
+    double t_prev_end = 0;
+    const bool had_prev = inflight;
+    if (inflight) {
+      if ((rc = oasm_step_end(ctx))) return rc;
+      t_prev_end = seconds_since(t0);
+      inflight = false;
+    }
+    // (3) launch this step, then hand out the previous one's results and free
+    // its ended streams while the device works
     const double ts = seconds_since(t0);
-    if ((rc = oasm_feed_many(ctx, uint32_t(batch.size()), b_sid.data(), tr->payload, b_off.data(),
-                             b_len.data())))
-      return rc;
-    if (!ending.empty() && (rc = oasm_end_streams(ctx, uint32_t(ending.size()), ending.data())))
-      return rc;
-    if ((rc = oasm_step(ctx))) return rc;
-    size_t nr = 0;
-    if ((rc = oasm_ready(ctx, OASM_ALL_STREAMS, &nr))) return rc;
-    drained.resize(nr);
-    size_t nd = 0;
-    if ((rc = oasm_drain(ctx, nr ? drained.data() : nullptr, nr, &nd))) return rc;
-    const double te = seconds_since(t0);
-    for (size_t r = 0; r < nd; ++r) {
-      drained[r].stream_id = ext_of[drained[r].stream_id];  // external stream ids
-      if (out && n_out < out_cap) out[n_out++] = drained[r];
+    if (!batch.empty()) {
+      if ((rc = oasm_step_begin(ctx))) return rc;
+      inflight = true;
     }
-    rs->kept += nd;
-    if (done_at)
-      for (uint64_t q : batch) done_at[q] = te;
-    rs->steps += 1;
-    rs->packets += batch.size();
-    rs->bytes += bytes;
-    rs->step_s_sum += te - ts;
-    rs->step_s_max = std::max(rs->step_s_max, te - ts);
-    if (!ending.empty()) {  // their last decisions are drained: free the slots
-      if ((rc = oasm_close_streams(ctx, uint32_t(ending.size()), ending.data()))) return rc;
-      for (uint32_t sd : ending) sid_of[ext_of[sd]] = -2;
-      open_now -= ending.size();
+    if (had_prev) {
+      size_t nr = 0;
+      if ((rc = oasm_ready(ctx, OASM_ALL_STREAMS, &nr))) return rc;
+      drained.resize(nr);
+      size_t nd = 0;
+      if ((rc = oasm_drain(ctx, nr ? drained.data() : nullptr, nr, &nd))) return rc;
+      for (size_t r = 0; r < nd; ++r) {
+        drained[r].stream_id = ext_of[drained[r].stream_id];  // external stream ids
+        if (out && n_out < out_cap) out[n_out++] = drained[r];
+      }
+      rs->kept += nd;
+      if (done_at)
+        for (uint64_t q : prev_batch) done_at[q] = t_prev_end;
+      rs->step_s_sum += t_prev_end - prev_start;
+      rs->step_s_max = std::max(rs->step_s_max, t_prev_end - prev_start);
+      if (!prev_ending.empty()) {  // their last decisions are drained: free the slots
+        if ((rc = oasm_close_streams(ctx, uint32_t(prev_ending.size()), prev_ending.data())))
+          return rc;
+        for (uint32_t sd : prev_ending) sid_of[ext_of[sd]] = -2;
+        open_now -= prev_ending.size();
+      }
+    }
+    if (!batch.empty()) {
+      rs->steps += 1;
+      rs->packets += batch.size();
+      rs->bytes += bytes;
+      prev_batch.swap(batch);
+      prev_ending.swap(ending);
+      prev_start = ts;
+    } else {
+      prev_batch.clear();
+      prev_ending.clear();
     }
   }
   rs->wall_s = seconds_since(t0);

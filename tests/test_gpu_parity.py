@@ -472,6 +472,63 @@ def test_zero_copy_feed_from_registered_host_memory():
         B.oasm_destroy(ctx)
 
 
+def test_split_steps_overlap_feeding_with_the_device():
+    """oasm_step_begin / oasm_step_end: input fed, streams opened and hits
+    drained while a step is in flight go to the next step; closing a stream
+    of the step in flight finishes it first.  Every stream's output equals the
+    oracle's."""
+    rng = np.random.default_rng(41)
+    pats, ks, _ = random_case(rng, 4, 24, 6, 40, 10, kmax=3)
+    texts = [random_case(rng, 4, 1, 6, 8, int(rng.integers(4000, 12000)))[2] for _ in range(6)]
+    for t in texts:
+        for p, k in zip(pats[:8], ks[:8]):
+            W.plant(rng, t, W.edit_copy(rng, p, k, W.DNA))
+    ctx = B.oasm_create(pats, ks, None, {"max_streams": 8})
+    got = {}
+    try:
+        sids = {i: B.oasm_open_stream(ctx) for i in range(3)}  # three now, three later
+        pos = [0] * len(texts)
+        B.oasm_step_begin(ctx)  # nothing pending: launches nothing
+        B.oasm_step_end(ctx)
+        rounds = 0
+        while any(p_ < t.size for p_, t in zip(pos, texts)):
+            if rounds == 2:
+                for i in range(3, 6):
+                    sids[i] = B.oasm_open_stream(ctx)  # while a step may be in flight
+            for i, sd in sids.items():
+                if pos[i] < texts[i].size:
+                    n = int(rng.integers(1, 3000))
+                    B.oasm_feed(ctx, sd, texts[i][pos[i]:pos[i] + n])
+                    pos[i] += n
+                    if pos[i] >= texts[i].size:
+                        B.oasm_end_stream(ctx, sd)
+            B.oasm_step_end(ctx)
+            B.oasm_step_begin(ctx)
+            with pytest.raises(B.OasmError) as ei:
+                B.oasm_step_begin(ctx)
+            assert ei.value.code == B.OASM_ESTATE
+            out = B.oasm_drain(ctx)
+            for r in out:
+                got.setdefault(int(r["stream_id"]), []).append(r)
+            rounds += 1
+        B.oasm_step_end(ctx)
+        B.oasm_step(ctx)
+        for r in B.oasm_drain(ctx):
+            got.setdefault(int(r["stream_id"]), []).append(r)
+        for i, sd in sids.items():
+            rows = [(int(r["pattern_id"]), int(r["decided_at"]), int(r["k"]), int(r["start"]),
+                     int(r["len"])) for r in got.get(sd, [])]
+            assert canon(rows) == oracle_rows(pats, ks, texts[i]), i
+        # closing a stream that is part of the step in flight finishes the step
+        sd = B.oasm_open_stream(ctx)
+        B.oasm_feed(ctx, sd, texts[0][:5000])
+        B.oasm_step_begin(ctx)
+        B.oasm_close_stream(ctx, sd)
+        B.oasm_step_end(ctx)
+    finally:
+        B.oasm_destroy(ctx)
+
+
 def test_int_peak_microbenchmark_runs():
     ops, ms = B.oasm_measure_int_peak(0)
     assert ops > 1e12 and ms > 0
