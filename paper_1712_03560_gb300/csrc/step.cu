@@ -166,7 +166,7 @@ int enqueue_step(oasm_ctx* ctx, StepPlan& pl, const WorkItem* d_items, const Reg
     f.set_mask = ctx->pset.cap - 1;
     f.bloom = ctx->d_pbloom;
     f.bloom_bits = ctx->pbloom_bits;
-    f.grid = ctx->num_sms * 2;
+    f.grid = ctx->num_sms * 3;
     if (f.n_segs > 0) {
       if (tm) CK(record_event(ctx, ctx->ev[8], s));
       CK(cudaMemsetAsync(ctx->pset.p, 0xff, ctx->pset.cap * sizeof(unsigned long long), s));
