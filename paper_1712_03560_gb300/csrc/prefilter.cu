@@ -14,8 +14,9 @@
 // segments, 32 start positions x at a time (one per lane).  The first four
 // bytes at x are tested against Bloom bits in shared memory, and only a pass
 // probes the directory of piece prefixes (open addressing, bounded probes).
-// The starts with a directory hit are worked through by the whole warp, its
-// lanes taking the pieces that share the prefix: each is compared in full
+// When few lanes hit, the whole warp works through the hits one at a time,
+// its lanes taking the pieces that share the prefix; when many hit (small
+// alphabets), each lane works through its own.  Each piece is compared in full
 // and proposes its 2K + 1 ends.  A (pattern, end) pair may be proposed by
 // several pieces, so proposals go through an open-addressing set of 64-bit
 // keys (arena offset of the end << 24 | pattern) and only the first insert
@@ -141,10 +142,8 @@ __device__ void flush_cands(const StepParams& P, const PrefArgs& F, WarpCands& w
 }
 
 // Resident blocks; each warp walks its own segments, 32 starts at a time (one
-// per lane).  A start whose 4-byte key passes the Bloom bits (shared memory)
-// probes the directory; the starts with a directory hit are then worked
-// through by the whole warp, one at a time, its lanes taking the entries
-// (pieces) that share the key.  No block-wide barrier after the Bloom load.
+// per lane); see the work mapping above.  No block-wide barrier after the
+// Bloom load.
 __global__ void __launch_bounds__(256) prefilter_kernel(const StepParams P, const PrefArgs F) {
   extern __shared__ __align__(16) uint32_t bloom_s[];
   __shared__ WarpCands wcs[kPrefWarps];
@@ -187,7 +186,18 @@ __global__ void __launch_bounds__(256) prefilter_kernel(const StepParams P, cons
         }
       }
       unsigned m = __ballot_sync(0xffffffffu, hit);
-      while (m) {
+      if (__popc(m) >= 4) {
+        // many starts hit (small alphabets): each lane works through its own
+        if (hit) {
+          const PrefSlot sl = F.dir[h];
+          const uint8_t* t = base + (x - w.base_pos);
+          for (uint32_t j = sl.start; j < sl.start + sl.count; ++j)
+            piece_entry(P, F, w, R.wi, x, t, j, wc);
+        }
+        __syncwarp();
+        m = 0;
+      }
+      while (m) {  // few hits: the whole warp takes them one at a time
         const int src = __ffs(m) - 1;
         m &= m - 1;
         const int64_t xs = __shfl_sync(0xffffffffu, x, src);
