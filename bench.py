@@ -299,7 +299,9 @@ def run_served(args):
         srv.reset_stats()
         st_best, kept_best = None, 0
         for g in SERVED_LOADS_GBPS:
-            tr = W.served(seed=int(5 + 10 * g), n_packets=n_pkt, gbps=g)
+            # overload points get a longer trace: a saturated replay of 200,000
+            # packets lasts only a few steps
+            tr = W.served(seed=int(5 + 10 * g), n_packets=n_pkt if g < 50 else 4 * n_pkt, gbps=g)
             st0 = srv.stats()
             r = srv.replay(tr, realtime=True, engine=args.served_engine,
                            zero_copy=args.served_zero_copy)
@@ -350,7 +352,7 @@ def run_served(args):
                        "step_budget_bytes": int(args.served_batch_mb * (1 << 20)),
                        "engine": args.served_engine,
                        "zero_copy": args.served_zero_copy,
-                       "packets_per_load": n_pkt, "l2": "per-step text is small; L2-resident"},
+                       "packets_per_load": n_pkt, "packets_per_overload_point": 4 * n_pkt, "l2": "per-step text is small; L2-resident"},
             "served": {"sweep": sweep, "sustained_gbps": best["achieved_gbps"],
                        "knee_offered_gbps": knee["offered_gbps"] if knee else None,
                        "p50_ms_at_knee": knee["p50_ms"] if knee else None,
