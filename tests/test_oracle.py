@@ -1,9 +1,10 @@
 """Pins for the CPU oracle against things other than itself.
 
 * the worked example printed in Sec. 4.2 (golden fixture),
-* an edit distance found by breadth-first search over single-symbol edits,
-  i.e. the definition of Sec. 3 ("minimum number of single-character edits")
-  with no dynamic programming at all,
+* an edit distance found by breadth-first search over single-symbol edits:
+  the definition of Sec. 3 (the fewest insertions, deletions and
+  substitutions that turn one string into the other), with no dynamic
+  programming at all,
 * brute-force enumeration of every substring (Fully Naive, Sec. 5.1),
 * textbook special cases (K = 0 reduces to leftmost non-overlapping exact
   search, done here with ``bytes.find``),
