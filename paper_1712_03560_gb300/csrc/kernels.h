@@ -66,7 +66,11 @@ struct PrefArgs {
   const uint32_t* bloom;         // 2^bloom_bits bits: two hash bits per piece prefix
   uint32_t bloom_bits;
   int32_t grid;                  // resident blocks (each walks many segments)
+  uint32_t dir_in_smem;          // 1: the directory (<= kPrefDirSmem bytes) is staged in
+                                 // shared memory and the Bloom bits are skipped
+  uint32_t pad2;
 };
+constexpr size_t kPrefDirSmem = 64 << 10;
 constexpr int kPrefSegMax = 4096;  // start positions per segment
 cudaError_t launch_prefilter(const StepParams& p, const PrefArgs& f, cudaStream_t s);
 cudaError_t prepare_prefilter_kernel(int max_smem_bytes);

@@ -145,11 +145,24 @@ __device__ void flush_cands(const StepParams& P, const PrefArgs& F, WarpCands& w
 // per lane); see the work mapping above.  No block-wide barrier after the
 // Bloom load.
 __global__ void __launch_bounds__(256) prefilter_kernel(const StepParams P, const PrefArgs F) {
-  extern __shared__ __align__(16) uint32_t bloom_s[];
+  extern __shared__ __align__(16) uint32_t dyn_s[];
   __shared__ WarpCands wcs[kPrefWarps];
   if (F.dir_bits == 0) return;
-  const uint32_t nbw = (1u << F.bloom_bits) >> 5;
-  for (uint32_t i = threadIdx.x; i < nbw; i += blockDim.x) bloom_s[i] = F.bloom[i];
+  // a small directory (small alphabets: every 4-byte key may be a prefix)
+  // lives in shared memory and needs no Bloom test; a large one stays in
+  // global memory behind the Bloom bits
+  const bool dir_local = F.dir_in_smem != 0;
+  uint32_t* bloom_s = dyn_s;
+  PrefSlot* dir_s = reinterpret_cast<PrefSlot*>(dyn_s);
+  if (dir_local) {
+    const uint32_t nw = (1u << F.dir_bits) * (sizeof(PrefSlot) / 4);
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(F.dir);
+    for (uint32_t i = threadIdx.x; i < nw; i += blockDim.x) dyn_s[i] = src[i];
+  } else {
+    const uint32_t nbw = (1u << F.bloom_bits) >> 5;
+    for (uint32_t i = threadIdx.x; i < nbw; i += blockDim.x) bloom_s[i] = F.bloom[i];
+  }
+  const PrefSlot* dir = dir_local ? dir_s : F.dir;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   WarpCands& wc = wcs[warp];
   if (lane == 0) {
@@ -171,11 +184,15 @@ __global__ void __launch_bounds__(256) prefilter_kernel(const StepParams P, cons
         const uint8_t* t = base + (x - w.base_pos);
         const uint32_t key = uint32_t(t[0]) | (uint32_t(t[1]) << 8) | (uint32_t(t[2]) << 16) |
                              (uint32_t(t[3]) << 24);
-        const uint32_t b1 = dir_hash(key, F.bloom_bits), b2 = bloom_h2(key, F.bloom_bits);
-        if ((bloom_s[b1 >> 5] >> (b1 & 31)) & (bloom_s[b2 >> 5] >> (b2 & 31)) & 1u) {
+        bool pass = dir_local;
+        if (!pass) {
+          const uint32_t b1 = dir_hash(key, F.bloom_bits), b2 = bloom_h2(key, F.bloom_bits);
+          pass = (bloom_s[b1 >> 5] >> (b1 & 31)) & (bloom_s[b2 >> 5] >> (b2 & 31)) & 1u;
+        }
+        if (pass) {
           h = dir_hash(key, F.dir_bits);
           for (uint32_t pr = 0; pr <= F.max_probe; ++pr) {
-            const PrefSlot sl = F.dir[h];
+            const PrefSlot sl = dir[h];
             if (sl.count == 0) break;
             if (sl.key == key) {
               hit = true;
@@ -189,7 +206,7 @@ __global__ void __launch_bounds__(256) prefilter_kernel(const StepParams P, cons
       if (__popc(m) >= 4) {
         // many starts hit (small alphabets): each lane works through its own
         if (hit) {
-          const PrefSlot sl = F.dir[h];
+          const PrefSlot sl = dir[h];
           const uint8_t* t = base + (x - w.base_pos);
           for (uint32_t j = sl.start; j < sl.start + sl.count; ++j)
             piece_entry(P, F, w, R.wi, x, t, j, wc);
@@ -202,7 +219,7 @@ __global__ void __launch_bounds__(256) prefilter_kernel(const StepParams P, cons
         m &= m - 1;
         const int64_t xs = __shfl_sync(0xffffffffu, x, src);
         const uint32_t hs = __shfl_sync(0xffffffffu, h, src);
-        const PrefSlot sl = F.dir[hs];
+        const PrefSlot sl = dir[hs];
         const uint8_t* ts = base + (xs - w.base_pos);
         for (uint32_t j = sl.start + lane; j < sl.start + sl.count; j += 32)
           piece_entry(P, F, w, R.wi, xs, ts, j, wc);
@@ -220,7 +237,8 @@ cudaError_t launch_prefilter(const StepParams& p, const PrefArgs& f, cudaStream_
   if (f.n_segs <= 0 || f.dir_bits == 0) return cudaSuccess;
   const int blocks = (f.n_segs + kPrefWarps - 1) / kPrefWarps;
   const int grid = blocks < f.grid ? blocks : f.grid;
-  const size_t smem = size_t(1) << (f.bloom_bits - 3);
+  const size_t smem = f.dir_in_smem ? (size_t(1) << f.dir_bits) * sizeof(PrefSlot)
+                                    : size_t(1) << (f.bloom_bits - 3);
   prefilter_kernel<<<grid, 32 * kPrefWarps, smem, s>>>(p, f);
   return cudaGetLastError();
 }

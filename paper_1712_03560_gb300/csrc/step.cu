@@ -166,6 +166,7 @@ int enqueue_step(oasm_ctx* ctx, StepPlan& pl, const WorkItem* d_items, const Reg
     f.set_mask = ctx->pset.cap - 1;
     f.bloom = ctx->d_pbloom;
     f.bloom_bits = ctx->pbloom_bits;
+    f.dir_in_smem = (size_t(1) << f.dir_bits) * sizeof(PrefSlot) <= kPrefDirSmem ? 1u : 0u;
     f.grid = ctx->num_sms * 3;
     if (f.n_segs > 0) {
       if (tm) CK(record_event(ctx, ctx->ev[8], s));
