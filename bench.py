@@ -234,27 +234,9 @@ SERVED_LOADS_GBPS = (0.5, 1.0, 2.0, 3.0, 4.0, 6.0, 10.0, 25.0, 100.0, 400.0)
 
 def filter_mask(patterns, ks, piece: int) -> list:
     """Which patterns cfg.prefilter_piece = piece routes to the piece filter
-    (the library's rule: a fixed minimum piece length, or with piece = 1 the
-    expected piece matches under the pattern set's symbol frequencies)."""
-    if piece == 0:
-        return [False] * len(patterns)
-    if piece >= 4:
-        return [p.size // (int(k) + 1) >= piece for p, k in zip(patterns, ks)]
-    cnt = np.bincount(np.concatenate(patterns), minlength=256).astype(np.float64)
-    f = cnt / cnt.sum()
-    out = []
-    for p, k in zip(patterns, ks):
-        m, parts = p.size, int(k) + 1
-        if m // parts < 4:
-            out.append(False)
-            continue
-        s, off = 0.0, 0
-        for j in range(parts):
-            q = m // parts + (1 if j < m % parts else 0)
-            s += float(np.prod(f[p[off:off + q]]))
-            off += q
-        out.append((2 * int(k) + 1) * s < (1.0 / 4500.0) * ((m + 31) // 32))
-    return out
+    (asked of the library, which applies the same rule at oasm_create)."""
+    from paper_1712_03560_gb300 import binding as B
+    return B.oasm_piece_filter_choice(patterns, ks, piece).tolist()
 
 
 def measured_hbm_gbs():

@@ -255,6 +255,14 @@ int oasm_flush(oasm_ctx *ctx, uint32_t sid, int end_of_stream, oasm_hit *out, si
  * is run.  OASM_ETRUNC when more than cap are queued (the rest stay). */
 int oasm_drain(oasm_ctx *ctx, oasm_hit *out, size_t cap, size_t *n_out);
 
+/* Which patterns a context created with cfg.prefilter_piece = prefilter_piece
+ * would search with the piece filter (on_filter[p] = 1) rather than the
+ * forward scan (0): the same rule oasm_create applies.  Host-only (no device
+ * is touched).  OASM_EINVAL for patterns or a setting oasm_create would
+ * reject. */
+int oasm_piece_filter_choice(const uint8_t *const *pat, const uint32_t *len, const uint32_t *k,
+                             uint32_t n_pat, uint32_t prefilter_piece, uint8_t *on_filter);
+
 /* Zero-copy input.  oasm_register_host pins [ptr, ptr + bytes) of the
  * caller's host memory and maps it for the device.  An oasm_feed_many whose
  * packets all lie in one registered range then copies nothing at the call:

@@ -100,7 +100,8 @@ EXPORTS = ["oasm_config_default", "oasm_rules_default", "oasm_create", "oasm_des
            "oasm_cuda_stream", "oasm_last_error", "oasm_strerror", "oasm_autotune",
            "oasm_measure_int_peak", "oasm_scan_ends_noalloc", "oasm_stream_state_size",
            "oasm_save_stream", "oasm_restore_stream", "oasm_replay", "oasm_register_host",
-           "oasm_unregister_host", "oasm_step_begin", "oasm_step_end"]
+           "oasm_unregister_host", "oasm_step_begin", "oasm_step_end",
+           "oasm_piece_filter_choice"]
 
 _lib = None
 _lock = threading.Lock()
@@ -156,6 +157,8 @@ def load(path: str | None = None):
             "oasm_replay": ([vp, ctypes.POINTER(oasm_trace), i32, u64, vp, vp, ctypes.c_size_t,
                              ctypes.POINTER(oasm_replay_stats)], i32),
             "oasm_register_host": ([vp, vp, ctypes.c_size_t], i32),
+            "oasm_piece_filter_choice": ([u8pp, ctypes.POINTER(u32), ctypes.POINTER(u32), u32, u32,
+                                          vp], i32),
             "oasm_unregister_host": ([vp, vp], i32),
         }
         for name, (args, res) in sig.items():
@@ -414,6 +417,20 @@ def oasm_strerror(code: int) -> str:
 
 def oasm_last_error(ctx=None) -> str:
     return load().oasm_last_error(ctx).decode()
+
+
+def oasm_piece_filter_choice(patterns, ks, prefilter_piece: int) -> np.ndarray:
+    """Boolean per pattern: searched by the piece filter (True) or the scan
+    under cfg.prefilter_piece = prefilter_piece (host-only, no device)."""
+    arrs = [_u8(p) for p in patterns]
+    n = len(arrs)
+    ptrs = (ctypes.c_void_p * max(n, 1))(*[a.ctypes.data for a in arrs])
+    lens = (ctypes.c_uint32 * max(n, 1))(*[a.size for a in arrs])
+    kk = (ctypes.c_uint32 * max(n, 1))(*[int(k) for k in ks])
+    out = np.zeros(max(n, 1), dtype=np.uint8)
+    _check(load().oasm_piece_filter_choice(ptrs, lens, kk, n, int(prefilter_piece),
+                                           out.ctypes.data))
+    return out[:n].astype(bool)
 
 
 def oasm_register_host(ctx, buf: np.ndarray):

@@ -773,6 +773,17 @@ int oasm_restore_stream(oasm_ctx* ctx, uint32_t sid, const void* buf, size_t n) 
   return OASM_OK;
 }
 
+int oasm_piece_filter_choice(const uint8_t* const* pat, const uint32_t* len, const uint32_t* k,
+                             uint32_t n_pat, uint32_t prefilter_piece, uint8_t* on_filter) {
+  if ((n_pat && (!pat || !len || !k || !on_filter)) ||
+      (prefilter_piece > 1 && (prefilter_piece < 4 || prefilter_piece > 128)))
+    return OASM_EINVAL;
+  for (uint32_t p = 0; p < n_pat; ++p)
+    if (!pat[p] || len[p] < 1 || len[p] > OASM_MAX_PATTERN_LEN || k[p] >= len[p]) return OASM_EINVAL;
+  choose_piece_filter(pat, len, k, n_pat, prefilter_piece, on_filter);
+  return OASM_OK;
+}
+
 int oasm_get_stats(oasm_ctx* ctx, oasm_stats* st) {
   if (!ctx || !st) return OASM_EINVAL;
   *st = ctx->st;

@@ -349,6 +349,8 @@ int wait_event(oasm_ctx* ctx, cudaEvent_t ev);
 void free_ctx(oasm_ctx* c);
 int build_prefilter(oasm_ctx* ctx, const std::vector<char>& pref);
 int build_tables(oasm_ctx* ctx);
+void choose_piece_filter(const uint8_t* const* pat, const uint32_t* len, const uint32_t* k,
+                         uint32_t n, uint32_t piece, uint8_t* on_filter);
 StepParams make_params(oasm_ctx* ctx, const WorkItem* d_items, uint32_t n_items, int sb, int kb);
 int bucket_gpw(const oasm_ctx* ctx, const Bucket& b);
 int64_t region_len(oasm_ctx* ctx, const Bucket& b, int64_t total_ends);

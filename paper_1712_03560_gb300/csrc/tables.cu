@@ -94,6 +94,42 @@ int build_prefilter(oasm_ctx* ctx, const std::vector<char>& pref) {
   return OASM_OK;
 }
 
+// Which patterns go to the piece filter:
+//   piece >= 4: every pattern whose K + 1 pieces are all at least that many
+//     symbols long;
+//   piece == 1 (automatic): a pattern with pieces of 4 or more symbols whose
+//     expected proposals per text position, (2K + 1) times the sum over its
+//     pieces of the product of their symbols' frequencies, stay under
+//     kAutoProposalsPerWord per word the scan would run.  The frequencies are
+//     those of all pattern bytes together (the patterns stand in for the
+//     text, which is not known yet).
+void choose_piece_filter(const uint8_t* const* pat, const uint32_t* len, const uint32_t* k,
+                         uint32_t n, uint32_t piece, uint8_t* on_filter) {
+  for (uint32_t p = 0; p < n; ++p) on_filter[p] = 0;
+  if (piece >= 4) {
+    for (uint32_t p = 0; p < n; ++p) on_filter[p] = len[p] / (k[p] + 1u) >= piece;
+  } else if (piece == 1) {
+    double cnt[256] = {0};
+    double tot = 0;
+    for (uint32_t p = 0; p < n; ++p)
+      for (uint32_t i = 0; i < len[p]; ++i) cnt[pat[p][i]] += 1, tot += 1;
+    for (uint32_t p = 0; p < n; ++p) {
+      const int m = int(len[p]), parts = int(k[p]) + 1;
+      if (m / parts < 4) continue;
+      double sum = 0;
+      int off = 0;
+      for (int j = 0; j < parts; ++j) {
+        const int q = m / parts + (j < m % parts ? 1 : 0);
+        double pr = 1;
+        for (int i = 0; i < q; ++i) pr *= cnt[pat[p][off + i]] / tot;
+        sum += pr;
+        off += q;
+      }
+      on_filter[p] = double(2 * k[p] + 1) * sum < kAutoProposalsPerWord * ((m + 31) / 32);
+    }
+  }
+}
+
 int build_tables(oasm_ctx* ctx) {
   const uint32_t n = ctx->n_pat;
   // reversed, bottom-aligned Peq (verification pass): [p][256][4]
@@ -223,38 +259,18 @@ int build_tables(oasm_ctx* ctx) {
     ctx->buckets.push_back(bk);
     return OASM_OK;
   };
-  // patterns for the piece filter instead of the forward scan:
-  //   prefilter_piece >= 4: every pattern whose K + 1 pieces are all at least
-  //     that many symbols long;
-  //   prefilter_piece == 1 (automatic): a pattern with pieces of 4 or more
-  //     symbols whose expected proposals per text position, (2K + 1) times the
-  //     sum over its pieces of the product of their symbols' frequencies,
-  //     stay under kAutoProposalsPerWord per word the scan would run.  The
-  //     frequencies are those of all pattern bytes together (the patterns
-  //     stand in for the text, which is not known yet).
+  // patterns for the piece filter instead of the forward scan
   std::vector<char> pref(n, 0);
-  if (ctx->cfg.prefilter_piece >= 4) {
-    for (uint32_t p = 0; p < n; ++p)
-      pref[p] = ctx->m[p] / (ctx->K[p] + 1u) >= ctx->cfg.prefilter_piece;
-  } else if (ctx->cfg.prefilter_piece == 1) {
-    double cnt[256] = {0};
-    double tot = 0;
-    for (uint32_t p = 0; p < n; ++p)
-      for (uint8_t c : ctx->pats[p]) cnt[c] += 1, tot += 1;
+  if (ctx->cfg.prefilter_piece) {
+    std::vector<const uint8_t*> ptr(n);
+    std::vector<uint32_t> len(n), kk(n);
     for (uint32_t p = 0; p < n; ++p) {
-      const int m = ctx->m[p], parts = ctx->K[p] + 1;
-      if (m / parts < 4) continue;
-      double sum = 0;
-      int off = 0;
-      for (int j = 0; j < parts; ++j) {
-        const int q = m / parts + (j < m % parts ? 1 : 0);
-        double pr = 1;
-        for (int i = 0; i < q; ++i) pr *= cnt[ctx->pats[p][off + i]] / tot;
-        sum += pr;
-        off += q;
-      }
-      pref[p] = double(2 * ctx->K[p] + 1) * sum < kAutoProposalsPerWord * ((m + 31) / 32);
+      ptr[p] = ctx->pats[p].data();
+      len[p] = ctx->m[p];
+      kk[p] = ctx->K[p];
     }
+    choose_piece_filter(ptr.data(), len.data(), kk.data(), n, ctx->cfg.prefilter_piece,
+                        reinterpret_cast<uint8_t*>(pref.data()));
   }
   if (ctx->cfg.prefilter_piece) {
     int rc = build_prefilter(ctx, pref);

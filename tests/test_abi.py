@@ -5,6 +5,8 @@ import ctypes
 import os
 import re
 
+import numpy as np
+
 import pytest
 
 from paper_1712_03560_gb300 import binding as B
@@ -86,3 +88,23 @@ def test_create_rejects_bad_config(field, value):
 def test_config_maker_rejects_unknown_fields():
     with pytest.raises(KeyError):
         B.oasm_config_make(prefilter=4)
+
+
+def test_piece_filter_choice_follows_its_rule():
+    """The host-only routing query (no device): fixed piece lengths, and the
+    automatic rule on a skewed byte set versus a 4-letter alphabet."""
+    rng = np.random.default_rng(3)
+    pats = [bytes(rng.integers(65, 69, size=m).astype(np.uint8)) for m in (8, 12, 16, 24, 32)]
+    ks = [1, 2, 3, 1, 0]
+    got = B.oasm_piece_filter_choice(pats, ks, 4)
+    assert got.tolist() == [len(p) // (k + 1) >= 4 for p, k in zip(pats, ks)]
+    assert not B.oasm_piece_filter_choice(pats, ks, 0).any()
+    # automatic: a 4-letter alphabet makes 4-symbol pieces match often; the
+    # same lengths over many distinct bytes make them rare
+    dna = [bytes(rng.integers(65, 69, size=20).astype(np.uint8)) for _ in range(50)]
+    wide = [bytes(rng.integers(0, 256, size=20).astype(np.uint8)) for _ in range(50)]
+    assert not B.oasm_piece_filter_choice(dna, [3] * 50, 1).any()      # pieces of 5 over 4 letters
+    assert B.oasm_piece_filter_choice(wide, [3] * 50, 1).all()         # pieces of 5 over 256 bytes
+    assert B.oasm_piece_filter_choice(dna, [0] * 50, 1).all()          # one piece of 20
+    with pytest.raises(B.OasmError):
+        B.oasm_piece_filter_choice(pats, ks, 3)
