@@ -249,17 +249,21 @@ def measured_hbm_gbs():
         return 6800.0, "fallback"
 
 
-def B_peak():
+def B_peak(dev: int = 0):
     from paper_1712_03560_gb300 import binding as B
-    return B.oasm_measure_int_peak(0)
+    return B.oasm_measure_int_peak(dev)
 
 
 def run_served(args):
-    """Load sweep of the serving loop: 4,096 byte streams, 2,000 signatures."""
+    """Load sweep of the serving loop: 4,096 byte streams, 2,000 signatures.
+    One server on one GPU: under torchrun, rank 0 runs it and the other
+    ranks exit without work."""
     import torch
     from paper_1712_03560_gb300 import serve
     from paper_1712_03560_gb300 import workloads as W
-    torch.cuda.set_device(0)
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     n_pkt = args.served_packets
     base = W.served(seed=5, n_packets=200, gbps=1.0)
     msum = sum(p.size for p in base.patterns)
@@ -267,8 +271,9 @@ def run_served(args):
             "m~U[8,64] K=2, Zipf(1.1) payload, 1% planted; latency = arrival to end of the step "
             "that matched the packet")
     sweep = []
-    clocks = Clocks(0)
-    with serve.Server(base.patterns, base.ks, max_streams=4096, timing=True,
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    clocks = Clocks(dev)
+    with serve.Server(base.patterns, base.ks, max_streams=4096, timing=True, device=dev,
                       prefilter_piece=args.prefilter,
                       max_batch_bytes=int(args.served_batch_mb * (1 << 20))) as srv:
         # warm-up: grow every step buffer to the sweep's sizes, then a paced pass
@@ -301,7 +306,7 @@ def run_served(args):
         st_all = srv.stats()
     best = max(sweep, key=lambda x: x["achieved_gbps"])
     # roofline of the scan over the steps of the best load point (library events)
-    peak_ops, _ = B_peak()
+    peak_ops, _ = B_peak(dev)
     fm = filter_mask(base.patterns, base.ks, args.prefilter)
     words = sum((p.size + 31) // 32 for p, on in zip(base.patterns, fm) if not on) \
         * st_best["text_bytes"]
