@@ -529,6 +529,28 @@ def test_split_steps_overlap_feeding_with_the_device():
         B.oasm_destroy(ctx)
 
 
+@pytest.mark.parametrize("seed", range(8))
+def test_fuzz_configurations(seed):
+    """Random combinations of alphabet, lengths, thresholds, rules, feed
+    splits and the library's execution choices (automaton on/off, lane groups
+    per warp, graphs, piece filter off/fixed/automatic): always the oracle's
+    output."""
+    rng = np.random.default_rng(5000 + seed)
+    sigma = int(rng.choice([2, 4, 20, 256]))
+    n_pat = int(rng.integers(1, 90))
+    mlo = int(rng.integers(1, 20))
+    mhi = int(rng.integers(mlo, 129))
+    pats, ks, text = random_case(rng, sigma, n_pat, mlo, mhi, int(rng.integers(0, 40000)),
+                                 kmax=int(rng.integers(0, 9)))
+    rules = RULE_SETS[int(rng.integers(0, len(RULE_SETS)))]
+    cfg = {"myers_only": int(rng.integers(0, 2)), "groups_per_warp": int(rng.integers(0, 3)),
+           "graphs": int(rng.integers(0, 2)),
+           "prefilter_piece": int(rng.choice([0, 1, 4, 6]))}
+    splits = np.sort(rng.integers(0, text.size + 1, size=int(rng.integers(0, 6))))
+    rows, _ = run_gpu(pats, ks, text, rules, splits=splits, cfg=cfg)
+    assert canon(rows) == oracle_rows(pats, ks, text, rules), (sigma, n_pat, mlo, mhi, cfg, rules)
+
+
 def test_int_peak_microbenchmark_runs():
     ops, ms = B.oasm_measure_int_peak(0)
     assert ops > 1e12 and ms > 0
