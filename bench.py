@@ -37,8 +37,8 @@ sys.path.insert(0, ROOT)
 OPS_PER_WORD_STEP = 16  # integer ops of one 32-bit column step of the scan
 # DRAM bytes per scan launch and text byte, from an ncu capture of one step's
 # four scan launches on the 64 MiB DNA dictionary with the current kernels
-# (69.1, 75.3, 73.2 and 70.2 MB, mean 71.95 MB per launch for 64 MiB;
-# profiles/scan_kernel_dictionary_dna_64m.md); traffic scales with the text
+# (69.1, 75.3, 73.2 and 70.2 MB, mean 71.95 MB per launch for 64 MiB);
+# traffic scales with the text
 SCAN_DRAM_BYTES_PER_TEXT_BYTE = {"dictionary_dna": 71.95e6 / (64 << 20),
                                  "dictionary_dna_64m": 71.95e6 / (64 << 20)}
 SM_COUNT = 152
