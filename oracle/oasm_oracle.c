@@ -33,7 +33,9 @@
  * Parity status: every function here is pinned by the -m "not gpu" tests
  * (worked example of Sec. 4.2, Fig. 1 values, brute force on tiny inputs,
  * closed forms and invariants).  The non-default readings of A, B, C and F
- * are pinned only by invariants and brute force of their own definitions.
+ * are pinned only by invariants and brute force of their own definitions:
+ * no value the paper prints tells them apart, so for those readings the
+ * parity is unpinned beyond the invariants.
  */
 #include <stdint.h>
 #include <stdlib.h>
