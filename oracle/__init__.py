@@ -13,6 +13,11 @@ Functions (each follows the passage cited in ``oasm_oracle.c``):
   sellers_ends   Less Naive end positions with their distance
   oasm           Algorithm 1 (Sec. 4) with the readings A-G of the C file
   oasm_dictionary  MOASM (Sec. 6.4): one independent Algorithm 1 per pattern
+
+Every function takes ``costs=(sub, ins, del)``: integer edit costs >= 1 in
+place of Eq. 1's unit terms (a variant outside the paper; ``ins`` is a text
+symbol matched by no pattern symbol, ``del`` a pattern symbol missing from
+the text).  ``None`` is the paper's unit-cost distance.
 """
 from __future__ import annotations
 
@@ -44,6 +49,10 @@ FLUSH_DTYPE = np.dtype([("decided_at", "<i8"), ("start", "<i8"), ("r", "<i8"), (
 class _Rules(ctypes.Structure):
     _fields_ = [("replace", ctypes.c_int32), ("order", ctypes.c_int32),
                 ("acc", ctypes.c_int32), ("cmp", ctypes.c_int32)]
+
+
+class _Costs(ctypes.Structure):
+    _fields_ = [("sub", ctypes.c_int32), ("ins", ctypes.c_int32), ("del_", ctypes.c_int32)]
 
 
 def build(force: bool = False) -> str:
@@ -79,6 +88,21 @@ def _load():
                                      ctypes.POINTER(_Rules), ctypes.c_void_p, ctypes.c_int64,
                                      ctypes.c_void_p, ctypes.c_int64, i64p]
             lib.orc_oasm.restype = ctypes.c_int64
+            cp = ctypes.POINTER(_Costs)
+            lib.orc_wlev.argtypes = [u8p, ctypes.c_int, u8p, ctypes.c_int, cp]
+            lib.orc_wlev.restype = ctypes.c_int
+            lib.orc_wlev_prefixes.argtypes = [u8p, ctypes.c_int, u8p, ctypes.c_int, cp, i32p]
+            lib.orc_wlev_prefixes.restype = None
+            lib.orc_wsellers.argtypes = [u8p, ctypes.c_int, u8p, ctypes.c_int64, cp, i32p]
+            lib.orc_wsellers.restype = ctypes.c_int
+            for fn in (lib.orc_whits, lib.orc_wsellers_ends):
+                fn.argtypes = [u8p, ctypes.c_int, ctypes.c_int, u8p, ctypes.c_int64, cp,
+                               ctypes.c_void_p, ctypes.c_int64]
+                fn.restype = ctypes.c_int64
+            lib.orc_woasm.argtypes = [u8p, ctypes.c_int, ctypes.c_int, u8p, ctypes.c_int64,
+                                      ctypes.POINTER(_Rules), cp, ctypes.c_void_p,
+                                      ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, i64p]
+            lib.orc_woasm.restype = ctypes.c_int64
             _lib = lib
     return _lib
 
@@ -98,23 +122,46 @@ def _ptr(a: np.ndarray, ctype=ctypes.c_uint8):
     return a.ctypes.data_as(ctypes.POINTER(ctype))
 
 
-def lev(p, s) -> int:
+def _costs(costs):
+    """None (unit costs) or a ctypes struct of (sub, ins, del), each an int >= 1."""
+    if costs is None:
+        return None
+    sub, ins, dele = (int(c) for c in costs)
+    if min(sub, ins, dele) < 1 or max(sub, ins, dele) > 255:
+        raise ValueError("edit costs must be integers in 1..255")
+    return _Costs(sub, ins, dele)
+
+
+def lev(p, s, costs=None) -> int:
     p, s = _u8(p), _u8(s)
-    return int(_load().orc_lev(_ptr(p), p.size, _ptr(s), s.size))
+    w = _costs(costs)
+    if w is None:
+        return int(_load().orc_lev(_ptr(p), p.size, _ptr(s), s.size))
+    return int(_load().orc_wlev(_ptr(p), p.size, _ptr(s), s.size, ctypes.byref(w)))
 
 
-def lev_prefixes(p, s) -> np.ndarray:
+def lev_prefixes(p, s, costs=None) -> np.ndarray:
     """out[l] = lev(p, s[:l]) for l = 0..len(s)."""
     p, s = _u8(p), _u8(s)
     out = np.zeros(s.size + 1, dtype=np.int32)
-    _load().orc_lev_prefixes(_ptr(p), p.size, _ptr(s), s.size, _ptr(out, ctypes.c_int32))
+    w = _costs(costs)
+    if w is None:
+        _load().orc_lev_prefixes(_ptr(p), p.size, _ptr(s), s.size, _ptr(out, ctypes.c_int32))
+    else:
+        _load().orc_wlev_prefixes(_ptr(p), p.size, _ptr(s), s.size, ctypes.byref(w),
+                                  _ptr(out, ctypes.c_int32))
     return out
 
 
-def sellers(p, t) -> np.ndarray:
+def sellers(p, t, costs=None) -> np.ndarray:
     p, t = _u8(p), _u8(t)
     out = np.zeros(t.size, dtype=np.int32)
-    _load().orc_sellers(_ptr(p), p.size, _ptr(t), t.size, _ptr(out, ctypes.c_int32))
+    w = _costs(costs)
+    if w is None:
+        _load().orc_sellers(_ptr(p), p.size, _ptr(t), t.size, _ptr(out, ctypes.c_int32))
+    else:
+        _load().orc_wsellers(_ptr(p), p.size, _ptr(t), t.size, ctypes.byref(w),
+                             _ptr(out, ctypes.c_int32))
     return out
 
 
@@ -123,11 +170,14 @@ def _check(p, K):
         raise ValueError("need 1 <= len(p) and 0 <= K < len(p)")
 
 
-def _collect(fn, p, K, t, cap0=1024):
+def _collect(fn, p, K, t, cap0=1024, w=None):
     cap = cap0
     while True:
         out = np.zeros(cap, dtype=HIT_DTYPE)
-        n = fn(_ptr(p), p.size, K, _ptr(t), t.size, out.ctypes.data, cap)
+        if w is None:
+            n = fn(_ptr(p), p.size, K, _ptr(t), t.size, out.ctypes.data, cap)
+        else:
+            n = fn(_ptr(p), p.size, K, _ptr(t), t.size, ctypes.byref(w), out.ctypes.data, cap)
         if n < 0:
             raise ValueError("oracle rejected the arguments")
         if n <= cap:
@@ -135,36 +185,47 @@ def _collect(fn, p, K, t, cap0=1024):
         cap = int(n)
 
 
-def hits(p, K: int, t) -> np.ndarray:
+def hits(p, K: int, t, costs=None) -> np.ndarray:
     """Eq. 2 hit set in (start, len) order; ``decided_at`` holds the end."""
     p, t = _u8(p), _u8(t)
     _check(p, K)
-    return _collect(_load().orc_hits, p, K, t)
+    w = _costs(costs)
+    lib = _load()
+    return _collect(lib.orc_hits if w is None else lib.orc_whits, p, K, t, w=w)
 
 
-def sellers_ends(p, K: int, t) -> np.ndarray:
+def sellers_ends(p, K: int, t, costs=None) -> np.ndarray:
     p, t = _u8(p), _u8(t)
     _check(p, K)
-    return _collect(_load().orc_sellers_ends, p, K, t)
+    w = _costs(costs)
+    lib = _load()
+    return _collect(lib.orc_sellers_ends if w is None else lib.orc_wsellers_ends, p, K, t, w=w)
 
 
 def _rules(replace="contained", order="per_start_length", acc="sum", cmp="gt") -> _Rules:
     return _Rules(REPLACE[replace], ORDER[order], ACC[acc], CMP[cmp])
 
 
-def oasm(p, K: int, t, rules: dict | None = None, trace: bool = False):
+def oasm(p, K: int, t, rules: dict | None = None, trace: bool = False, costs=None):
     """Algorithm 1 over one finite text.  Returns kept hits (and flush rows)."""
     p, t = _u8(p), _u8(t)
     _check(p, K)
     ru = _rules(**(rules or {}))
+    w = _costs(costs)
     lib = _load()
     cap, tcap = 256, 256 if trace else 0
     while True:
         out = np.zeros(cap, dtype=HIT_DTYPE)
         tr = np.zeros(max(tcap, 1), dtype=FLUSH_DTYPE)
         tn = ctypes.c_int64(0)
-        n = lib.orc_oasm(_ptr(p), p.size, K, _ptr(t), t.size, ctypes.byref(ru), out.ctypes.data,
-                         cap, tr.ctypes.data if trace else None, tcap, ctypes.byref(tn))
+        if w is None:
+            n = lib.orc_oasm(_ptr(p), p.size, K, _ptr(t), t.size, ctypes.byref(ru),
+                             out.ctypes.data, cap, tr.ctypes.data if trace else None, tcap,
+                             ctypes.byref(tn))
+        else:
+            n = lib.orc_woasm(_ptr(p), p.size, K, _ptr(t), t.size, ctypes.byref(ru),
+                              ctypes.byref(w), out.ctypes.data, cap,
+                              tr.ctypes.data if trace else None, tcap, ctypes.byref(tn))
         if n < 0:
             raise ValueError("oracle rejected the arguments")
         if n <= cap and (not trace or tn.value <= tcap):
@@ -175,7 +236,7 @@ def oasm(p, K: int, t, rules: dict | None = None, trace: bool = False):
 
 
 def oasm_dictionary(patterns, ks, t, rules: dict | None = None, threads: int | None = None,
-                    mode: str = "oasm"):
+                    mode: str = "oasm", costs=None):
     """MOASM: independent Algorithm 1 instances, one per pattern, same text.
 
     Returns a structured array with a ``pattern_id`` column, sorted by
@@ -183,9 +244,9 @@ def oasm_dictionary(patterns, ks, t, rules: dict | None = None, threads: int | N
     so a thread pool runs the patterns on several host cores.
     """
     t = _u8(t)
-    fn = {"oasm": lambda p, k: oasm(p, k, t, rules),
-          "hits": lambda p, k: hits(p, k, t),
-          "ends": lambda p, k: sellers_ends(p, k, t)}[mode]
+    fn = {"oasm": lambda p, k: oasm(p, k, t, rules, costs=costs),
+          "hits": lambda p, k: hits(p, k, t, costs=costs),
+          "ends": lambda p, k: sellers_ends(p, k, t, costs=costs)}[mode]
     threads = threads or os.cpu_count() or 1
     with ThreadPoolExecutor(max_workers=threads) as ex:
         parts = list(ex.map(lambda a: fn(_u8(a[0]), int(a[1])), zip(patterns, ks)))

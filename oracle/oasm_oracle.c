@@ -18,6 +18,17 @@
  *   orc_oasm           Algorithm 1 (Sec. 4): loop over starts i, inner loop
  *                      over lengths l, priority rules R1-R3 (Sec. 4.1),
  *                      validation counters r(k) and Eq. 3 (Sec. 4.2).
+ *   orc_w*             the same functions under integer edit costs: Eq. 1
+ *                      with the three unit terms replaced by a substitution
+ *                      cost, an insertion cost (a text symbol that matches no
+ *                      pattern symbol) and a deletion cost (a pattern symbol
+ *                      missing from the text).  This is a variant outside the
+ *                      paper, whose costs are unit (Sec. 3); with costs
+ *                      (1, 1, 1) every orc_w* function equals its unit form.
+ *                      Reading W: a hit's priority level is its weighted
+ *                      distance k in 0..K, and Algorithm 1 runs unchanged
+ *                      over the weighted hits (every cost >= 1, so a hit
+ *                      still has l in [l_p - K, l_p + K]).
  *
  * Readings taken where the paper is ambiguous or garbled (each selectable):
  *   A  same-priority replacement: CONTAINED (default) / SAME_END / NEVER
@@ -48,6 +59,20 @@ typedef struct {
     int32_t cmp;     /* 0 GT, 1 GE */
 } orc_rules;
 
+/* Edit costs: every cost is an integer >= 1. */
+typedef struct {
+    int32_t sub; /* a pattern symbol aligned with a different text symbol */
+    int32_t ins; /* a text symbol aligned with no pattern symbol */
+    int32_t del; /* a pattern symbol aligned with no text symbol */
+} orc_costs;
+
+static const orc_costs kUnit = {1, 1, 1};
+
+static int costs_ok(const orc_costs *c) {
+    return c && c->sub >= 1 && c->ins >= 1 && c->del >= 1 && c->sub <= 255 && c->ins <= 255 &&
+           c->del <= 255;
+}
+
 typedef struct {
     int64_t start;      /* i */
     int64_t decided_at; /* iteration of Algorithm 1 at which it was added to S */
@@ -72,21 +97,23 @@ static int imin3(int a, int b, int c) {
     return m < c ? m : c;
 }
 
-/* Eq. 1: c[n][m] with c[n][0] = n, c[0][m] = m and the unit-cost recurrence.
- * The whole (l_p+1) x (l+1) matrix is built, exactly as written. */
-int orc_lev(const uint8_t *p, int lp, const uint8_t *s, int l) {
+/* Eq. 1: c[n][m] with c[n][0] = n, c[0][m] = m and the unit-cost recurrence
+ * (weighted: c[n][0] = n del, c[0][m] = m ins, and the terms +del, +ins,
+ * +sub*delta).  The whole (l_p+1) x (l+1) matrix is built, exactly as written. */
+int orc_wlev(const uint8_t *p, int lp, const uint8_t *s, int l, const orc_costs *w) {
+    if (!costs_ok(w)) return -1;
     int rows = lp + 1, cols = l + 1;
     int *c = (int *)malloc(sizeof(int) * (size_t)rows * (size_t)cols);
     if (!c) return -1;
     for (int n = 0; n <= lp; n++) {
         for (int m = 0; m <= l; m++) {
             int v;
-            if (m == 0) v = n;
-            else if (n == 0) v = m;
+            if (m == 0) v = n * w->del;
+            else if (n == 0) v = m * w->ins;
             else {
                 int delta = (p[n - 1] != s[m - 1]);
-                v = imin3(c[(n - 1) * cols + m] + 1, c[n * cols + m - 1] + 1,
-                          c[(n - 1) * cols + m - 1] + delta);
+                v = imin3(c[(n - 1) * cols + m] + w->del, c[n * cols + m - 1] + w->ins,
+                          c[(n - 1) * cols + m - 1] + delta * w->sub);
             }
             c[n * cols + m] = v;
         }
@@ -96,20 +123,25 @@ int orc_lev(const uint8_t *p, int lp, const uint8_t *s, int l) {
     return r;
 }
 
+int orc_lev(const uint8_t *p, int lp, const uint8_t *s, int l) {
+    return orc_wlev(p, lp, s, l, &kUnit);
+}
+
 /* Eq. 1 filled column by column (Sec. 3: only the previous column is kept)
  * against s[0..L-1]; out[l] = c[l_p][l] = lev(p, s[0..l-1]) for l = 0..L.
  * One matrix gives the distance of every prefix of s (Fig. 1(a)). */
-void orc_lev_prefixes(const uint8_t *p, int lp, const uint8_t *s, int L, int32_t *out) {
+void orc_wlev_prefixes(const uint8_t *p, int lp, const uint8_t *s, int L, const orc_costs *w,
+                       int32_t *out) {
     int *col = (int *)malloc(sizeof(int) * (size_t)(lp + 1));
-    for (int n = 0; n <= lp; n++) col[n] = n; /* column m = 0 */
+    for (int n = 0; n <= lp; n++) col[n] = n * w->del; /* column m = 0 */
     out[0] = col[lp];
     for (int m = 1; m <= L; m++) {
-        int diag = col[0]; /* c[0][m-1] */
-        col[0] = m;        /* c[0][m] */
+        int diag = col[0];  /* c[0][m-1] */
+        col[0] = m * w->ins; /* c[0][m] */
         for (int n = 1; n <= lp; n++) {
             int left = col[n]; /* c[n][m-1]; col[n-1] already holds c[n-1][m] */
             int delta = (p[n - 1] != s[m - 1]);
-            int v = imin3(left + 1, col[n - 1] + 1, diag + delta);
+            int v = imin3(left + w->ins, col[n - 1] + w->del, diag + delta * w->sub);
             diag = left;
             col[n] = v;
         }
@@ -118,40 +150,54 @@ void orc_lev_prefixes(const uint8_t *p, int lp, const uint8_t *s, int L, int32_t
     free(col);
 }
 
+void orc_lev_prefixes(const uint8_t *p, int lp, const uint8_t *s, int L, int32_t *out) {
+    orc_wlev_prefixes(p, lp, s, L, &kUnit, out);
+}
+
 /* Less Naive (Sec. 5.1): the dummy row is all zeros, so c[l_p][e+1] is the
  * smallest distance between p and any substring of t ending at e. */
 typedef struct {
     const uint8_t *p;
     int lp;
+    orc_costs w;
     int *col;
 } sellers_state;
 
-static void sellers_init(sellers_state *st, const uint8_t *p, int lp) {
+static void sellers_init(sellers_state *st, const uint8_t *p, int lp, const orc_costs *w) {
     st->p = p;
     st->lp = lp;
+    st->w = *w;
     st->col = (int *)malloc(sizeof(int) * (size_t)(lp + 1));
-    for (int n = 0; n <= lp; n++) st->col[n] = n;
+    for (int n = 0; n <= lp; n++) st->col[n] = n * w->del;
 }
 
 static int sellers_step(sellers_state *st, uint8_t sym) {
     int *col = st->col;
+    const orc_costs *w = &st->w;
     int diag = col[0];
     col[0] = 0; /* zero dummy row: a match may start anywhere */
     for (int n = 1; n <= st->lp; n++) {
         int left = col[n];
         int delta = (st->p[n - 1] != sym);
-        int v = imin3(left + 1, col[n - 1] + 1, diag + delta);
+        int v = imin3(left + w->ins, col[n - 1] + w->del, diag + delta * w->sub);
         diag = left;
         col[n] = v;
     }
     return col[st->lp];
 }
 
-void orc_sellers(const uint8_t *p, int lp, const uint8_t *t, int64_t n, int32_t *D) {
+int orc_wsellers(const uint8_t *p, int lp, const uint8_t *t, int64_t n, const orc_costs *w,
+                 int32_t *D) {
+    if (!costs_ok(w)) return -1;
     sellers_state st;
-    sellers_init(&st, p, lp);
+    sellers_init(&st, p, lp, w);
     for (int64_t e = 0; e < n; e++) D[e] = sellers_step(&st, t[e]);
     free(st.col);
+    return 0;
+}
+
+void orc_sellers(const uint8_t *p, int lp, const uint8_t *t, int64_t n, int32_t *D) {
+    orc_wsellers(p, lp, t, n, &kUnit, D);
 }
 
 /* Shared driver: for each start i, the distances k(l) = lev(p, t(i;l)) for
@@ -162,6 +208,7 @@ typedef struct {
     const uint8_t *p, *t;
     int lp, K;
     int64_t n;
+    orc_costs w;
     sellers_state sl;
     int64_t next_e;
     int32_t *ring; /* D[e] for the most recent ends */
@@ -170,9 +217,9 @@ typedef struct {
 } start_scanner;
 
 static void scanner_init(start_scanner *sc, const uint8_t *p, int lp, int K,
-                         const uint8_t *t, int64_t n) {
-    sc->p = p; sc->t = t; sc->lp = lp; sc->K = K; sc->n = n;
-    sellers_init(&sc->sl, p, lp);
+                         const uint8_t *t, int64_t n, const orc_costs *w) {
+    sc->p = p; sc->t = t; sc->lp = lp; sc->K = K; sc->n = n; sc->w = *w;
+    sellers_init(&sc->sl, p, lp, w);
     sc->next_e = 0;
     int sz = 1;
     while (sz < lp + K + 2) sz <<= 1;
@@ -206,7 +253,7 @@ static int scanner_start(start_scanner *sc, int64_t i, int32_t *kl) {
         if (sc->ring[e & sc->ringmask] <= K) { any = 1; break; }
     if (!any) return 0;
     int L = (int)(hi - i + 1);
-    orc_lev_prefixes(sc->p, lp, sc->t + i, L, sc->pref);
+    orc_wlev_prefixes(sc->p, lp, sc->t + i, L, &sc->w, sc->pref);
     int found = 0;
     for (int l = lp - K; l <= lp + K; l++) {
         if (l < 1 || l > L) continue;
@@ -217,11 +264,11 @@ static int scanner_start(start_scanner *sc, int64_t i, int32_t *kl) {
 }
 
 /* Eq. 2: the hit set H in (i, l) order.  Returns |H|; writes at most cap. */
-int64_t orc_hits(const uint8_t *p, int lp, int K, const uint8_t *t, int64_t n,
-                 orc_hit *out, int64_t cap) {
-    if (lp < 1 || K < 0 || K >= lp) return -1;
+int64_t orc_whits(const uint8_t *p, int lp, int K, const uint8_t *t, int64_t n,
+                  const orc_costs *w, orc_hit *out, int64_t cap) {
+    if (lp < 1 || K < 0 || K >= lp || !costs_ok(w)) return -1;
     start_scanner sc;
-    scanner_init(&sc, p, lp, K, t, n);
+    scanner_init(&sc, p, lp, K, t, n, w);
     int32_t *kl = (int32_t *)malloc(sizeof(int32_t) * (size_t)(2 * K + 1));
     int64_t cnt = 0;
     for (int64_t i = 0; i < n; i++) {
@@ -242,13 +289,18 @@ int64_t orc_hits(const uint8_t *p, int lp, int K, const uint8_t *t, int64_t n,
     return cnt;
 }
 
+int64_t orc_hits(const uint8_t *p, int lp, int K, const uint8_t *t, int64_t n,
+                 orc_hit *out, int64_t cap) {
+    return orc_whits(p, lp, K, t, n, &kUnit, out, cap);
+}
+
 /* Less Naive output: every end e with D[e] <= K, reported with the shortest
  * length l in [l_p-K, l_p+K] whose substring ending at e attains D[e]. */
-int64_t orc_sellers_ends(const uint8_t *p, int lp, int K, const uint8_t *t, int64_t n,
-                         orc_hit *out, int64_t cap) {
-    if (lp < 1 || K < 0 || K >= lp) return -1;
+int64_t orc_wsellers_ends(const uint8_t *p, int lp, int K, const uint8_t *t, int64_t n,
+                          const orc_costs *w, orc_hit *out, int64_t cap) {
+    if (lp < 1 || K < 0 || K >= lp || !costs_ok(w)) return -1;
     sellers_state st;
-    sellers_init(&st, p, lp);
+    sellers_init(&st, p, lp, w);
     int32_t *pref = (int32_t *)malloc(sizeof(int32_t) * (size_t)(lp + K + 1));
     uint8_t *rev_s = (uint8_t *)malloc((size_t)(lp + K));
     uint8_t *rev_p = (uint8_t *)malloc((size_t)lp);
@@ -259,10 +311,11 @@ int64_t orc_sellers_ends(const uint8_t *p, int lp, int K, const uint8_t *t, int6
         if (d > K) continue;
         int L = lp + K;
         if ((int64_t)L > e + 1) L = (int)(e + 1);
-        /* lev is unchanged when both strings are reversed, so one matrix of the
-         * reversed pattern against t[e], t[e-1], ... gives every length ending at e */
+        /* lev is unchanged when both strings are reversed (an alignment read
+         * backwards keeps its operations), so one matrix of the reversed
+         * pattern against t[e], t[e-1], ... gives every length ending at e */
         for (int a = 0; a < L; a++) rev_s[a] = t[e - a];
-        orc_lev_prefixes(rev_p, lp, rev_s, L, pref);
+        orc_wlev_prefixes(rev_p, lp, rev_s, L, w, pref);
         int best = -1;
         for (int l = lp - K; l <= lp + K && l <= L; l++) {
             if (l < 1) continue;
@@ -278,6 +331,11 @@ int64_t orc_sellers_ends(const uint8_t *p, int lp, int K, const uint8_t *t, int6
     }
     free(pref); free(rev_s); free(rev_p); free(st.col);
     return cnt;
+}
+
+int64_t orc_sellers_ends(const uint8_t *p, int lp, int K, const uint8_t *t, int64_t n,
+                         orc_hit *out, int64_t cap) {
+    return orc_wsellers_ends(p, lp, K, t, n, &kUnit, out, cap);
 }
 
 /* ---------------------------------------------------------------------------
@@ -314,16 +372,16 @@ static void apply_rules(const orc_rules *ru, mem_row *mem, int *idx, int *ins,
     /* otherwise the substring is discarded */
 }
 
-int64_t orc_oasm(const uint8_t *p, int lp, int K, const uint8_t *t, int64_t n,
-                 const orc_rules *rules_in, orc_hit *out, int64_t cap,
-                 orc_flush_row *trace, int64_t trace_cap, int64_t *trace_n) {
-    if (lp < 1 || K < 0 || K >= lp) return -1;
+int64_t orc_woasm(const uint8_t *p, int lp, int K, const uint8_t *t, int64_t n,
+                  const orc_rules *rules_in, const orc_costs *w, orc_hit *out, int64_t cap,
+                  orc_flush_row *trace, int64_t trace_cap, int64_t *trace_n) {
+    if (lp < 1 || K < 0 || K >= lp || !costs_ok(w)) return -1;
     orc_rules ru = {0, 0, 0, 0};
     if (rules_in) ru = *rules_in;
     mem_row *mem = (mem_row *)calloc((size_t)(K + 1), sizeof(mem_row));
     int32_t *kl = (int32_t *)malloc(sizeof(int32_t) * (size_t)(2 * K + 1));
     start_scanner sc;
-    scanner_init(&sc, p, lp, K, t, n);
+    scanner_init(&sc, p, lp, K, t, n, w);
     int idx = K, ins = 0;
     int64_t acc = 0, cnt = 0, tcnt = 0;
 
@@ -383,4 +441,10 @@ int64_t orc_oasm(const uint8_t *p, int lp, int K, const uint8_t *t, int64_t n,
     free(kl);
     scanner_free(&sc);
     return cnt;
+}
+
+int64_t orc_oasm(const uint8_t *p, int lp, int K, const uint8_t *t, int64_t n,
+                 const orc_rules *rules_in, orc_hit *out, int64_t cap,
+                 orc_flush_row *trace, int64_t trace_cap, int64_t *trace_n) {
+    return orc_woasm(p, lp, K, t, n, rules_in, &kUnit, out, cap, trace, trace_cap, trace_n);
 }

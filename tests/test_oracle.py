@@ -327,15 +327,50 @@ def test_invariants_every_rule_set(ri):
                 assert r["r"] == f - r["start"] + 1  # r(j) counts from insertion
 
 
+def check_window_layout(kept):
+    """What Eq. 3 with GT and SUM guarantees about the kept hits:
+    * a window's lower-level hits end at least two symbols before the start
+      of its top hit (r(j) - l(top) > l(j) with r(j) = f - i_j + 1);
+    * the hits of one window all lie before those of the next window.
+    Lower-level hits of one window may overlap each other: the comparison
+    bounds their ends by the top hit's start minus the lengths accumulated
+    so far, not by the position of the other lower hits."""
+    groups = {}
+    for h in kept:
+        groups.setdefault(int(h["decided_at"]), []).append(h)
+    prev_end = -1
+    for f in sorted(groups):
+        g = groups[f]
+        top = min(g, key=lambda h: int(h["k"]))
+        assert int(top["start"] + top["len"] - 1) == f
+        for h in g:
+            if h is not top:
+                assert int(h["start"] + h["len"] - 1) < int(top["start"]) - 1
+        assert min(int(h["start"]) for h in g) > prev_end
+        prev_end = f
+
+
 @pytest.mark.parametrize("seed", range(6))
-def test_default_rules_keep_disjoint_hits(seed):
+def test_default_rules_keep_lower_hits_clear_of_the_top_hit(seed):
     rng = np.random.default_rng(500 + seed)
     for _ in range(60):
         p, K, t = _random_case(rng)
-        kept = oracle.oasm(p, K, t)
-        iv = sorted((int(h["start"]), int(h["start"] + h["len"] - 1)) for h in kept)
-        for (a0, a1), (b0, b1) in zip(iv, iv[1:]):
-            assert a1 < b0, iv
+        check_window_layout(oracle.oasm(p, K, t))
+
+
+def test_lower_level_hits_of_one_window_may_overlap():
+    """p = [1,1,0,1,1], K = 3: the window decided at f = 33 keeps its top hit
+    (29, l=5, k=0), and at levels 2 and 3 two hits that both start at 23:
+    Eq. 3 gives r(2) - 5 = 11 - 5 = 6 > 3 and r(3) - (5 + 3) = 3 > 2."""
+    rng = np.random.default_rng(44)
+    for _ in range(109):
+        p, K, t = _random_case(rng)
+    assert p.tolist() == [1, 1, 0, 1, 1] and K == 3
+    kept = oracle.oasm(p, K, t)
+    rows = sorted((int(h["start"]), int(h["len"]), int(h["k"])) for h in kept
+                  if int(h["decided_at"]) == 33)
+    assert rows == [(23, 2, 3), (23, 3, 2), (29, 5, 0)]
+    check_window_layout(kept)
 
 
 def test_windows_cover_every_hit_start_once():
@@ -380,3 +415,173 @@ def test_oracle_rejects_bad_thresholds():
         oracle.oasm(b"ACGT", 4, b"ACGTACGT")  # K < l_p is required (Sec. 6.3)
     with pytest.raises(ValueError):
         oracle.hits(b"", 0, b"ACGT")
+
+
+# --------------------------------------------------------------------------
+# integer edit costs (a variant outside the paper: Eq. 1 with the unit terms
+# replaced by a substitution, an insertion and a deletion cost)
+
+def dijkstra_distances(p: bytes, alphabet: bytes, maxlen: int, costs):
+    """Cheapest sequence of single-symbol edits turning p into every string
+    of length <= maxlen: deleting a symbol of p costs ``del``, inserting a
+    text symbol ``ins``, replacing one ``sub``.  The definition, searched
+    over strings, with no alignment matrix."""
+    import heapq
+    sub, ins, dele = costs
+    dist = {p: 0}
+    heap = [(0, p)]
+    while heap:
+        d, s = heapq.heappop(heap)
+        if d > dist[s]:
+            continue
+        nbrs = []
+        for i in range(len(s)):
+            nbrs.append((s[:i] + s[i + 1:], dele))
+            for c in alphabet:
+                if c != s[i]:
+                    nbrs.append((s[:i] + bytes([c]) + s[i + 1:], sub))
+        if len(s) < maxlen:
+            for i in range(len(s) + 1):
+                for c in alphabet:
+                    nbrs.append((s[:i] + bytes([c]) + s[i:], ins))
+        for t, w in nbrs:
+            if d + w < dist.get(t, 1 << 30):
+                dist[t] = d + w
+                heapq.heappush(heap, (d + w, t))
+    return dist
+
+
+COST_SETS = [(1, 1, 1), (2, 1, 1), (1, 2, 3), (3, 1, 2), (1, 4, 1), (5, 2, 2), (2, 3, 1)]
+
+
+@pytest.mark.parametrize("costs", COST_SETS)
+def test_weighted_lev_matches_cheapest_edit_sequence(costs):
+    alpha = b"AC"
+    strings = list(all_strings(alpha, 5))
+    for p in strings[1:]:
+        dist = dijkstra_distances(p, alpha, 6, costs)
+        for s in strings:
+            assert oracle.lev(p, s, costs=costs) == dist[s], (p, s, costs)
+
+
+def lcs_brute(a: bytes, b: bytes) -> int:
+    """Longest common subsequence by trying every subsequence of a."""
+    for L in range(len(a), -1, -1):
+        for idx in itertools.combinations(range(len(a)), L):
+            sub = bytes(a[i] for i in idx)
+            it = iter(b)
+            if all(c in it for c in sub):
+                return L
+    return 0
+
+
+def test_weighted_lev_without_useful_substitutions_is_indel_distance():
+    """sub >= ins + del: a substitution never beats a deletion plus an
+    insertion, so the distance is del (m - LCS) + ins (n - LCS)."""
+    rng = np.random.default_rng(21)
+    for _ in range(300):
+        p = bytes(rng.choice(list(b"ACG"), size=int(rng.integers(1, 7))).tolist())
+        s = bytes(rng.choice(list(b"ACG"), size=int(rng.integers(0, 7))).tolist())
+        ins, dele = int(rng.integers(1, 4)), int(rng.integers(1, 4))
+        sub = ins + dele + int(rng.integers(0, 3))
+        c = lcs_brute(p, s)
+        assert oracle.lev(p, s, costs=(sub, ins, dele)) == dele * (len(p) - c) + ins * (len(s) - c)
+
+
+def test_weighted_lev_with_costly_indels_is_hamming():
+    """Insertions and deletions dearer than any substitution pattern: equal
+    lengths give sub times the Hamming distance."""
+    rng = np.random.default_rng(22)
+    for _ in range(300):
+        m = int(rng.integers(1, 12))
+        p = rng.integers(0, 4, size=m).astype(np.uint8)
+        s = rng.integers(0, 4, size=m).astype(np.uint8)
+        sub = int(rng.integers(1, 4))
+        big = sub * m + 1
+        assert oracle.lev(p, s, costs=(sub, big, big)) == sub * int((p != s).sum())
+
+
+def test_weighted_lev_swaps_insertion_and_deletion_with_the_strings():
+    """Reading an alignment from the other string turns insertions into
+    deletions: d_(sub,ins,del)(p, s) = d_(sub,del,ins)(s, p)."""
+    rng = np.random.default_rng(23)
+    for _ in range(400):
+        p = rng.integers(0, 3, size=int(rng.integers(1, 10))).astype(np.uint8)
+        s = rng.integers(0, 3, size=int(rng.integers(1, 10))).astype(np.uint8)
+        sub, ins, dele = (int(x) for x in rng.integers(1, 6, size=3))
+        assert oracle.lev(p, s, costs=(sub, ins, dele)) == oracle.lev(s, p, costs=(sub, dele, ins))
+        # scaling every cost scales the distance
+        assert oracle.lev(p, s, costs=(3 * sub, 3 * ins, 3 * dele)) == \
+            3 * oracle.lev(p, s, costs=(sub, ins, dele))
+
+
+@pytest.mark.parametrize("costs", [(2, 1, 1), (1, 2, 3), (3, 1, 2)])
+def test_weighted_lev_prefixes_sellers_hits_and_ends_brute_force(costs):
+    rng = np.random.default_rng(sum(costs))
+    for _ in range(40):
+        m = int(rng.integers(1, 8))
+        K = int(rng.integers(0, m))
+        p = rng.integers(0, 3, size=m).astype(np.uint8)
+        t = rng.integers(0, 3, size=int(rng.integers(1, 35))).astype(np.uint8)
+        lv = lambda a, b: oracle.lev(a, b, costs=costs)  # noqa: E731
+        pref = oracle.lev_prefixes(p, t, costs=costs)
+        assert [int(x) for x in pref] == [lv(p, t[:l]) for l in range(t.size + 1)]
+        D = oracle.sellers(p, t, costs=costs)
+        for e in range(t.size):
+            best = min([lv(p, t[i:e + 1]) for i in range(e + 1)] + [m * costs[2]])
+            assert D[e] == best
+        want = fully_naive(p, K, t, lv)
+        H = oracle.hits(p, K, t, costs=costs)
+        assert sorted((int(h["start"]), int(h["len"]), int(h["k"])) for h in H) == want
+        ends = oracle.sellers_ends(p, K, t, costs=costs)
+        assert ends["decided_at"].tolist() == sorted({i + l - 1 for i, l, _ in want})
+        for r in ends:
+            e = int(r["decided_at"])
+            assert r["k"] == D[e] and lv(p, t[int(r["start"]):e + 1]) == r["k"]
+
+
+@pytest.mark.parametrize("costs", [(2, 1, 1), (1, 2, 3), (3, 1, 2), (1, 1, 1)])
+def test_weighted_oasm_invariants(costs):
+    """Kept hits are weighted hits at their own distance; each window's
+    lower-level hits end before its top hit, windows do not interleave; the
+    first window keeps a hit at least as good as the first hit."""
+    rng = np.random.default_rng(40 + costs[0] + 3 * costs[1])
+    for _ in range(120):
+        p, K, t = _random_case(rng)
+        H = {(int(h["start"]), int(h["len"])): int(h["k"])
+             for h in oracle.hits(p, K, t, costs=costs)}
+        kept = oracle.oasm(p, K, t, costs=costs)
+        for r in kept:
+            assert H[(int(r["start"]), int(r["len"]))] == int(r["k"])
+            assert oracle.lev(p, t[int(r["start"]):int(r["start"] + r["len"])], costs=costs) == r["k"]
+        check_window_layout(kept)
+        if H:
+            assert len(kept) >= 1
+            # the first hit in (start, length) order opens the first window,
+            # which keeps a hit at least as good
+            first = min(H)
+            assert min(int(r["k"]) for r in kept if r["decided_at"] == kept["decided_at"].min()) \
+                <= H[first]
+    # unit costs given explicitly are the paper's distance
+    g = load_golden()
+    a = oracle.oasm(g["pattern"], g["K"], g["text"], costs=(1, 1, 1))
+    b = oracle.oasm(g["pattern"], g["K"], g["text"])
+    assert a.tolist() == b.tolist()
+
+
+def test_weighted_k0_is_exact_search_under_any_costs():
+    """With K = 0 no edit fits whatever the costs: greedy exact search."""
+    rng = np.random.default_rng(44)
+    for _ in range(30):
+        p = bytes(rng.choice(list(b"AC"), size=int(rng.integers(2, 5))).tolist())
+        t = bytes(rng.choice(list(b"AC"), size=200).tolist())
+        costs = tuple(int(x) for x in rng.integers(1, 4, size=3))
+        kept = oracle.oasm(p, 0, t, costs=costs)
+        assert sorted(int(r["start"]) for r in kept) == greedy_exact(p, t)
+
+
+def test_oracle_rejects_bad_costs():
+    with pytest.raises(ValueError):
+        oracle.lev(b"AC", b"A", costs=(0, 1, 1))
+    with pytest.raises(ValueError):
+        oracle.hits(b"ACG", 1, b"ACGT", costs=(1, 256, 1))
