@@ -3,7 +3,8 @@
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                     [--workload dictionary_dna|dictionary_dna_64m|plain_dna|plain_dna_1g|
-                     bytes_zipf|bytes_zipf_256m|many_texts|many_texts_256m|served]
+                     bytes_zipf|bytes_zipf_256m|many_texts|many_texts_256m|served|
+                     dictionary_dna_weighted] [--costs SUB,INS,DEL]
 
 One step = one pass of the whole path over the workload: open a stream, feed
 the text, end it and flush (stage, bit-parallel scan, anchored verification,
@@ -15,7 +16,10 @@ Printed: one JSON line with the metric (GCUPS: sum over patterns of m times
 text symbols, per second), device-resident throughput (`value`), end-to-end
 throughput through host buffers (`e2e`), the scan kernel's roofline against
 the integer issue peak, the CPU oracle on a bounded sample, and the SM
-clocks seen during the timed region.  Under torchrun every rank runs its own
+clocks seen during the timed region.  With integer edit costs (--costs, or the
+dictionary_dna_weighted workload: the DNA dictionary with substitution 1,
+insertion 2, deletion 2) the path is the weighted one: the wave-front dynamic
+program replaces the bit-parallel scan.  Under torchrun every rank runs its own
 replica (a different seed) on its own GPU (weak scaling); rank 0 prints.
 """
 from __future__ import annotations
@@ -35,6 +39,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 OPS_PER_WORD_STEP = 16  # integer ops of one 32-bit column step of the scan
+# integer ops of one cell of the weighted dynamic program: three adds, two
+# minimums, and a compare and a select for the substitution cost
+OPS_PER_DP_CELL = 7
+WEIGHTED_DEFAULT_COSTS = (1, 2, 2)
 # DRAM bytes per scan launch and text byte, from an ncu capture of one step's
 # four scan launches on the 64 MiB DNA dictionary with the current kernels
 # (69.1, 75.3, 73.2 and 70.2 MB, mean 71.95 MB per launch for 64 MiB);
@@ -71,9 +79,21 @@ def parse():
                          "long use the exact piece filter instead of the scan (0 = off, "
                          "1 = automatic per pattern; default 1 for the served signatures, "
                          "0 elsewhere)")
+    ap.add_argument("--costs", default=None,
+                    help="integer edit costs SUB,INS,DEL (each 1..255): the weighted path "
+                         "(oasm_create_weighted); default 1,2,2 for dictionary_dna_weighted, "
+                         "unit costs (the bit-parallel path) elsewhere")
     a = ap.parse_args()
     if a.prefilter is None:
         a.prefilter = 1 if a.workload == "served" else 0
+    if a.costs is not None:
+        a.costs = tuple(int(x) for x in a.costs.split(","))
+        if len(a.costs) != 3:
+            raise SystemExit("--costs takes SUB,INS,DEL")
+    elif a.workload.endswith("_weighted"):
+        a.costs = WEIGHTED_DEFAULT_COSTS
+    if a.costs is not None:
+        a.prefilter = 0  # the weighted path has no piece filter
     return a
 
 
@@ -82,6 +102,9 @@ def make_workload(name: str, seed_offset: int):
     if name == "dictionary_dna":
         return W.dictionary_dna(seed=2 + 1000 * seed_offset), \
             "dictionary_dna: 1024 DNA patterns m~U[8,32] K=floor(m/10), 256 MiB iid DNA text, 1000 planted copies/pattern"
+    if name == "dictionary_dna_weighted":
+        return W.dictionary_dna(seed=2 + 1000 * seed_offset), \
+            "dictionary_dna_weighted: 1024 DNA patterns m~U[8,32] K=floor(m/10), 256 MiB iid DNA text, 1000 planted copies/pattern, integer edit costs"
     if name == "dictionary_dna_64m":
         return W.dictionary_dna(seed=2 + 1000 * seed_offset, n=64 << 20, copies=250), \
             "dictionary_dna_64m: 1024 DNA patterns m~U[8,32] K=floor(m/10), 64 MiB iid DNA text, 250 planted copies/pattern"
@@ -164,7 +187,7 @@ class Clocks:
                 if any(r[3].replace(".", "").isdigit() for r in rows) else None}
 
 
-def cpu_baseline(wl, budget_s: float):
+def cpu_baseline(wl, budget_s: float, costs=None):
     """The oracle as it stands on a bounded sample: whole text, a subset of patterns."""
     import oracle
     cores = os.cpu_count() or 1
@@ -172,7 +195,7 @@ def cpu_baseline(wl, budget_s: float):
     # estimate the per-pattern cost on a prefix, then size the sample
     probe = text[: min(text.size, 1 << 22)]
     t0 = time.perf_counter()
-    oracle.oasm(wl.patterns[0], int(wl.ks[0]), probe)
+    oracle.oasm(wl.patterns[0], int(wl.ks[0]), probe, costs=costs)
     per_sym = (time.perf_counter() - t0) / max(1, probe.size)
     per_pat = per_sym * text.size
     n_pat = int(max(1, min(len(wl.patterns), cores * max(1, int(budget_s / max(per_pat, 1e-9))))))
@@ -184,7 +207,7 @@ def cpu_baseline(wl, budget_s: float):
     pats = [wl.patterns[i] for i in idx]
     ks = [int(wl.ks[i]) for i in idx]
     t0 = time.perf_counter()
-    res = oracle.oasm_dictionary(pats, ks, text, threads=cores)
+    res = oracle.oasm_dictionary(pats, ks, text, threads=cores, costs=costs)
     dt = time.perf_counter() - t0
     cells = sum(p.size for p in pats) * text.size
     return {"value": cells / dt / 1e9, "unit": "GCUPS", "cores": min(cores, n_pat), "kind": "oracle",
@@ -202,7 +225,7 @@ def run_reference(args):
     text = wl.texts[0] if len(wl.texts) == 1 else np.concatenate(wl.texts[:50])
     probe = text[: min(text.size, 1 << 21)]
     t0 = time.perf_counter()
-    oracle.oasm(wl.patterns[0], int(wl.ks[0]), probe)
+    oracle.oasm(wl.patterns[0], int(wl.ks[0]), probe, costs=args.costs)
     per_sym = (time.perf_counter() - t0) / max(1, probe.size)
     # each step: `cores` patterns over a prefix sized for ~6 s of work
     n_sym = int(min(text.size, max(1 << 16, 6.0 / max(per_sym, 1e-12))))
@@ -212,10 +235,11 @@ def run_reference(args):
     ks = [int(wl.ks[i]) for i in idx]
     sample = text[:n_sym]
     for _ in range(args.warmup):
-        oracle.oasm_dictionary(pats, ks, sample[: min(n_sym, 1 << 16)], threads=cores)
+        oracle.oasm_dictionary(pats, ks, sample[: min(n_sym, 1 << 16)], threads=cores,
+                               costs=args.costs)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        oracle.oasm_dictionary(pats, ks, sample, threads=cores)
+        oracle.oasm_dictionary(pats, ks, sample, threads=cores, costs=args.costs)
     dt = time.perf_counter() - t0
     cells = sum(p.size for p in pats) * n_sym * args.steps
     val = cells / dt / 1e9
@@ -223,7 +247,8 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": desc, "l2": "oracle on host cores"},
+            "config": {"workload": desc, "l2": "oracle on host cores",
+                       "costs": list(args.costs) if args.costs else None},
             "cpu_baseline": {"value": val, "unit": "GCUPS", "cores": n_pat, "kind": "oracle",
                              "sample": f"{n_pat} of {len(wl.patterns)} patterns x {n_sym} text symbols per step"},
             "e2e": {"value": val, "unit": "GCUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -388,7 +413,7 @@ def main():
     wl, desc = make_workload(args.workload, rank)
     ctx = B.oasm_create(wl.patterns, wl.ks, None,
                         {"device": dev, "timing": 1, "max_streams": max(64, len(wl.texts)),
-                         "prefilter_piece": args.prefilter})
+                         "prefilter_piece": args.prefilter}, costs=args.costs)
     stream = torch.cuda.ExternalStream(B.oasm_cuda_stream(ctx), device=dev)
     dtexts = [torch.from_numpy(t).to(f"cuda:{dev}") for t in wl.texts]
     torch.cuda.synchronize()
@@ -483,12 +508,23 @@ def main():
     exec_ops_launch = st["word_steps"] / max(1, args.steps) * OPS_PER_WORD_STEP / launches_step
     achieved = exec_ops_launch / (scan_ms_launch * 1e-3) / 1e12
     derived_peak = SM_COUNT * 128 * SM_MAX_MHZ * 1e6 / 1e12
-    tpb = SCAN_DRAM_BYTES_PER_TEXT_BYTE.get(args.workload)
+    units = "executed lane word-steps x 16 ops (a packed lane counts once)"
+    kname, opu = "scan_kernel (all classes of a step)", OPS_PER_WORD_STEP
+    if args.costs is not None:
+        # weighted path: a unit is one cell of the dynamic program; executed
+        # cells count every row of a pattern's 32 W-row column
+        cells_alg = sum(p.size for p in wl.patterns) * wl.text_bytes
+        achieved_alg = cells_alg * OPS_PER_DP_CELL / launches_step / (scan_ms_launch * 1e-3) / 1e12
+        achieved = st["word_steps"] / max(1, args.steps) * OPS_PER_DP_CELL / launches_step \
+            / (scan_ms_launch * 1e-3) / 1e12
+        units = "executed dynamic-program cells (32 W rows per pattern) x 7 ops"
+        kname, opu = "wscan_kernel (weighted wave-front, all classes of a step)", OPS_PER_DP_CELL
+    tpb = None if args.costs is not None else SCAN_DRAM_BYTES_PER_TEXT_BYTE.get(args.workload)
     traffic = tpb * wl.text_bytes if tpb else None
     hbm_peak = measured_hbm_gbs()
     roofline = {"bound": "alu", "achieved": achieved, "peak": derived_peak, "unit": "Tops/s",
                 "frac": achieved / derived_peak,
-                "units": "executed lane word-steps x 16 ops (a packed lane counts once)",
+                "units": units,
                 "achieved_algorithmic": achieved_alg, "frac_algorithmic": achieved_alg / derived_peak,
                 "traffic": traffic,
                 "hbm": None if traffic is None else {
@@ -497,8 +533,8 @@ def main():
                     "peak_source": hbm_peak[1]},
                 "peak_measured_mix": peak_ops / 1e12,
                 "frac_of_measured_mix": achieved * 1e12 / peak_ops,
-                "kernel": "scan_kernel (all classes of a step)", "kernel_ms_per_launch": scan_ms_launch,
-                "ops_per_word_step": OPS_PER_WORD_STEP}
+                "kernel": kname, "kernel_ms_per_launch": scan_ms_launch,
+                "ops_per_word_step": opu}
 
     # ---- end to end through host buffers
     e2e = None
@@ -531,13 +567,14 @@ def main():
     cpu = None
     parity = None
     if not args.no_cpu and world == 1:
-        cpu, (idx, text, ores) = cpu_baseline(wl, args.cpu_seconds)
+        cpu, (idx, text, ores) = cpu_baseline(wl, args.cpu_seconds, args.costs)
         # the sampled patterns' GPU output must equal the oracle's on that sample
         if True:
             from paper_1712_03560_gb300 import binding as B2
             sub_pats = [wl.patterns[i] for i in idx]
             sub_ks = [int(wl.ks[i]) for i in idx]
-            with B2.Matcher(sub_pats, sub_ks, prefilter_piece=args.prefilter) as mt:
+            with B2.Matcher(sub_pats, sub_ks, costs=args.costs,
+                            prefilter_piece=args.prefilter) as mt:
                 g = mt.search(torch.from_numpy(np.ascontiguousarray(text)).to(f"cuda:{dev}"),
                               device=True)
             got = sorted((int(r["pattern_id"]), int(r["decided_at"]), int(r["k"]),
@@ -551,7 +588,7 @@ def main():
     # patterns whose pieces rarely match go to the exact filter, the rest stay
     # on the scan; device-resident inputs, timed like the main value
     alt = None
-    if args.prefilter == 0 and not args.no_alt and world == 1:
+    if args.prefilter == 0 and not args.no_alt and world == 1 and args.costs is None:
         B.oasm_destroy(ctx)
         ctx = None
         ctx2 = B.oasm_create(wl.patterns, wl.ks, None,
@@ -620,7 +657,9 @@ def main():
                    "patterns": len(wl.patterns), "l2": "inputs larger than L2 (text > 129 MB)"
                    if wl.text_bytes > (129 << 20) else "input smaller than L2",
                    "parallelism": f"replicas x{world}", "autotune": tuned,
-                   "prefilter_piece": args.prefilter},
+                   "prefilter_piece": args.prefilter,
+                   "costs": None if args.costs is None else
+                   dict(zip(("sub", "ins", "del"), args.costs))},
         "text_gbps": text_gbps,
         "occurrences_per_step": int(kept),
         "kernel_ms": {k: st[k] / args.steps for k in ("copy_ms", "scan_ms", "prefilter_ms",

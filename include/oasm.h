@@ -92,7 +92,7 @@ typedef struct {
     uint64_t mem_budget;       /* device bytes for per-stream state; 0 = no limit
                                   beyond what the device has */
     uint32_t region_bytes;     /* scan tile length in text symbols; 0 = automatic */
-    uint32_t tile_warps;       /* warps per scan block; 0 = automatic */
+    uint32_t tile_warps;       /* warps per scan block, 0..16; 0 = automatic */
     int32_t timing;            /* 1: time each kernel class with CUDA events */
     uint32_t flush_timeout_ms; /* bound on every host wait (default 600000) */
     void *cuda_stream;         /* cudaStream_t to run on; NULL = library-owned */
@@ -172,6 +172,33 @@ int oasm_rules_default(oasm_rules *rules);
 int oasm_create(const uint8_t *const *pat, const uint32_t *len, const uint32_t *k,
                 uint32_t n_pat, const oasm_rules *rules, const oasm_config *cfg,
                 oasm_ctx **out);
+
+/* Integer edit costs (a variant outside the paper, whose Eq. 1 has unit
+ * costs).  Each replaces one of Eq. 1's three +1 terms:
+ *   sub  a pattern symbol aligned with a different text symbol (the +delta)
+ *   ins  a text symbol aligned with no pattern symbol
+ *   del  a pattern symbol aligned with no text symbol
+ * Every cost is an integer in 1..255.  A hit of Eq. 2 is then a substring
+ * whose weighted distance k is <= K; k is its priority level in Algorithm 1,
+ * which runs unchanged.  Because every cost is >= 1, a hit still has a length
+ * in [l_p - K, l_p + K]. */
+typedef struct {
+    uint32_t sub;
+    uint32_t ins;
+    uint32_t del;
+} oasm_costs;
+
+/* oasm_create with integer edit costs.  costs == NULL is oasm_create (unit
+ * costs, the bit-parallel scan).  A non-NULL costs, even (1, 1, 1), selects
+ * the weighted path: a wave-front (anti-diagonal) dynamic program over each
+ * pattern's rows in place of the bit-parallel scan, a plain dynamic program
+ * in place of the bit-parallel verification, the same filter.  The piece
+ * filter and the automaton classes do not apply to it (cfg->prefilter_piece
+ * and cfg->myers_only are ignored).  Errors as oasm_create, plus OASM_EINVAL
+ * for a cost outside 1..255. */
+int oasm_create_weighted(const uint8_t *const *pat, const uint32_t *len, const uint32_t *k,
+                         uint32_t n_pat, const oasm_rules *rules, const oasm_costs *costs,
+                         const oasm_config *cfg, oasm_ctx **out);
 
 /* Frees every host and device resource of the context.  Safe on NULL and on a
  * context whose creation failed half way.  Waits (bounded) for device work. */

@@ -80,6 +80,10 @@ class oasm_stats(ctypes.Structure):
                 ("host_wait_ms", ctypes.c_double), ("host_post_ms", ctypes.c_double)]
 
 
+class oasm_costs(ctypes.Structure):
+    _fields_ = [("sub", ctypes.c_uint32), ("ins", ctypes.c_uint32), ("del_", ctypes.c_uint32)]
+
+
 class oasm_trace(ctypes.Structure):
     _fields_ = [("t", ctypes.c_void_p), ("stream", ctypes.c_void_p), ("off", ctypes.c_void_p),
                 ("len", ctypes.c_void_p), ("last", ctypes.c_void_p), ("payload", ctypes.c_void_p),
@@ -93,7 +97,8 @@ class oasm_replay_stats(ctypes.Structure):
                [(n, ctypes.c_double) for n in ("wall_s", "step_s_sum", "step_s_max")]
 
 
-EXPORTS = ["oasm_config_default", "oasm_rules_default", "oasm_create", "oasm_destroy",
+EXPORTS = ["oasm_config_default", "oasm_rules_default", "oasm_create", "oasm_create_weighted",
+           "oasm_destroy",
            "oasm_open_stream", "oasm_close_stream", "oasm_open_streams", "oasm_end_streams",
            "oasm_close_streams", "oasm_feed", "oasm_feed_many", "oasm_feed_device",
            "oasm_end_stream", "oasm_step", "oasm_flush", "oasm_drain", "oasm_ready", "oasm_get_stats", "oasm_reset_stats",
@@ -125,6 +130,9 @@ def load(path: str | None = None):
             "oasm_create": ([u8pp, ctypes.POINTER(u32), ctypes.POINTER(u32), u32,
                              ctypes.POINTER(oasm_rules), ctypes.POINTER(oasm_config),
                              ctypes.POINTER(vp)], i32),
+            "oasm_create_weighted": ([u8pp, ctypes.POINTER(u32), ctypes.POINTER(u32), u32,
+                                      ctypes.POINTER(oasm_rules), ctypes.POINTER(oasm_costs),
+                                      ctypes.POINTER(oasm_config), ctypes.POINTER(vp)], i32),
             "oasm_destroy": ([vp], i32),
             "oasm_open_stream": ([vp, ctypes.POINTER(u32)], i32),
             "oasm_close_stream": ([vp, u32], i32),
@@ -202,7 +210,9 @@ def _u8(a) -> np.ndarray:
 
 
 def oasm_create(patterns, ks, rules: oasm_rules | dict | None = None,
-                cfg: oasm_config | dict | None = None):
+                cfg: oasm_config | dict | None = None, costs=None):
+    """costs: None (unit costs, oasm_create) or (sub, ins, del), which calls
+    oasm_create_weighted."""
     lib = load()
     pats = [_u8(p) for p in patterns]
     n = len(pats)
@@ -214,8 +224,14 @@ def oasm_create(patterns, ks, rules: oasm_rules | dict | None = None,
     if isinstance(cfg, dict):
         cfg = oasm_config_make(**cfg)
     ctx = ctypes.c_void_p()
-    rc = lib.oasm_create(ptrs, lens, kk, n, ctypes.byref(rules) if rules else None,
-                         ctypes.byref(cfg) if cfg else None, ctypes.byref(ctx))
+    if costs is None:
+        rc = lib.oasm_create(ptrs, lens, kk, n, ctypes.byref(rules) if rules else None,
+                             ctypes.byref(cfg) if cfg else None, ctypes.byref(ctx))
+    else:
+        w = oasm_costs(*(int(c) for c in costs))
+        rc = lib.oasm_create_weighted(ptrs, lens, kk, n, ctypes.byref(rules) if rules else None,
+                                      ctypes.byref(w), ctypes.byref(cfg) if cfg else None,
+                                      ctypes.byref(ctx))
     _check(rc, None)
     return ctx
 
@@ -482,8 +498,8 @@ def oasm_replay(ctx, times, streams, offs, lens, last, payload, n_streams: int,
 class Matcher:
     """Convenience owner of one context (still marshalling only)."""
 
-    def __init__(self, patterns, ks, rules=None, **cfg):
-        self.ctx = oasm_create(patterns, ks, rules, cfg or None)
+    def __init__(self, patterns, ks, rules=None, costs=None, **cfg):
+        self.ctx = oasm_create(patterns, ks, rules, cfg or None, costs=costs)
 
     def close(self):
         if self.ctx is not None:

@@ -90,9 +90,9 @@ void free_ctx(oasm_ctx* c) {
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
   auto f = [](void* p) { if (p) cudaFree(p); };
-  f(c->d_m); f(c->d_K); f(c->d_mem_off); f(c->d_peq_rev);
+  f(c->d_m); f(c->d_K); f(c->d_mem_off); f(c->d_peq_rev); f(c->d_wpat);
   f(c->d_pdir); f(c->d_pent); f(c->d_pbytes); f(c->d_poff); f(c->pset.p); f(c->d_pbloom);
-  for (auto& b : c->buckets) { f(b.d_groups); f(b.d_peq); }
+  for (auto& b : c->buckets) { f(b.d_groups); f(b.d_peq); f(b.d_wrow); }
   f(c->d_tails); f(c->d_hdr); f(c->d_mem);
   f(c->arena.p); f(c->upload.p); f(c->stage[0].d.p); f(c->stage[1].d.p); f(c->cand.p); f(c->keys.p);
   f(c->keys_alt.p); f(c->out.p); f(c->pool_hdr.p); f(c->pool_mem.p); f(c->pair_pool.p);
@@ -180,6 +180,12 @@ const char* oasm_last_error(oasm_ctx* ctx) {
 int oasm_create(const uint8_t* const* pat, const uint32_t* len, const uint32_t* k,
                 uint32_t n_pat, const oasm_rules* rules, const oasm_config* cfg,
                 oasm_ctx** out) {
+  return oasm_create_weighted(pat, len, k, n_pat, rules, nullptr, cfg, out);
+}
+
+int oasm_create_weighted(const uint8_t* const* pat, const uint32_t* len, const uint32_t* k,
+                         uint32_t n_pat, const oasm_rules* rules, const oasm_costs* costs,
+                         const oasm_config* cfg, oasm_ctx** out) {
   g_create_err.clear();
   if (!out) return OASM_EINVAL;
   *out = nullptr;
@@ -205,9 +211,16 @@ int oasm_create(const uint8_t* const* pat, const uint32_t* len, const uint32_t* 
     g_create_err = "rules field out of range";
     return OASM_EINVAL;
   }
-  if (cfg && (cfg->groups_per_warp > 2 ||
+  if (cfg && (cfg->groups_per_warp > 2 || cfg->tile_warps > 16 ||
               (cfg->prefilter_piece > 1 && (cfg->prefilter_piece < 4 || cfg->prefilter_piece > 128)))) {
-    g_create_err = "config: groups_per_warp must be 0, 1 or 2; prefilter_piece 0, 1 or 4..128";
+    g_create_err =
+        "config: groups_per_warp must be 0, 1 or 2; tile_warps 0..16; prefilter_piece 0, 1 or "
+        "4..128";
+    return OASM_EINVAL;
+  }
+  if (costs && (costs->sub < 1 || costs->sub > 255 || costs->ins < 1 || costs->ins > 255 ||
+                costs->del < 1 || costs->del > 255)) {
+    g_create_err = "edit costs must be integers in 1..255";
     return OASM_EINVAL;
   }
   if (cfg && cfg->prefilter_piece && n_pat >= (1u << 24)) {
@@ -219,6 +232,12 @@ int oasm_create(const uint8_t* const* pat, const uint32_t* len, const uint32_t* 
   if (cfg) ctx->cfg = *cfg;
   if (ctx->cfg.max_streams == 0) ctx->cfg.max_streams = 64;
   ctx->rules = Rules{ru.replace, ru.order, ru.acc, ru.cmp, ru.output};
+  if (costs) {  // the weighted path has no piece filter and no automaton classes
+    ctx->weighted = true;
+    ctx->costs = *costs;
+    ctx->cfg.prefilter_piece = 0;
+    ctx->cfg.myers_only = 0;
+  }
   ctx->debug = getenv("OASM_DEBUG") != nullptr;
   ctx->device = ctx->cfg.device;
   auto bail = [&](int rc) {
@@ -273,6 +292,7 @@ int oasm_create(const uint8_t* const* pat, const uint32_t* len, const uint32_t* 
       h = fnv1a(h, pat[p], len[p]);
     }
     h = fnv1a(h, &ctx->rules, sizeof ctx->rules);
+    if (ctx->weighted) h = fnv1a(h, &ctx->costs, sizeof ctx->costs);
     ctx->fingerprint = h;
   }
   // stream slots: tail, window headers and level rows for every pattern
@@ -832,7 +852,8 @@ int oasm_autotune(oasm_ctx* ctx, const uint8_t* dsample, size_t n, char* report,
     // two groups per warp exist for one-word classes in the dictionary mapping;
     // a configured value is kept
     const int g_lo = bucket_gpw(ctx, b) == 2 && ctx->cfg.groups_per_warp ? 2 : 1;
-    const int g_hi = (dict && b.W == 1 && ctx->cfg.groups_per_warp != 1) ? 2 : 1;
+    const bool wdp = b.algo == kAlgoWeighted;
+    const int g_hi = (dict && b.W == 1 && ctx->cfg.groups_per_warp != 1 && !wdp) ? 2 : 1;
     auto time_cfg = [&](int go, int wo, int co, double so, float* out_ms) -> int {
       if (scan_smem_bytes(b.W, wo, dict ? co : 0, go) > size_t(max_smem)) {
         *out_ms = 1e30f;
@@ -865,6 +886,10 @@ int oasm_autotune(oasm_ctx* ctx, const uint8_t* dsample, size_t n, char* report,
       a.chunk = co;
       a.algo = b.algo;
       a.gpw = go;
+      a.wrow = b.d_wrow;
+      a.c_sub = int(ctx->costs.sub);
+      a.c_ins = int(ctx->costs.ins);
+      a.c_del = int(ctx->costs.del);
       a.items = reinterpret_cast<const WorkItem*>(ctx->upload.p);
       a.arena = ctx->arena.p;
       a.cand = ctx->cand.p;
@@ -901,7 +926,8 @@ int oasm_autotune(oasm_ctx* ctx, const uint8_t* dsample, size_t n, char* report,
       }
     // phase 2: text buffer size x region length for the winner
     for (int co : chunk_opts) {
-      if (!dict && co != chunk_opts[0]) continue;  // the segment mapping stages no text
+      // the segment mapping and the weighted path stage no text in TMA buffers
+      if ((!dict || wdp) && co != chunk_opts[0]) continue;
       for (double so : scale_opts) {
         float ms;
         if ((rc = time_cfg(bg, bw, co, so, &ms))) return rc;

@@ -208,6 +208,10 @@ struct Bucket {
   std::vector<LaneGroup> groups;
   LaneGroup* d_groups = nullptr;
   uint32_t* d_peq = nullptr;
+  // weighted path (algo == kAlgoWeighted): one pattern per group; per group
+  // 32 W rows of 16 bits, lane-major (lane l holds rows W l .. W l + W - 1):
+  // the pattern symbol, or kWildRow for the rows above the pattern
+  uint16_t* d_wrow = nullptr;
 };
 
 template <class T>
@@ -274,6 +278,11 @@ struct oasm_ctx {
   uint8_t* d_K = nullptr;
   uint32_t* d_mem_off = nullptr;
   uint32_t* d_peq_rev = nullptr;
+  // integer edit costs (oasm_create_weighted): the weighted dynamic program
+  // replaces the bit-parallel scan and verification
+  bool weighted = false;
+  oasm_costs costs{1, 1, 1};
+  uint8_t* d_wpat = nullptr;  // [n_pat][OASM_MAX_PATTERN_LEN] pattern symbols
   std::vector<Bucket> buckets;
   // piece filter (cfg.prefilter_piece): tables of the patterns it serves
   uint32_t n_pref_pat = 0;

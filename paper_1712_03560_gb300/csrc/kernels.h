@@ -20,13 +20,20 @@ struct ScanArgs {
   int32_t chunk;             // text bytes per TMA buffer (dictionary mapping)
   int32_t algo;              // 0: Myers/Hyyro bit-vectors; 1 + K: automaton for K <= 2 (W = 1)
   int32_t gpw;               // lane groups per warp: 1, or 2 (dictionary mapping, W = 1)
-  int32_t pad;
+  int32_t c_sub, c_ins, c_del;  // edit costs (algo == kAlgoWeighted)
+  const uint16_t* wrow;      // weighted path: [n_groups][32 W] row symbols (kWildRow above
+                             // the pattern), lane-major
   const WorkItem* items;
   const uint8_t* arena;
   Candidate* cand;
   unsigned long long cap_cand;
   StepCounters* ctr;
 };
+
+// Weighted dynamic program over a pattern's rows (oasm_create_weighted): a
+// bucket of this algo holds one pattern per group, W rows per lane.
+constexpr int kAlgoWeighted = 8;
+constexpr uint16_t kWildRow = 0x100;  // a row above the pattern: matches every symbol
 
 // Shared memory of one scan block: the Peq tables of its gpw lane groups (256
 // rows of W x 32 words each), two text buffers per warp (dictionary mapping)

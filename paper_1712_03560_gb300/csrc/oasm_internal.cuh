@@ -143,6 +143,9 @@ struct StepParams {
   const uint8_t* K;          // [n_pat]
   const uint32_t* mem_off;   // [n_pat] first MemRow of pattern p in a slot
   const uint32_t* peq_rev;   // [n_pat][256][4]
+  const uint8_t* wpat;       // [n_pat][128] pattern symbols (weighted path)
+  int32_t weighted;          // 1: integer edit costs, plain dynamic program
+  int32_t c_sub, c_ins, c_del;
   uint32_t n_pat;
   uint32_t mem_stride;       // MemRow entries per slot
   Rules rules;

@@ -105,6 +105,47 @@ __device__ void anchored_pass(const uint32_t* __restrict__ peq, const uint8_t* _
   }
 }
 
+// Weighted verification (integer edit costs): the column dynamic program of
+// Eq. 1 with costs c_sub, c_ins, c_del, the reversed pattern against t[e],
+// t[e-1], ... (an alignment read backwards keeps its operations, so the
+// distance is unchanged), one column of l_p + 1 cells per length.  Writes
+// dist[l] = weighted distance of t[e-l+1..e] for l = 1..lmax.
+__device__ void weighted_anchored(const StepParams& P, int p, const uint8_t* __restrict__ tend,
+                                  int m, int lmax, int8_t* dist) {
+  const uint8_t* pat = P.wpat + size_t(p) * OASM_MAX_PATTERN_LEN;
+  const int cs = P.c_sub, ci = P.c_ins, cd = P.c_del;
+  int col[OASM_MAX_PATTERN_LEN + 1];
+  for (int r = 0; r <= m; ++r) col[r] = r * cd;
+  for (int l = 1; l <= lmax; ++l) {
+    const uint8_t c = tend[-(l - 1)];
+    int diag = col[0];
+    col[0] = l * ci;
+    for (int r = 1; r <= m; ++r) {
+      const int left = col[r];
+      const int v = min(min(left + ci, col[r - 1] + cd), diag + (pat[m - r] == c ? 0 : cs));
+      diag = left;
+      col[r] = v;
+    }
+    dist[l] = int8_t(min(col[m], 127));
+  }
+}
+
+// Distances of every length ending at tend (bit-parallel, or the weighted
+// dynamic program).
+__device__ __forceinline__ void lengths_at(const StepParams& P, int p, const uint8_t* tend,
+                                           int m, int lmax, int8_t* dist) {
+  if (P.weighted) {
+    weighted_anchored(P, p, tend, m, lmax, dist);
+    return;
+  }
+  const int W = (m + 31) >> 5;
+  const uint32_t* pq = P.peq_rev + size_t(p) * 256 * 4;
+  if (W == 1) anchored_pass<1>(pq, tend, m, lmax, dist);
+  else if (W == 2) anchored_pass<2>(pq, tend, m, lmax, dist);
+  else if (W == 3) anchored_pass<3>(pq, tend, m, lmax, dist);
+  else anchored_pass<4>(pq, tend, m, lmax, dist);
+}
+
 // Canonical order of emitted records: (work item, pattern, decided_at, k,
 // length), packed like the hit keys so it fits the same bit budget.
 __device__ __forceinline__ unsigned long long out_key(const StepParams& P, uint64_t pair,
@@ -148,12 +189,7 @@ __global__ void __launch_bounds__(256) verify_kernel(const StepParams P) {
         if (P.rules.output == OASM_OUT_ENDS) {
           if (e >= w.e_prev && e < w.e_new) {
             const int lmax = int(min(int64_t(m + K), e - lo_start + 1));
-            const int W = (m + 31) >> 5;
-            const uint32_t* pq = P.peq_rev + size_t(p) * 256 * 4;
-            if (W == 1) anchored_pass<1>(pq, tend, m, lmax, dist);
-            else if (W == 2) anchored_pass<2>(pq, tend, m, lmax, dist);
-            else if (W == 3) anchored_pass<3>(pq, tend, m, lmax, dist);
-            else anchored_pass<4>(pq, tend, m, lmax, dist);
+            lengths_at(P, p, tend, m, lmax, dist);
             int best = 127, bl = 0;
             for (int l = 1; l <= lmax; ++l)
               if (dist[l] < best) { best = dist[l]; bl = l; }
@@ -174,12 +210,7 @@ __global__ void __launch_bounds__(256) verify_kernel(const StepParams P) {
           const int lmax = int(min(int64_t(m + K), e - smin + 1));
           const int lmin = int(max(int64_t(max(1, m - K)), e - fn + 1));
           if (lmin <= lmax) {
-            const int W = (m + 31) >> 5;
-            const uint32_t* pq = P.peq_rev + size_t(p) * 256 * 4;
-            if (W == 1) anchored_pass<1>(pq, tend, m, lmax, dist);
-            else if (W == 2) anchored_pass<2>(pq, tend, m, lmax, dist);
-            else if (W == 3) anchored_pass<3>(pq, tend, m, lmax, dist);
-            else anchored_pass<4>(pq, tend, m, lmax, dist);
+            lengths_at(P, p, tend, m, lmax, dist);
             const uint64_t pair = uint64_t(c.wi) * P.n_pat + uint64_t(p);
             for (int l = lmin; l <= lmax; ++l) {
               const int k = dist[l];

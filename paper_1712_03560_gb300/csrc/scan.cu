@@ -771,6 +771,124 @@ __global__ void __launch_bounds__(512) scan_kernel(const ScanArgs A) {
   }
 }
 
+// ------------------------------------------------------ weighted path
+// Integer edit costs (oasm_create_weighted): Eq. 1 with costs c_sub, c_ins,
+// c_del and Sellers' zero row, filled as a wave-front over anti-diagonals
+// (the paper's own order of evaluation, Sec. 3, Fig. 1(b)), one warp per
+// (pattern, region).  Lane l holds rows W l .. W l + W - 1 of a 32 W-row
+// column whose bottom l_p rows are the pattern's (the rows above match
+// every symbol and stay 0).  At step s lane l fills column e = x0 + s - l:
+// the row above its first row at columns e and e - 1 is lane l - 1's last
+// row at steps s - 1 and s - 2, and the symbol t[e] is the one lane l - 1
+// used at step s - 1, so both travel down in one shuffle per step, packed as
+// (value << 8) | symbol.  Lane 31's last row is D[e]: a candidate end when
+// it is <= K (the same test as the bit-parallel scan's).
+//
+// Per cell: three adds, two minimums and a compare-select for the
+// substitution cost; per lane and step one shuffle, one shared-memory load
+// (the symbol for lane 0) and the candidate bit.
+template <int W, bool kPro>
+__device__ __forceinline__ void wdp_step(uint32_t& xout, int (&col)[W], int& up_prev,
+                                         const uint32_t (&pc)[W], const int (&csub)[W], int ci,
+                                         int cd, uint32_t sym0, int lane, bool active) {
+  uint32_t xin = __shfl_up_sync(kFull, xout, 1);
+  if (lane == 0) xin = sym0;  // the row above lane 0 is Sellers' zero row
+  const uint32_t sym = xin & 0xffu;
+  const int up_cur = int(xin >> 8);
+  int diag = up_prev, up = up_cur;
+  int nv[W];
+#pragma unroll
+  for (int q = 0; q < W; ++q) {
+    const int left = col[q];
+    const int sub = (pc[q] == sym) ? 0 : csub[q];
+    const int v = min(min(diag + sub, left + ci), up + cd);
+    diag = left;
+    nv[q] = v;
+    up = v;
+  }
+  if (!kPro || active) {
+#pragma unroll
+    for (int q = 0; q < W; ++q) col[q] = nv[q];
+    up_prev = up_cur;
+    xout = (uint32_t(nv[W - 1]) << 8) | sym;
+  }
+}
+
+template <int W>
+__global__ void __launch_bounds__(512) wscan_kernel(const ScanArgs A) {
+  __shared__ uint8_t sb[16][32];  // per warp: the symbols of the current 32-step block
+  const int ng = A.n_groups;
+  const int g = blockIdx.x % ng;
+  const int rb = blockIdx.x / ng;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int r = rb * A.warps + warp;
+  if (r >= A.n_regions || warp >= 16) return;  // the whole warp leaves together
+  const Region R = A.regions[r];
+  const WorkItem wi = A.items[R.wi];
+  const LaneGroup& G = A.groups[g];
+  const int pid = G.pat[0], m = G.m[0], K = G.K[0];
+  const int ci = A.c_ins, cd = A.c_del;
+  const int top = 32 * W - m;  // rows above the pattern
+  uint32_t pc[W];
+  int csub[W], col[W];
+#pragma unroll
+  for (int q = 0; q < W; ++q) {
+    const int row = W * lane + q;
+    const uint32_t v = A.wrow[size_t(g) * 32 * W + row];
+    const bool wild = (v & kWildRow) != 0;
+    pc[q] = v;
+    csub[q] = wild ? 0 : A.c_sub;
+    col[q] = wild ? 0 : (row - top + 1) * cd;  // column x0 - 1: row r costs r deletions
+  }
+  const int above = W * lane - 1;
+  int up_prev = (lane == 0 || above < top) ? 0 : (above - top + 1) * cd;
+  uint32_t xout = uint32_t(col[W - 1]) << 8;
+  const int64_t a = R.a, b = R.b;
+  if (b <= a) return;
+  const int64_t x0 = a - G.ov;  // warm-up: l_p + K - 1 symbols before the region
+  int64_t rep_lo = max(a, wi.e_prev - 2 * int64_t(K));
+  rep_lo = max(rep_lo, int64_t(0));
+  // step s fills column x0 + s - lane; lane 31 reports ends in [rep_lo, b)
+  const int t_lo = int(rep_lo - x0 + 31), t_hi = int(b - x0 + 31);
+  const int nblk = (t_hi + 31) / 32;
+  const uint8_t* src = A.arena + (int64_t(wi.arena_base) + (x0 - wi.base_pos));
+  Emitter em;
+  uint8_t nb = src[lane];
+  for (int v = 0; v < nblk; ++v) {
+    __syncwarp();
+    sb[warp][lane] = nb;
+    __syncwarp();
+    if (v + 1 < nblk) nb = src[32 * (v + 1) + lane];  // next block, read ahead
+    uint32_t cm = 0;
+    if (v == 0) {
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        wdp_step<W, true>(xout, col, up_prev, pc, csub, ci, cd, sb[warp][j], lane, j >= lane);
+        cm = __funnelshift_l(uint32_t(col[W - 1] - K - 1), cm, 1);
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        wdp_step<W, false>(xout, col, up_prev, pc, csub, ci, cd, sb[warp][j], lane, true);
+        cm = __funnelshift_l(uint32_t(col[W - 1] - K - 1), cm, 1);
+      }
+    }
+    const uint32_t c = (lane == 31) ? (cm & block_mask32(t_lo, t_hi, v)) : 0u;
+    if (__any_sync(kFull, c != 0))
+      em.put(A, lane, c, x0 + 32 * v - 31, R.wi, pid, wi.base_pos, 31);
+  }
+  em.finish(A, lane);
+}
+
+template <int W>
+cudaError_t launch_wdp(const ScanArgs& a, cudaStream_t st) {
+  if (a.warps < 1 || a.warps > 16) return cudaErrorInvalidValue;
+  const long long grid = (long long)((a.n_regions + a.warps - 1) / a.warps) * a.n_groups;
+  if (grid <= 0) return cudaSuccess;
+  wscan_kernel<W><<<unsigned(grid), a.warps * 32, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
 template <int W, bool kDict, int ALG = 0, int GPW = 1>
 cudaError_t launch_w(const ScanArgs& a, cudaStream_t st) {
   const size_t smem = scan_smem_bytes(W, a.warps, kDict ? a.chunk : 0, GPW);
@@ -814,6 +932,15 @@ cudaError_t prepare_scan_kernels(int max_smem_bytes) {
 
 cudaError_t launch_scan(const ScanArgs& a, cudaStream_t s) {
   const bool d = a.dict != 0;
+  if (a.algo == kAlgoWeighted) {
+    switch (a.W) {
+      case 1: return launch_wdp<1>(a, s);
+      case 2: return launch_wdp<2>(a, s);
+      case 3: return launch_wdp<3>(a, s);
+      case 4: return launch_wdp<4>(a, s);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   if (a.gpw == 2) {  // two lane groups per warp: one-word classes, dictionary mapping
     if (a.W != 1 || !d) return cudaErrorInvalidValue;
     switch (a.algo) {

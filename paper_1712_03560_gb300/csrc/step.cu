@@ -140,6 +140,10 @@ int enqueue_step(oasm_ctx* ctx, StepPlan& pl, const WorkItem* d_items, const Reg
     a.chunk = b.chunk;
     a.algo = b.algo;
     a.gpw = bucket_gpw(ctx, b);
+    a.wrow = b.d_wrow;
+    a.c_sub = int(ctx->costs.sub);
+    a.c_ins = int(ctx->costs.ins);
+    a.c_del = int(ctx->costs.del);
     a.items = d_items;
     a.arena = ctx->arena.p;
     a.cand = ctx->cand.p;
@@ -536,6 +540,8 @@ int step_end(oasm_ctx* ctx) {
     uint64_t lanes = 0;
     for (const auto& g : b.groups)
       for (int l = 0; l < kLaneGroup; l += g.nseg) lanes += g.pat[l] >= 0 ? 1 : 0;
+    // weighted path: every lane of a pattern's warp runs W rows of cells
+    if (b.algo == kAlgoWeighted) lanes = uint64_t(b.groups.size()) * kLaneGroup;
     ctx->st.word_steps += lanes * uint64_t(b.W) * pl.new_bytes;
   }
   release_stages(ctx);

@@ -130,6 +130,61 @@ void choose_piece_filter(const uint8_t* const* pat, const uint32_t* len, const u
   }
 }
 
+// Weighted path: one bucket per row count W = ceil(l_p / 32); each group is
+// one pattern, scanned by one warp whose lane l holds rows W l .. W l + W - 1
+// of a 32 W-row column.  The pattern takes the bottom l_p rows, so its last
+// row is the last row of lane 31; the rows above it match every symbol and
+// stay at distance 0, like the zero row of Sellers' recurrence.
+static int build_weighted(oasm_ctx* ctx) {
+  const uint32_t n = ctx->n_pat;
+  std::vector<uint8_t> wp(size_t(n) * OASM_MAX_PATTERN_LEN, 0);
+  for (uint32_t p = 0; p < n; ++p)
+    std::copy(ctx->pats[p].begin(), ctx->pats[p].end(), wp.begin() + size_t(p) * OASM_MAX_PATTERN_LEN);
+  CK(cudaMalloc(&ctx->d_wpat, wp.size()));
+  CK(cudaMemcpy(ctx->d_wpat, wp.data(), wp.size(), cudaMemcpyHostToDevice));
+  for (int W = 1; W <= kMaxW; ++W) {
+    std::vector<uint32_t> ids;
+    for (uint32_t p = 0; p < n; ++p)
+      if ((ctx->m[p] + 31) / 32 == W) ids.push_back(p);
+    if (ids.empty()) continue;
+    Bucket bk;
+    bk.W = W;
+    bk.algo = kAlgoWeighted;
+    std::vector<uint16_t> rows;
+    for (uint32_t p : ids) {
+      LaneGroup G;
+      memset(&G, 0, sizeof G);
+      for (int l = 0; l < kLaneGroup; ++l) G.pat[l] = -1;
+      for (int q = 0; q < kMaxSlots; ++q)
+        for (int l = 0; l < kLaneGroup; ++l) G.lastbit[q][l] = 31;
+      for (int q = 0; q + 1 < kMaxSlots; ++q)
+        for (int l = 0; l < kLaneGroup; ++l) G.xpat[q][l] = -1;
+      const int m = ctx->m[p];
+      G.pat[0] = int32_t(p);
+      G.m[0] = uint8_t(m);
+      G.K[0] = ctx->K[p];
+      G.nseg = 1;
+      G.W = W;
+      G.nslot = 1;
+      G.ov = m + ctx->K[p] - 1;
+      bk.kmax = std::max<int>(bk.kmax, ctx->K[p]);
+      bk.ov_max = std::max(bk.ov_max, G.ov);
+      bk.groups.push_back(G);
+      const int nrow = 32 * W, top = nrow - m;
+      for (int r = 0; r < nrow; ++r)
+        rows.push_back(r < top ? kWildRow : uint16_t(ctx->pats[p][r - top]));
+    }
+    bk.gpw = 1;
+    CK(cudaMalloc(&bk.d_groups, bk.groups.size() * sizeof(LaneGroup)));
+    CK(cudaMemcpy(bk.d_groups, bk.groups.data(), bk.groups.size() * sizeof(LaneGroup),
+                  cudaMemcpyHostToDevice));
+    CK(cudaMalloc(&bk.d_wrow, rows.size() * sizeof(uint16_t)));
+    CK(cudaMemcpy(bk.d_wrow, rows.data(), rows.size() * sizeof(uint16_t), cudaMemcpyHostToDevice));
+    ctx->buckets.push_back(bk);
+  }
+  return OASM_OK;
+}
+
 int build_tables(oasm_ctx* ctx) {
   const uint32_t n = ctx->n_pat;
   // reversed, bottom-aligned Peq (verification pass): [p][256][4]
@@ -259,6 +314,7 @@ int build_tables(oasm_ctx* ctx) {
     ctx->buckets.push_back(bk);
     return OASM_OK;
   };
+  if (ctx->weighted) return build_weighted(ctx);
   // patterns for the piece filter instead of the forward scan
   std::vector<char> pref(n, 0);
   if (ctx->cfg.prefilter_piece) {
@@ -304,6 +360,11 @@ StepParams make_params(oasm_ctx* ctx, const WorkItem* d_items, uint32_t n_items,
   P.K = ctx->d_K;
   P.mem_off = ctx->d_mem_off;
   P.peq_rev = ctx->d_peq_rev;
+  P.wpat = ctx->d_wpat;
+  P.weighted = ctx->weighted ? 1 : 0;
+  P.c_sub = int(ctx->costs.sub);
+  P.c_ins = int(ctx->costs.ins);
+  P.c_del = int(ctx->costs.del);
   P.n_pat = ctx->n_pat;
   P.mem_stride = ctx->mem_stride;
   P.rules = ctx->rules;
@@ -338,7 +399,7 @@ StepParams make_params(oasm_ctx* ctx, const WorkItem* d_items, uint32_t n_items,
 // Lane groups per warp for a bucket: the configured value where the kernel
 // has that form (one-word class, dictionary mapping), else the tuned one.
 int bucket_gpw(const oasm_ctx* ctx, const Bucket& b) {
-  if (b.W != 1 || b.max_nseg != 1) return 1;
+  if (b.W != 1 || b.max_nseg != 1 || b.algo == kAlgoWeighted) return 1;
   const uint32_t c = ctx->cfg.groups_per_warp;
   return c == 1 || c == 2 ? int(c) : b.gpw;
 }

@@ -13,9 +13,10 @@ def gpu_rows(res: np.ndarray):
              int(r["len"])) for r in res]
 
 
-def oracle_rows(patterns, ks, text, rules=None, mode="oasm", threads=None):
+def oracle_rows(patterns, ks, text, rules=None, mode="oasm", threads=None, costs=None):
     """Canonical (pattern_id, decided_at, k, start, len) rows from the oracle."""
-    res = oracle.oasm_dictionary(patterns, ks, text, rules, threads=threads, mode=mode)
+    res = oracle.oasm_dictionary(patterns, ks, text, rules, threads=threads, mode=mode,
+                                 costs=costs)
     if mode == "hits":  # decided_at is the end for raw hits; order like the library
         pass
     rows = [(int(r["pattern_id"]), int(r["decided_at"]), int(r["k"]), int(r["start"]),
@@ -27,10 +28,11 @@ def canon(rows):
     return sorted(rows, key=lambda x: (x[0], x[1], x[2], x[3], x[4]))
 
 
-def run_gpu(patterns, ks, text, rules=None, splits=None, device_feed=False, cfg=None):
+def run_gpu(patterns, ks, text, rules=None, splits=None, device_feed=False, cfg=None,
+            costs=None):
     """Feeds `text` as one stream (in pieces when `splits` is given) and ends it."""
     r = dict(rules or {})
-    ctx = B.oasm_create(patterns, ks, r or None, cfg)
+    ctx = B.oasm_create(patterns, ks, r or None, cfg, costs=costs)
     try:
         sid = B.oasm_open_stream(ctx)
         text = np.asarray(text, dtype=np.uint8)

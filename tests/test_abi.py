@@ -39,6 +39,7 @@ def test_struct_sizes_match_header():
     assert ctypes.sizeof(B.oasm_rules) == 20
     # oasm_config: 4+4+8+4+4+4+4+8+4+4+4+4
     assert ctypes.sizeof(B.oasm_config) == 56
+    assert ctypes.sizeof(B.oasm_costs) == 12
 
 
 @pytest.mark.parametrize("lens,ks", [([0], [0]), ([129], [1]), ([8], [8]), ([20], [16]), ([], [])])
@@ -69,7 +70,7 @@ def test_strerror_and_null_safety():
 
 
 @pytest.mark.parametrize("field,value", [("groups_per_warp", 3), ("prefilter_piece", 2),
-                                         ("prefilter_piece", 129)])
+                                         ("prefilter_piece", 129), ("tile_warps", 17)])
 def test_create_rejects_bad_config(field, value):
     """Config fields out of range are rejected on the host, before any device work."""
     lib = B.load()
@@ -83,6 +84,22 @@ def test_create_rejects_bad_config(field, value):
     assert rc == B.OASM_EINVAL
     assert not ctx.value
     assert b"config" in lib.oasm_last_error(None)
+
+
+@pytest.mark.parametrize("costs", [(0, 1, 1), (1, 0, 1), (1, 1, 0), (256, 1, 1), (1, 1, 300)])
+def test_create_weighted_rejects_bad_costs(costs):
+    """Edit costs outside 1..255 are rejected on the host, before any device work."""
+    lib = B.load()
+    pats = [b"ACGTACGTACGT"]
+    ptrs = (ctypes.c_void_p * 1)(ctypes.cast(ctypes.c_char_p(pats[0]), ctypes.c_void_p))
+    L = (ctypes.c_uint32 * 1)(12)
+    K = (ctypes.c_uint32 * 1)(1)
+    w = B.oasm_costs(*costs)
+    ctx = ctypes.c_void_p()
+    rc = lib.oasm_create_weighted(ptrs, L, K, 1, None, ctypes.byref(w), None, ctypes.byref(ctx))
+    assert rc == B.OASM_EINVAL
+    assert not ctx.value
+    assert b"cost" in lib.oasm_last_error(None)
 
 
 def test_config_maker_rejects_unknown_fields():
