@@ -45,10 +45,10 @@ OPS_PER_DP_CELL = 7
 WEIGHTED_DEFAULT_COSTS = (1, 2, 2)
 # DRAM bytes per scan launch and text byte, from an ncu capture of one step's
 # four scan launches on the 64 MiB DNA dictionary with the current kernels
-# (69.1, 75.3, 73.2 and 70.2 MB, mean 71.95 MB per launch for 64 MiB);
+# (69.0, 75.4, 75.9 and 70.1 MB, mean 72.6 MB per launch for 64 MiB);
 # traffic scales with the text
-SCAN_DRAM_BYTES_PER_TEXT_BYTE = {"dictionary_dna": 71.95e6 / (64 << 20),
-                                 "dictionary_dna_64m": 71.95e6 / (64 << 20)}
+SCAN_DRAM_BYTES_PER_TEXT_BYTE = {"dictionary_dna": 72.6e6 / (64 << 20),
+                                 "dictionary_dna_64m": 72.6e6 / (64 << 20)}
 SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
 
@@ -79,6 +79,9 @@ def parse():
                          "long use the exact piece filter instead of the scan (0 = off, "
                          "1 = automatic per pattern; default 1 for the served signatures, "
                          "0 elsewhere)")
+    ap.add_argument("--text-mib", type=int, default=None,
+                    help="text size of the dictionary_dna workloads in MiB (planted copies "
+                         "scale with it); for small profiling captures")
     ap.add_argument("--costs", default=None,
                     help="integer edit costs SUB,INS,DEL (each 1..255): the weighted path "
                          "(oasm_create_weighted); default 1,2,2 for dictionary_dna_weighted, "
@@ -97,8 +100,13 @@ def parse():
     return a
 
 
-def make_workload(name: str, seed_offset: int):
+def make_workload(name: str, seed_offset: int, text_mib: int | None = None):
     from paper_1712_03560_gb300 import workloads as W
+    if text_mib is not None and name.startswith("dictionary_dna"):
+        n = int(text_mib) << 20
+        return W.dictionary_dna(seed=2 + 1000 * seed_offset, n=n, copies=max(1, 1000 * n >> 28)), \
+            (f"{name} at {text_mib} MiB: 1024 DNA patterns m~U[8,32] K=floor(m/10), "
+             f"{text_mib} MiB iid DNA text, {max(1, 1000 * n >> 28)} planted copies/pattern")
     if name == "dictionary_dna":
         return W.dictionary_dna(seed=2 + 1000 * seed_offset), \
             "dictionary_dna: 1024 DNA patterns m~U[8,32] K=floor(m/10), 256 MiB iid DNA text, 1000 planted copies/pattern"
@@ -219,7 +227,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    wl, desc = make_workload(args.workload, 0)
+    wl, desc = make_workload(args.workload, 0, args.text_mib)
     import oracle
     cores = os.cpu_count() or 1
     text = wl.texts[0] if len(wl.texts) == 1 else np.concatenate(wl.texts[:50])
@@ -410,7 +418,7 @@ def main():
 
     from paper_1712_03560_gb300 import binding as B
 
-    wl, desc = make_workload(args.workload, rank)
+    wl, desc = make_workload(args.workload, rank, args.text_mib)
     ctx = B.oasm_create(wl.patterns, wl.ks, None,
                         {"device": dev, "timing": 1, "max_streams": max(64, len(wl.texts)),
                          "prefilter_piece": args.prefilter}, costs=args.costs)

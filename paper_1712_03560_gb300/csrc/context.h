@@ -208,10 +208,11 @@ struct Bucket {
   std::vector<LaneGroup> groups;
   LaneGroup* d_groups = nullptr;
   uint32_t* d_peq = nullptr;
-  // weighted path (algo == kAlgoWeighted): one pattern per group; per group
-  // 32 W rows of 16 bits, lane-major (lane l holds rows W l .. W l + W - 1):
-  // the pattern symbol, or kWildRow for the rows above the pattern
-  uint16_t* d_wrow = nullptr;
+  // weighted path (algo == kAlgoWeighted): per group (one warp's column of
+  // 32 x kWRows rows holding several patterns) one 32-bit row word per row,
+  // lane-major (lane l holds rows kWRows l .. kWRows l + kWRows - 1); see
+  // kWildRow / kWFirstLane for the fields
+  uint32_t* d_wrow = nullptr;
 };
 
 template <class T>

@@ -21,8 +21,7 @@ struct ScanArgs {
   int32_t algo;              // 0: Myers/Hyyro bit-vectors; 1 + K: automaton for K <= 2 (W = 1)
   int32_t gpw;               // lane groups per warp: 1, or 2 (dictionary mapping, W = 1)
   int32_t c_sub, c_ins, c_del;  // edit costs (algo == kAlgoWeighted)
-  const uint16_t* wrow;      // weighted path: [n_groups][32 W] row symbols (kWildRow above
-                             // the pattern), lane-major
+  const uint32_t* wrow;      // weighted path: [n_groups][32 kWRows] row words, lane-major
   const WorkItem* items;
   const uint8_t* arena;
   Candidate* cand;
@@ -30,10 +29,17 @@ struct ScanArgs {
   StepCounters* ctr;
 };
 
-// Weighted dynamic program over a pattern's rows (oasm_create_weighted): a
-// bucket of this algo holds one pattern per group, W rows per lane.
+// Weighted dynamic program over patterns' rows (oasm_create_weighted).  A
+// group is one warp's column of 32 lanes x kWRows rows; patterns sit in runs
+// of whole lanes, each ending at the last row of its last lane (rows above a
+// pattern in its first lane are wild).  A row word holds the pattern symbol
+// (bits 0-7), kWildRow, the row's index within its pattern, 1-based
+// (bits 16-23; 0 for a wild row), and kWFirstLane on every row of a
+// pattern's first lane (the row above that lane is Sellers' zero row).
 constexpr int kAlgoWeighted = 8;
-constexpr uint16_t kWildRow = 0x100;  // a row above the pattern: matches every symbol
+constexpr int kWRows = 4;
+constexpr uint32_t kWildRow = 0x100u;
+constexpr uint32_t kWFirstLane = 1u << 24;
 
 // Shared memory of one scan block: the Peq tables of its gpw lane groups (256
 // rows of W x 32 words each), two text buffers per warp (dictionary mapping)

@@ -775,30 +775,33 @@ __global__ void __launch_bounds__(512) scan_kernel(const ScanArgs A) {
 // Integer edit costs (oasm_create_weighted): Eq. 1 with costs c_sub, c_ins,
 // c_del and Sellers' zero row, filled as a wave-front over anti-diagonals
 // (the paper's own order of evaluation, Sec. 3, Fig. 1(b)), one warp per
-// (pattern, region).  Lane l holds rows W l .. W l + W - 1 of a 32 W-row
-// column whose bottom l_p rows are the pattern's (the rows above match
-// every symbol and stay 0).  At step s lane l fills column e = x0 + s - l:
-// the row above its first row at columns e and e - 1 is lane l - 1's last
-// row at steps s - 1 and s - 2, and the symbol t[e] is the one lane l - 1
-// used at step s - 1, so both travel down in one shuffle per step, packed as
-// (value << 8) | symbol.  Lane 31's last row is D[e]: a candidate end when
-// it is <= K (the same test as the bit-parallel scan's).
+// (group, region).  A group is a column of 32 lanes x R rows holding several
+// patterns, each in a run of whole lanes that ends at the last row of its
+// last lane.  At step s lane l fills column e = x0 + s - l: the row above its
+// first row at columns e and e - 1 is lane l - 1's last row at steps s - 1
+// and s - 2, and the symbol t[e] is the one lane l - 1 used at step s - 1, so
+// both travel down in one shuffle per step, packed as (value << 8) | symbol.
+// A pattern's first lane drops the value (the row above it is Sellers' zero
+// row).  The last row of a pattern's last lane is D[e]: a candidate end when
+// it is <= K (the bit-parallel scan's test).
 //
 // Per cell: three adds, two minimums and a compare-select for the
 // substitution cost; per lane and step one shuffle, one shared-memory load
-// (the symbol for lane 0) and the candidate bit.
-template <int W, bool kPro>
-__device__ __forceinline__ void wdp_step(uint32_t& xout, int (&col)[W], int& up_prev,
-                                         const uint32_t (&pc)[W], const int (&csub)[W], int ci,
-                                         int cd, uint32_t sym0, int lane, bool active) {
+// (the symbol for lane 0), the zero-row mask and the candidate bit.
+template <int R, bool kPro>
+__device__ __forceinline__ void wdp_step(uint32_t& xout, int (&col)[R], int& up_prev,
+                                         const uint32_t (&pc)[R], const int (&csub)[R], int ci,
+                                         int cd, uint32_t keep, uint32_t sym0, int lane,
+                                         bool active) {
   uint32_t xin = __shfl_up_sync(kFull, xout, 1);
-  if (lane == 0) xin = sym0;  // the row above lane 0 is Sellers' zero row
+  if (lane == 0) xin = sym0;
+  xin &= keep;  // a pattern's first lane: the row above is the zero row
   const uint32_t sym = xin & 0xffu;
   const int up_cur = int(xin >> 8);
   int diag = up_prev, up = up_cur;
-  int nv[W];
+  int nv[R];
 #pragma unroll
-  for (int q = 0; q < W; ++q) {
+  for (int q = 0; q < R; ++q) {
     const int left = col[q];
     const int sub = (pc[q] == sym) ? 0 : csub[q];
     const int v = min(min(diag + sub, left + ci), up + cd);
@@ -808,13 +811,13 @@ __device__ __forceinline__ void wdp_step(uint32_t& xout, int (&col)[W], int& up_
   }
   if (!kPro || active) {
 #pragma unroll
-    for (int q = 0; q < W; ++q) col[q] = nv[q];
+    for (int q = 0; q < R; ++q) col[q] = nv[q];
     up_prev = up_cur;
-    xout = (uint32_t(nv[W - 1]) << 8) | sym;
+    xout = (uint32_t(nv[R - 1]) << 8) | sym;
   }
 }
 
-template <int W>
+template <int R>
 __global__ void __launch_bounds__(512) wscan_kernel(const ScanArgs A) {
   __shared__ uint8_t sb[16][32];  // per warp: the symbols of the current 32-step block
   const int ng = A.n_groups;
@@ -823,34 +826,35 @@ __global__ void __launch_bounds__(512) wscan_kernel(const ScanArgs A) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int r = rb * A.warps + warp;
   if (r >= A.n_regions || warp >= 16) return;  // the whole warp leaves together
-  const Region R = A.regions[r];
-  const WorkItem wi = A.items[R.wi];
+  const Region Rg = A.regions[r];
+  const WorkItem wi = A.items[Rg.wi];
   const LaneGroup& G = A.groups[g];
-  const int pid = G.pat[0], m = G.m[0], K = G.K[0];
+  const int pid = G.pat[lane], K = G.K[lane];  // pid >= 0: the last lane of a pattern
   const int ci = A.c_ins, cd = A.c_del;
-  const int top = 32 * W - m;  // rows above the pattern
-  uint32_t pc[W];
-  int csub[W], col[W];
+  const uint32_t* wr = A.wrow + size_t(g) * 32 * R;
+  uint32_t pc[R];
+  int csub[R], col[R];
+  bool first = false;
 #pragma unroll
-  for (int q = 0; q < W; ++q) {
-    const int row = W * lane + q;
-    const uint32_t v = A.wrow[size_t(g) * 32 * W + row];
-    const bool wild = (v & kWildRow) != 0;
-    pc[q] = v;
+  for (int q = 0; q < R; ++q) {
+    const uint32_t w = wr[R * lane + q];
+    const bool wild = (w & kWildRow) != 0;
+    first = (w & kWFirstLane) != 0;
+    pc[q] = wild ? kWildRow : (w & 0xffu);  // a wild row never equals a symbol
     csub[q] = wild ? 0 : A.c_sub;
-    col[q] = wild ? 0 : (row - top + 1) * cd;  // column x0 - 1: row r costs r deletions
+    col[q] = int((w >> 16) & 0xffu) * cd;  // column x0 - 1: row i of a pattern costs i deletions
   }
-  const int above = W * lane - 1;
-  int up_prev = (lane == 0 || above < top) ? 0 : (above - top + 1) * cd;
-  uint32_t xout = uint32_t(col[W - 1]) << 8;
-  const int64_t a = R.a, b = R.b;
+  const uint32_t keep = first ? 0xffu : 0xffffffffu;
+  int up_prev = (first || lane == 0) ? 0 : int((wr[R * lane - 1] >> 16) & 0xffu) * cd;
+  uint32_t xout = uint32_t(col[R - 1]) << 8;
+  const int64_t a = Rg.a, b = Rg.b;
   if (b <= a) return;
-  const int64_t x0 = a - G.ov;  // warm-up: l_p + K - 1 symbols before the region
+  const int64_t x0 = a - G.ov;  // warm-up: the group's largest l_p + K - 1
   int64_t rep_lo = max(a, wi.e_prev - 2 * int64_t(K));
   rep_lo = max(rep_lo, int64_t(0));
-  // step s fills column x0 + s - lane; lane 31 reports ends in [rep_lo, b)
-  const int t_lo = int(rep_lo - x0 + 31), t_hi = int(b - x0 + 31);
-  const int nblk = (t_hi + 31) / 32;
+  // lane l reports the ends in [rep_lo, b) at steps rep_lo - x0 + l ..
+  const int t_lo = int(rep_lo - x0 + lane), t_hi = pid >= 0 ? int(b - x0 + lane) : t_lo;
+  const int nblk = int((b - x0 + 31 + 31) / 32);
   const uint8_t* src = A.arena + (int64_t(wi.arena_base) + (x0 - wi.base_pos));
   Emitter em;
   uint8_t nb = src[lane];
@@ -863,29 +867,30 @@ __global__ void __launch_bounds__(512) wscan_kernel(const ScanArgs A) {
     if (v == 0) {
 #pragma unroll
       for (int j = 0; j < 32; ++j) {
-        wdp_step<W, true>(xout, col, up_prev, pc, csub, ci, cd, sb[warp][j], lane, j >= lane);
-        cm = __funnelshift_l(uint32_t(col[W - 1] - K - 1), cm, 1);
+        wdp_step<R, true>(xout, col, up_prev, pc, csub, ci, cd, keep, sb[warp][j], lane,
+                          j >= lane);
+        cm = __funnelshift_l(uint32_t(col[R - 1] - K - 1), cm, 1);
       }
     } else {
 #pragma unroll
       for (int j = 0; j < 32; ++j) {
-        wdp_step<W, false>(xout, col, up_prev, pc, csub, ci, cd, sb[warp][j], lane, true);
-        cm = __funnelshift_l(uint32_t(col[W - 1] - K - 1), cm, 1);
+        wdp_step<R, false>(xout, col, up_prev, pc, csub, ci, cd, keep, sb[warp][j], lane, true);
+        cm = __funnelshift_l(uint32_t(col[R - 1] - K - 1), cm, 1);
       }
     }
-    const uint32_t c = (lane == 31) ? (cm & block_mask32(t_lo, t_hi, v)) : 0u;
+    const uint32_t c = cm & block_mask32(t_lo, t_hi, v);
     if (__any_sync(kFull, c != 0))
-      em.put(A, lane, c, x0 + 32 * v - 31, R.wi, pid, wi.base_pos, 31);
+      em.put(A, lane, c, x0 + 32 * v - lane, Rg.wi, pid, wi.base_pos, 31);
   }
   em.finish(A, lane);
 }
 
-template <int W>
+template <int R>
 cudaError_t launch_wdp(const ScanArgs& a, cudaStream_t st) {
   if (a.warps < 1 || a.warps > 16) return cudaErrorInvalidValue;
   const long long grid = (long long)((a.n_regions + a.warps - 1) / a.warps) * a.n_groups;
   if (grid <= 0) return cudaSuccess;
-  wscan_kernel<W><<<unsigned(grid), a.warps * 32, 0, st>>>(a);
+  wscan_kernel<R><<<unsigned(grid), a.warps * 32, 0, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -932,15 +937,7 @@ cudaError_t prepare_scan_kernels(int max_smem_bytes) {
 
 cudaError_t launch_scan(const ScanArgs& a, cudaStream_t s) {
   const bool d = a.dict != 0;
-  if (a.algo == kAlgoWeighted) {
-    switch (a.W) {
-      case 1: return launch_wdp<1>(a, s);
-      case 2: return launch_wdp<2>(a, s);
-      case 3: return launch_wdp<3>(a, s);
-      case 4: return launch_wdp<4>(a, s);
-      default: return cudaErrorInvalidValue;
-    }
-  }
+  if (a.algo == kAlgoWeighted) return a.W == kWRows ? launch_wdp<kWRows>(a, s) : cudaErrorInvalidValue;
   if (a.gpw == 2) {  // two lane groups per warp: one-word classes, dictionary mapping
     if (a.W != 1 || !d) return cudaErrorInvalidValue;
     switch (a.algo) {

@@ -130,11 +130,11 @@ void choose_piece_filter(const uint8_t* const* pat, const uint32_t* len, const u
   }
 }
 
-// Weighted path: one bucket per row count W = ceil(l_p / 32); each group is
-// one pattern, scanned by one warp whose lane l holds rows W l .. W l + W - 1
-// of a 32 W-row column.  The pattern takes the bottom l_p rows, so its last
-// row is the last row of lane 31; the rows above it match every symbol and
-// stay at distance 0, like the zero row of Sellers' recurrence.
+// Weighted path: one bucket; each group is one warp's column of 32 lanes x
+// kWRows rows.  A pattern takes ceil(l_p / kWRows) whole lanes and ends at
+// the last row of its last lane; the rows above it in its first lane match
+// every symbol.  Patterns are packed into groups first-fit by decreasing
+// lane count, so short patterns share a warp.
 static int build_weighted(oasm_ctx* ctx) {
   const uint32_t n = ctx->n_pat;
   std::vector<uint8_t> wp(size_t(n) * OASM_MAX_PATTERN_LEN, 0);
@@ -142,46 +142,70 @@ static int build_weighted(oasm_ctx* ctx) {
     std::copy(ctx->pats[p].begin(), ctx->pats[p].end(), wp.begin() + size_t(p) * OASM_MAX_PATTERN_LEN);
   CK(cudaMalloc(&ctx->d_wpat, wp.size()));
   CK(cudaMemcpy(ctx->d_wpat, wp.data(), wp.size(), cudaMemcpyHostToDevice));
-  for (int W = 1; W <= kMaxW; ++W) {
-    std::vector<uint32_t> ids;
-    for (uint32_t p = 0; p < n; ++p)
-      if ((ctx->m[p] + 31) / 32 == W) ids.push_back(p);
-    if (ids.empty()) continue;
-    Bucket bk;
-    bk.W = W;
-    bk.algo = kAlgoWeighted;
-    std::vector<uint16_t> rows;
-    for (uint32_t p : ids) {
-      LaneGroup G;
-      memset(&G, 0, sizeof G);
-      for (int l = 0; l < kLaneGroup; ++l) G.pat[l] = -1;
-      for (int q = 0; q < kMaxSlots; ++q)
-        for (int l = 0; l < kLaneGroup; ++l) G.lastbit[q][l] = 31;
-      for (int q = 0; q + 1 < kMaxSlots; ++q)
-        for (int l = 0; l < kLaneGroup; ++l) G.xpat[q][l] = -1;
-      const int m = ctx->m[p];
-      G.pat[0] = int32_t(p);
-      G.m[0] = uint8_t(m);
-      G.K[0] = ctx->K[p];
-      G.nseg = 1;
-      G.W = W;
-      G.nslot = 1;
-      G.ov = m + ctx->K[p] - 1;
-      bk.kmax = std::max<int>(bk.kmax, ctx->K[p]);
-      bk.ov_max = std::max(bk.ov_max, G.ov);
-      bk.groups.push_back(G);
-      const int nrow = 32 * W, top = nrow - m;
-      for (int r = 0; r < nrow; ++r)
-        rows.push_back(r < top ? kWildRow : uint16_t(ctx->pats[p][r - top]));
+  std::vector<uint32_t> ids(n);
+  for (uint32_t p = 0; p < n; ++p) ids[p] = p;
+  std::stable_sort(ids.begin(), ids.end(),
+                   [&](uint32_t a0, uint32_t b0) { return ctx->m[a0] > ctx->m[b0]; });
+  std::vector<std::vector<uint32_t>> warps;  // patterns of each group, in lane order
+  std::vector<int> used;
+  for (uint32_t p : ids) {
+    const int L = (ctx->m[p] + kWRows - 1) / kWRows;
+    size_t g = 0;
+    while (g < warps.size() && used[g] + L > kLaneGroup) ++g;
+    if (g == warps.size()) {
+      warps.emplace_back();
+      used.push_back(0);
     }
-    bk.gpw = 1;
-    CK(cudaMalloc(&bk.d_groups, bk.groups.size() * sizeof(LaneGroup)));
-    CK(cudaMemcpy(bk.d_groups, bk.groups.data(), bk.groups.size() * sizeof(LaneGroup),
-                  cudaMemcpyHostToDevice));
-    CK(cudaMalloc(&bk.d_wrow, rows.size() * sizeof(uint16_t)));
-    CK(cudaMemcpy(bk.d_wrow, rows.data(), rows.size() * sizeof(uint16_t), cudaMemcpyHostToDevice));
-    ctx->buckets.push_back(bk);
+    warps[g].push_back(p);
+    used[g] += L;
   }
+  Bucket bk;
+  bk.W = kWRows;
+  bk.algo = kAlgoWeighted;
+  bk.gpw = 1;
+  std::vector<uint32_t> rows;
+  for (const auto& wv : warps) {
+    LaneGroup G;
+    memset(&G, 0, sizeof G);
+    for (int l = 0; l < kLaneGroup; ++l) G.pat[l] = -1;
+    for (int q = 0; q < kMaxSlots; ++q)
+      for (int l = 0; l < kLaneGroup; ++l) G.lastbit[q][l] = 31;
+    for (int q = 0; q + 1 < kMaxSlots; ++q)
+      for (int l = 0; l < kLaneGroup; ++l) G.xpat[q][l] = -1;
+    G.nseg = 1;
+    G.W = kWRows;
+    G.nslot = 1;
+    G.ov = 1;
+    std::vector<uint32_t> wr(size_t(kLaneGroup) * kWRows, kWildRow | kWFirstLane);
+    int lane = 0;
+    for (uint32_t p : wv) {
+      const int m = ctx->m[p], L = (m + kWRows - 1) / kWRows;
+      const int top = L * kWRows - m;  // wild rows above the pattern in its first lane
+      for (int r = 0; r < L * kWRows; ++r) {
+        const int l = lane + r / kWRows;
+        uint32_t w = (r < top) ? kWildRow
+                               : uint32_t(ctx->pats[p][r - top]) | (uint32_t(r - top + 1) << 16);
+        if (l == lane) w |= kWFirstLane;
+        wr[size_t(l) * kWRows + r % kWRows] = w;
+      }
+      const int last = lane + L - 1;
+      G.pat[last] = int32_t(p);
+      G.m[last] = uint8_t(m);
+      G.K[last] = ctx->K[p];
+      G.ov = std::max(G.ov, m + ctx->K[p] - 1);
+      bk.kmax = std::max<int>(bk.kmax, ctx->K[p]);
+      lane += L;
+    }
+    bk.ov_max = std::max(bk.ov_max, G.ov);
+    bk.groups.push_back(G);
+    rows.insert(rows.end(), wr.begin(), wr.end());
+  }
+  CK(cudaMalloc(&bk.d_groups, bk.groups.size() * sizeof(LaneGroup)));
+  CK(cudaMemcpy(bk.d_groups, bk.groups.data(), bk.groups.size() * sizeof(LaneGroup),
+                cudaMemcpyHostToDevice));
+  CK(cudaMalloc(&bk.d_wrow, rows.size() * sizeof(uint32_t)));
+  CK(cudaMemcpy(bk.d_wrow, rows.data(), rows.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
+  ctx->buckets.push_back(bk);
   return OASM_OK;
 }
 
