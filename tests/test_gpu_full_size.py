@@ -27,16 +27,17 @@ def rows(res, keep=None):
     return sorted(out)
 
 
-def oracle_sample(wl_patterns, wl_ks, idx, text):
+def oracle_sample(wl_patterns, wl_ks, idx, text, costs=None):
     res = oracle.oasm_dictionary([wl_patterns[i] for i in idx], [int(wl_ks[i]) for i in idx],
-                                 text, threads=min(len(idx), os.cpu_count() or 1))
+                                 text, threads=min(len(idx), os.cpu_count() or 1), costs=costs)
     return sorted((int(idx[int(r["pattern_id"])]), int(r["decided_at"]), int(r["k"]),
                    int(r["start"]), int(r["len"])) for r in res)
 
 
-def tuned_context(wl):
+def tuned_context(wl, costs=None):
     import torch
-    ctx = B.oasm_create(wl.patterns, wl.ks, None, {"max_streams": max(64, len(wl.texts))})
+    ctx = B.oasm_create(wl.patterns, wl.ks, None, {"max_streams": max(64, len(wl.texts))},
+                        costs=costs)
     big = max(wl.texts, key=lambda t: t.size)
     sample = torch.from_numpy(big[: min(big.size, 32 << 20)].copy()).cuda()
     B.oasm_autotune(ctx, sample)
@@ -62,6 +63,23 @@ def test_dictionary_dna_full_size():
         B.oasm_destroy(ctx)
     idx = [0, 204, 409, 614, 819, 1023]
     want = oracle_sample(wl.patterns, wl.ks, idx, wl.texts[0])
+    assert len(want) > 0
+    assert rows(res, set(idx)) == want
+
+
+def test_dictionary_dna_weighted_full_size():
+    """The weighted path (edit costs 1, 2, 2) on the 1,024-pattern, 256 MiB
+    DNA dictionary; 6 patterns checked over the whole text."""
+    import torch
+    wl = W.dictionary_dna()
+    costs = (1, 2, 2)
+    ctx = tuned_context(wl, costs)
+    try:
+        res = search_one(ctx, torch.from_numpy(wl.texts[0]).cuda())
+    finally:
+        B.oasm_destroy(ctx)
+    idx = [3, 200, 411, 618, 822, 1020]
+    want = oracle_sample(wl.patterns, wl.ks, idx, wl.texts[0], costs)
     assert len(want) > 0
     assert rows(res, set(idx)) == want
 
