@@ -32,15 +32,17 @@ import numpy as np
 class Server:
     def __init__(self, patterns, ks, max_streams: int = 4096, mem_budget: int = 0, rules=None,
                  device: int = 0, max_batch_bytes: int = 8 << 20, graphs: bool = True,
-                 timing: bool = False, prefilter_piece: int = 0, lib=None):
+                 timing: bool = False, prefilter_piece: int = 0, lib=None, costs=None):
         if lib is None:
             from . import binding as lib
         self.B = lib
+        # costs: integer edit costs (sub, ins, del) select the weighted path
+        kw = {} if costs is None else {"costs": tuple(costs)}
         self.ctx = lib.oasm_create(patterns, ks, rules,
                                    {"device": device, "max_streams": max_streams,
                                     "mem_budget": mem_budget, "graphs": 1 if graphs else 0,
                                     "timing": 1 if timing else 0,
-                                    "prefilter_piece": int(prefilter_piece)})
+                                    "prefilter_piece": int(prefilter_piece)}, **kw)
         self.max_batch_bytes = int(max_batch_bytes)
 
     def stats(self) -> dict:

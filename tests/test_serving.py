@@ -154,3 +154,27 @@ def test_served_streams_match_oracle_alone_and_in_the_mix(slots, budget, realtim
             assert canon([(int(r["pattern_id"]), int(r["decided_at"]), int(r["k"]),
                            int(r["start"]), int(r["len"])) for r in alone]) == want
     assert some > 0
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("engine", ["python", "native"])
+def test_served_streams_under_edit_costs_match_oracle(engine):
+    """The serving loop on the weighted path: every stream's kept hits equal
+    the oracle's under the same edit costs."""
+    from parity_util import canon, oracle_rows
+    costs = (2, 1, 1)
+    tr = W.served(seed=8, n_streams=32, n_sig=24, mlo=8, mhi=64, gbps=0.2, duration=0.04,
+                  life=0.5, planted_frac=0.05)
+    with serve.Server(tr.patterns, tr.ks, max_streams=16, max_batch_bytes=20000,
+                      costs=costs) as srv:
+        res = srv.replay(tr, realtime=False, collect=True, engine=engine)
+    assert res["packets"] == tr.n_packets and res["steps"] >= 2
+    some = 0
+    for ext, t in enumerate(tr.stream_texts()):
+        got = res["hits"].get(ext)
+        rows = [] if got is None else [(int(r["pattern_id"]), int(r["decided_at"]), int(r["k"]),
+                                        int(r["start"]), int(r["len"])) for r in got]
+        want = oracle_rows(tr.patterns, tr.ks, t, costs=costs)
+        assert canon(rows) == want, ext
+        some += len(want)
+    assert some > 0
