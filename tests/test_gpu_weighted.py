@@ -144,3 +144,14 @@ def test_weighted_state_does_not_restore_into_a_unit_cost_context():
     finally:
         B.oasm_destroy(a)
         B.oasm_destroy(b)
+
+
+@pytest.mark.parametrize("costs", [(255, 255, 255), (1, 255, 255), (255, 1, 1), (16, 16, 1)])
+def test_weighted_extreme_costs(costs):
+    """Costs at the ends of their range: edits dearer than K leave only exact
+    matches; dear indels leave substitutions only; dear substitutions leave
+    indels only.  K up to 15, lengths up to 128."""
+    rng = np.random.default_rng(38 + costs[0] + costs[2])
+    pats, ks, text = random_case(rng, 4, 20, 16, 128, 20000, kmax=15)
+    got, _ = run_gpu(pats, ks, text, costs=costs)
+    assert canon(got) == oracle_rows(pats, ks, text, costs=costs)
