@@ -79,6 +79,9 @@ def parse():
                          "long use the exact piece filter instead of the scan (0 = off, "
                          "1 = automatic per pattern; default 1 for the served signatures, "
                          "0 elsewhere)")
+    ap.add_argument("--graphs", type=int, default=1,
+                    help="cfg.graphs: launch each step as a captured CUDA graph, updated in "
+                         "place while its shape repeats (1, default) or directly (0)")
     ap.add_argument("--text-mib", type=int, default=None,
                     help="text size of the dictionary_dna workloads in MiB (planted copies "
                          "scale with it); for small profiling captures")
@@ -421,7 +424,8 @@ def main():
     wl, desc = make_workload(args.workload, rank, args.text_mib)
     ctx = B.oasm_create(wl.patterns, wl.ks, None,
                         {"device": dev, "timing": 1, "max_streams": max(64, len(wl.texts)),
-                         "prefilter_piece": args.prefilter}, costs=args.costs)
+                         "prefilter_piece": args.prefilter, "graphs": args.graphs},
+                        costs=args.costs)
     stream = torch.cuda.ExternalStream(B.oasm_cuda_stream(ctx), device=dev)
     dtexts = [torch.from_numpy(t).to(f"cuda:{dev}") for t in wl.texts]
     torch.cuda.synchronize()
@@ -476,6 +480,7 @@ def main():
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
+    builds_warmup = int(B.oasm_get_stats(ctx)["graph_builds"])
     B.oasm_reset_stats(ctx)
     for k in host_ms:
         host_ms[k] = 0.0
@@ -601,7 +606,7 @@ def main():
         ctx = None
         ctx2 = B.oasm_create(wl.patterns, wl.ks, None,
                              {"device": dev, "timing": 1, "max_streams": max(64, len(wl.texts)),
-                              "prefilter_piece": 1})
+                              "prefilter_piece": 1, "graphs": args.graphs})
         try:
             stream2 = torch.cuda.ExternalStream(B.oasm_cuda_stream(ctx2), device=dev)
             if not args.no_autotune:
@@ -665,7 +670,7 @@ def main():
                    "patterns": len(wl.patterns), "l2": "inputs larger than L2 (text > 129 MB)"
                    if wl.text_bytes > (129 << 20) else "input smaller than L2",
                    "parallelism": f"replicas x{world}", "autotune": tuned,
-                   "prefilter_piece": args.prefilter,
+                   "prefilter_piece": args.prefilter, "graphs": args.graphs,
                    "costs": None if args.costs is None else
                    dict(zip(("sub", "ins", "del"), args.costs))},
         "text_gbps": text_gbps,
@@ -689,6 +694,9 @@ def main():
         "candidates_per_step": st["candidates"] / args.steps,
         "hits_per_step": st["hits"] / args.steps,
         "gpu_launches": int(st["launches"]),
+        # executable graphs instantiated: during warm-up, and during the timed
+        # steps (0 there: each timed step updated the cached graph in place)
+        "graph_builds": {"warmup": builds_warmup, "timed": int(st["graph_builds"])},
         "reruns": int(st["reruns"]),
         "roofline": roofline,
         "e2e": e2e,

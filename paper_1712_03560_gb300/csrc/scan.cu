@@ -779,25 +779,21 @@ __global__ void __launch_bounds__(512) scan_kernel(const ScanArgs A) {
 // patterns, each in a run of whole lanes that ends at the last row of its
 // last lane.  At step s lane l fills column e = x0 + s - l: the row above its
 // first row at columns e and e - 1 is lane l - 1's last row at steps s - 1
-// and s - 2, and the symbol t[e] is the one lane l - 1 used at step s - 1, so
-// both travel down in one shuffle per step, packed as (value << 8) | symbol.
-// A pattern's first lane drops the value (the row above it is Sellers' zero
-// row).  The last row of a pattern's last lane is D[e]: a candidate end when
-// it is <= K (the bit-parallel scan's test).
+// and s - 2, which arrives by one shuffle per step; a pattern's first lane
+// masks it to 0 (the row above is Sellers' zero row).  Each lane reads its
+// own symbol t[e] from a per-warp buffer holding the previous and the
+// current 32-symbol block, at a per-lane base plus the step (no address
+// arithmetic per step).  The last row of a pattern's last lane is D[e]: a
+// candidate end when it is <= K (the bit-parallel scan's test).
 //
 // Per cell: three adds, two minimums and a compare-select for the
-// substitution cost; per lane and step one shuffle, one shared-memory load
-// (the symbol for lane 0), the zero-row mask and the candidate bit.
+// substitution cost; per lane and step one shuffle, one shared-memory load,
+// the zero-row mask and the candidate bit.
 template <int R, bool kPro>
-__device__ __forceinline__ void wdp_step(uint32_t& xout, int (&col)[R], int& up_prev,
+__device__ __forceinline__ void wdp_step(uint32_t& vout, int (&col)[R], int& up_prev,
                                          const uint32_t (&pc)[R], const int (&csub)[R], int ci,
-                                         int cd, uint32_t keep, uint32_t sym0, int lane,
-                                         bool active) {
-  uint32_t xin = __shfl_up_sync(kFull, xout, 1);
-  if (lane == 0) xin = sym0;
-  xin &= keep;  // a pattern's first lane: the row above is the zero row
-  const uint32_t sym = xin & 0xffu;
-  const int up_cur = int(xin >> 8);
+                                         int cd, uint32_t keep, uint32_t sym, bool active) {
+  const int up_cur = int(__shfl_up_sync(kFull, vout, 1) & keep);
   int diag = up_prev, up = up_cur;
   int nv[R];
 #pragma unroll
@@ -813,13 +809,13 @@ __device__ __forceinline__ void wdp_step(uint32_t& xout, int (&col)[R], int& up_
 #pragma unroll
     for (int q = 0; q < R; ++q) col[q] = nv[q];
     up_prev = up_cur;
-    xout = (uint32_t(nv[R - 1]) << 8) | sym;
+    vout = uint32_t(nv[R - 1]);
   }
 }
 
 template <int R>
 __global__ void __launch_bounds__(512) wscan_kernel(const ScanArgs A) {
-  __shared__ uint8_t sb[16][32];  // per warp: the symbols of the current 32-step block
+  __shared__ uint8_t sb[16][64];  // per warp: the previous and the current 32-symbol block
   const int ng = A.n_groups;
   const int g = blockIdx.x % ng;
   const int rb = blockIdx.x / ng;
@@ -844,9 +840,9 @@ __global__ void __launch_bounds__(512) wscan_kernel(const ScanArgs A) {
     csub[q] = wild ? 0 : A.c_sub;
     col[q] = int((w >> 16) & 0xffu) * cd;  // column x0 - 1: row i of a pattern costs i deletions
   }
-  const uint32_t keep = first ? 0xffu : 0xffffffffu;
+  const uint32_t keep = first ? 0u : 0xffffffffu;  // lane 0 is always a first lane
+  uint32_t vout = uint32_t(col[R - 1]);
   int up_prev = (first || lane == 0) ? 0 : int((wr[R * lane - 1] >> 16) & 0xffu) * cd;
-  uint32_t xout = uint32_t(col[R - 1]) << 8;
   const int64_t a = Rg.a, b = Rg.b;
   if (b <= a) return;
   const int64_t x0 = a - G.ov;  // warm-up: the group's largest l_p + K - 1
@@ -856,25 +852,29 @@ __global__ void __launch_bounds__(512) wscan_kernel(const ScanArgs A) {
   const int t_lo = int(rep_lo - x0 + lane), t_hi = pid >= 0 ? int(b - x0 + lane) : t_lo;
   const int nblk = int((b - x0 + 31 + 31) / 32);
   const uint8_t* src = A.arena + (int64_t(wi.arena_base) + (x0 - wi.base_pos));
+  // step j of block v: lane l needs t[x0 + 32 v + j - l] = sb[warp][32 - l + j]
+  // (the previous block's bytes sit at 0..31, the current block's at 32..63)
+  const uint8_t* mys = &sb[warp][32 - lane];
   Emitter em;
-  uint8_t nb = src[lane];
+  uint8_t nb = src[lane], pb = 0;
   for (int v = 0; v < nblk; ++v) {
     __syncwarp();
-    sb[warp][lane] = nb;
+    sb[warp][lane] = pb;
+    sb[warp][32 + lane] = nb;
+    pb = nb;
     __syncwarp();
     if (v + 1 < nblk) nb = src[32 * (v + 1) + lane];  // next block, read ahead
     uint32_t cm = 0;
-    if (v == 0) {
+    if (v == 0) {  // lane l starts at step l (column x0)
 #pragma unroll
       for (int j = 0; j < 32; ++j) {
-        wdp_step<R, true>(xout, col, up_prev, pc, csub, ci, cd, keep, sb[warp][j], lane,
-                          j >= lane);
+        wdp_step<R, true>(vout, col, up_prev, pc, csub, ci, cd, keep, mys[j], j >= lane);
         cm = __funnelshift_l(uint32_t(col[R - 1] - K - 1), cm, 1);
       }
     } else {
 #pragma unroll
       for (int j = 0; j < 32; ++j) {
-        wdp_step<R, false>(xout, col, up_prev, pc, csub, ci, cd, keep, sb[warp][j], lane, true);
+        wdp_step<R, false>(vout, col, up_prev, pc, csub, ci, cd, keep, mys[j], true);
         cm = __funnelshift_l(uint32_t(col[R - 1] - K - 1), cm, 1);
       }
     }
