@@ -46,7 +46,11 @@
  * closed forms and invariants).  The non-default readings of A, B, C and F
  * are pinned only by invariants and brute force of their own definitions:
  * no value the paper prints tells them apart, so for those readings the
- * parity is unpinned beyond the invariants.
+ * parity is unpinned beyond the invariants.  The orc_w* functions are pinned
+ * by the cheapest edit sequence found by Dijkstra over strings, closed forms
+ * (indel distance through a brute-force LCS, Hamming distance), the
+ * insertion/deletion swap and scaling invariants, and brute force over
+ * substrings; the paper prints no weighted value.
  */
 #include <stdint.h>
 #include <stdlib.h>
