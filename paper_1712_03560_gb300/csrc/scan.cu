@@ -787,9 +787,10 @@ __global__ void __launch_bounds__(512) scan_kernel(const ScanArgs A) {
 // candidate end when it is <= K (the bit-parallel scan's test).
 //
 // Per cell: three adds, two minimums and a compare-select for the
-// substitution cost; per lane and step one shuffle, one shared-memory load,
-// the zero-row mask and the candidate bit.
-template <int R, bool kPro>
+// substitution cost (with equal insertion and deletion costs, kEq, one add
+// fewer: min(left + c, up + c) = min(left, up) + c); per lane and step one
+// shuffle, one shared-memory load, the zero-row mask and the candidate bit.
+template <int R, bool kPro, bool kEq>
 __device__ __forceinline__ void wdp_step(uint32_t& vout, int (&col)[R], int& up_prev,
                                          const uint32_t (&pc)[R], const int (&csub)[R], int ci,
                                          int cd, uint32_t keep, uint32_t sym, bool active) {
@@ -800,7 +801,8 @@ __device__ __forceinline__ void wdp_step(uint32_t& vout, int (&col)[R], int& up_
   for (int q = 0; q < R; ++q) {
     const int left = col[q];
     const int sub = (pc[q] == sym) ? 0 : csub[q];
-    const int v = min(min(diag + sub, left + ci), up + cd);
+    const int v = kEq ? min(diag + sub, min(left, up) + ci)
+                      : min(min(diag + sub, left + ci), up + cd);
     diag = left;
     nv[q] = v;
     up = v;
@@ -813,7 +815,7 @@ __device__ __forceinline__ void wdp_step(uint32_t& vout, int (&col)[R], int& up_
   }
 }
 
-template <int R>
+template <int R, bool kEq>
 __global__ void __launch_bounds__(512) wscan_kernel(const ScanArgs A) {
   __shared__ uint8_t sb[16][64];  // per warp: the previous and the current 32-symbol block
   const int ng = A.n_groups;
@@ -868,13 +870,13 @@ __global__ void __launch_bounds__(512) wscan_kernel(const ScanArgs A) {
     if (v == 0) {  // lane l starts at step l (column x0)
 #pragma unroll
       for (int j = 0; j < 32; ++j) {
-        wdp_step<R, true>(vout, col, up_prev, pc, csub, ci, cd, keep, mys[j], j >= lane);
+        wdp_step<R, true, kEq>(vout, col, up_prev, pc, csub, ci, cd, keep, mys[j], j >= lane);
         cm = __funnelshift_l(uint32_t(col[R - 1] - K - 1), cm, 1);
       }
     } else {
 #pragma unroll
       for (int j = 0; j < 32; ++j) {
-        wdp_step<R, false>(vout, col, up_prev, pc, csub, ci, cd, keep, mys[j], true);
+        wdp_step<R, false, kEq>(vout, col, up_prev, pc, csub, ci, cd, keep, mys[j], true);
         cm = __funnelshift_l(uint32_t(col[R - 1] - K - 1), cm, 1);
       }
     }
@@ -890,7 +892,10 @@ cudaError_t launch_wdp(const ScanArgs& a, cudaStream_t st) {
   if (a.warps < 1 || a.warps > 16) return cudaErrorInvalidValue;
   const long long grid = (long long)((a.n_regions + a.warps - 1) / a.warps) * a.n_groups;
   if (grid <= 0) return cudaSuccess;
-  wscan_kernel<R><<<unsigned(grid), a.warps * 32, 0, st>>>(a);
+  if (a.c_ins == a.c_del)
+    wscan_kernel<R, true><<<unsigned(grid), a.warps * 32, 0, st>>>(a);
+  else
+    wscan_kernel<R, false><<<unsigned(grid), a.warps * 32, 0, st>>>(a);
   return cudaGetLastError();
 }
 
