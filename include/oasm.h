@@ -404,6 +404,16 @@ int oasm_autotune(oasm_ctx *ctx, const uint8_t *dsample, size_t n, char *report,
  * of that launch.  Used as the roofline peak of the scan. */
 int oasm_measure_int_peak(int device, double *ops_per_s, double *ms);
 
+/* Failure-detection self-test of the bounded device waits (no paper
+ * passage: the library's own failure detection).  Launches one block that
+ * polls an mbarrier at most spin_limit times; with arrive = 0 nothing
+ * completes the barrier, the poll runs out and the call returns
+ * OASM_ETIMEOUT, exactly as a scan whose copy never lands reports
+ * OASM_ETIMEOUT.  With arrive = 1 the barrier completes: OASM_OK.  No fault,
+ * trap or hang is involved; the device stays usable.  Errors: OASM_EINVAL
+ * (spin_limit == 0), OASM_ENOMEM, OASM_ECUDA. */
+int oasm_selftest_wait(int device, uint32_t spin_limit, int arrive);
+
 /* ---- search without device allocation (no counterpart in the paper) ----
  * For callers that cannot call cudaMalloc: code running inside a framework
  * whose caching allocator already holds the device's memory, code under a

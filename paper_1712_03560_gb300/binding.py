@@ -106,7 +106,7 @@ EXPORTS = ["oasm_config_default", "oasm_rules_default", "oasm_create", "oasm_cre
            "oasm_measure_int_peak", "oasm_scan_ends_noalloc", "oasm_stream_state_size",
            "oasm_save_stream", "oasm_restore_stream", "oasm_replay", "oasm_register_host",
            "oasm_unregister_host", "oasm_step_begin", "oasm_step_end",
-           "oasm_piece_filter_choice"]
+           "oasm_piece_filter_choice", "oasm_selftest_wait"]
 
 _lib = None
 _lock = threading.Lock()
@@ -155,6 +155,7 @@ def load(path: str | None = None):
             "oasm_last_error": ([vp], ctypes.c_char_p),
             "oasm_strerror": ([i32], ctypes.c_char_p),
             "oasm_autotune": ([vp, vp, ctypes.c_size_t, ctypes.c_char_p, ctypes.c_size_t], i32),
+            "oasm_selftest_wait": ([i32, u32, i32], i32),
             "oasm_measure_int_peak": ([i32, ctypes.POINTER(ctypes.c_double),
                                        ctypes.POINTER(ctypes.c_double)], i32),
             "oasm_stream_state_size": ([vp, ctypes.POINTER(ctypes.c_size_t)], i32),
@@ -385,6 +386,12 @@ def oasm_measure_int_peak(device: int = 0):
     ops, ms = ctypes.c_double(), ctypes.c_double()
     _check(load().oasm_measure_int_peak(device, ctypes.byref(ops), ctypes.byref(ms)))
     return ops.value, ms.value
+
+
+def oasm_selftest_wait(device: int = 0, spin_limit: int = 1 << 16, arrive: bool = False) -> int:
+    """Bounded-wait self-test: the library's status code (OASM_ETIMEOUT when
+    nothing completes the barrier, OASM_OK when it completes)."""
+    return int(load().oasm_selftest_wait(device, spin_limit, 1 if arrive else 0))
 
 
 def oasm_scan_ends_noalloc(patterns, ks, d_text, d_out, cap: int, n: int | None = None,

@@ -59,7 +59,48 @@ __global__ void __launch_bounds__(256) int_mix_kernel(uint32_t* out, int iters, 
   out[blockIdx.x * blockDim.x + threadIdx.x] = r;
 }
 
+// Bounded-wait self-test: one thread initialises an mbarrier for one arrival
+// and polls phase 0 with the non-blocking test_wait at most spin_limit
+// times.  With arrive = 0 nothing ever arrives, so the poll runs out and a
+// timeout is recorded -- the same bounded-wait-then-report path the scan's
+// waits take, exercised without a fault, a trap or a hang.  No asynchronous
+// copy targets the barrier, so the block may leave with the phase
+// incomplete.
+__global__ void wait_selftest_kernel(uint32_t spin_limit, int arrive, unsigned* status) {
+  __shared__ __align__(8) unsigned long long bar;
+  if (threadIdx.x != 0) return;
+  const uint32_t b = uint32_t(__cvta_generic_to_shared(&bar));
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b) : "memory");
+  if (arrive) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(b) : "memory");
+  uint32_t ok = 0;
+  for (uint32_t i = 0; i < spin_limit && !ok; ++i) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], 0;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(b)
+        : "memory");
+  }
+  *status = ok ? 0u : 1u;
+}
+
 }  // namespace
+
+extern "C" int oasm_selftest_wait(int device, uint32_t spin_limit, int arrive) {
+  if (spin_limit == 0) return OASM_EINVAL;
+  if (cudaSetDevice(device) != cudaSuccess) return OASM_ECUDA;
+  unsigned* st = nullptr;
+  if (cudaMalloc(&st, sizeof(unsigned)) != cudaSuccess) return OASM_ENOMEM;
+  unsigned h = 2;
+  cudaMemset(st, 0xff, sizeof(unsigned));
+  wait_selftest_kernel<<<1, 32>>>(spin_limit, arrive, st);
+  const cudaError_t e = cudaMemcpy(&h, st, sizeof h, cudaMemcpyDeviceToHost);
+  cudaFree(st);
+  if (e != cudaSuccess || cudaGetLastError() != cudaSuccess) return OASM_ECUDA;
+  if (h == 1u) return OASM_ETIMEOUT;
+  return h == 0u ? OASM_OK : OASM_ECUDA;
+}
 
 extern "C" int oasm_measure_int_peak(int device, double* ops_per_s, double* ms) {
   if (!ops_per_s) return OASM_EINVAL;

@@ -665,3 +665,16 @@ def test_graph_launched_steps_equal_direct_launches():
     assert 1 <= sg["graph_builds"] < sg["steps"]
     assert sd["graph_builds"] == 0
     assert sg["scan_ms"] > 0
+
+
+def test_bounded_wait_reports_timeout_and_device_stays_usable():
+    """Failure detection without a fault: a device wait on a barrier that
+    nothing completes runs out of its bound and reports OASM_ETIMEOUT; the
+    completed barrier reports OASM_OK; afterwards a search still matches the
+    oracle."""
+    assert B.oasm_selftest_wait(0, 1 << 16, arrive=False) == B.OASM_ETIMEOUT
+    assert B.oasm_selftest_wait(0, 1 << 16, arrive=True) == B.OASM_OK
+    rng = np.random.default_rng(71)
+    pats, ks, text = random_case(rng, 4, 8, 6, 30, 5000, kmax=3)
+    got, _ = run_gpu(pats, ks, text)
+    assert canon(got) == oracle_rows(pats, ks, text)
