@@ -425,6 +425,7 @@ int oasm_close_streams(oasm_ctx* ctx, uint32_t n, const uint32_t* sids) {
 }
 
 int oasm_feed(oasm_ctx* ctx, uint32_t sid, const uint8_t* chunk, size_t n) {
+  oasm::NvtxRange nvtx_("oasm_feed");
   int rc = check_sid(ctx, sid);
   if (rc) return rc;
   if (n == 0) return OASM_OK;
@@ -518,6 +519,7 @@ int oasm_unregister_host(oasm_ctx* ctx, const void* ptr) {
 
 int oasm_feed_many(oasm_ctx* ctx, uint32_t n, const uint32_t* sid, const uint8_t* buf,
                    const uint64_t* off, const uint32_t* len) {
+  oasm::NvtxRange nvtx_("oasm_feed_many");
   if (!ctx) return OASM_EINVAL;
   if (n == 0) return OASM_OK;
   if (!sid || !buf || !off || !len) return fail(ctx, OASM_EINVAL, "null argument");
@@ -592,6 +594,7 @@ int oasm_feed_many(oasm_ctx* ctx, uint32_t n, const uint32_t* sid, const uint8_t
 }
 
 int oasm_feed_device(oasm_ctx* ctx, uint32_t sid, const uint8_t* dchunk, size_t n) {
+  oasm::NvtxRange nvtx_("oasm_feed_device");
   int rc = check_sid(ctx, sid);
   if (rc) return rc;
   if (n == 0) return OASM_OK;
@@ -612,16 +615,19 @@ int oasm_end_stream(oasm_ctx* ctx, uint32_t sid) {
 }
 
 int oasm_step(oasm_ctx* ctx) {
+  oasm::NvtxRange nvtx_("oasm_step");
   if (!ctx) return OASM_EINVAL;
   return run_step(ctx);
 }
 
 int oasm_step_begin(oasm_ctx* ctx) {
+  oasm::NvtxRange nvtx_("oasm_step_begin");
   if (!ctx) return OASM_EINVAL;
   return step_begin(ctx);
 }
 
 int oasm_step_end(oasm_ctx* ctx) {
+  oasm::NvtxRange nvtx_("oasm_step_end");
   if (!ctx) return OASM_EINVAL;
   return step_end(ctx);
 }
@@ -642,6 +648,7 @@ static void merge_runs(StreamRec& s) {
 
 int oasm_flush(oasm_ctx* ctx, uint32_t sid, int end_of_stream, oasm_hit* out, size_t cap,
                size_t* n_out) {
+  oasm::NvtxRange nvtx_("oasm_flush");
   int rc = check_sid(ctx, sid);
   if (rc) return rc;
   if (n_out) *n_out = 0;
@@ -668,6 +675,7 @@ int oasm_flush(oasm_ctx* ctx, uint32_t sid, int end_of_stream, oasm_hit* out, si
 }
 
 int oasm_drain(oasm_ctx* ctx, oasm_hit* out, size_t cap, size_t* n_out) {
+  oasm::NvtxRange nvtx_("oasm_drain");
   if (!ctx) return OASM_EINVAL;
   if (n_out) *n_out = 0;
   // plan: streams in id order, each stream's queue already one canonical run

@@ -4,6 +4,7 @@
 // launching and finishing a batched step).  Not part of the public ABI.
 #pragma once
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <unistd.h>
 
 #include <algorithm>
@@ -24,6 +25,15 @@
 #include "kernels.h"
 
 namespace oasm {
+
+// NVTX range over a library call: named ranges for Nsight tools around feed,
+// step and flush; without an attached tool a push/pop is a pointer test.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 constexpr size_t kFrontPad = 1024;   // arena bytes before the first work item
 constexpr size_t kEndPad = 2048;     // arena bytes after the last one
