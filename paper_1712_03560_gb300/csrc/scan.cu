@@ -736,6 +736,9 @@ __global__ void __launch_bounds__(512) scan_kernel(const ScanArgs A) {
   const bool peq_ok = mbar_wait(bar_peq, 0);
   if (!peq_ok) {
     if (threadIdx.x == 0) atomicOr(&A.ctr->overflow, 1u << kTimeoutBit);
+    // the Peq copies may still be in flight into this block's shared memory:
+    // a second bounded wait for them, then leave
+    mbar_wait(bar_peq, 0);
     return;
   }
   const int r = rb * A.warps + warp;
