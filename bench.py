@@ -79,6 +79,9 @@ def parse():
                          "long use the exact piece filter instead of the scan (0 = off, "
                          "1 = automatic per pattern; default 1 for the served signatures, "
                          "0 elsewhere)")
+    ap.add_argument("--tuning-cache", default=None,
+                    help="JSON file of autotuned launch settings keyed by GPU and pattern "
+                         "set: reused when the key is there, written after tuning otherwise")
     ap.add_argument("--graphs", type=int, default=1,
                     help="cfg.graphs: launch each step as a captured CUDA graph, updated in "
                          "place while its shape repeats (1, default) or directly (0)")
@@ -433,7 +436,15 @@ def main():
     if not args.no_autotune:
         # tile shapes for this GPU and pattern set, timed on a slice of the text
         big = max(dtexts, key=lambda t: t.numel())
-        tuned = json.loads(B.oasm_autotune(ctx, big[: min(big.numel(), 32 << 20)]))
+        sample = big[: min(big.numel(), 32 << 20)]
+        if args.tuning_cache:
+            from paper_1712_03560_gb300 import tuning as TU
+            key = TU.cache_key(torch.cuda.get_device_name(dev), wl.patterns, wl.ks, args.costs,
+                               {"prefilter_piece": args.prefilter})
+            how = TU.autotune_cached(B, ctx, sample, key, args.tuning_cache)
+            tuned = {"buckets": B.oasm_get_tuning(ctx), "source": how}
+        else:
+            tuned = json.loads(B.oasm_autotune(ctx, sample))
         print(json.dumps({"autotune": tuned}), file=sys.stderr, flush=True)
         for bk in tuned["buckets"]:
             bk.pop("trials", None)

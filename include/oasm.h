@@ -404,6 +404,31 @@ int oasm_autotune(oasm_ctx *ctx, const uint8_t *dsample, size_t n, char *report,
  * of that launch.  Used as the roofline peak of the scan. */
 int oasm_measure_int_peak(int device, double *ops_per_s, double *ms);
 
+/* Launch settings of one scan class, as oasm_autotune picks them (no paper
+ * passage: the batched form's tile shapes).  A context has one class per
+ * (word count, algorithm); oasm_get_tuning lists them in the context's
+ * order, so a caller can store them (keyed by the GPU and the pattern set)
+ * and give them back to a new context with the same patterns through
+ * oasm_set_tuning instead of timing again. */
+typedef struct {
+    int32_t words;           /* W: 32-bit words per lane (rows per lane, weighted path) */
+    int32_t algo;            /* 0 Myers/Hyyro, 1 + K automaton for K <= 2, 8 weighted */
+    int32_t groups_per_warp; /* 1, or 2 (one-word dictionary classes) */
+    int32_t warps;           /* warps per scan block, 1..16 */
+    int32_t chunk;           /* TMA text buffer bytes: 512, 1024 or 2048 */
+    float region_scale;      /* region length factor, (0, 16] */
+} oasm_tuning;
+
+/* Copies the context's class settings into out[0..cap) and their count into
+ * *n.  OASM_ETRUNC when cap < *n (nothing is copied then). */
+int oasm_get_tuning(oasm_ctx *ctx, oasm_tuning *out, uint32_t cap, uint32_t *n);
+
+/* Sets every class's launch settings; t[i] must name class i's words and
+ * algo (as oasm_get_tuning lists them) and n the class count.  OASM_EINVAL
+ * for a mismatch or a value out of range (nothing is changed then).
+ * Finishes a step in flight first. */
+int oasm_set_tuning(oasm_ctx *ctx, const oasm_tuning *t, uint32_t n);
+
 /* Failure-detection self-test of the bounded device waits (no paper
  * passage: the library's own failure detection).  Launches one block that
  * polls an mbarrier at most spin_limit times; with arrive = 0 nothing

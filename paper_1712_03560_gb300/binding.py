@@ -84,6 +84,12 @@ class oasm_costs(ctypes.Structure):
     _fields_ = [("sub", ctypes.c_uint32), ("ins", ctypes.c_uint32), ("del_", ctypes.c_uint32)]
 
 
+class oasm_tuning(ctypes.Structure):
+    _fields_ = [("words", ctypes.c_int32), ("algo", ctypes.c_int32),
+                ("groups_per_warp", ctypes.c_int32), ("warps", ctypes.c_int32),
+                ("chunk", ctypes.c_int32), ("region_scale", ctypes.c_float)]
+
+
 class oasm_trace(ctypes.Structure):
     _fields_ = [("t", ctypes.c_void_p), ("stream", ctypes.c_void_p), ("off", ctypes.c_void_p),
                 ("len", ctypes.c_void_p), ("last", ctypes.c_void_p), ("payload", ctypes.c_void_p),
@@ -106,7 +112,8 @@ EXPORTS = ["oasm_config_default", "oasm_rules_default", "oasm_create", "oasm_cre
            "oasm_measure_int_peak", "oasm_scan_ends_noalloc", "oasm_stream_state_size",
            "oasm_save_stream", "oasm_restore_stream", "oasm_replay", "oasm_register_host",
            "oasm_unregister_host", "oasm_step_begin", "oasm_step_end",
-           "oasm_piece_filter_choice", "oasm_selftest_wait"]
+           "oasm_piece_filter_choice", "oasm_selftest_wait", "oasm_get_tuning",
+           "oasm_set_tuning"]
 
 _lib = None
 _lock = threading.Lock()
@@ -156,6 +163,8 @@ def load(path: str | None = None):
             "oasm_strerror": ([i32], ctypes.c_char_p),
             "oasm_autotune": ([vp, vp, ctypes.c_size_t, ctypes.c_char_p, ctypes.c_size_t], i32),
             "oasm_selftest_wait": ([i32, u32, i32], i32),
+            "oasm_get_tuning": ([vp, ctypes.POINTER(oasm_tuning), u32, ctypes.POINTER(u32)], i32),
+            "oasm_set_tuning": ([vp, ctypes.POINTER(oasm_tuning), u32], i32),
             "oasm_measure_int_peak": ([i32, ctypes.POINTER(ctypes.c_double),
                                        ctypes.POINTER(ctypes.c_double)], i32),
             "oasm_stream_state_size": ([vp, ctypes.POINTER(ctypes.c_size_t)], i32),
@@ -386,6 +395,29 @@ def oasm_measure_int_peak(device: int = 0):
     ops, ms = ctypes.c_double(), ctypes.c_double()
     _check(load().oasm_measure_int_peak(device, ctypes.byref(ops), ctypes.byref(ms)))
     return ops.value, ms.value
+
+
+TUNING_FIELDS = ("words", "algo", "groups_per_warp", "warps", "chunk", "region_scale")
+
+
+def oasm_get_tuning(ctx) -> list:
+    """Launch settings of every scan class, as dicts of TUNING_FIELDS."""
+    lib = load()
+    n = ctypes.c_uint32(0)
+    rc = lib.oasm_get_tuning(ctx, None, 0, ctypes.byref(n))
+    if rc not in (OASM_OK, OASM_ETRUNC):
+        _check(rc, ctx)
+    arr = (oasm_tuning * max(1, n.value))()
+    _check(lib.oasm_get_tuning(ctx, arr, n.value, ctypes.byref(n)), ctx)
+    return [{f: getattr(arr[i], f) for f in TUNING_FIELDS} for i in range(n.value)]
+
+
+def oasm_set_tuning(ctx, entries):
+    arr = (oasm_tuning * max(1, len(entries)))()
+    for i, e in enumerate(entries):
+        for f in TUNING_FIELDS:
+            setattr(arr[i], f, e[f])
+    return _check(load().oasm_set_tuning(ctx, arr, len(entries)), ctx)
 
 
 def oasm_selftest_wait(device: int = 0, spin_limit: int = 1 << 16, arrive: bool = False) -> int:

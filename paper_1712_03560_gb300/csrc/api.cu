@@ -826,6 +826,50 @@ int oasm_reset_stats(oasm_ctx* ctx) {
 
 void* oasm_cuda_stream(oasm_ctx* ctx) { return ctx ? static_cast<void*>(ctx->stream) : nullptr; }
 
+int oasm_get_tuning(oasm_ctx* ctx, oasm_tuning* out, uint32_t cap, uint32_t* n) {
+  if (!ctx || !n) return OASM_EINVAL;
+  *n = uint32_t(ctx->buckets.size());
+  if (cap < *n) return OASM_ETRUNC;
+  if (*n && !out) return OASM_EINVAL;
+  for (size_t i = 0; i < ctx->buckets.size(); ++i) {
+    const Bucket& b = ctx->buckets[i];
+    out[i] = oasm_tuning{b.W, b.algo, bucket_gpw(ctx, b), b.warps, b.chunk, float(b.region_scale)};
+  }
+  return OASM_OK;
+}
+
+int oasm_set_tuning(oasm_ctx* ctx, const oasm_tuning* t, uint32_t n) {
+  if (!ctx || (n && !t)) return OASM_EINVAL;
+  if (n != ctx->buckets.size())
+    return fail(ctx, OASM_EINVAL, "tuning for %u classes, the context has %zu", n,
+                ctx->buckets.size());
+  int max_smem = 0;
+  cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
+  for (uint32_t i = 0; i < n; ++i) {
+    const Bucket& b = ctx->buckets[i];
+    const oasm_tuning& x = t[i];
+    const bool dict = b.max_nseg == 1, wdp = b.algo == kAlgoWeighted;
+    const bool gpw_ok = x.groups_per_warp == 1 ||
+                        (x.groups_per_warp == 2 && b.W == 1 && dict && !wdp);
+    const bool chunk_ok = x.chunk == 512 || x.chunk == 1024 || x.chunk == 2048;
+    if (x.words != b.W || x.algo != b.algo || !gpw_ok || x.warps < 1 || x.warps > 16 ||
+        !chunk_ok || !(x.region_scale > 0.f && x.region_scale <= 16.f) ||
+        (!wdp && scan_smem_bytes(b.W, x.warps, dict ? x.chunk : 0, x.groups_per_warp) >
+                     size_t(max_smem)))
+      return fail(ctx, OASM_EINVAL, "tuning entry %u does not fit class %u", i, i);
+  }
+  int rc;
+  if ((rc = step_end(ctx))) return rc;
+  for (uint32_t i = 0; i < n; ++i) {
+    Bucket& b = ctx->buckets[i];
+    b.gpw = t[i].groups_per_warp;
+    b.warps = t[i].warps;
+    b.chunk = t[i].chunk;
+    b.region_scale = t[i].region_scale;
+  }
+  return OASM_OK;
+}
+
 int oasm_autotune(oasm_ctx* ctx, const uint8_t* dsample, size_t n, char* report,
                   size_t report_cap) {
   if (!ctx || !dsample || n < 4096) return OASM_EINVAL;

@@ -678,3 +678,35 @@ def test_bounded_wait_reports_timeout_and_device_stays_usable():
     pats, ks, text = random_case(rng, 4, 8, 6, 30, 5000, kmax=3)
     got, _ = run_gpu(pats, ks, text)
     assert canon(got) == oracle_rows(pats, ks, text)
+
+
+def test_tuning_moves_between_contexts():
+    """oasm_get_tuning / oasm_set_tuning: the settings one context's
+    autotuner picked go to a second context over the same patterns, whose
+    search still matches the oracle; entries that do not fit are rejected."""
+    import torch
+    rng = np.random.default_rng(72)
+    pats, ks, text = random_case(rng, 4, 90, 6, 70, 120000, kmax=3)
+    a = B.oasm_create(pats, ks, None, None)
+    b = B.oasm_create(pats, ks, None, None)
+    try:
+        B.oasm_autotune(a, torch.from_numpy(text[:65536].copy()).cuda())
+        ta = B.oasm_get_tuning(a)
+        B.oasm_set_tuning(b, ta)
+        assert B.oasm_get_tuning(b) == ta
+        with pytest.raises(B.OasmError):
+            B.oasm_set_tuning(b, ta[:-1])
+        bad = [dict(e) for e in ta]
+        bad[0]["warps"] = 17
+        with pytest.raises(B.OasmError):
+            B.oasm_set_tuning(b, bad)
+        assert B.oasm_get_tuning(b) == ta  # a rejected call changes nothing
+        sid = B.oasm_open_stream(b)
+        B.oasm_feed(b, sid, text)
+        res = B.oasm_flush(b, sid, end_of_stream=True)
+        got = [(int(r["pattern_id"]), int(r["decided_at"]), int(r["k"]), int(r["start"]),
+                int(r["len"])) for r in res]
+        assert canon(got) == oracle_rows(pats, ks, text)
+    finally:
+        B.oasm_destroy(a)
+        B.oasm_destroy(b)
