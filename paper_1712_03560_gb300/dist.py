@@ -15,11 +15,12 @@ from __future__ import annotations
 import numpy as np
 
 
-def shard_patterns(lengths, world: int) -> list:
-    """Pattern ids per rank, greedily balanced by ceil(l_p / 32) word count
-    (longest first, each to the least loaded rank); ids stay sorted."""
+def shard_patterns(lengths, world: int, unit: int = 32) -> list:
+    """Pattern ids per rank, greedily balanced by ceil(l_p / unit) (longest
+    first, each to the least loaded rank); ids stay sorted.  unit = 32: the
+    bit-parallel scan's words; unit = 4: the weighted path's lanes of 4 rows."""
     lengths = np.asarray(lengths, dtype=np.int64)
-    words = (lengths + 31) // 32
+    words = (lengths + unit - 1) // unit
     order = np.argsort(-words, kind="stable")
     load = np.zeros(world, dtype=np.int64)
     parts = [[] for _ in range(world)]

@@ -22,6 +22,17 @@ def test_shards_cover_every_pattern_once_and_balance_words():
         assert max(words) - min(words) <= 4
 
 
+def test_weighted_shards_balance_lanes():
+    """The weighted path's work is a lane of 4 rows per started 4 symbols."""
+    rng = np.random.default_rng(1)
+    lens = rng.integers(1, 129, size=777)
+    for world in (2, 3, 8):
+        parts = D.shard_patterns(lens, world, unit=4)
+        assert sorted(p for part in parts for p in part) == list(range(777))
+        lanes = [int(((lens[part] + 3) // 4).sum()) for part in parts]
+        assert max(lanes) - min(lanes) <= 32
+
+
 def _free_port():
     s = socket.socket()
     s.bind(("127.0.0.1", 0))
