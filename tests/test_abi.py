@@ -125,3 +125,12 @@ def test_piece_filter_choice_follows_its_rule():
     assert B.oasm_piece_filter_choice(dna, [0] * 50, 1).all()          # one piece of 20
     with pytest.raises(B.OasmError):
         B.oasm_piece_filter_choice(pats, ks, 3)
+
+
+def test_tuning_and_selftest_reject_bad_arguments_on_the_host():
+    """No context or no count: rejected before any device work."""
+    lib = B.load()
+    n = ctypes.c_uint32(0)
+    assert lib.oasm_get_tuning(None, None, 0, ctypes.byref(n)) == B.OASM_EINVAL
+    assert lib.oasm_set_tuning(None, None, 0) == B.OASM_EINVAL
+    assert lib.oasm_selftest_wait(0, 0, 0) == B.OASM_EINVAL
