@@ -110,6 +110,65 @@ def test_scheduler_feeds_every_packet_once_in_stream_order(slots, budget):
         assert res["max_waiting_streams"] > 0
 
 
+class MemLimitedLib(FakeLib):
+    """Admission refused by memory (OASM_ENOMEM) below the slot count."""
+
+    def __init__(self, slots, mem_streams):
+        super().__init__(slots)
+        self.mem_streams = mem_streams
+
+    def oasm_open_stream(self, ctx):
+        if len(self.open) >= self.mem_streams:
+            raise self.OasmError(self.OASM_ENOMEM)
+        return super().oasm_open_stream(ctx)
+
+
+def test_scheduler_waits_out_admission_refused_by_memory():
+    """Host fault injection: the library refuses new streams for memory while
+    slots are free; the scheduler keeps them waiting and still feeds every
+    packet exactly once, in order."""
+    tr = W.served(seed=5, n_streams=10, n_sig=4, gbps=1.0, duration=0.004, life=0.4)
+    lib = MemLimitedLib(slots=8, mem_streams=3)
+    srv = serve.Server([b"AB"], [0], max_streams=8, lib=lib, max_batch_bytes=4000)
+    res = srv.replay(tr, realtime=False)
+    got = sorted(e[2] for e in lib.log if e[0] == "close")
+    assert got == sorted(bytes(t) for t in tr.stream_texts() if t.size)
+    assert res["max_waiting_streams"] > 0
+    live, peak = 0, 0
+    for e in lib.log:
+        live += {"open": 1, "close": -1}.get(e[0], 0)
+        peak = max(peak, live)
+    assert peak <= 3
+
+
+class FailingStepLib(FakeLib):
+    """A step that reports a device-wait timeout (OASM_ETIMEOUT) on its third call."""
+    OASM_ETIMEOUT = -5
+
+    def __init__(self, slots):
+        super().__init__(slots)
+        self.steps = 0
+
+    def oasm_step(self, ctx):
+        self.steps += 1
+        if self.steps == 3:
+            raise self.OasmError(self.OASM_ETIMEOUT)
+        super().oasm_step(ctx)
+
+
+def test_scheduler_surfaces_a_failed_step():
+    """Host fault injection: a step that fails (a bounded device wait ran
+    out) ends the replay with that error at once instead of hanging or
+    dropping it."""
+    tr = W.served(seed=6, n_streams=6, n_sig=4, gbps=1.0, duration=0.004, life=0.4)
+    lib = FailingStepLib(6)
+    srv = serve.Server([b"AB"], [0], max_streams=6, lib=lib, max_batch_bytes=2000)
+    with pytest.raises(FakeLib.OasmError) as ei:
+        srv.replay(tr, realtime=False)
+    assert ei.value.code == FailingStepLib.OASM_ETIMEOUT
+    assert lib.steps == 3
+
+
 def test_scheduler_realtime_pacing_batches_arrivals():
     tr = W.served(seed=4, n_streams=8, n_sig=4, gbps=0.05, duration=0.05)
     lib = FakeLib(8)
