@@ -155,3 +155,32 @@ def test_weighted_extreme_costs(costs):
     pats, ks, text = random_case(rng, 4, 20, 16, 128, 20000, kmax=15)
     got, _ = run_gpu(pats, ks, text, costs=costs)
     assert canon(got) == oracle_rows(pats, ks, text, costs=costs)
+
+
+def test_weighted_stream_moves_to_another_weighted_context():
+    """Save a weighted stream mid-text, restore it into a second context with
+    the same patterns and costs, continue: both halves' hits together equal
+    the uninterrupted result."""
+    rng = np.random.default_rng(39)
+    costs = (2, 1, 3)
+    pats, ks, text = random_case(rng, 4, 30, 6, 90, 20000, kmax=4)
+    cut = int(rng.integers(1, text.size))
+    want = oracle_rows(pats, ks, text, costs=costs)
+    a = B.oasm_create(pats, ks, None, None, costs=costs)
+    b = B.oasm_create(pats, ks, None, None, costs=costs)
+    try:
+        sa = B.oasm_open_stream(a)
+        B.oasm_feed(a, sa, text[:cut])
+        first = B.oasm_flush(a, sa)
+        state = B.oasm_save_stream(a, sa)
+        B.oasm_close_stream(a, sa)
+        sb = B.oasm_open_stream(b)
+        B.oasm_restore_stream(b, sb, state)
+        B.oasm_feed(b, sb, text[cut:])
+        second = B.oasm_flush(b, sb, end_of_stream=True)
+        rows = [(int(r["pattern_id"]), int(r["decided_at"]), int(r["k"]), int(r["start"]),
+                 int(r["len"])) for r in np.concatenate([first, second])]
+        assert canon(rows) == want
+    finally:
+        B.oasm_destroy(a)
+        B.oasm_destroy(b)
