@@ -585,3 +585,22 @@ def test_oracle_rejects_bad_costs():
         oracle.lev(b"AC", b"A", costs=(0, 1, 1))
     with pytest.raises(ValueError):
         oracle.hits(b"ACG", 1, b"ACGT", costs=(1, 256, 1))
+
+
+@pytest.mark.parametrize("costs", [(2, 1, 1), (1, 2, 1), (1, 1, 3)])
+def test_weighted_hits_exhaustive_binary(costs):
+    """Every binary pattern of length 1-4, every K < m, every binary text of
+    length 7: the weighted hit set equals Fully Naive enumeration with the
+    distances of the cheapest edit sequence (Dijkstra, no alignment matrix)."""
+    alpha = b"AC"
+    texts = [bytes(t) for t in itertools.product(alpha, repeat=7)]
+    for m in range(1, 5):
+        for p in itertools.product(alpha, repeat=m):
+            p = bytes(p)
+            dist = dijkstra_distances(p, alpha, 8, costs)
+            for K in range(m):
+                for t in texts[::3]:
+                    want = fully_naive(p, K, t, lambda a, b: dist[b])
+                    got = sorted((int(h["start"]), int(h["len"]), int(h["k"]))
+                                 for h in oracle.hits(p, K, t, costs=costs))
+                    assert got == want, (p, K, t)
