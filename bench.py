@@ -79,6 +79,10 @@ def parse():
                          "long use the exact piece filter instead of the scan (0 = off, "
                          "1 = automatic per pattern; default 1 for the served signatures, "
                          "0 elsewhere)")
+    ap.add_argument("--output", default="filtered", choices=["filtered", "ends", "all_hits"],
+                    help="rules.output: the filtered occurrence set (OASM, default), every "
+                         "Less Naive end, or every hit of Eq. 2 unfiltered (the raw counts of "
+                         "the paper's Table 1 comparison)")
     ap.add_argument("--tuning-cache", default=None,
                     help="JSON file of autotuned launch settings keyed by GPU and pattern "
                          "set: reused when the key is there, written after tuning otherwise")
@@ -201,7 +205,10 @@ class Clocks:
                 if any(r[3].replace(".", "").isdigit() for r in rows) else None}
 
 
-def cpu_baseline(wl, budget_s: float, costs=None):
+ORACLE_MODE = {"filtered": "oasm", "ends": "ends", "all_hits": "hits"}
+
+
+def cpu_baseline(wl, budget_s: float, costs=None, output: str = "filtered"):
     """The oracle as it stands on a bounded sample: whole text, a subset of patterns."""
     import oracle
     cores = os.cpu_count() or 1
@@ -221,7 +228,8 @@ def cpu_baseline(wl, budget_s: float, costs=None):
     pats = [wl.patterns[i] for i in idx]
     ks = [int(wl.ks[i]) for i in idx]
     t0 = time.perf_counter()
-    res = oracle.oasm_dictionary(pats, ks, text, threads=cores, costs=costs)
+    res = oracle.oasm_dictionary(pats, ks, text, threads=cores, costs=costs,
+                                 mode=ORACLE_MODE[output])
     dt = time.perf_counter() - t0
     cells = sum(p.size for p in pats) * text.size
     return {"value": cells / dt / 1e9, "unit": "GCUPS", "cores": min(cores, n_pat), "kind": "oracle",
@@ -250,10 +258,11 @@ def run_reference(args):
     sample = text[:n_sym]
     for _ in range(args.warmup):
         oracle.oasm_dictionary(pats, ks, sample[: min(n_sym, 1 << 16)], threads=cores,
-                               costs=args.costs)
+                               costs=args.costs, mode=ORACLE_MODE[args.output])
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        oracle.oasm_dictionary(pats, ks, sample, threads=cores, costs=args.costs)
+        oracle.oasm_dictionary(pats, ks, sample, threads=cores, costs=args.costs,
+                               mode=ORACLE_MODE[args.output])
     dt = time.perf_counter() - t0
     cells = sum(p.size for p in pats) * n_sym * args.steps
     val = cells / dt / 1e9
@@ -262,7 +271,8 @@ def run_reference(args):
             "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "config": {"workload": desc, "l2": "oracle on host cores",
-                       "costs": list(args.costs) if args.costs else None},
+                       "costs": list(args.costs) if args.costs else None,
+                       "output": args.output},
             "cpu_baseline": {"value": val, "unit": "GCUPS", "cores": n_pat, "kind": "oracle",
                              "sample": f"{n_pat} of {len(wl.patterns)} patterns x {n_sym} text symbols per step"},
             "e2e": {"value": val, "unit": "GCUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -425,7 +435,8 @@ def main():
     from paper_1712_03560_gb300 import binding as B
 
     wl, desc = make_workload(args.workload, rank, args.text_mib)
-    ctx = B.oasm_create(wl.patterns, wl.ks, None,
+    rules = None if args.output == "filtered" else {"output": args.output}
+    ctx = B.oasm_create(wl.patterns, wl.ks, rules,
                         {"device": dev, "timing": 1, "max_streams": max(64, len(wl.texts)),
                          "prefilter_piece": args.prefilter, "graphs": args.graphs},
                         costs=args.costs)
@@ -591,13 +602,13 @@ def main():
     cpu = None
     parity = None
     if not args.no_cpu and world == 1:
-        cpu, (idx, text, ores) = cpu_baseline(wl, args.cpu_seconds, args.costs)
+        cpu, (idx, text, ores) = cpu_baseline(wl, args.cpu_seconds, args.costs, args.output)
         # the sampled patterns' GPU output must equal the oracle's on that sample
         if True:
             from paper_1712_03560_gb300 import binding as B2
             sub_pats = [wl.patterns[i] for i in idx]
             sub_ks = [int(wl.ks[i]) for i in idx]
-            with B2.Matcher(sub_pats, sub_ks, costs=args.costs,
+            with B2.Matcher(sub_pats, sub_ks, rules=rules, costs=args.costs,
                             prefilter_piece=args.prefilter) as mt:
                 g = mt.search(torch.from_numpy(np.ascontiguousarray(text)).to(f"cuda:{dev}"),
                               device=True)
@@ -612,7 +623,8 @@ def main():
     # patterns whose pieces rarely match go to the exact filter, the rest stay
     # on the scan; device-resident inputs, timed like the main value
     alt = None
-    if args.prefilter == 0 and not args.no_alt and world == 1 and args.costs is None:
+    if args.prefilter == 0 and not args.no_alt and world == 1 and args.costs is None and \
+            args.output == "filtered":
         B.oasm_destroy(ctx)
         ctx = None
         ctx2 = B.oasm_create(wl.patterns, wl.ks, None,
@@ -682,6 +694,7 @@ def main():
                    if wl.text_bytes > (129 << 20) else "input smaller than L2",
                    "parallelism": f"replicas x{world}", "autotune": tuned,
                    "prefilter_piece": args.prefilter, "graphs": args.graphs,
+                   "output": args.output,
                    "costs": None if args.costs is None else
                    dict(zip(("sub", "ins", "del"), args.costs))},
         "text_gbps": text_gbps,

@@ -11,7 +11,7 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-@pytest.mark.parametrize("extra", [[], ["--costs", "1,2,2"]])
+@pytest.mark.parametrize("extra", [[], ["--costs", "1,2,2"], ["--output", "ends"]])
 def test_reference_arm_prints_one_contract_line(extra):
     cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
            "--workload", "plain_dna", "--steps", "1", "--warmup", "0"] + extra
@@ -27,7 +27,8 @@ def test_reference_arm_prints_one_contract_line(extra):
     assert d["impl"] == "reference" and d["metric"] == "GCUPS" and d["value"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
-    assert d["config"]["costs"] == ([1, 2, 2] if extra else None)
+    assert d["config"]["costs"] == ([1, 2, 2] if "--costs" in extra else None)
+    assert d["config"]["output"] == (extra[1] if "--output" in extra else "filtered")
 
 
 def test_bench_help_lists_the_options():
