@@ -114,6 +114,12 @@ typedef struct {
                                   1: automatic, per pattern, from the expected
                                   number of piece matches (symbol frequencies of
                                   the pattern set) against the scan's cost */
+    int32_t full_words;        /* 0 (default): classes of 32 or more patterns longer
+                                  than 32 symbols run the cut-off scan: only each
+                                  pattern's first 32 rows are computed while none
+                                  of them comes within K of a match (the rows below
+                                  then all exceed K), every word otherwise; same
+                                  output.  1: every word at every step */
 } oasm_config;
 
 /* One occurrence added to S (or, for the raw outputs, one hit/end). */
@@ -412,7 +418,8 @@ int oasm_measure_int_peak(int device, double *ops_per_s, double *ms);
  * oasm_set_tuning instead of timing again. */
 typedef struct {
     int32_t words;           /* W: 32-bit words per lane (rows per lane, weighted path) */
-    int32_t algo;            /* 0 Myers/Hyyro, 1 + K automaton for K <= 2, 8 weighted */
+    int32_t algo;            /* 0 Myers/Hyyro, 1 + K automaton for K <= 2, 8 weighted,
+                                9 Myers/Hyyro with the cut-off (multi-word classes) */
     int32_t groups_per_warp; /* 1, or 2 (one-word dictionary classes) */
     int32_t warps;           /* warps per scan block, 1..16 */
     int32_t chunk;           /* TMA text buffer bytes: 512, 1024 or 2048 */

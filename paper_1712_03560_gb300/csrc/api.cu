@@ -92,7 +92,7 @@ void free_ctx(oasm_ctx* c) {
   auto f = [](void* p) { if (p) cudaFree(p); };
   f(c->d_m); f(c->d_K); f(c->d_mem_off); f(c->d_peq_rev); f(c->d_wpat);
   f(c->d_pdir); f(c->d_pent); f(c->d_pbytes); f(c->d_poff); f(c->pset.p); f(c->d_pbloom);
-  for (auto& b : c->buckets) { f(b.d_groups); f(b.d_peq); f(b.d_wrow); }
+  for (auto& b : c->buckets) { f(b.d_groups); f(b.d_peq); f(b.d_peq_hi); f(b.d_wrow); }
   f(c->d_tails); f(c->d_hdr); f(c->d_mem);
   f(c->arena.p); f(c->upload.p); f(c->stage[0].d.p); f(c->stage[1].d.p); f(c->cand.p); f(c->keys.p);
   f(c->keys_alt.p); f(c->out.p); f(c->pool_hdr.p); f(c->pool_mem.p); f(c->pair_pool.p);
@@ -212,10 +212,11 @@ int oasm_create_weighted(const uint8_t* const* pat, const uint32_t* len, const u
     return OASM_EINVAL;
   }
   if (cfg && (cfg->groups_per_warp > 2 || cfg->tile_warps > 16 ||
-              (cfg->prefilter_piece > 1 && (cfg->prefilter_piece < 4 || cfg->prefilter_piece > 128)))) {
+              (cfg->prefilter_piece > 1 && (cfg->prefilter_piece < 4 || cfg->prefilter_piece > 128)) ||
+              cfg->full_words < 0 || cfg->full_words > 1)) {
     g_create_err =
         "config: groups_per_warp must be 0, 1 or 2; tile_warps 0..16; prefilter_piece 0, 1 or "
-        "4..128";
+        "4..128; full_words 0 or 1";
     return OASM_EINVAL;
   }
   if (costs && (costs->sub < 1 || costs->sub > 255 || costs->ins < 1 || costs->ins > 255 ||
@@ -854,8 +855,8 @@ int oasm_set_tuning(oasm_ctx* ctx, const oasm_tuning* t, uint32_t n) {
     const bool chunk_ok = x.chunk == 512 || x.chunk == 1024 || x.chunk == 2048;
     if (x.words != b.W || x.algo != b.algo || !gpw_ok || x.warps < 1 || x.warps > 16 ||
         !chunk_ok || !(x.region_scale > 0.f && x.region_scale <= 16.f) ||
-        (!wdp && scan_smem_bytes(b.W, x.warps, dict ? x.chunk : 0, x.groups_per_warp) >
-                     size_t(max_smem)))
+        (!wdp && scan_smem_bytes(b.W, x.warps, dict ? x.chunk : 0, x.groups_per_warp,
+                                 b.algo) > size_t(max_smem)))
       return fail(ctx, OASM_EINVAL, "tuning entry %u does not fit class %u", i, i);
   }
   int rc;
@@ -907,7 +908,7 @@ int oasm_autotune(oasm_ctx* ctx, const uint8_t* dsample, size_t n, char* report,
     const bool wdp = b.algo == kAlgoWeighted;
     const int g_hi = (dict && b.W == 1 && ctx->cfg.groups_per_warp != 1 && !wdp) ? 2 : 1;
     auto time_cfg = [&](int go, int wo, int co, double so, float* out_ms) -> int {
-      if (scan_smem_bytes(b.W, wo, dict ? co : 0, go) > size_t(max_smem)) {
+      if (scan_smem_bytes(b.W, wo, dict ? co : 0, go, b.algo) > size_t(max_smem)) {
         *out_ms = 1e30f;
         return OASM_OK;
       }
@@ -928,6 +929,7 @@ int oasm_autotune(oasm_ctx* ctx, const uint8_t* dsample, size_t n, char* report,
       ScanArgs a{};
       a.groups = b.d_groups;
       a.peq = b.d_peq;
+      a.peq_hi = b.d_peq_hi;
       a.n_groups = int(b.groups.size());
       a.W = b.W;
       a.regions = reinterpret_cast<const Region*>(ctx->upload.p + 256);

@@ -207,7 +207,8 @@ inline bool canon_less(const oasm_hit& a, const oasm_hit& b) {
 
 struct Bucket {
   int W = 0;
-  int algo = 0;           // 0: Myers/Hyyro bit-vectors; 1 + K: automaton for K <= 2
+  int algo = 0;           // 0: Myers/Hyyro bit-vectors; 1 + K: automaton for K <= 2;
+                          // kAlgoCut: multi-word Myers/Hyyro with the cut-off
   int max_nseg = 1;
   int warps = 8;          // warps per scan block
   int chunk = 1024;       // text bytes per TMA buffer (dictionary mapping)
@@ -218,6 +219,7 @@ struct Bucket {
   std::vector<LaneGroup> groups;
   LaneGroup* d_groups = nullptr;
   uint32_t* d_peq = nullptr;
+  uint32_t* d_peq_hi = nullptr;  // cut-off classes: the whole W-word table (d_peq: word 0)
   // weighted path (algo == kAlgoWeighted): per group (one warp's column of
   // 32 x kWRows rows holding several patterns) one 32-bit row word per row,
   // lane-major (lane l holds rows kWRows l .. kWRows l + kWRows - 1); see

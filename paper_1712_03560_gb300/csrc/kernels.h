@@ -18,10 +18,13 @@ struct ScanArgs {
   int32_t resv;              // candidate slots a warp reserves at a time
   int32_t dict;              // 1: dictionary mapping (one pattern per lane, nseg = 1)
   int32_t chunk;             // text bytes per TMA buffer (dictionary mapping)
-  int32_t algo;              // 0: Myers/Hyyro bit-vectors; 1 + K: automaton for K <= 2 (W = 1)
+  int32_t algo;              // 0: Myers/Hyyro bit-vectors; 1 + K: automaton for K <= 2 (W = 1);
+                             // kAlgoCut: Myers/Hyyro with the cut-off (W >= 2)
   int32_t gpw;               // lane groups per warp: 1, or 2 (dictionary mapping, W = 1)
   int32_t c_sub, c_ins, c_del;  // edit costs (algo == kAlgoWeighted)
   const uint32_t* wrow;      // weighted path: [n_groups][32 kWRows] row words, lane-major
+  const uint32_t* peq_hi;    // cut-off classes: [n_groups][256][W][32] in global memory
+                             // (peq then holds word 0 only: [n_groups][256][32])
   const WorkItem* items;
   const uint8_t* arena;
   Candidate* cand;
@@ -37,15 +40,20 @@ struct ScanArgs {
 // (bits 16-23; 0 for a wild row), and kWFirstLane on every row of a
 // pattern's first lane (the row above that lane is Sellers' zero row).
 constexpr int kAlgoWeighted = 8;
+// Multi-word Myers/Hyyro classes with the cut-off of the blocks-based scan:
+// only word 0 (pattern rows 1..32) runs while no lane's first 32 rows come
+// within K of a match; see scan.cu.  Rows are low-aligned (row r at bit r - 1).
+constexpr int kAlgoCut = 9;
 constexpr int kWRows = 4;
 constexpr uint32_t kWildRow = 0x100u;
 constexpr uint32_t kWFirstLane = 1u << 24;
 
 // Shared memory of one scan block: the Peq tables of its gpw lane groups (256
-// rows of W x 32 words each), two text buffers per warp (dictionary mapping)
-// and the mbarriers.
-inline size_t scan_smem_bytes(int W, int warps, int chunk, int gpw = 1) {
-  return size_t(256) * 128 * W * gpw + size_t(warps) * 2 * chunk + size_t(1 + 2 * warps) * 8;
+// rows of W x 32 words each; word 0 only for the cut-off classes), two text
+// buffers per warp (dictionary mapping) and the mbarriers.
+inline size_t scan_smem_bytes(int W, int warps, int chunk, int gpw = 1, int algo = 0) {
+  const int w = algo == kAlgoCut ? 1 : W;
+  return size_t(256) * 128 * w * gpw + size_t(warps) * 2 * chunk + size_t(1 + 2 * warps) * 8;
 }
 
 cudaError_t launch_scan(const ScanArgs& a, cudaStream_t s);

@@ -702,6 +702,194 @@ __device__ void scan_segments(const ScanArgs& A, const char* peq, const LaneGrou
   em.finish(A, lane);
 }
 
+// ------------------------------------------- dictionary mapping, cut-off
+// Multi-word patterns (33..128 symbols) with the cut-off of Myers' blocks-based
+// scan (Myers 1999, Sec. 5; Ukkonen's cut-off).  Rows are low-aligned: pattern
+// row r sits at bit r - 1 of the W-word column, so word 0 holds rows 1..32.
+//
+// Let lact(e) be the last row whose value is <= K in column e.  A cell of
+// column e + 1 below row lact(e) + 1 exceeds K (each of its predecessors does
+// and no step lowers a value), so lact(e + 1) <= lact(e) + 1.  Hence, while
+// every row from 32 down exceeds K, the rows below 32 stay above K for as
+// long as row 32 itself does: only word 0 has to be computed, and no end can
+// be a candidate (D[e] is row l_p > 32).
+//
+// First form (every lane on word 0 alone): a 32-step block runs word 0 and
+// counts the steps where D[32] <= K.  If no lane counted one, the block is
+// done.  Otherwise the block is run again from its saved start in the full
+// form, with words 1..W-1 re-entered as if each row below 32 were one more
+// than the row above (Pv = all ones, Mv = 0): those values are at least the
+// true ones, and every cell whose true value is <= K is computed exactly,
+// because its cheapest predecessor is <= K too and was exact (the rows below
+// 32 exceed K at the block start).  The full form records the candidate bit
+// of every step.  At the end of each full block a lane may leave the full
+// form when row 32 exceeds K and, for every word w >= 1, the value at the row
+// above the word minus the word's count of -1 steps (Mv bits) exceeds K: no
+// row from 32 down is then within K.  The warp leaves when every lane may.
+//
+// The full form reads words 1..W-1 of Peq from global memory (L1/L2): it runs
+// near matches only.  Shared memory holds word 0 of the group's table.
+
+// Word 0 alone: the first 32 rows; s tracks D[32] - K - 1.
+__device__ __forceinline__ void cut_word0_step(uint32_t& Pv, uint32_t& Mv, int& s, uint32_t eq) {
+  const uint32_t x = eq & Pv;
+  const uint32_t sum = x + Pv;
+  const uint32_t xv = eq | Mv;
+  const uint32_t xh = (sum ^ Pv) | eq;
+  const uint32_t ph = Mv | ~(xh | Pv);
+  const uint32_t mh = Pv & xh;
+  s = sub_top(add_top(s, ph), mh);
+  const uint32_t phs = shl1(ph), mhs = shl1(mh);
+  Pv = mhs | ~(xv | phs);
+  Mv = phs & xv;
+}
+
+// Every word (low-aligned rows): s0 tracks D[32] - K - 1, sL tracks
+// D[l_p] - K - 1 (row l_p at bit 31 - sh of word W - 1).
+template <int W>
+__device__ __forceinline__ void cut_full_step(uint32_t (&Pv)[W], uint32_t (&Mv)[W], int& s0,
+                                              int& sL, const uint32_t (&eq)[W], uint32_t sh) {
+  uint32_t x[W], sum[W];
+#pragma unroll
+  for (int w = 0; w < W; ++w) x[w] = eq[w] & Pv[w];
+  add_words<W>(x, Pv, sum);
+  uint32_t php = 0, mhp = 0;
+#pragma unroll
+  for (int w = 0; w < W; ++w) {
+    const uint32_t xv = eq[w] | Mv[w];
+    const uint32_t xh = (sum[w] ^ Pv[w]) | eq[w];
+    const uint32_t ph = Mv[w] | ~(xh | Pv[w]);
+    const uint32_t mh = Pv[w] & xh;
+    if (w == 0) s0 = sub_top(add_top(s0, ph), mh);
+    if (w == W - 1) sL = sub_top(add_top(sL, ph << sh), mh << sh);
+    const uint32_t phs = (w == 0) ? shl1(ph) : __funnelshift_l(php, ph, 1);
+    const uint32_t mhs = (w == 0) ? shl1(mh) : __funnelshift_l(mhp, mh, 1);
+    php = ph;
+    mhp = mh;
+    Pv[w] = mhs | ~(xv | phs);
+    Mv[w] = phs & xv;
+  }
+}
+
+template <int W>
+__device__ void scan_dict_cut(const ScanArgs& A, const char* peq0, const uint32_t* ghi,
+                              uint8_t* tbuf, uint32_t bar0, const LaneGroup& G, const Region& R,
+                              const WorkItem& wi, int lane) {
+  const LaneSetup L = lane_setup(A, G, R, wi, lane, G.ov);
+  const uint32_t lane_off = uint32_t(lane) * 4u;
+  const uint32_t sh = 31u - uint32_t((L.m - 1) & 31);  // row l_p to bit 31 of word W - 1
+  const uint32_t lastmask = 0xffffffffu >> sh;          // rows of word W - 1 up to l_p
+  uint32_t Pv[W], Mv[W];
+#pragma unroll
+  for (int w = 0; w < W; ++w) {
+    Pv[w] = 0xffffffffu;
+    Mv[w] = 0u;
+  }
+  // before the first symbol every row r holds r: D[32] = 32 > K
+  int s0 = 31 - L.K, sL = L.m - L.K - 1;
+  bool full = false;             // warp-uniform
+  uint32_t n_full = 0, n_redo = 0;
+  Emitter em;
+  const int nbytes = (L.nvec * 16 + kBlk - 1) / kBlk * kBlk;
+  const bool ok = stream_blocks(A, tbuf, bar0, A.arena + L.ad_al, nbytes, lane,
+                                [&](const uint8_t* tv, int v) {
+    if (!full) {
+      const uint32_t P0 = Pv[0], M0 = Mv[0];
+      const int s00 = s0;
+      int act = 0;
+#pragma unroll
+      for (int j = 0; j < kBlk; ++j) {
+        const uint32_t eq0 = *reinterpret_cast<const uint32_t*>(peq0 + mad_lo(tv[j], 128u, lane_off));
+        cut_word0_step(Pv[0], Mv[0], s0, eq0);
+        act = add_top(act, uint32_t(s0));  // steps with D[32] <= K
+      }
+      if (!__any_sync(kFull, act != 0)) return;
+      // a lane's first 32 rows came within K: the block again, every word
+      Pv[0] = P0;
+      Mv[0] = M0;
+      s0 = s00;
+#pragma unroll
+      for (int w = 1; w < W; ++w) {
+        Pv[w] = 0xffffffffu;
+        Mv[w] = 0u;
+      }
+      sL = s00 + (L.m - 32);  // D[l_p] = D[32] + (l_p - 32)
+      full = true;
+      ++n_redo;
+    }
+    uint32_t cm = 0;
+#pragma unroll 8
+    for (int j = 0; j < kBlk; ++j) {
+      const uint32_t sym = tv[j];
+      uint32_t eq[W];
+      eq[0] = *reinterpret_cast<const uint32_t*>(peq0 + mad_lo(sym, 128u, lane_off));
+      const uint32_t* row = ghi + sym * (32u * W) + uint32_t(lane);
+#pragma unroll
+      for (int w = 1; w < W; ++w) eq[w] = __ldg(row + 32 * w);
+      cut_full_step<W>(Pv, Mv, s0, sL, eq, sh);
+      cm = __funnelshift_l(uint32_t(sL), cm, 1);  // shifts in the sign of sL
+    }
+    ++n_full;
+    const uint32_t c = cm & block_mask32(L.t_lo, L.t_hi, v);
+    if (__any_sync(kFull, c != 0))
+      em.put(A, lane, c, L.spos + kBlk * v, R.wi, L.pid, wi.base_pos, kBlk - 1);
+    // leave the full form when no row from 32 down is within K in any lane
+    bool drop = s0 >= 0;
+    int d = s0 + L.K + 1;  // D[32]
+#pragma unroll
+    for (int w = 1; w < W; ++w) {
+      const uint32_t mk = (w == W - 1) ? lastmask : 0xffffffffu;
+      drop = drop && d - __popc(Mv[w] & mk) > L.K;
+      if (w < W - 1) d += __popc(Pv[w]) - __popc(Mv[w]);
+    }
+    full = !__all_sync(kFull, drop || L.pid < 0);
+  });
+  if (ok) em.finish(A, lane);
+  // executed words beyond word 0 of every step: the full blocks' upper words
+  // and the first-form passes that were run again
+  const uint32_t active = __popc(__ballot_sync(kFull, L.pid >= 0));
+  if (lane == 0 && (n_full | n_redo))
+    atomicAdd(&A.ctr->word_steps, (unsigned long long)active * kBlk *
+                                       (uint64_t(n_full) * (W - 1) + n_redo));
+}
+
+template <int W>
+__global__ void __launch_bounds__(512) scan_cut_kernel(const ScanArgs A) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  constexpr uint32_t kPeqBytes = 256u * 128u;  // word 0 of the group's table
+  const int g = blockIdx.x % A.n_groups;
+  const int rb = blockIdx.x / A.n_groups;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint8_t* tbase = smem + kPeqBytes;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(tbase + size_t(A.warps) * 2 * A.chunk);
+  const uint32_t bar_peq = smem_u32(bars);
+  if (threadIdx.x == 0) mbar_init(bar_peq, 1);
+  if (lane == 0) {
+    mbar_init(smem_u32(bars + 1 + 2 * warp), 1);
+    mbar_init(smem_u32(bars + 2 + 2 * warp), 1);
+  }
+  fence_mbar_init();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    mbar_expect_tx(bar_peq, kPeqBytes);
+    const uint8_t* src = reinterpret_cast<const uint8_t*>(A.peq) + size_t(g) * kPeqBytes;
+    tma_load_1d(smem_u32(smem), src, kPeqBytes, bar_peq);
+  }
+  const bool peq_ok = mbar_wait(bar_peq, 0);
+  if (!peq_ok) {
+    if (threadIdx.x == 0) atomicOr(&A.ctr->overflow, 1u << kTimeoutBit);
+    mbar_wait(bar_peq, 0);  // the copy may still be in flight: wait again (bounded), then leave
+    return;
+  }
+  const int r = rb * A.warps + warp;
+  if (r >= A.n_regions) return;  // the whole warp leaves together
+  const Region R = A.regions[r];
+  const WorkItem wi = A.items[R.wi];
+  uint8_t* tb = tbase + size_t(warp) * 2 * A.chunk;
+  scan_dict_cut<W>(A, reinterpret_cast<const char*>(smem), A.peq_hi + size_t(g) * 256 * 32 * W,
+                   tb, smem_u32(bars + 1 + 2 * warp), A.groups[g], R, wi, lane);
+}
+
 // GPW lane groups per warp (dictionary mapping, W = 1 only): blocks of the
 // grid walk the class's groups GPW at a time.
 template <int W, bool kDict, int ALG, int GPW>
@@ -912,6 +1100,15 @@ cudaError_t launch_w(const ScanArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+template <int W>
+cudaError_t launch_cut(const ScanArgs& a, cudaStream_t st) {
+  const size_t smem = scan_smem_bytes(W, a.warps, a.chunk, 1, kAlgoCut);
+  const long long grid = (long long)((a.n_regions + a.warps - 1) / a.warps) * a.n_groups;
+  if (grid <= 0) return cudaSuccess;
+  scan_cut_kernel<W><<<unsigned(grid), a.warps * 32, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
 template <int W, bool kDict, int ALG = 0, int GPW = 1>
 cudaError_t allow_smem(int bytes) {
   return cudaFuncSetAttribute(scan_kernel<W, kDict, ALG, GPW>,
@@ -940,12 +1137,27 @@ cudaError_t prepare_scan_kernels(int max_smem_bytes) {
   set(allow_smem<1, true, 1, 2>(max_smem_bytes));
   set(allow_smem<1, true, 2, 2>(max_smem_bytes));
   set(allow_smem<1, true, 3, 2>(max_smem_bytes));
+  set(cudaFuncSetAttribute(scan_cut_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           max_smem_bytes));
+  set(cudaFuncSetAttribute(scan_cut_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           max_smem_bytes));
+  set(cudaFuncSetAttribute(scan_cut_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           max_smem_bytes));
   return e;
 }
 
 cudaError_t launch_scan(const ScanArgs& a, cudaStream_t s) {
   const bool d = a.dict != 0;
   if (a.algo == kAlgoWeighted) return a.W == kWRows ? launch_wdp<kWRows>(a, s) : cudaErrorInvalidValue;
+  if (a.algo == kAlgoCut) {  // multi-word classes, dictionary mapping, one group per warp
+    if (!d || a.gpw != 1 || !a.peq_hi) return cudaErrorInvalidValue;
+    switch (a.W) {
+      case 2: return launch_cut<2>(a, s);
+      case 3: return launch_cut<3>(a, s);
+      case 4: return launch_cut<4>(a, s);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   if (a.gpw == 2) {  // two lane groups per warp: one-word classes, dictionary mapping
     if (a.W != 1 || !d) return cudaErrorInvalidValue;
     switch (a.algo) {

@@ -130,6 +130,7 @@ int enqueue_step(oasm_ctx* ctx, StepPlan& pl, const WorkItem* d_items, const Reg
     ScanArgs a{};
     a.groups = b.d_groups;
     a.peq = b.d_peq;
+    a.peq_hi = b.d_peq_hi;
     a.n_groups = int(b.groups.size());
     a.W = b.W;
     a.regions = d_regions + pl.region_off[bi];
@@ -333,6 +334,7 @@ int finish_step(oasm_ctx* ctx, StepPlan& pl, const WorkItem* d_items, bool* over
     cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[5]); ctx->st.step_ms += ms;
   }
   ctx->st.candidates += c.n_cand;
+  ctx->st.word_steps += c.word_steps;  // cut-off classes: words run beyond word 0
   ctx->st.prefilter_candidates += c.n_pref;
   ctx->st.hits += c.n_hits;
   ctx->st.kept += c.n_out;
@@ -542,7 +544,9 @@ int step_end(oasm_ctx* ctx) {
       for (int l = 0; l < kLaneGroup; l += g.nseg) lanes += g.pat[l] >= 0 ? 1 : 0;
     // weighted path: every lane of a pattern's warp runs W rows of cells
     if (b.algo == kAlgoWeighted) lanes = uint64_t(b.groups.size()) * kLaneGroup;
-    ctx->st.word_steps += lanes * uint64_t(b.W) * pl.new_bytes;
+    // cut-off classes: word 0 at every step here; the words they ran beyond it
+    // are counted on the device (finish_step)
+    ctx->st.word_steps += lanes * uint64_t(b.algo == kAlgoCut ? 1 : b.W) * pl.new_bytes;
   }
   release_stages(ctx);
   ctx->st.host_post_ms += ms_since(t_adv);

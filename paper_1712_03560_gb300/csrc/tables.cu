@@ -247,7 +247,7 @@ int build_tables(oasm_ctx* ctx) {
     bk.W = W;
     bk.algo = algo;
     std::vector<std::vector<uint32_t>> lanes;  // patterns of each lane
-    if (algo > 0) {
+    if (algo > 0 && algo <= 3) {
       std::stable_sort(ids.begin(), ids.end(),
                        [&](uint32_t a0, uint32_t b0) { return ctx->m[a0] > ctx->m[b0]; });
       std::vector<int> used;
@@ -299,7 +299,9 @@ int build_tables(oasm_ctx* ctx) {
         G.pat[l] = int32_t(lp[0]);
         G.seg[l] = uint8_t(sg);
         G.K[l] = ctx->K[lp[0]];
-        int off = (algo > 0) ? 0 : 32 * W - ctx->m[lp[0]];  // Myers lanes are top-aligned
+        // Myers lanes are top-aligned (the last row at bit 31 of the top word);
+        // cut-off lanes and automaton lanes start at bit 0
+        int off = (algo != 0) ? 0 : 32 * W - ctx->m[lp[0]];
         for (size_t q = 0; q < lp.size(); ++q) {
           const uint32_t p = lp[q];
           const auto& s = ctx->pats[p];
@@ -312,7 +314,7 @@ int build_tables(oasm_ctx* ctx) {
             const int bit = off + j;
             peq[base + size_t(s[j]) * RW + size_t(bit >> 5) * 32 + l] |= 1u << (bit & 31);
           }
-          if (algo > 0) {
+          if (algo > 0 && algo <= 3) {
             G.first[l] |= 1u << off;
             G.last[l] |= 1u << (off + m - 1);
             G.lastbit[q][l] = uint8_t(off + m - 1);
@@ -333,6 +335,18 @@ int build_tables(oasm_ctx* ctx) {
     CK(cudaMalloc(&bk.d_groups, bk.groups.size() * sizeof(LaneGroup)));
     CK(cudaMemcpy(bk.d_groups, bk.groups.data(), bk.groups.size() * sizeof(LaneGroup),
                   cudaMemcpyHostToDevice));
+    if (algo == kAlgoCut) {
+      // the scan stages only word 0 of each lane (rows 1..32) in shared
+      // memory; the whole table stays in global memory for the full form
+      std::vector<uint32_t> w0(bk.groups.size() * size_t(256) * 32);
+      for (size_t g = 0; g < bk.groups.size(); ++g)
+        for (size_t c = 0; c < 256; ++c)
+          for (size_t l = 0; l < 32; ++l)
+            w0[(g * 256 + c) * 32 + l] = peq[g * 256 * RW + c * RW + l];
+      CK(cudaMalloc(&bk.d_peq_hi, peq.size() * 4));
+      CK(cudaMemcpy(bk.d_peq_hi, peq.data(), peq.size() * 4, cudaMemcpyHostToDevice));
+      peq.swap(w0);
+    }
     CK(cudaMalloc(&bk.d_peq, peq.size() * 4));
     CK(cudaMemcpy(bk.d_peq, peq.data(), peq.size() * 4, cudaMemcpyHostToDevice));
     ctx->buckets.push_back(bk);
@@ -372,7 +386,11 @@ int build_tables(oasm_ctx* ctx) {
       }
     }
     if (ids.empty()) continue;
-    int rc = add_bucket(W, 0, ids);
+    // multi-word classes of 32 or more patterns (dictionary mapping) run the
+    // cut-off form of the scan unless every word is asked for
+    const int algo = (W >= 2 && ids.size() >= size_t(kLaneGroup) && !ctx->cfg.full_words)
+                         ? kAlgoCut : 0;
+    int rc = add_bucket(W, algo, ids);
     if (rc) return rc;
   }
   return OASM_OK;

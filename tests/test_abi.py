@@ -37,8 +37,8 @@ def test_library_exports_every_declared_symbol():
 def test_struct_sizes_match_header():
     assert ctypes.sizeof(B.oasm_hit) == 32
     assert ctypes.sizeof(B.oasm_rules) == 20
-    # oasm_config: 4+4+8+4+4+4+4+8+4+4+4+4
-    assert ctypes.sizeof(B.oasm_config) == 56
+    # oasm_config: 4+4+8+4+4+4+4+8+4+4+4+4+4, padded to 8
+    assert ctypes.sizeof(B.oasm_config) == 64
     assert ctypes.sizeof(B.oasm_costs) == 12
 
 
@@ -70,7 +70,8 @@ def test_strerror_and_null_safety():
 
 
 @pytest.mark.parametrize("field,value", [("groups_per_warp", 3), ("prefilter_piece", 2),
-                                         ("prefilter_piece", 129), ("tile_warps", 17)])
+                                         ("prefilter_piece", 129), ("tile_warps", 17),
+                                         ("full_words", 2), ("full_words", -1)])
 def test_create_rejects_bad_config(field, value):
     """Config fields out of range are rejected on the host, before any device work."""
     lib = B.load()
