@@ -43,10 +43,13 @@
  *
  * Parity status: every function here is pinned by the -m "not gpu" tests
  * (worked example of Sec. 4.2, Fig. 1 values, brute force on tiny inputs,
- * closed forms and invariants).  The non-default readings of A, B, C and F
- * are pinned only by invariants and brute force of their own definitions:
- * no value the paper prints tells them apart, so for those readings the
- * parity is unpinned beyond the invariants.  The orc_w* functions are pinned
+ * closed forms and invariants).  No value the paper prints tells the
+ * non-default readings of A, B, C and F apart; each is pinned by small cases
+ * worked out by hand from the reading's definition, whose hit sets come from
+ * breadth-first search over edits, and in which that reading changes the kept
+ * set (same_end, never, ge, last, per_start_best and its shortest-length
+ * tie-break).  The Less Naive ends report the shortest in-range length that
+ * attains D[e], checked against Eq. 1 for every shorter one.  The orc_w* functions are pinned
  * by the cheapest edit sequence found by Dijkstra over strings, closed forms
  * (indel distance through a brute-force LCS, Hamming distance), the
  * insertion/deletion swap and scaling invariants, and brute force over

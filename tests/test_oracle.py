@@ -221,6 +221,77 @@ def test_sellers_ends_are_hit_ends():
             assert r["k"] == D[e]
             assert oracle.lev(p, t[int(r["start"]):e + 1]) == r["k"]
             assert r["start"] + r["len"] - 1 == e
+            # the reported length is the shortest in-range one attaining D[e]
+            for ll in range(max(1, m - K), int(r["len"])):
+                if e - ll + 1 >= 0:
+                    assert oracle.lev(p, t[e - ll + 1:e + 1]) > r["k"], (e, ll)
+
+
+RULE_GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "rule_readings.txt")
+
+
+def load_rule_cases():
+    """Cases of tests/golden/rule_readings.txt: the hit set and the kept set
+    under each reading, worked out by hand from the readings' definitions."""
+    cases, cur = [], None
+    for line in open(RULE_GOLDEN):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        key, _, rest = line.partition(" ")
+        if key == "case":
+            cur = {"name": rest, "hits": [], "kept": {}}
+            cases.append(cur)
+        elif key in ("pattern", "text"):
+            cur[key] = rest.encode()
+        elif key == "K":
+            cur["K"] = int(rest)
+        elif key == "hit":
+            cur["hits"].append(tuple(int(x) for x in rest.split()))
+        elif key == "kept":
+            reading, _, rows = rest.partition(":")
+            rules = {} if reading == "default" else dict([reading.split("=")])
+            cur["kept"][reading] = (rules, sorted(tuple(int(x) for x in r.split())
+                                                  for r in rows.split(";") if r.strip()))
+    return cases
+
+
+RULE_CASES = load_rule_cases()
+
+
+@pytest.mark.parametrize("ci", range(len(RULE_CASES)), ids=[c["name"] for c in RULE_CASES])
+def test_rule_readings_hand_worked_cases(ci):
+    """Each non-default reading (same_end, never, ge, last, per_start_best)
+    changes the kept set of at least one case, and every case's kept set under
+    every reading is the hand-derived one.  The hit sets themselves are checked
+    against distances from breadth-first search over edits."""
+    c = RULE_CASES[ci]
+    p, t, K = c["pattern"], c["text"], c["K"]
+    H = oracle.hits(p, K, t)
+    assert [(int(h["start"]), int(h["len"]), int(h["k"])) for h in H] == c["hits"]
+    # H itself, from breadth-first search over single-symbol edits of p
+    alphabet = bytes(sorted(set(p + t)))
+    dist = bfs_distances(p, alphabet, len(p) + K)
+    brute = [(i, ln, dist[t[i:i + ln]]) for i in range(len(t))
+             for ln in range(max(1, len(p) - K), len(p) + K + 1)
+             if i + ln <= len(t) and dist[t[i:i + ln]] <= K]
+    assert brute == c["hits"]
+    for reading, (rules, want) in c["kept"].items():
+        got = sorted((int(x["start"]), int(x["len"]), int(x["k"]), int(x["decided_at"]))
+                     for x in oracle.oasm(p, K, t, rules))
+        assert got == want, (c["name"], reading)
+
+
+def test_rule_readings_each_change_some_kept_set():
+    """The hand-worked cases tell every reading from the default."""
+    changed = set()
+    for c in RULE_CASES:
+        base = c["kept"]["default"][1]
+        for reading, (_, want) in c["kept"].items():
+            if want != base:
+                changed.add(reading)
+    assert changed == {"replace=same_end", "replace=never", "cmp=ge", "acc=last",
+                       "order=per_start_best"}
 
 
 # --------------------------------------------------------------------------
