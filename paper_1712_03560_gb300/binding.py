@@ -427,14 +427,32 @@ def oasm_selftest_wait(device: int = 0, spin_limit: int = 1 << 16, arrive: bool 
     return int(load().oasm_selftest_wait(device, spin_limit, 1 if arrive else 0))
 
 
+def _check_device_buffer(d, need_bytes: int, what: str):
+    """A contiguous CUDA tensor on the current device holding need_bytes."""
+    import torch
+    if not hasattr(d, "data_ptr") or not d.is_cuda or not d.is_contiguous():
+        raise OasmError(OASM_EINVAL, f"{what} must be a contiguous CUDA tensor")
+    if d.device.index != torch.cuda.current_device():
+        raise OasmError(OASM_EINVAL, f"{what} is on cuda:{d.device.index}, the current "
+                                     f"device is cuda:{torch.cuda.current_device()}")
+    have = d.numel() * d.element_size()
+    if need_bytes > have:
+        raise OasmError(OASM_EINVAL, f"{what} holds {have} bytes, the call needs {need_bytes}")
+
+
 def oasm_scan_ends_noalloc(patterns, ks, d_text, d_out, cap: int, n: int | None = None,
-                           stream: int = 0) -> int:
+                           stream: int | None = None) -> int:
     """Less Naive ends of up to 64 patterns over a device text, allocating no
     device memory (for callers that cannot allocate: see include/oasm.h).
 
-    ``d_out`` is the caller's device buffer of ``cap`` records of
-    ``END_DTYPE`` (16 bytes each).  Returns the number of ends found, which
+    ``d_text`` is a CUDA tensor of at least ``n`` bytes (default: all of it)
+    and ``d_out`` one of at least ``cap`` records of ``END_DTYPE`` (16 bytes
+    each), both on the current device; anything smaller is rejected here, so
+    the kernel never reads or writes past them.  ``stream`` is a
+    cudaStream_t handle; by default torch's current stream, the one the
+    caller's tensors were filled on.  Returns the number of ends found, which
     may exceed ``cap`` (then only ``cap`` were written)."""
+    import torch
     lib = load()
     pats = [_u8(p) for p in patterns]
     m = len(pats)
@@ -442,7 +460,13 @@ def oasm_scan_ends_noalloc(patterns, ks, d_text, d_out, cap: int, n: int | None 
     lens = (ctypes.c_uint32 * m)(*[p.size for p in pats])
     kk = (ctypes.c_uint32 * m)(*[int(k) for k in ks])
     if n is None:
-        n = d_text.numel()
+        n = d_text.numel() * d_text.element_size()
+    if n < 0 or cap < 0:
+        raise OasmError(OASM_EINVAL, "n and cap must be >= 0")
+    _check_device_buffer(d_text, n, "d_text")
+    _check_device_buffer(d_out, cap * END_DTYPE.itemsize, "d_out")
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
     found = ctypes.c_uint64(0)
     rc = lib.oasm_scan_ends_noalloc(ptrs, lens, kk, m, _dev_ptr(d_text) if n else None, n,
                                     _dev_ptr(d_out) if cap else None, cap, ctypes.byref(found),
