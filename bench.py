@@ -2,21 +2,27 @@
 """Benchmark of the OASM device path on GB300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload dictionary_dna|dictionary_dna_64m|plain_dna|plain_dna_1g|
-                     bytes_zipf|bytes_zipf_256m|many_texts|many_texts_256m|served|
-                     dictionary_dna_weighted] [--costs SUB,INS,DEL]
+                    [--workload bytes_zipf|dictionary_dna|dictionary_dna_64m|plain_dna|
+                     plain_dna_1g|bytes_zipf_256m|many_texts|many_texts_256m|served|
+                     dictionary_dna_weighted] [--costs SUB,INS,DEL] [--no-extras]
 
 One step = one pass of the whole path over the workload: open a stream, feed
 the text, end it and flush (stage, bit-parallel scan, anchored verification,
 ordering, filter, emit), all through the C ABI.  The default workload is the
-DNA dictionary scan: 1,024 DNA patterns (m ~ U[8,32], K = floor(m/10)) over a
-256 MiB text with 1,000 planted copies per pattern.
+largest single-GPU configuration, the batched dictionary of uneven byte
+patterns: 4,096 patterns (m log-uniform in [16, 128], K uniform in
+[1, min(8, m/4)]) over a 1 GiB Zipf(1.1) byte text with 500 planted copies
+per pattern.
 
 Printed: one JSON line with the metric (GCUPS: sum over patterns of m times
 text symbols, per second), device-resident throughput (`value`), end-to-end
 throughput through host buffers (`e2e`), the scan kernel's roofline against
 the integer issue peak, the CPU oracle on a bounded sample, and the SM
-clocks seen during the timed region.  With integer edit costs (--costs, or the
+clocks seen during the timed region.  The default run adds, as extra keys,
+the same measurements (fewer steps) for the DNA dictionary (1,024 patterns,
+256 MiB), the plain one-pattern kernel (m = 8, K = 2 over 1 GiB of DNA) and a
+compact served block (the native serving loop at three offered loads, p50 and
+p99 latency).  With integer edit costs (--costs, or the
 dictionary_dna_weighted workload: the DNA dictionary with substitution 1,
 insertion 2, deletion 2) the path is the weighted one: the wave-front dynamic
 program replaces the bit-parallel scan.  Under torchrun every rank runs its own
@@ -49,8 +55,10 @@ WEIGHTED_DEFAULT_COSTS = (1, 2, 2)
 # traffic scales with the text
 SCAN_DRAM_BYTES_PER_TEXT_BYTE = {"dictionary_dna": 72.6e6 / (64 << 20),
                                  "dictionary_dna_64m": 72.6e6 / (64 << 20)}
-SM_COUNT = 152
-SM_MAX_MHZ = 2070.0
+# integer lanes per SM that can issue one integer instruction per clock (four
+# sub-partitions of 32 lanes): the derived peak is SMs x 128 x SM clock
+INT_LANES_PER_SM = 128
+DEFAULT_WORKLOAD = "bytes_zipf"
 
 
 def parse():
@@ -59,13 +67,16 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="dictionary_dna")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-alt", action="store_true",
                     help="skip the extra measurement with the automatic piece filter")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the extra workloads of the default run (DNA dictionary, plain "
+                         "one-pattern kernel, served block)")
     ap.add_argument("--served-packets", type=int, default=200000)
     ap.add_argument("--served-engine", default="native", choices=["native", "python"],
                     help="serving loop: inside the library (oasm_replay) or in Python")
@@ -270,9 +281,8 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": desc, "l2": "oracle on host cores",
-                       "costs": list(args.costs) if args.costs else None,
-                       "output": args.output},
+            "config": run_config(args, wl, desc, int(os.environ.get("WORLD_SIZE", "1"))),
+            "runs_on": "the oracle on the host cores",
             "cpu_baseline": {"value": val, "unit": "GCUPS", "cores": n_pat, "kind": "oracle",
                              "sample": f"{n_pat} of {len(wl.patterns)} patterns x {n_sym} text symbols per step"},
             "e2e": {"value": val, "unit": "GCUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -297,11 +307,6 @@ def measured_hbm_gbs():
             return float(json.load(f)["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
-
-
-def B_peak(dev: int = 0):
-    from paper_1712_03560_gb300 import binding as B
-    return B.oasm_measure_int_peak(dev)
 
 
 def run_served(args):
@@ -351,24 +356,29 @@ def run_served(args):
                                                  "p99_ms", "max_ms", "steps", "mean_batch_bytes",
                                                  "step_ms_p50", "step_ms_p99", "step_ms_mean",
                                                  "step_ms_max", "gcups", "packets",
-                                                 "phase_ms_per_step")})
+                                                 "phase_ms_per_step", "reruns", "graph_builds",
+                                                 "buffer_grows", "slowest_step")})
         clk = clocks.stop()
         st_all = srv.stats()
     best = max(sweep, key=lambda x: x["achieved_gbps"])
     # roofline of the scan over the steps of the best load point (library events)
-    peak_ops, _ = B_peak(dev)
+    peaks = int_peaks(dev)
+    derived = derived_peak_tops(dev, clk)
     fm = filter_mask(base.patterns, base.ks, args.prefilter)
     words = sum((p.size + 31) // 32 for p, on in zip(base.patterns, fm) if not on) \
         * st_best["text_bytes"]
     scan_ms = st_best["scan_ms"]
     achieved_alg = words * OPS_PER_WORD_STEP / max(scan_ms * 1e-3, 1e-12) / 1e12
     achieved = st_best["word_steps"] * OPS_PER_WORD_STEP / max(scan_ms * 1e-3, 1e-12) / 1e12
-    derived_peak = SM_COUNT * 128 * SM_MAX_MHZ * 1e6 / 1e12
+    derived_peak = derived["tops"]
     roofline = {"bound": "alu", "achieved": achieved, "peak": derived_peak, "unit": "Tops/s",
                 "frac": achieved / derived_peak, "traffic": None,
+                "peak_source": (f"derived: {derived['sms']} SMs x {INT_LANES_PER_SM} integer "
+                                f"lanes x {derived['sm_mhz']:.0f} MHz"),
                 "units": "executed lane word-steps x 16 ops (a packed lane counts once)",
                 "achieved_algorithmic": achieved_alg, "frac_algorithmic": achieved_alg / derived_peak,
-                "peak_measured_mix": peak_ops / 1e12, "frac_of_measured_mix": achieved * 1e12 / peak_ops,
+                "measured_peaks_tops": peaks, "peak_measured_mix": peaks["scan_step"],
+                "frac_of_measured_mix": achieved / peaks["scan_step"],
                 "kernel": "scan_kernel (all classes of a step)",
                 "kernel_ms_per_launch": scan_ms / max(1, st_best["scan_launches"]),
                 "ops_per_word_step": OPS_PER_WORD_STEP,
@@ -412,29 +422,61 @@ def run_served(args):
     print(json.dumps(line), flush=True)
 
 
-def main():
-    args = parse()
-    if args.impl == "reference":
-        return run_reference(args)
-    if args.workload == "served":
-        return run_served(args)
-
+def sm_count(dev: int) -> int:
     import torch
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
-    else:
-        torch.cuda.set_device(0)
-    dev = torch.cuda.current_device()
+    return int(torch.cuda.get_device_properties(dev).multi_processor_count)
 
+
+def sm_max_mhz(dev: int, clk: dict | None = None) -> tuple:
+    """The GPU's maximum SM clock: from the samples of the timed region, else
+    one nvidia-smi query; (MHz, source)."""
+    if clk and clk.get("sm_max_mhz"):
+        return float(clk["sm_max_mhz"]), "nvidia-smi during the timed region"
+    try:
+        out = subprocess.run(["nvidia-smi", "--query-gpu=clocks.max.sm",
+                              "--format=csv,noheader,nounits", "-i", str(dev)],
+                             capture_output=True, text=True, timeout=20).stdout.strip()
+        return float(out.splitlines()[0]), "nvidia-smi"
+    except Exception:
+        return 2070.0, "the GB300's nominal maximum (no nvidia-smi)"
+
+
+def derived_peak_tops(dev: int, clk: dict | None = None) -> dict:
+    """Integer issue peak from unit counts and the clock: every SM issues one
+    32-lane integer instruction per clock in each of its four sub-partitions."""
+    sms = sm_count(dev)
+    mhz, src = sm_max_mhz(dev, clk)
+    return {"tops": sms * INT_LANES_PER_SM * mhz * 1e6 / 1e12, "sms": sms, "sm_mhz": mhz,
+            "clock_source": src}
+
+
+def int_peaks(dev: int) -> dict:
+    """Measured integer issue rates (T ops/s) of the three microbenchmark mixes."""
+    from paper_1712_03560_gb300 import binding as B
+    return {mix: B.oasm_measure_int_peak_mix(dev, mix)[0] / 1e12 for mix in B.INT_MIXES}
+
+
+def run_config(args, wl, desc, world: int) -> dict:
+    """The workload keys of the JSON line (the same for both arms)."""
+    return {"workload": desc, "text_bytes": int(wl.text_bytes),
+            "patterns": len(wl.patterns), "l2": "inputs larger than L2 (text > 129 MB)"
+            if wl.text_bytes > (129 << 20) else "input smaller than L2",
+            "parallelism": f"replicas x{world}",
+            "prefilter_piece": args.prefilter, "graphs": args.graphs,
+            "output": args.output,
+            "costs": None if args.costs is None else dict(zip(("sub", "ins", "del"), args.costs))}
+
+
+def measure_workload(args, name, dev, steps, warmup, *, rank=0, world=1, dist=None,
+                     with_e2e=True, with_cpu=True, with_alt=True):
+    """One workload through the C ABI: `steps` timed steps on device-resident
+    input (CUDA events on the library's stream), the scan's roofline, and
+    optionally the end-to-end run through host buffers, the oracle on a
+    bounded sample with a parity check, and the automatic piece filter."""
+    import torch
     from paper_1712_03560_gb300 import binding as B
 
-    wl, desc = make_workload(args.workload, rank, args.text_mib)
+    wl, desc = make_workload(name, rank, args.text_mib if name == args.workload else None)
     rules = None if args.output == "filtered" else {"output": args.output}
     ctx = B.oasm_create(wl.patterns, wl.ks, rules,
                         {"device": dev, "timing": 1, "max_streams": max(64, len(wl.texts)),
@@ -456,7 +498,7 @@ def main():
             tuned = {"buckets": B.oasm_get_tuning(ctx), "source": how}
         else:
             tuned = json.loads(B.oasm_autotune(ctx, sample))
-        print(json.dumps({"autotune": tuned}), file=sys.stderr, flush=True)
+        print(json.dumps({"autotune": name, **tuned}), file=sys.stderr, flush=True)
         for bk in tuned["buckets"]:
             bk.pop("trials", None)
 
@@ -495,7 +537,8 @@ def main():
                 B.oasm_feed(ctx, s, t)
         return run_one(submit)
 
-    for _ in range(args.warmup):
+    kept = 0
+    for _ in range(warmup):
         kept = step_device()
 
     # ---- timed region: device-resident inputs
@@ -512,7 +555,7 @@ def main():
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         kept = step_device()
     ev1.record(stream)
     ev1.synchronize()
@@ -522,58 +565,70 @@ def main():
         dist.barrier()
     ms = ev0.elapsed_time(ev1)
     st = B.oasm_get_stats(ctx)
-    host_step_ms = {k: v / args.steps for k, v in host_ms.items()}
+    host_step_ms = {k: v / steps for k, v in host_ms.items()}
     if dist:
         t = torch.tensor([ms], device=f"cuda:{dev}")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     cells_step = wl.cells
-    value = cells_step * args.steps * world / (ms * 1e-3) / 1e9
-    text_gbps = wl.text_bytes * args.steps * world / (ms * 1e-3) / 1e9
+    value = cells_step * steps * world / (ms * 1e-3) / 1e9
+    text_gbps = wl.text_bytes * steps * world / (ms * 1e-3) / 1e9
 
     # ---- roofline of the dominant kernel (the forward scan), measured live
-    peak_ops, _ = B.oasm_measure_int_peak(dev)
+    peaks = int_peaks(dev)
+    derived = derived_peak_tops(dev, clk)
     scan_ms_launch = st["scan_ms"] / max(1, st["scan_launches"])
     fm = filter_mask(wl.patterns, wl.ks, args.prefilter)
-    words = sum((p.size + 31) // 32 for p, on in zip(wl.patterns, fm) if not on) * wl.text_bytes
-    launches_step = max(1, st["scan_launches"] // max(1, args.steps))
+    launches_step = max(1, st["scan_launches"] // max(1, steps))
+    # algorithmic words: what the scan's algorithm must run per text symbol --
+    # every word of a one-pass pattern, word 0 of a cut-off class pattern
+    # (the words it runs beyond that near matches are in the executed count)
+    cut_classes = {b["words"] for b in B.oasm_get_tuning(ctx) if b["algo"] == 9}
+    words = sum((1 if (p.size + 31) // 32 in cut_classes else (p.size + 31) // 32)
+                for p, on in zip(wl.patterns, fm) if not on) * wl.text_bytes
     alg_ops_launch = words * OPS_PER_WORD_STEP / launches_step
     achieved_alg = alg_ops_launch / (scan_ms_launch * 1e-3) / 1e12
     # executed work: lane word-steps the scan ran (oasm_stats.word_steps)
-    exec_ops_launch = st["word_steps"] / max(1, args.steps) * OPS_PER_WORD_STEP / launches_step
+    exec_ops_launch = st["word_steps"] / max(1, steps) * OPS_PER_WORD_STEP / launches_step
     achieved = exec_ops_launch / (scan_ms_launch * 1e-3) / 1e12
-    derived_peak = SM_COUNT * 128 * SM_MAX_MHZ * 1e6 / 1e12
-    units = "executed lane word-steps x 16 ops (a packed lane counts once)"
+    units = ("executed lane word-steps x 16 ops (a packed lane counts once; a cut-off "
+             "class counts word 0 of every step plus the words its full form ran)")
     kname, opu = "scan_kernel (all classes of a step)", OPS_PER_WORD_STEP
     if args.costs is not None:
         # weighted path: a unit is one cell of the dynamic program; executed
         # cells count every row of a pattern's 32 W-row column
         cells_alg = sum(p.size for p in wl.patterns) * wl.text_bytes
         achieved_alg = cells_alg * OPS_PER_DP_CELL / launches_step / (scan_ms_launch * 1e-3) / 1e12
-        achieved = st["word_steps"] / max(1, args.steps) * OPS_PER_DP_CELL / launches_step \
+        achieved = st["word_steps"] / max(1, steps) * OPS_PER_DP_CELL / launches_step \
             / (scan_ms_launch * 1e-3) / 1e12
         units = "executed dynamic-program cells (32 W rows per pattern) x 7 ops"
         kname, opu = "wscan_kernel (weighted wave-front, all classes of a step)", OPS_PER_DP_CELL
-    tpb = None if args.costs is not None else SCAN_DRAM_BYTES_PER_TEXT_BYTE.get(args.workload)
-    traffic = tpb * wl.text_bytes if tpb else None
+    tpb = None if args.costs is not None else SCAN_DRAM_BYTES_PER_TEXT_BYTE.get(name)
+    traffic = tpb * wl.text_bytes / launches_step if tpb else None
     hbm_peak = measured_hbm_gbs()
-    roofline = {"bound": "alu", "achieved": achieved, "peak": derived_peak, "unit": "Tops/s",
-                "frac": achieved / derived_peak,
+    peak = derived["tops"]
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+                "frac": achieved / peak,
+                "peak_source": (f"derived: {derived['sms']} SMs x {INT_LANES_PER_SM} integer "
+                                f"lanes x {derived['sm_mhz']:.0f} MHz ({derived['clock_source']})"),
                 "units": units,
-                "achieved_algorithmic": achieved_alg, "frac_algorithmic": achieved_alg / derived_peak,
+                "achieved_algorithmic": achieved_alg, "frac_algorithmic": achieved_alg / peak,
                 "traffic": traffic,
                 "hbm": None if traffic is None else {
                     "achieved_gbs": traffic / (scan_ms_launch * 1e-3) / 1e9, "peak_gbs": hbm_peak[0],
                     "frac": traffic / (scan_ms_launch * 1e-3) / 1e9 / hbm_peak[0],
                     "peak_source": hbm_peak[1]},
-                "peak_measured_mix": peak_ops / 1e12,
-                "frac_of_measured_mix": achieved * 1e12 / peak_ops,
+                "measured_peaks_tops": peaks,
+                "peak_measured_mix": peaks["scan_step"],
+                "frac_of_measured_mix": achieved / peaks["scan_step"],
                 "kernel": kname, "kernel_ms_per_launch": scan_ms_launch,
+                "launches_per_step": launches_step,
                 "ops_per_word_step": opu}
 
-    # ---- end to end through host buffers
+    # ---- end to end through host buffers (pinned-free: oasm_feed copies the
+    # caller's pageable bytes into the library's pinned staging)
     e2e = None
-    if not args.no_e2e:
+    if with_e2e:
         host = [np.ascontiguousarray(t) for t in wl.texts]
         step_host(host)
         torch.cuda.synchronize()
@@ -581,7 +636,7 @@ def main():
             dist.barrier()
         t0 = time.perf_counter()
         kept_h = 0
-        for _ in range(args.steps):
+        for _ in range(steps):
             kept_h = step_host(host)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
@@ -589,44 +644,60 @@ def main():
             t = torch.tensor([dt], device=f"cuda:{dev}")
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             dt = float(t.item())
-        e2e = {"value": cells_step * args.steps * world / dt / 1e9, "unit": "GCUPS",
+        e2e = {"value": cells_step * steps * world / dt / 1e9, "unit": "GCUPS",
                "h2d_bytes_per_step": int(wl.text_bytes), "d2h_bytes_per_step": int(kept_h * 32 + 48),
-               "ms_per_step": dt / args.steps * 1e3}
+               "ms_per_step": dt / steps * 1e3, "steps": steps}
 
+    res = {"wl": wl, "desc": desc, "value": value, "ms_per_step": ms / steps,
+           "text_gbps": text_gbps, "occurrences_per_step": int(kept), "clocks": clk,
+           "kernel_ms": {k: st[k] / steps for k in ("copy_ms", "scan_ms", "prefilter_ms",
+                                                     "verify_ms", "order_ms", "filter_ms",
+                                                     "step_ms")},
+           "prefilter": None if not args.prefilter else {
+               "piece": args.prefilter if args.prefilter >= 4 else "auto",
+               "patterns": int(sum(fm)),
+               "candidates_per_step": st["prefilter_candidates"] / steps,
+               "text_gbs": None if st["prefilter_ms"] <= 0 else
+               wl.text_bytes * steps / (st["prefilter_ms"] * 1e-3) / 1e9},
+           "host_ms_per_step": host_step_ms,
+           "library_host_ms_per_step": {k: st[k] / steps for k in
+                                        ("host_plan_ms", "host_launch_ms", "host_wait_ms",
+                                         "host_post_ms")},
+           "candidates_per_step": st["candidates"] / steps,
+           "hits_per_step": st["hits"] / steps,
+           "gpu_launches": int(st["launches"]),
+           "graph_builds": {"warmup": builds_warmup, "timed": int(st["graph_builds"])},
+           "reruns": int(st["reruns"]), "buffer_grows_timed": int(st["buffer_grows"]),
+           "roofline": roofline, "e2e": e2e, "autotune": tuned,
+           "cpu_baseline": None, "parity_sample": None, "with_piece_filter": None}
     if rank != 0:
         B.oasm_destroy(ctx)
-        if dist:
-            dist.destroy_process_group()
-        return
+        return res
 
-    cpu = None
-    parity = None
-    if not args.no_cpu and world == 1:
+    want = idx = text = None
+    if with_cpu and world == 1:
         cpu, (idx, text, ores) = cpu_baseline(wl, args.cpu_seconds, args.costs, args.output)
+        res["cpu_baseline"] = cpu
         # the sampled patterns' GPU output must equal the oracle's on that sample
-        if True:
-            from paper_1712_03560_gb300 import binding as B2
-            sub_pats = [wl.patterns[i] for i in idx]
-            sub_ks = [int(wl.ks[i]) for i in idx]
-            with B2.Matcher(sub_pats, sub_ks, rules=rules, costs=args.costs,
-                            prefilter_piece=args.prefilter) as mt:
-                g = mt.search(torch.from_numpy(np.ascontiguousarray(text)).to(f"cuda:{dev}"),
-                              device=True)
-            got = sorted((int(r["pattern_id"]), int(r["decided_at"]), int(r["k"]),
-                          int(r["start"]), int(r["len"])) for r in g)
-            want = sorted((int(r["pattern_id"]), int(r["decided_at"]), int(r["k"]),
-                           int(r["start"]), int(r["len"])) for r in ores)
-            parity = {"patterns": len(idx), "text_symbols": int(text.size),
-                      "occurrences": len(want), "equal": got == want}
+        sub_pats = [wl.patterns[i] for i in idx]
+        sub_ks = [int(wl.ks[i]) for i in idx]
+        with B.Matcher(sub_pats, sub_ks, rules=rules, costs=args.costs,
+                       prefilter_piece=args.prefilter) as mt:
+            g = mt.search(torch.from_numpy(np.ascontiguousarray(text)).to(f"cuda:{dev}"),
+                          device=True)
+        got = sorted((int(r["pattern_id"]), int(r["decided_at"]), int(r["k"]),
+                      int(r["start"]), int(r["len"])) for r in g)
+        want = sorted((int(r["pattern_id"]), int(r["decided_at"]), int(r["k"]),
+                       int(r["start"]), int(r["len"])) for r in ores)
+        res["parity_sample"] = {"patterns": len(idx), "text_symbols": int(text.size),
+                                "occurrences": len(want), "equal": got == want}
+    B.oasm_destroy(ctx)
 
     # ---- the same workload with the automatic piece filter (prefilter_piece = 1):
     # patterns whose pieces rarely match go to the exact filter, the rest stay
     # on the scan; device-resident inputs, timed like the main value
-    alt = None
-    if args.prefilter == 0 and not args.no_alt and world == 1 and args.costs is None and \
-            args.output == "filtered":
-        B.oasm_destroy(ctx)
-        ctx = None
+    if with_alt and args.prefilter == 0 and not args.no_alt and world == 1 and \
+            args.costs is None and args.output == "filtered":
         ctx2 = B.oasm_create(wl.patterns, wl.ks, None,
                              {"device": dev, "timing": 1, "max_streams": max(64, len(wl.texts)),
                               "prefilter_piece": 1, "graphs": args.graphs})
@@ -645,14 +716,14 @@ def main():
                 B.oasm_step(ctx2)
                 last[0] = B.oasm_drain(ctx2)
                 B.oasm_close_streams(ctx2, sids)
-            for _ in range(args.warmup):
+            for _ in range(warmup):
                 step2()
             torch.cuda.synchronize()
             B.oasm_reset_stats(ctx2)
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream2)
-            for _ in range(args.steps):
+            for _ in range(steps):
                 step2()
             e1.record(stream2)
             e1.synchronize()
@@ -660,77 +731,144 @@ def main():
             st2 = B.oasm_get_stats(ctx2)
             fm2 = filter_mask(wl.patterns, wl.ks, 1)
             par2 = None
-            if parity is not None and len(wl.texts) == 1:
+            if want is not None and len(wl.texts) == 1:
                 # the sampled patterns' rows of the full output against the oracle
                 sel = set(int(i) for i in idx)
                 full = text.size == wl.texts[0].size
                 lim = {i: text.size - wl.patterns[i].size - int(wl.ks[i]) for i in sel}
-                out2 = last[0]
                 pos = {int(i): j for j, i in enumerate(idx)}
                 got2 = sorted((pos[int(r["pattern_id"])], int(r["decided_at"]), int(r["k"]),
-                               int(r["start"]), int(r["len"])) for r in out2
+                               int(r["start"]), int(r["len"])) for r in last[0]
                               if int(r["pattern_id"]) in sel and
                               (full or int(r["decided_at"]) <= lim[int(r["pattern_id"])]))
                 want2 = sorted(w for w in want if full or w[1] <= lim[int(idx[w[0]])])
                 par2 = {"patterns": len(idx), "occurrences": len(want2), "equal": got2 == want2}
-            alt = {"path": "automatic piece filter + scan (prefilter_piece = 1)",
-                   "value": cells_step * args.steps / (ms2 * 1e-3) / 1e9, "unit": "GCUPS",
-                   "ms_per_step": ms2 / args.steps,
-                   "patterns_on_filter": int(sum(fm2)),
-                   "kernel_ms": {k: st2[k] / args.steps for k in ("scan_ms", "prefilter_ms",
-                                                                  "verify_ms", "order_ms",
-                                                                  "filter_ms", "step_ms")},
-                   "parity_sample": par2}
+            res["with_piece_filter"] = {
+                "path": "automatic piece filter + scan (prefilter_piece = 1)",
+                "value": cells_step * steps / (ms2 * 1e-3) / 1e9, "unit": "GCUPS",
+                "ms_per_step": ms2 / steps,
+                "patterns_on_filter": int(sum(fm2)),
+                "kernel_ms": {k: st2[k] / steps for k in ("scan_ms", "prefilter_ms", "verify_ms",
+                                                         "order_ms", "filter_ms", "step_ms")},
+                "parity_sample": par2}
         finally:
             B.oasm_destroy(ctx2)
+    del dtexts
+    torch.cuda.empty_cache()
+    return res
 
+
+def served_block(args, dev: int) -> dict:
+    """Compact served measurement: the native serving loop (continuous
+    batching, split steps, automatic piece filter, steps of at most 32 MiB)
+    over 4,096 byte streams and 2,000 signatures, at an offered load below the
+    knee, near it and beyond saturation; latency = packet arrival to the end
+    of the step that matched it."""
+    from paper_1712_03560_gb300 import serve
+    from paper_1712_03560_gb300 import workloads as W
+    base = W.served(seed=5, n_packets=200, gbps=1.0)
+    loads = ((1.0, 50_000), (25.0, 100_000), (400.0, 400_000))
+    out = []
+    with serve.Server(base.patterns, base.ks, max_streams=4096, timing=True, device=dev,
+                      prefilter_piece=1, max_batch_bytes=32 << 20) as srv:
+        # warm-up: full 32 MiB steps grow every step buffer to its final size,
+        # then a paced pass at a low load
+        srv.replay(W.served(seed=99, n_packets=100_000, gbps=10.0), realtime=False,
+                   engine="native")
+        srv.replay(W.served(seed=98, n_packets=20000, gbps=1.0), realtime=True, engine="native")
+        for g, n_pkt in loads:
+            tr = W.served(seed=int(5 + 10 * g), n_packets=n_pkt, gbps=g)
+            r = srv.replay(tr, realtime=True, engine="native")
+            out.append({k: r.get(k) for k in ("offered_gbps", "achieved_gbps", "p50_ms", "p99_ms",
+                                               "max_ms", "steps", "packets", "step_ms_mean",
+                                               "reruns", "graph_builds", "buffer_grows",
+                                               "slowest_step")})
+    return {"workload": "4096 byte streams, packets U[64,1500] B, Poisson arrivals, 2000 "
+                        "signatures m~U[8,64] K=2; native loop, split steps, automatic piece "
+                        "filter, steps <= 32 MiB",
+            "loads": out, "sustained_gbps": max(x["achieved_gbps"] for x in out)}
+
+
+def extra_entry(m: dict) -> dict:
+    """The short form of a measurement for an extra key of the line."""
+    rf = m["roofline"]
+    return {"workload": m["desc"], "value": m["value"], "unit": "GCUPS",
+            "ms_per_step": m["ms_per_step"], "text_gbps": m["text_gbps"],
+            "e2e": None if m["e2e"] is None else {k: m["e2e"][k] for k in ("value", "ms_per_step",
+                                                                         "steps")},
+            "frac": rf["frac"], "frac_of_measured_mix": rf["frac_of_measured_mix"],
+            "occurrences_per_step": m["occurrences_per_step"],
+            "kernel_ms": m["kernel_ms"],
+            "scan_share_of_step": m["kernel_ms"]["scan_ms"] / max(m["ms_per_step"], 1e-9),
+            "host_ms_per_step": m["host_ms_per_step"]}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    if args.workload == "served":
+        return run_served(args)
+
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+
+    m = measure_workload(args, args.workload, dev, args.steps, args.warmup, rank=rank,
+                         world=world, dist=dist)
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
     line = {
-        "metric": "GCUPS", "value": value, "unit": "GCUPS", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "metric": "GCUPS", "value": m["value"], "unit": "GCUPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": m["ms_per_step"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic",
-        "config": {"workload": desc, "text_bytes": int(wl.text_bytes),
-                   "patterns": len(wl.patterns), "l2": "inputs larger than L2 (text > 129 MB)"
-                   if wl.text_bytes > (129 << 20) else "input smaller than L2",
-                   "parallelism": f"replicas x{world}", "autotune": tuned,
-                   "prefilter_piece": args.prefilter, "graphs": args.graphs,
-                   "output": args.output,
-                   "costs": None if args.costs is None else
-                   dict(zip(("sub", "ins", "del"), args.costs))},
-        "text_gbps": text_gbps,
-        "occurrences_per_step": int(kept),
-        "kernel_ms": {k: st[k] / args.steps for k in ("copy_ms", "scan_ms", "prefilter_ms",
-                                                        "verify_ms", "order_ms", "filter_ms",
-                                                        "step_ms")},
-        "prefilter": None if not args.prefilter else {
-            "piece": args.prefilter if args.prefilter >= 4 else "auto",
-            "patterns": int(sum(fm)),
-            "candidates_per_step": st["prefilter_candidates"] / args.steps,
-            # one pass over the text: bytes read per second against the HBM copy peak
-            "text_gbs": None if st["prefilter_ms"] <= 0 else
-            wl.text_bytes * args.steps / (st["prefilter_ms"] * 1e-3) / 1e9,
-            "hbm_frac": None if st["prefilter_ms"] <= 0 else
-            wl.text_bytes * args.steps / (st["prefilter_ms"] * 1e-3) / 1e9 / measured_hbm_gbs()[0]},
-        "host_ms_per_step": host_step_ms,
-        "library_host_ms_per_step": {k: st[k] / args.steps for k in
-                                     ("host_plan_ms", "host_launch_ms", "host_wait_ms",
-                                      "host_post_ms")},
-        "candidates_per_step": st["candidates"] / args.steps,
-        "hits_per_step": st["hits"] / args.steps,
-        "gpu_launches": int(st["launches"]),
+        "config": run_config(args, m["wl"], m["desc"], world),
+        "text_gbps": m["text_gbps"],
+        "occurrences_per_step": m["occurrences_per_step"],
+        "kernel_ms": m["kernel_ms"],
+        "prefilter": m["prefilter"],
+        "host_ms_per_step": m["host_ms_per_step"],
+        "library_host_ms_per_step": m["library_host_ms_per_step"],
+        "candidates_per_step": m["candidates_per_step"],
+        "hits_per_step": m["hits_per_step"],
+        "gpu_launches": m["gpu_launches"],
         # executable graphs instantiated: during warm-up, and during the timed
         # steps (0 there: each timed step updated the cached graph in place)
-        "graph_builds": {"warmup": builds_warmup, "timed": int(st["graph_builds"])},
-        "reruns": int(st["reruns"]),
-        "roofline": roofline,
-        "e2e": e2e,
-        "cpu_baseline": cpu,
-        "parity_sample": parity,
-        "with_piece_filter": alt,
-        "clocks": clk,
+        "graph_builds": m["graph_builds"],
+        "reruns": m["reruns"],
+        "roofline": m["roofline"],
+        "e2e": m["e2e"],
+        "cpu_baseline": m["cpu_baseline"],
+        "parity_sample": m["parity_sample"],
+        "with_piece_filter": m["with_piece_filter"],
+        "autotune": m["autotune"],
+        "clocks": m["clocks"],
     }
+    del m
+    if world == 1 and not args.no_extras and args.workload == DEFAULT_WORKLOAD and \
+            args.costs is None and args.output == "filtered" and args.prefilter == 0:
+        # the other dictionary and the plain one-pattern kernel, fewer steps;
+        # the served loop at three loads
+        ks = min(args.steps, 10)
+        for key, name in (("dictionary_dna", "dictionary_dna"), ("plain_kernel", "plain_dna_1g")):
+            x = measure_workload(args, name, dev, ks, 3, with_cpu=False, with_alt=False)
+            line[key] = extra_entry(x)
+            line[key]["steps"], line[key]["warmup"] = ks, 3
+            del x
+        line["served"] = served_block(args, dev)
     print(json.dumps(line), flush=True)
-    B.oasm_destroy(ctx)
     if dist:
         dist.destroy_process_group()
 

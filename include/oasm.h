@@ -158,6 +158,9 @@ typedef struct {
     double host_wait_ms;     /* host time waiting for the device to finish a step */
     double host_post_ms;     /* host time after a step: counters, records into the
                                 stream queues, stream bookkeeping */
+    uint64_t buffer_grows;   /* device or pinned host buffers reallocated larger
+                                (each a cudaMalloc or cudaHostAlloc on the call's
+                                path, and a free of the old buffer) */
 } oasm_stats;
 
 /* Fills *cfg / *rules with the defaults described above. */
@@ -336,6 +339,17 @@ typedef struct {
     double wall_s;               /* first arrival window to last drain */
     double step_s_sum;           /* feed + step + drain, summed over steps */
     double step_s_max;
+    /* what the library did during the replay (oasm_stats differences), and
+       during its slowest step (launch to results queued): steps re-run after
+       a buffer grew, step graphs instantiated, buffers reallocated */
+    uint64_t reruns;
+    uint64_t graph_builds;
+    uint64_t buffer_grows;
+    uint64_t slowest_step;       /* index of the step that took step_s_max */
+    uint64_t slowest_bytes;      /* its payload bytes */
+    uint64_t slowest_reruns;
+    uint64_t slowest_graph_builds;
+    uint64_t slowest_buffer_grows;
 } oasm_replay_stats;
 
 /* Online matching of many concurrent streams (the paper's online setting,
@@ -402,12 +416,20 @@ int oasm_autotune(oasm_ctx *ctx, const uint8_t *dsample, size_t n, char *report,
                   size_t report_cap);
 
 /* ---- measurement utility (no counterpart in the paper) ------------------
- * Measures the integer issue rate of `device` on a synthetic kernel whose
- * instruction mix is that of one 32-bit column step of the forward scan
- * (eight 3-input logic ops, two adds, four shifts, one byte permute; no
- * memory traffic).  *ops_per_s receives integer operations per second over
- * the whole GPU (best of five timed launches), *ms (may be NULL) the time
- * of that launch.  Used as the roofline peak of the scan. */
+ * Integer issue rate of `device` on a synthetic kernel (no memory traffic):
+ * each thread runs eight independent chains of 15 integer operations per
+ * step.  `mix` selects the operations:
+ *   0  ALU pipe only: 3-input logic ops, adds, funnel shifts, byte permutes
+ *   1  integer multiply-adds with register operands (the FMA pipe)
+ *   2  one 32-bit column step of the forward scan in the scan's own PTX
+ *      forms (7 logic ops, 1 add, 2 shifts as multiplies, 3 high-word
+ *      multiply-adds, 1 address multiply-add, 1 byte permute), which the
+ *      compiler spreads over both pipes as it does in the scan
+ * *ops_per_s receives integer operations per second over the whole GPU (best
+ * of five timed launches), *ms (may be NULL) the time of that launch.
+ * OASM_EINVAL for another mix or a NULL ops_per_s.
+ * oasm_measure_int_peak is mix 2: the measured roofline peak of the scan. */
+int oasm_measure_int_peak_mix(int device, int mix, double *ops_per_s, double *ms);
 int oasm_measure_int_peak(int device, double *ops_per_s, double *ms);
 
 /* Launch settings of one scan class, as oasm_autotune picks them (no paper

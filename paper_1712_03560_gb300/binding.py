@@ -78,7 +78,8 @@ class oasm_stats(ctypes.Structure):
                [("scan_launches", ctypes.c_uint64), ("graph_builds", ctypes.c_uint64),
                 ("prefilter_ms", ctypes.c_double), ("prefilter_candidates", ctypes.c_uint64),
                 ("host_plan_ms", ctypes.c_double), ("host_launch_ms", ctypes.c_double),
-                ("host_wait_ms", ctypes.c_double), ("host_post_ms", ctypes.c_double)]
+                ("host_wait_ms", ctypes.c_double), ("host_post_ms", ctypes.c_double),
+                ("buffer_grows", ctypes.c_uint64)]
 
 
 class oasm_costs(ctypes.Structure):
@@ -101,7 +102,10 @@ class oasm_trace(ctypes.Structure):
 class oasm_replay_stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in ("steps", "packets", "bytes", "kept", "n_out",
                                                 "streams_admitted", "max_waiting_streams")] + \
-               [(n, ctypes.c_double) for n in ("wall_s", "step_s_sum", "step_s_max")]
+               [(n, ctypes.c_double) for n in ("wall_s", "step_s_sum", "step_s_max")] + \
+               [(n, ctypes.c_uint64) for n in ("reruns", "graph_builds", "buffer_grows",
+                                                "slowest_step", "slowest_bytes", "slowest_reruns",
+                                                "slowest_graph_builds", "slowest_buffer_grows")]
 
 
 EXPORTS = ["oasm_config_default", "oasm_rules_default", "oasm_create", "oasm_create_weighted",
@@ -110,7 +114,8 @@ EXPORTS = ["oasm_config_default", "oasm_rules_default", "oasm_create", "oasm_cre
            "oasm_close_streams", "oasm_feed", "oasm_feed_many", "oasm_feed_device",
            "oasm_end_stream", "oasm_step", "oasm_flush", "oasm_drain", "oasm_ready", "oasm_get_stats", "oasm_reset_stats",
            "oasm_cuda_stream", "oasm_last_error", "oasm_strerror", "oasm_autotune",
-           "oasm_measure_int_peak", "oasm_scan_ends_noalloc", "oasm_stream_state_size",
+           "oasm_measure_int_peak", "oasm_measure_int_peak_mix", "oasm_scan_ends_noalloc",
+           "oasm_stream_state_size",
            "oasm_save_stream", "oasm_restore_stream", "oasm_replay", "oasm_register_host",
            "oasm_unregister_host", "oasm_step_begin", "oasm_step_end",
            "oasm_piece_filter_choice", "oasm_selftest_wait", "oasm_get_tuning",
@@ -168,6 +173,8 @@ def load(path: str | None = None):
             "oasm_set_tuning": ([vp, ctypes.POINTER(oasm_tuning), u32], i32),
             "oasm_measure_int_peak": ([i32, ctypes.POINTER(ctypes.c_double),
                                        ctypes.POINTER(ctypes.c_double)], i32),
+            "oasm_measure_int_peak_mix": ([i32, i32, ctypes.POINTER(ctypes.c_double),
+                                           ctypes.POINTER(ctypes.c_double)], i32),
             "oasm_stream_state_size": ([vp, ctypes.POINTER(ctypes.c_size_t)], i32),
             "oasm_save_stream": ([vp, u32, vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)], i32),
             "oasm_restore_stream": ([vp, u32, vp, ctypes.c_size_t], i32),
@@ -395,6 +402,19 @@ def oasm_measure_int_peak(device: int = 0):
     """(integer ops per second, ms of the best launch) of the scan's op mix."""
     ops, ms = ctypes.c_double(), ctypes.c_double()
     _check(load().oasm_measure_int_peak(device, ctypes.byref(ops), ctypes.byref(ms)))
+    return ops.value, ms.value
+
+
+INT_MIXES = {"alu": 0, "multiply_add": 1, "scan_step": 2}
+
+
+def oasm_measure_int_peak_mix(device: int = 0, mix: str = "scan_step"):
+    """(integer ops per second, ms of the best launch) of one mix of
+    INT_MIXES: the ALU pipe alone, integer multiply-adds alone, or the scan's
+    column step."""
+    ops, ms = ctypes.c_double(), ctypes.c_double()
+    _check(load().oasm_measure_int_peak_mix(device, INT_MIXES[mix], ctypes.byref(ops),
+                                            ctypes.byref(ms)))
     return ops.value, ms.value
 
 

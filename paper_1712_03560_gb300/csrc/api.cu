@@ -39,6 +39,7 @@ int ensure_host(oasm_ctx* ctx, uint8_t** p, size_t* cap, size_t n, size_t keep) 
   size_t want = std::max<size_t>(n, *cap + *cap / 2);
   want = std::max<size_t>(want, 1 << 16);
   uint8_t* q = nullptr;
+  ctx->st.buffer_grows += 1;
   cudaError_t e = cudaHostAlloc(&q, want, cudaHostAllocDefault);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -105,7 +106,8 @@ void free_ctx(oasm_ctx* c) {
   if (c->h_upload) cudaFreeHost(c->h_upload);
   if (c->h_out) cudaFreeHost(c->h_out);
   for (auto& e : c->ev) if (e) cudaEventDestroy(e);
-  if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+  for (auto& g : c->graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
   if (c->done) cudaEventDestroy(c->done);
   if (c->staged) cudaEventDestroy(c->staged);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
@@ -252,6 +254,8 @@ int oasm_create_weighted(const uint8_t* const* pat, const uint32_t* len, const u
     return bail(OASM_ECUDA);
   }
   cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device);
+  if (ctx->num_sms < 1) ctx->num_sms = 1;
+  ctx->sort_blocks = 2 * ctx->num_sms;
   {
     int max_smem = 0;
     cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
@@ -322,7 +326,7 @@ int oasm_create_weighted(const uint8_t* const* pat, const uint32_t* len, const u
   for (uint32_t i = 0; i < S; ++i) ctx->free_slots.push(i);
   if (cudaMalloc(&ctx->d_ctr, sizeof(StepCounters)) != cudaSuccess ||
       cudaHostAlloc(&ctx->h_ctr, sizeof(StepCounters), cudaHostAllocDefault) != cudaSuccess ||
-      cudaMalloc(&ctx->d_hist, size_t(256) * kSortBlocks * 4) != cudaSuccess) {
+      cudaMalloc(&ctx->d_hist, size_t(256) * ctx->sort_blocks * 4) != cudaSuccess) {
     cudaGetLastError();
     fail(ctx, OASM_ENOMEM, "step counters");
     return bail(OASM_ENOMEM);

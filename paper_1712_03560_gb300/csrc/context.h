@@ -38,7 +38,6 @@ struct NvtxRange {
 constexpr size_t kFrontPad = 1024;   // arena bytes before the first work item
 constexpr size_t kEndPad = 2048;     // arena bytes after the last one
 constexpr size_t kChunk = 1 << 20;   // largest gather copy per block
-constexpr int kSortBlocks = 2 * 152;
 
 struct Piece {
   bool dev;
@@ -353,7 +352,20 @@ struct oasm_ctx {
   cudaEvent_t ev[9] = {};  // 0-5 step phases, 6-7 autotune, 8 piece filter start
   cudaEvent_t done = nullptr;
   cudaEvent_t staged = nullptr;  // host staging copies of the step in flight done
-  cudaGraphExec_t graph_exec = nullptr;  // the last captured step, updated in place
+  // executable step graphs, one per step topology (which kernels a step
+  // launches: its scan classes, the piece filter, the sort passes the key
+  // width needs), each updated in place while its topology repeats; the least
+  // recently used one is dropped when a new topology needs a slot
+  struct GraphSlot {
+    uint64_t topo = 0;
+    uint64_t used = 0;
+    cudaGraphExec_t exec = nullptr;
+  };
+  static constexpr size_t kGraphSlots = 8;
+  std::vector<GraphSlot> graphs;
+  uint64_t graph_clock = 0;
+  uint64_t step_topo = 0;    // topology of the step being enqueued
+  int sort_blocks = 2 * 152; // radix-sort blocks: two per SM
   bool capturing = false;
 
   oasm_stats st{};
@@ -407,6 +419,7 @@ int ensure(oasm_ctx* ctx, DevArray<T>& a, size_t n, const char* what) {
   if (a.p) cudaFree(a.p);
   a.p = nullptr;
   a.cap = 0;
+  ctx->st.buffer_grows += 1;
   cudaError_t e = cudaMalloc(&a.p, want * sizeof(T));
   if (e != cudaSuccess) {
     cudaGetLastError();

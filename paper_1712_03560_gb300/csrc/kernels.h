@@ -118,7 +118,7 @@ cudaError_t launch_sort(const SortArgs& a, unsigned long long** keys_out, uint32
 // dst[i] = src[idx[i]] for i < min(*count, cap)
 cudaError_t launch_permute(const DevHit* src, const uint32_t* idx, DevHit* dst,
                            const unsigned long long* count, unsigned long long cap,
-                           cudaStream_t s);
+                           int num_sms, cudaStream_t s);
 cudaError_t launch_filter(const StepParams& p, const unsigned long long* sorted, cudaStream_t s);
 cudaError_t launch_finalize(const StepParams& p, cudaStream_t s);
 cudaError_t launch_tails(const StepParams& p, cudaStream_t s);

@@ -173,6 +173,8 @@ struct StepParams {
   unsigned long long cap_pool;
   int32_t* pair_pool;            // [n_items * n_pat] pool index or -1
   StepCounters* ctr;
+  int32_t num_sms;               // the device's SM count (grid sizes of the step kernels)
+  int32_t pad_sms;
   // key packing
   int32_t start_bits;            // bits of start - base_pos
   int32_t key_bits;              // total significant bits of a key

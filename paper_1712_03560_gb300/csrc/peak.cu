@@ -1,15 +1,20 @@
-// peak.cu -- integer issue-rate microbenchmark used as the roofline
-// denominator of the forward scan (a logic/add/shift-bound kernel: no tensor
-// cores, negligible HBM traffic).
+// peak.cu -- integer issue-rate microbenchmarks used as the roofline
+// denominators of the forward scan (a logic/add/shift-bound kernel: no tensor
+// cores, negligible HBM traffic), and the bounded-wait self-test.
 //
-// Each thread runs 8 independent dependency chains; one chain step issues the
-// operation mix of one 32-bit bit-vector column step of the scan:
-//   8 x lop3.b32  (the 3-input logic of Xv, Xh, Ph, Mh, Pv, Mv and the Peq mask)
-//   2 x add.u32   (the carry-propagating add and the score update)
-//   4 x shf       (two funnel shifts of the horizontal deltas, score bit, mask)
-//   1 x prmt.b32  (symbol byte -> shared-memory address)
-// = 15 integer operations, no loads.  The result is a store of the chains'
-// xor so nothing is dead code.
+// Each thread runs 8 independent dependency chains of 15 integer operations
+// per chain step, no loads; the chains' xor is stored so nothing is dead code.
+// Three mixes:
+//   0 ALU pipe:   8 lop3, 2 add, 4 funnel shifts, 1 byte permute
+//   1 multiply:   15 multiply-adds with register operands (the FMA pipe's
+//                 integer forms)
+//   2 scan step:  the operations of one 32-bit column step of the scan in the
+//                 PTX forms the scan uses: 7 lop3, 1 add, 2 shifts written as
+//                 multiplies by 2, 3 high-word multiply-adds by 2 (score and
+//                 candidate count), 1 multiply-add (the Peq address), 1 byte
+//                 permute (the symbol).  ptxas spreads the constant-multiplier
+//                 forms over the ALU and FMA pipes as in the scan, so this mix
+//                 measures the issue rate the scan itself can reach.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -21,41 +26,84 @@ namespace {
 constexpr int kChains = 8;
 constexpr int kOpsPerStep = 15;
 
+template <int MIX>
+__device__ __forceinline__ void mix_step(uint32_t& x, uint32_t& y, uint32_t& t) {
+  if constexpr (MIX == 0) {
+    asm volatile(
+        "lop3.b32 %0, %0, %1, 0x5a5a5a5a, 0x96;\n\t"
+        "lop3.b32 %1, %1, %0, 0x0f0f0f0f, 0xe8;\n\t"
+        "add.u32 %0, %0, %1;\n\t"
+        "lop3.b32 %0, %0, %1, 0x33333333, 0x1e;\n\t"
+        "lop3.b32 %1, %1, %0, 0x55555555, 0x78;\n\t"
+        "shf.l.wrap.b32 %2, %0, %1, 1;\n\t"
+        "lop3.b32 %0, %0, %2, %1, 0xb4;\n\t"
+        "shf.l.wrap.b32 %1, %1, %0, 1;\n\t"
+        "lop3.b32 %1, %1, %2, %0, 0x6c;\n\t"
+        "add.u32 %0, %0, %2;\n\t"
+        "shf.r.wrap.b32 %2, %1, %0, 31;\n\t"
+        "lop3.b32 %0, %0, %2, %1, 0x2d;\n\t"
+        "prmt.b32 %2, %0, %1, 0x6504;\n\t"
+        "shf.l.wrap.b32 %1, %2, %1, 1;\n\t"
+        "lop3.b32 %0, %0, %1, %2, 0x96;"
+        : "+r"(x), "+r"(y), "+r"(t));
+  } else if constexpr (MIX == 1) {
+    asm volatile(
+        "mad.lo.u32 %0, %0, %1, %2;\n\t"
+        "mad.lo.u32 %1, %1, %2, %0;\n\t"
+        "mad.lo.u32 %2, %2, %0, %1;\n\t"
+        "mad.hi.u32 %0, %0, %1, %2;\n\t"
+        "mad.lo.u32 %1, %1, %2, %0;\n\t"
+        "mad.lo.u32 %2, %2, %0, %1;\n\t"
+        "mad.hi.u32 %0, %0, %1, %2;\n\t"
+        "mad.lo.u32 %1, %1, %2, %0;\n\t"
+        "mad.lo.u32 %2, %2, %0, %1;\n\t"
+        "mad.hi.u32 %0, %0, %1, %2;\n\t"
+        "mad.lo.u32 %1, %1, %2, %0;\n\t"
+        "mad.lo.u32 %2, %2, %0, %1;\n\t"
+        "mad.hi.u32 %0, %0, %1, %2;\n\t"
+        "mad.lo.u32 %1, %1, %2, %0;\n\t"
+        "mad.lo.u32 %2, %2, %0, %1;"
+        : "+r"(x), "+r"(y), "+r"(t));
+  } else {
+    // x: Pv, y: Mv, t: the score; the match mask and address come from them
+    asm volatile(
+        "{\n\t.reg .b32 eq, sum, xv, xh, ph, mh, phs, mhs, sym;\n\t"
+        "prmt.b32 sym, %0, 0, 0x4440;\n\t"
+        "mad.lo.u32 eq, sym, 128, %1;\n\t"
+        "lop3.b32 sum, eq, %0, 0, 0xc0;\n\t"
+        "add.u32 sum, sum, %0;\n\t"
+        "lop3.b32 xv, eq, %1, 0, 0xfc;\n\t"
+        "lop3.b32 xh, sum, %0, eq, 0xbe;\n\t"
+        "lop3.b32 ph, %1, xh, %0, 0xf1;\n\t"
+        "lop3.b32 mh, %0, xh, 0, 0xc0;\n\t"
+        "mad.hi.u32 %2, ph, 2, %2;\n\t"
+        "mad.hi.s32 %2, mh, 2, %2;\n\t"
+        "mul.lo.u32 phs, ph, 2;\n\t"
+        "mul.lo.u32 mhs, mh, 2;\n\t"
+        "lop3.b32 %0, mhs, xv, phs, 0xf1;\n\t"
+        "lop3.b32 %1, phs, xv, 0, 0xc0;\n\t"
+        "mad.hi.u32 %2, %2, 2, %2;\n\t"
+        "}"
+        : "+r"(x), "+r"(y), "+r"(t));
+  }
+}
+
+template <int MIX>
 __global__ void __launch_bounds__(256) int_mix_kernel(uint32_t* out, int iters, uint32_t seed) {
-  uint32_t a[kChains], b[kChains];
+  uint32_t a[kChains], b[kChains], c3[kChains];
 #pragma unroll
   for (int c = 0; c < kChains; ++c) {
     a[c] = seed ^ (threadIdx.x * 2654435761u) ^ (c * 40503u);
     b[c] = a[c] * 747796405u + blockIdx.x;
+    c3[c] = b[c] ^ 0x9e3779b9u;
   }
   for (int it = 0; it < iters; ++it) {
 #pragma unroll
-    for (int c = 0; c < kChains; ++c) {
-      uint32_t x = a[c], y = b[c], t;
-      asm volatile(
-          "lop3.b32 %0, %0, %1, 0x5a5a5a5a, 0x96;\n\t"
-          "lop3.b32 %1, %1, %0, 0x0f0f0f0f, 0xe8;\n\t"
-          "add.u32 %0, %0, %1;\n\t"
-          "lop3.b32 %0, %0, %1, 0x33333333, 0x1e;\n\t"
-          "lop3.b32 %1, %1, %0, 0x55555555, 0x78;\n\t"
-          "shf.l.wrap.b32 %2, %0, %1, 1;\n\t"
-          "lop3.b32 %0, %0, %2, %1, 0xb4;\n\t"
-          "shf.l.wrap.b32 %1, %1, %0, 1;\n\t"
-          "lop3.b32 %1, %1, %2, %0, 0x6c;\n\t"
-          "add.u32 %0, %0, %2;\n\t"
-          "shf.r.wrap.b32 %2, %1, %0, 31;\n\t"
-          "lop3.b32 %0, %0, %2, %1, 0x2d;\n\t"
-          "prmt.b32 %2, %0, %1, 0x6504;\n\t"
-          "shf.l.wrap.b32 %1, %2, %1, 1;\n\t"
-          "lop3.b32 %0, %0, %1, %2, 0x96;"
-          : "+r"(x), "+r"(y), "=r"(t));
-      a[c] = x;
-      b[c] = y;
-    }
+    for (int c = 0; c < kChains; ++c) mix_step<MIX>(a[c], b[c], c3[c]);
   }
   uint32_t r = 0;
 #pragma unroll
-  for (int c = 0; c < kChains; ++c) r ^= a[c] ^ b[c];
+  for (int c = 0; c < kChains; ++c) r ^= a[c] ^ b[c] ^ c3[c];
   out[blockIdx.x * blockDim.x + threadIdx.x] = r;
 }
 
@@ -102,13 +150,16 @@ extern "C" int oasm_selftest_wait(int device, uint32_t spin_limit, int arrive) {
   return h == 0u ? OASM_OK : OASM_ECUDA;
 }
 
-extern "C" int oasm_measure_int_peak(int device, double* ops_per_s, double* ms) {
+namespace {
+
+template <int MIX>
+int measure_mix(int device, double* ops_per_s, double* ms) {
   if (!ops_per_s) return OASM_EINVAL;
   if (cudaSetDevice(device) != cudaSuccess) return OASM_ECUDA;
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, int_mix_kernel, 256, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, int_mix_kernel<MIX>, 256, 0);
   if (per_sm < 1) per_sm = 1;
   const int blocks = sms * per_sm;
   const int threads = 256;
@@ -121,7 +172,7 @@ extern "C" int oasm_measure_int_peak(int device, double* ops_per_s, double* ms) 
   float best = 1e30f;
   for (int rep = 0; rep < 6; ++rep) {
     cudaEventRecord(e0);
-    int_mix_kernel<<<blocks, threads>>>(out, iters, 12345u + rep);
+    int_mix_kernel<MIX><<<blocks, threads>>>(out, iters, 12345u + rep);
     cudaEventRecord(e1);
     cudaEventSynchronize(e1);
     float t = 0;
@@ -136,4 +187,19 @@ extern "C" int oasm_measure_int_peak(int device, double* ops_per_s, double* ms) 
   *ops_per_s = ops / (double(best) * 1e-3);
   if (ms) *ms = best;
   return OASM_OK;
+}
+
+}  // namespace
+
+extern "C" int oasm_measure_int_peak_mix(int device, int mix, double* ops_per_s, double* ms) {
+  switch (mix) {
+    case 0: return measure_mix<0>(device, ops_per_s, ms);
+    case 1: return measure_mix<1>(device, ops_per_s, ms);
+    case 2: return measure_mix<2>(device, ops_per_s, ms);
+    default: return OASM_EINVAL;
+  }
+}
+
+extern "C" int oasm_measure_int_peak(int device, double* ops_per_s, double* ms) {
+  return measure_mix<2>(device, ops_per_s, ms);
 }

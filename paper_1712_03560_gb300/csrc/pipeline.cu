@@ -644,7 +644,7 @@ cudaError_t launch_gather(const CopyChunk* chunks, int n, uint8_t* arena, cudaSt
 
 cudaError_t launch_verify(const StepParams& p, cudaStream_t s) {
   // the candidate count lives on the device: size for the capacity, loop inside
-  const int grid = grid_for(p.cap_cand, 256, 152 * 16);
+  const int grid = grid_for(p.cap_cand, 256, p.num_sms * 16);
   verify_kernel<<<grid, 256, 0, s>>>(p);
   return cudaGetLastError();
 }
@@ -671,20 +671,20 @@ cudaError_t launch_sort(const SortArgs& a, unsigned long long** keys_out, uint32
 
 cudaError_t launch_permute(const DevHit* src, const uint32_t* idx, DevHit* dst,
                            const unsigned long long* count, unsigned long long cap,
-                           cudaStream_t s) {
-  permute_kernel<<<grid_for(cap, 256, 152 * 8), 256, 0, s>>>(src, idx, dst, count, cap);
+                           int num_sms, cudaStream_t s) {
+  permute_kernel<<<grid_for(cap, 256, num_sms * 8), 256, 0, s>>>(src, idx, dst, count, cap);
   return cudaGetLastError();
 }
 
 cudaError_t launch_filter(const StepParams& p, const unsigned long long* sorted, cudaStream_t s) {
-  const int grid = grid_for(p.cap_hits, 128, 152 * 32);
+  const int grid = grid_for(p.cap_hits, 128, p.num_sms * 32);
   filter_kernel<<<grid, 128, 0, s>>>(p, sorted);
   return cudaGetLastError();
 }
 
 cudaError_t launch_finalize(const StepParams& p, cudaStream_t s) {
   const unsigned long long npairs = (unsigned long long)p.n_items * p.n_pat;
-  finalize_kernel<<<grid_for(npairs, 256, 152 * 16), 256, 0, s>>>(p);
+  finalize_kernel<<<grid_for(npairs, 256, p.num_sms * 16), 256, 0, s>>>(p);
   return cudaGetLastError();
 }
 

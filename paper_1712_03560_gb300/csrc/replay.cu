@@ -75,6 +75,10 @@ int oasm_replay(oasm_ctx* ctx, const oasm_trace* tr, int realtime, uint64_t max_
   std::vector<uint64_t> prev_batch;
   std::vector<uint32_t> prev_ending;
   double prev_start = 0;
+  uint64_t prev_bytes = 0;
+  // library counters: at the start, and before the step in flight was launched
+  oasm_stats st0{}, st_launch{}, st_now{};
+  if ((rc = oasm_get_stats(ctx, &st0))) return rc;
   while (i < n || !waiting.empty() || n_held || inflight) {
     const double now = seconds_since(t0);
     const uint64_t j =
@@ -182,7 +186,10 @@ int oasm_replay(oasm_ctx* ctx, const oasm_trace* tr, int realtime, uint64_t max_
     // (3) launch this step, then hand out the previous one's results and free
     // its ended streams while the device works
     const double ts = seconds_since(t0);
+    oasm_stats st_prev_launch = st_launch;
+    if ((rc = oasm_get_stats(ctx, &st_now))) return rc;  // after the previous step's end
     if (!batch.empty()) {
+      st_launch = st_now;
       if ((rc = oasm_step_begin(ctx))) return rc;
       inflight = true;
     }
@@ -200,7 +207,16 @@ int oasm_replay(oasm_ctx* ctx, const oasm_trace* tr, int realtime, uint64_t max_
       if (done_at)
         for (uint64_t q : prev_batch) done_at[q] = t_prev_end;
       rs->step_s_sum += t_prev_end - prev_start;
-      rs->step_s_max = std::max(rs->step_s_max, t_prev_end - prev_start);
+      if (t_prev_end - prev_start > rs->step_s_max) {
+        // the slowest step so far: what the library did from its launch to
+        // the end of its results (a re-run, a new graph, a buffer grown)
+        rs->step_s_max = t_prev_end - prev_start;
+        rs->slowest_step = rs->steps - 1;
+        rs->slowest_bytes = prev_bytes;
+        rs->slowest_reruns = st_now.reruns - st_prev_launch.reruns;
+        rs->slowest_graph_builds = st_now.graph_builds - st_prev_launch.graph_builds;
+        rs->slowest_buffer_grows = st_now.buffer_grows - st_prev_launch.buffer_grows;
+      }
       if (!prev_ending.empty()) {  // their last decisions are drained: free the slots
         if ((rc = oasm_close_streams(ctx, uint32_t(prev_ending.size()), prev_ending.data())))
           return rc;
@@ -215,6 +231,7 @@ int oasm_replay(oasm_ctx* ctx, const oasm_trace* tr, int realtime, uint64_t max_
       prev_batch.swap(batch);
       prev_ending.swap(ending);
       prev_start = ts;
+      prev_bytes = bytes;
     } else {
       prev_batch.clear();
       prev_ending.clear();
@@ -222,6 +239,10 @@ int oasm_replay(oasm_ctx* ctx, const oasm_trace* tr, int realtime, uint64_t max_
   }
   rs->wall_s = seconds_since(t0);
   rs->n_out = n_out;
+  if ((rc = oasm_get_stats(ctx, &st_now))) return rc;
+  rs->reruns = st_now.reruns - st0.reruns;
+  rs->graph_builds = st_now.graph_builds - st0.graph_builds;
+  rs->buffer_grows = st_now.buffer_grows - st0.buffer_grows;
   return rs->kept > n_out && out ? OASM_ETRUNC : OASM_OK;
 }
 

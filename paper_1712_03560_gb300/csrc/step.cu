@@ -119,6 +119,11 @@ int enqueue_step(oasm_ctx* ctx, StepPlan& pl, const WorkItem* d_items, const Reg
   cudaStream_t s = ctx->stream;
   const uint32_t n_items = uint32_t(pl.items.size());
   const bool tm = ctx->cfg.timing != 0;
+  // the step's topology: which launches it makes (graphs are cached per topology)
+  uint64_t topo = 1469598103934665603ull;
+  auto topo_add = [&topo](uint64_t v) { topo = (topo ^ v) * 1099511628211ull; };
+  topo_add(tm ? 1 : 0);
+  topo_add(pl.chunks.empty() ? 0 : 1);
   if (tm) CK(record_event(ctx, ctx->ev[0], s));
   CK(cudaMemsetAsync(ctx->d_ctr, 0, sizeof(StepCounters), s));
   CK(cudaMemsetAsync(ctx->pair_pool.p, 0xff, size_t(n_items) * ctx->n_pat * sizeof(int32_t), s));
@@ -150,6 +155,7 @@ int enqueue_step(oasm_ctx* ctx, StepPlan& pl, const WorkItem* d_items, const Reg
     a.cand = ctx->cand.p;
     a.cap_cand = ctx->cand.cap;
     a.ctr = ctx->d_ctr;
+    topo_add(a.n_regions == 0 ? 0 : 2 + bi);
     if (a.n_regions == 0) continue;
     CK(launch_scan(a, s));
     ctx->st.launches += 1;
@@ -173,6 +179,7 @@ int enqueue_step(oasm_ctx* ctx, StepPlan& pl, const WorkItem* d_items, const Reg
     f.bloom_bits = ctx->pbloom_bits;
     f.dir_in_smem = (size_t(1) << f.dir_bits) * sizeof(PrefSlot) <= kPrefDirSmem ? 1u : 0u;
     f.grid = ctx->num_sms * 3;
+    topo_add(f.n_segs > 0 ? 0x51 : 0x50);
     if (f.n_segs > 0) {
       if (tm) CK(record_event(ctx, ctx->ev[8], s));
       CK(cudaMemsetAsync(ctx->pset.p, 0xff, ctx->pset.cap * sizeof(unsigned long long), s));
@@ -188,8 +195,9 @@ int enqueue_step(oasm_ctx* ctx, StepPlan& pl, const WorkItem* d_items, const Reg
   if (ctx->rules.output == OASM_OUT_FILTERED) {
     int nl = 0;
     SortArgs sa{P.keys, P.keys_alt, nullptr, nullptr, &ctx->d_ctr->n_hits, P.cap_hits,
-                kKBits, pl.kb, ctx->d_hist, kSortBlocks};
+                kKBits, pl.kb, ctx->d_hist, ctx->sort_blocks};
     CK(launch_sort(sa, &sorted, nullptr, &nl, s));
+    topo_add(0x100 + nl);
     ctx->st.launches += uint64_t(nl);
     if (tm) CK(record_event(ctx, ctx->ev[4], s));
     CK(launch_filter(P, sorted, s));
@@ -205,13 +213,17 @@ int enqueue_step(oasm_ctx* ctx, StepPlan& pl, const WorkItem* d_items, const Reg
     unsigned long long* ks = nullptr;
     uint32_t* vs = nullptr;
     SortArgs sa{ctx->okeys.p, ctx->okeys_alt.p, ctx->ovals.p, ctx->ovals_alt.p,
-                &ctx->d_ctr->n_out, P.cap_out, 0, pl.kb, ctx->d_hist, kSortBlocks};
+                &ctx->d_ctr->n_out, P.cap_out, 0, pl.kb, ctx->d_hist, ctx->sort_blocks};
     CK(launch_sort(sa, &ks, &vs, &nl, s));
-    CK(launch_permute(ctx->out.p, vs, ctx->out_sorted.p, &ctx->d_ctr->n_out, P.cap_out, s));
+    topo_add(0x200 + nl);
+    CK(launch_permute(ctx->out.p, vs, ctx->out_sorted.p, &ctx->d_ctr->n_out, P.cap_out,
+                      ctx->num_sms, s));
     ctx->st.launches += uint64_t(nl) + 1;
   }
   if (tm) CK(record_event(ctx, ctx->ev[5], s));
   CK(cudaMemcpyAsync(ctx->h_ctr, ctx->d_ctr, sizeof(StepCounters), cudaMemcpyDeviceToHost, s));
+  topo_add(uint64_t(ctx->rules.output));
+  ctx->step_topo = topo;
   return OASM_OK;
 }
 
@@ -240,27 +252,45 @@ int launch_step(oasm_ctx* ctx, StepPlan& pl, const WorkItem* d_items, const Regi
       return rc;
     }
     CK(ec);
+    // the cached executable graph of this topology, updated in place; a new
+    // topology takes a free slot or the least recently used one
+    oasm_ctx::GraphSlot* slot = nullptr;
+    for (auto& gs : ctx->graphs)
+      if (gs.exec && gs.topo == ctx->step_topo) slot = &gs;
     bool updated = false;
-    if (ctx->graph_exec) {
+    if (slot) {
       cudaGraphExecUpdateResultInfo info;
-      updated = cudaGraphExecUpdate(ctx->graph_exec, g, &info) == cudaSuccess;
+      updated = cudaGraphExecUpdate(slot->exec, g, &info) == cudaSuccess;
       if (!updated) {
         cudaGetLastError();
-        cudaGraphExecDestroy(ctx->graph_exec);
-        ctx->graph_exec = nullptr;
+        cudaGraphExecDestroy(slot->exec);
+        slot->exec = nullptr;
       }
+    } else {
+      if (ctx->graphs.size() < oasm_ctx::kGraphSlots) {
+        ctx->graphs.emplace_back();
+        slot = &ctx->graphs.back();
+      } else {
+        slot = &ctx->graphs[0];
+        for (auto& gs : ctx->graphs)
+          if (gs.used < slot->used) slot = &gs;
+        if (slot->exec) cudaGraphExecDestroy(slot->exec);
+        slot->exec = nullptr;
+      }
+      slot->topo = ctx->step_topo;
     }
     if (!updated) {
-      const cudaError_t ei = cudaGraphInstantiate(&ctx->graph_exec, g, 0);
+      const cudaError_t ei = cudaGraphInstantiate(&slot->exec, g, 0);
       if (ei != cudaSuccess) {
         cudaGraphDestroy(g);
-        ctx->graph_exec = nullptr;
+        slot->exec = nullptr;
         return fail(ctx, OASM_ECUDA, "cudaGraphInstantiate failed: %s", cudaGetErrorString(ei));
       }
       ctx->st.graph_builds += 1;
     }
+    slot->used = ++ctx->graph_clock;
     cudaGraphDestroy(g);
-    CK(cudaGraphLaunch(ctx->graph_exec, s));
+    CK(cudaGraphLaunch(slot->exec, s));
   } else {
     if ((rc = enqueue_step(ctx, pl, d_items, d_regions, d_chunks))) return rc;
   }
@@ -345,6 +375,7 @@ int finish_step(oasm_ctx* ctx, StepPlan& pl, const WorkItem* d_items, bool* over
       if (ctx->h_out) cudaFreeHost(ctx->h_out);
       ctx->h_out = nullptr;
       ctx->h_out_cap = 0;
+      ctx->st.buffer_grows += 1;
       if (cudaHostAlloc(&ctx->h_out, n * sizeof(DevHit), cudaHostAllocDefault) != cudaSuccess) {
         cudaGetLastError();
         return fail(ctx, OASM_ENOMEM, "pinned allocation for %zu records failed", n);

@@ -432,6 +432,7 @@ StepParams make_params(oasm_ctx* ctx, const WorkItem* d_items, uint32_t n_items,
   P.cap_pool = std::min(ctx->pool_hdr.cap, ctx->pool_mem.cap / (kMaxK + 1));
   P.pair_pool = ctx->pair_pool.p;
   P.ctr = ctx->d_ctr;
+  P.num_sms = ctx->num_sms;
   P.start_bits = sb;
   P.key_bits = kb;
   return P;

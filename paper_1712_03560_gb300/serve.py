@@ -243,6 +243,14 @@ class Server:
             "streams_admitted": int(st["streams_admitted"]),
             "max_waiting_streams": int(st["max_waiting_streams"]),
             "engine": "native",
+            # what the library did during the replay, and during its slowest step
+            "reruns": int(st["reruns"]), "graph_builds": int(st["graph_builds"]),
+            "buffer_grows": int(st["buffer_grows"]),
+            "slowest_step": {"index": int(st["slowest_step"]), "ms": st["step_s_max"] * 1e3,
+                             "bytes": int(st["slowest_bytes"]),
+                             "reruns": int(st["slowest_reruns"]),
+                             "graph_builds": int(st["slowest_graph_builds"]),
+                             "buffer_grows": int(st["slowest_buffer_grows"])},
         }
         if collect:
             out = {}

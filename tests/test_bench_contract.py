@@ -27,7 +27,12 @@ def test_reference_arm_prints_one_contract_line(extra):
     assert d["impl"] == "reference" and d["metric"] == "GCUPS" and d["value"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
-    assert d["config"]["costs"] == ([1, 2, 2] if "--costs" in extra else None)
+    assert d["config"]["costs"] == ({"sub": 1, "ins": 2, "del": 2} if "--costs" in extra
+                                    else None)
+    # the workload keys are the ones the GPU arm prints for the same arguments
+    for k in ("workload", "text_bytes", "patterns", "l2", "parallelism", "prefilter_piece",
+              "graphs", "output", "costs"):
+        assert k in d["config"], k
     assert d["config"]["output"] == (extra[1] if "--output" in extra else "filtered")
 
 

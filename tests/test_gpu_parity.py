@@ -667,6 +667,26 @@ def test_graph_launched_steps_equal_direct_launches():
     assert sg["scan_ms"] > 0
 
 
+def test_graph_cache_keeps_one_executable_per_step_topology():
+    """Steps whose launch sequence alternates (the piece filter only when a
+    step spans a whole piece start, sort passes that depend on the step's
+    span) keep one cached graph per topology: after the first step of each
+    topology no graph is built again, and the output equals direct launches."""
+    rng = np.random.default_rng(701)
+    pats, ks, text = random_case(rng, 256, 48, 12, 60, 200000, kmax=3)
+    # alternate short and long steps so consecutive steps differ in shape
+    cuts, pos = [], 0
+    for i in range(40):
+        pos += 700 if i % 2 else 9000
+        cuts.append(pos)
+    cfg = {"graphs": 1, "prefilter_piece": 1}
+    g, sg = run_gpu(pats, ks, text, splits=cuts, cfg=cfg)
+    d, sd = run_gpu(pats, ks, text, splits=cuts, cfg={"prefilter_piece": 1})
+    assert canon(g) == canon(d) == oracle_rows(pats, ks, text)
+    assert sg["steps"] >= 40
+    assert sg["graph_builds"] <= 8
+
+
 def test_bounded_wait_reports_timeout_and_device_stays_usable():
     """Failure detection without a fault: a device wait on a barrier that
     nothing completes runs out of its bound and reports OASM_ETIMEOUT; the
