@@ -422,9 +422,10 @@ int oasm_autotune(oasm_ctx *ctx, const uint8_t *dsample, size_t n, char *report,
  *   0  ALU pipe only: 3-input logic ops, adds, funnel shifts, byte permutes
  *   1  integer multiply-adds with register operands (the FMA pipe)
  *   2  one 32-bit column step of the forward scan in the scan's own PTX
- *      forms (7 logic ops, 1 add, 2 shifts as multiplies, 3 high-word
- *      multiply-adds, 1 address multiply-add, 1 byte permute), which the
- *      compiler spreads over both pipes as it does in the scan
+ *      forms (7 logic ops, 1 add, 2 shifts and the table address as
+ *      multiply-adds, 2 high-word multiply-adds for the score, 1 or for the
+ *      candidate flag, 1 byte permute), spread over the ALU and FMA pipes as
+ *      in the scan
  * *ops_per_s receives integer operations per second over the whole GPU (best
  * of five timed launches), *ms (may be NULL) the time of that launch.
  * OASM_EINVAL for another mix or a NULL ops_per_s.

@@ -30,6 +30,8 @@ struct ScanArgs {
   Candidate* cand;
   unsigned long long cap_cand;
   StepCounters* ctr;
+  uint32_t two;              // 2, and the bytes of one symbol's Peq row, as kernel
+  uint32_t row_bytes;        // arguments (set by the launchers; see fma_dbl in scan.cu)
 };
 
 // Weighted dynamic program over patterns' rows (oasm_create_weighted).  A

@@ -9,12 +9,11 @@
 //   1 multiply:   15 multiply-adds with register operands (the FMA pipe's
 //                 integer forms)
 //   2 scan step:  the operations of one 32-bit column step of the scan in the
-//                 PTX forms the scan uses: 7 lop3, 1 add, 2 shifts written as
-//                 multiplies by 2, 3 high-word multiply-adds by 2 (score and
-//                 candidate count), 1 multiply-add (the Peq address), 1 byte
-//                 permute (the symbol).  ptxas spreads the constant-multiplier
-//                 forms over the ALU and FMA pipes as in the scan, so this mix
-//                 measures the issue rate the scan itself can reach.
+//                 PTX forms the scan uses: 7 lop3, 1 add, 2 shifts and the Peq
+//                 address as multiply-adds by kernel arguments (2 and the row
+//                 size: they stay on the FMA pipe), 2 high-word multiply-adds
+//                 by 2 (the score), 1 or (the candidate flag), 1 byte permute
+//                 (the symbol): the issue rate the scan itself can reach.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -27,7 +26,8 @@ constexpr int kChains = 8;
 constexpr int kOpsPerStep = 15;
 
 template <int MIX>
-__device__ __forceinline__ void mix_step(uint32_t& x, uint32_t& y, uint32_t& t) {
+__device__ __forceinline__ void mix_step(uint32_t& x, uint32_t& y, uint32_t& t, uint32_t& f,
+                                         uint32_t two, uint32_t rowb) {
   if constexpr (MIX == 0) {
     asm volatile(
         "lop3.b32 %0, %0, %1, 0x5a5a5a5a, 0x96;\n\t"
@@ -65,11 +65,12 @@ __device__ __forceinline__ void mix_step(uint32_t& x, uint32_t& y, uint32_t& t) 
         "mad.lo.u32 %2, %2, %0, %1;"
         : "+r"(x), "+r"(y), "+r"(t));
   } else {
-    // x: Pv, y: Mv, t: the score; the match mask and address come from them
+    // x: Pv, y: Mv, t: the score, f: the candidate flag; the match mask and
+    // address come from them
     asm volatile(
         "{\n\t.reg .b32 eq, sum, xv, xh, ph, mh, phs, mhs, sym;\n\t"
         "prmt.b32 sym, %0, 0, 0x4440;\n\t"
-        "mad.lo.u32 eq, sym, 128, %1;\n\t"
+        "mad.lo.u32 eq, sym, %5, %1;\n\t"
         "lop3.b32 sum, eq, %0, 0, 0xc0;\n\t"
         "add.u32 sum, sum, %0;\n\t"
         "lop3.b32 xv, eq, %1, 0, 0xfc;\n\t"
@@ -78,32 +79,35 @@ __device__ __forceinline__ void mix_step(uint32_t& x, uint32_t& y, uint32_t& t) 
         "lop3.b32 mh, %0, xh, 0, 0xc0;\n\t"
         "mad.hi.u32 %2, ph, 2, %2;\n\t"
         "mad.hi.s32 %2, mh, 2, %2;\n\t"
-        "mul.lo.u32 phs, ph, 2;\n\t"
-        "mul.lo.u32 mhs, mh, 2;\n\t"
+        "mad.lo.u32 phs, ph, %4, 0;\n\t"
+        "mad.lo.u32 mhs, mh, %4, 0;\n\t"
         "lop3.b32 %0, mhs, xv, phs, 0xf1;\n\t"
         "lop3.b32 %1, phs, xv, 0, 0xc0;\n\t"
-        "mad.hi.u32 %2, %2, 2, %2;\n\t"
+        "or.b32 %3, %3, %2;\n\t"
         "}"
-        : "+r"(x), "+r"(y), "+r"(t));
+        : "+r"(x), "+r"(y), "+r"(t), "+r"(f)
+        : "r"(two), "r"(rowb));
   }
 }
 
 template <int MIX>
-__global__ void __launch_bounds__(256) int_mix_kernel(uint32_t* out, int iters, uint32_t seed) {
-  uint32_t a[kChains], b[kChains], c3[kChains];
+__global__ void __launch_bounds__(256) int_mix_kernel(uint32_t* out, int iters, uint32_t seed,
+                                                      uint32_t two, uint32_t rowb) {
+  uint32_t a[kChains], b[kChains], c3[kChains], f[kChains];
 #pragma unroll
   for (int c = 0; c < kChains; ++c) {
     a[c] = seed ^ (threadIdx.x * 2654435761u) ^ (c * 40503u);
     b[c] = a[c] * 747796405u + blockIdx.x;
     c3[c] = b[c] ^ 0x9e3779b9u;
+    f[c] = 0u;
   }
   for (int it = 0; it < iters; ++it) {
 #pragma unroll
-    for (int c = 0; c < kChains; ++c) mix_step<MIX>(a[c], b[c], c3[c]);
+    for (int c = 0; c < kChains; ++c) mix_step<MIX>(a[c], b[c], c3[c], f[c], two, rowb);
   }
   uint32_t r = 0;
 #pragma unroll
-  for (int c = 0; c < kChains; ++c) r ^= a[c] ^ b[c] ^ c3[c];
+  for (int c = 0; c < kChains; ++c) r ^= a[c] ^ b[c] ^ c3[c] ^ f[c];
   out[blockIdx.x * blockDim.x + threadIdx.x] = r;
 }
 
@@ -172,7 +176,7 @@ int measure_mix(int device, double* ops_per_s, double* ms) {
   float best = 1e30f;
   for (int rep = 0; rep < 6; ++rep) {
     cudaEventRecord(e0);
-    int_mix_kernel<MIX><<<blocks, threads>>>(out, iters, 12345u + rep);
+    int_mix_kernel<MIX><<<blocks, threads>>>(out, iters, 12345u + rep, 2u, 128u);
     cudaEventRecord(e1);
     cudaEventSynchronize(e1);
     float t = 0;

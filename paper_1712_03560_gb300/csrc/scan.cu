@@ -111,9 +111,14 @@ __device__ __forceinline__ uint32_t mad_lo(uint32_t a, uint32_t b, uint32_t c) {
   asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(c));
   return r;
 }
-__device__ __forceinline__ uint32_t shl1(uint32_t x) {  // x << 1 as a multiply
+// x * two + c with `two` a kernel argument (2): the compiler cannot turn it
+// into a shift or LEA, so it stays a multiply-add on the FMA pipe.  The scan's
+// logic ops saturate the ALU pipe while the FMA pipe idles (measured on GB300:
+// each pipe issues about one warp instruction every other clock, together
+// about one per clock), so the shifts and the Peq address go there.
+__device__ __forceinline__ uint32_t fma_dbl(uint32_t x, uint32_t two, uint32_t c = 0u) {
   uint32_t r;
-  asm("mul.lo.u32 %0, %1, 2;" : "=r"(r) : "r"(x));
+  asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(x), "r"(two), "r"(c));
   return r;
 }
 
@@ -158,7 +163,7 @@ __device__ __forceinline__ void add_words<4>(const uint32_t (&a)[4], const uint3
 // the bottom word).  s tracks score - K - 1 and is negative iff D[e] <= K.
 template <int W>
 __device__ __forceinline__ void search_step(uint32_t (&Pv)[W], uint32_t (&Mv)[W], int& s,
-                                            const uint32_t (&eq)[W]) {
+                                            const uint32_t (&eq)[W], uint32_t two) {
   uint32_t x[W], sum[W];
 #pragma unroll
   for (int w = 0; w < W; ++w) x[w] = eq[w] & Pv[w];
@@ -171,8 +176,8 @@ __device__ __forceinline__ void search_step(uint32_t (&Pv)[W], uint32_t (&Mv)[W]
     const uint32_t ph = Mv[w] | ~(xh | Pv[w]);
     const uint32_t mh = Pv[w] & xh;
     if (w == W - 1) s = sub_top(add_top(s, ph), mh);
-    const uint32_t phs = (w == 0) ? shl1(ph) : __funnelshift_l(php, ph, 1);
-    const uint32_t mhs = (w == 0) ? shl1(mh) : __funnelshift_l(mhp, mh, 1);
+    const uint32_t phs = (w == 0) ? fma_dbl(ph, two) : __funnelshift_l(php, ph, 1);
+    const uint32_t mhs = (w == 0) ? fma_dbl(mh, two) : __funnelshift_l(mhp, mh, 1);
     php = ph;
     mhp = mh;
     Pv[w] = mhs | ~(xv | phs);
@@ -395,13 +400,14 @@ __device__ void scan_dict(const ScanArgs& A, const char* peq, uint8_t* tbuf, uin
   Emitter em;
   bool record = false;  // warp-uniform: record every step instead of count + replay
   int blocks = 0, replays = 0;
+  const uint32_t two = A.two, rowb = A.row_bytes;
   auto step_all = [&](uint32_t sym) {
-    const uint32_t addr = mad_lo(sym, 128u * W, lane_off);
+    const uint32_t addr = fma_dbl(sym, rowb, lane_off);
 #pragma unroll
     for (int v = 0; v < GPW; ++v) {
       uint32_t eq[W];
       load_eq<W>(peq + v * kPeqBytes, addr, eq);
-      search_step<W>(Pv[v], Mv[v], s[v], eq);
+      search_step<W>(Pv[v], Mv[v], s[v], eq, two);
     }
   };
   // whole blocks: up to 16 symbols past the region, inside the arena padding
@@ -444,11 +450,11 @@ __device__ void scan_dict(const ScanArgs& A, const char* peq, uint8_t* tbuf, uin
       for (int j = 0; j < kBlk; ++j) {
         step_all(tv[j]);
 #pragma unroll
-        for (int g = 0; g < GPW; ++g) cnt[g] = add_top(cnt[g], uint32_t(s[g]));  // steps with s < 0
+        for (int g = 0; g < GPW; ++g) cnt[g] |= s[g];  // sign set once a step had s < 0
       }
       bool any = false;
 #pragma unroll
-      for (int g = 0; g < GPW; ++g) any |= cnt[g] != 0 && vm[g] != 0;
+      for (int g = 0; g < GPW; ++g) any |= cnt[g] < 0 && vm[g] != 0;
       emit = __any_sync(kFull, any);
       if (emit) {
         // rare: replay the block from its saved state, recording each step
@@ -559,6 +565,8 @@ __device__ void scan_dict_nfa(const ScanArgs& A, const char* peq, uint8_t* tbuf,
     for (int j = 0; j <= KL; ++j) Rs[g][j] = E[g] * ((1u << j) - 1u);
   }
   const uint32_t lane_off = uint32_t(lane) * 4u;
+  // (the automaton's immediate-2 multiply-adds and address stay as they are:
+  // measured, moving them to runtime multipliers slowed the K = 2 class)
   auto step_all = [&](uint32_t sym) {
     const uint32_t addr = mad_lo(sym, 128u, lane_off);
 #pragma unroll
@@ -692,7 +700,7 @@ __device__ void scan_segments(const ScanArgs& A, const char* peq, const LaneGrou
       const uint32_t sym = __byte_perm(wd4[j >> 2], 0u, 0x4440u | uint32_t(j & 3));
       uint32_t eq[W];
       load_eq<W>(peq, mad_lo(sym, 128u * W, lane_off), eq);
-      search_step<W>(Pv, Mv, s, eq);
+      search_step<W>(Pv, Mv, s, eq, A.two);
       cm = __funnelshift_l(uint32_t(s), cm, 1);  // shifts in the sign of s
     }
     const uint32_t c16 = cm & block_mask(L.t_lo, L.t_hi, v);
@@ -731,7 +739,8 @@ __device__ void scan_segments(const ScanArgs& A, const char* peq, const LaneGrou
 // near matches only.  Shared memory holds word 0 of the group's table.
 
 // Word 0 alone: the first 32 rows; s tracks D[32] - K - 1.
-__device__ __forceinline__ void cut_word0_step(uint32_t& Pv, uint32_t& Mv, int& s, uint32_t eq) {
+__device__ __forceinline__ void cut_word0_step(uint32_t& Pv, uint32_t& Mv, int& s, uint32_t eq,
+                                               uint32_t two) {
   const uint32_t x = eq & Pv;
   const uint32_t sum = x + Pv;
   const uint32_t xv = eq | Mv;
@@ -739,7 +748,7 @@ __device__ __forceinline__ void cut_word0_step(uint32_t& Pv, uint32_t& Mv, int& 
   const uint32_t ph = Mv | ~(xh | Pv);
   const uint32_t mh = Pv & xh;
   s = sub_top(add_top(s, ph), mh);
-  const uint32_t phs = shl1(ph), mhs = shl1(mh);
+  const uint32_t phs = fma_dbl(ph, two), mhs = fma_dbl(mh, two);
   Pv = mhs | ~(xv | phs);
   Mv = phs & xv;
 }
@@ -748,7 +757,8 @@ __device__ __forceinline__ void cut_word0_step(uint32_t& Pv, uint32_t& Mv, int& 
 // D[l_p] - K - 1 (row l_p at bit 31 - sh of word W - 1).
 template <int W>
 __device__ __forceinline__ void cut_full_step(uint32_t (&Pv)[W], uint32_t (&Mv)[W], int& s0,
-                                              int& sL, const uint32_t (&eq)[W], uint32_t sh) {
+                                              int& sL, const uint32_t (&eq)[W], uint32_t sh,
+                                              uint32_t two) {
   uint32_t x[W], sum[W];
 #pragma unroll
   for (int w = 0; w < W; ++w) x[w] = eq[w] & Pv[w];
@@ -762,8 +772,8 @@ __device__ __forceinline__ void cut_full_step(uint32_t (&Pv)[W], uint32_t (&Mv)[
     const uint32_t mh = Pv[w] & xh;
     if (w == 0) s0 = sub_top(add_top(s0, ph), mh);
     if (w == W - 1) sL = sub_top(add_top(sL, ph << sh), mh << sh);
-    const uint32_t phs = (w == 0) ? shl1(ph) : __funnelshift_l(php, ph, 1);
-    const uint32_t mhs = (w == 0) ? shl1(mh) : __funnelshift_l(mhp, mh, 1);
+    const uint32_t phs = (w == 0) ? fma_dbl(ph, two) : __funnelshift_l(php, ph, 1);
+    const uint32_t mhs = (w == 0) ? fma_dbl(mh, two) : __funnelshift_l(mhp, mh, 1);
     php = ph;
     mhp = mh;
     Pv[w] = mhs | ~(xv | phs);
@@ -789,6 +799,7 @@ __device__ void scan_dict_cut(const ScanArgs& A, const char* peq0, const uint32_
   int s0 = 31 - L.K, sL = L.m - L.K - 1;
   bool full = false;             // warp-uniform
   uint32_t n_full = 0, n_redo = 0;
+  const uint32_t two = A.two, rowb = A.row_bytes;
   Emitter em;
   const int nbytes = (L.nvec * 16 + kBlk - 1) / kBlk * kBlk;
   const bool ok = stream_blocks(A, tbuf, bar0, A.arena + L.ad_al, nbytes, lane,
@@ -799,11 +810,12 @@ __device__ void scan_dict_cut(const ScanArgs& A, const char* peq0, const uint32_
       int act = 0;
 #pragma unroll
       for (int j = 0; j < kBlk; ++j) {
-        const uint32_t eq0 = *reinterpret_cast<const uint32_t*>(peq0 + mad_lo(tv[j], 128u, lane_off));
-        cut_word0_step(Pv[0], Mv[0], s0, eq0);
-        act = add_top(act, uint32_t(s0));  // steps with D[32] <= K
+        const uint32_t eq0 =
+            *reinterpret_cast<const uint32_t*>(peq0 + fma_dbl(tv[j], rowb, lane_off));
+        cut_word0_step(Pv[0], Mv[0], s0, eq0, two);
+        act |= s0;  // sign set once a step had D[32] <= K
       }
-      if (!__any_sync(kFull, act != 0)) return;
+      if (!__any_sync(kFull, act < 0)) return;
       // a lane's first 32 rows came within K: the block again, every word
       Pv[0] = P0;
       Mv[0] = M0;
@@ -822,11 +834,11 @@ __device__ void scan_dict_cut(const ScanArgs& A, const char* peq0, const uint32_
     for (int j = 0; j < kBlk; ++j) {
       const uint32_t sym = tv[j];
       uint32_t eq[W];
-      eq[0] = *reinterpret_cast<const uint32_t*>(peq0 + mad_lo(sym, 128u, lane_off));
+      eq[0] = *reinterpret_cast<const uint32_t*>(peq0 + fma_dbl(sym, rowb, lane_off));
       const uint32_t* row = ghi + sym * (32u * W) + uint32_t(lane);
 #pragma unroll
       for (int w = 1; w < W; ++w) eq[w] = __ldg(row + 32 * w);
-      cut_full_step<W>(Pv, Mv, s0, sL, eq, sh);
+      cut_full_step<W>(Pv, Mv, s0, sL, eq, sh, two);
       cm = __funnelshift_l(uint32_t(sL), cm, 1);  // shifts in the sign of sL
     }
     ++n_full;
@@ -1091,7 +1103,10 @@ cudaError_t launch_wdp(const ScanArgs& a, cudaStream_t st) {
 }
 
 template <int W, bool kDict, int ALG = 0, int GPW = 1>
-cudaError_t launch_w(const ScanArgs& a, cudaStream_t st) {
+cudaError_t launch_w(const ScanArgs& a0, cudaStream_t st) {
+  ScanArgs a = a0;
+  a.two = 2u;
+  a.row_bytes = 128u * W;  // one symbol's row of the group's table
   const size_t smem = scan_smem_bytes(W, a.warps, kDict ? a.chunk : 0, GPW);
   const long long blocks_r = (a.n_regions + a.warps - 1) / a.warps;
   const long long grid = blocks_r * ((a.n_groups + GPW - 1) / GPW);
@@ -1101,7 +1116,10 @@ cudaError_t launch_w(const ScanArgs& a, cudaStream_t st) {
 }
 
 template <int W>
-cudaError_t launch_cut(const ScanArgs& a, cudaStream_t st) {
+cudaError_t launch_cut(const ScanArgs& a0, cudaStream_t st) {
+  ScanArgs a = a0;
+  a.two = 2u;
+  a.row_bytes = 128u;  // word 0 of the table
   const size_t smem = scan_smem_bytes(W, a.warps, a.chunk, 1, kAlgoCut);
   const long long grid = (long long)((a.n_regions + a.warps - 1) / a.warps) * a.n_groups;
   if (grid <= 0) return cudaSuccess;
