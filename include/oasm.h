@@ -371,6 +371,31 @@ typedef struct {
 int oasm_replay(oasm_ctx *ctx, const oasm_trace *trace, int realtime, uint64_t max_batch_bytes,
                 double *done_at, oasm_hit *out, size_t out_cap, oasm_replay_stats *rs);
 
+/* The serving loop's calls into the library, as a table: oasm_replay binds
+ * it to a context (handle = the oasm_ctx*, each entry the library call of the
+ * same name).  oasm_replay_ops runs the same loop through any table with the
+ * same contracts, e.g. a fake library on the host that refuses admission or
+ * fails a step, to test the scheduler without a device.  Every entry but
+ * get_stats (may be NULL: no library counters in the stats) must be set;
+ * OASM_EINVAL otherwise. */
+typedef struct {
+    void *handle;
+    int (*open_streams)(void *handle, uint32_t n, uint32_t *sids, uint32_t *n_opened);
+    int (*feed_many)(void *handle, uint32_t n, const uint32_t *sid, const uint8_t *buf,
+                     const uint64_t *off, const uint32_t *len);
+    int (*end_streams)(void *handle, uint32_t n, const uint32_t *sids);
+    int (*close_streams)(void *handle, uint32_t n, const uint32_t *sids);
+    int (*step_begin)(void *handle);
+    int (*step_end)(void *handle);
+    int (*ready)(void *handle, uint32_t sid, size_t *n);
+    int (*drain)(void *handle, oasm_hit *out, size_t cap, size_t *n_out);
+    int (*get_stats)(void *handle, oasm_stats *st);
+} oasm_serve_ops;
+
+int oasm_replay_ops(const oasm_serve_ops *ops, const oasm_trace *trace, int realtime,
+                    uint64_t max_batch_bytes, double *done_at, oasm_hit *out, size_t out_cap,
+                    oasm_replay_stats *rs);
+
 /* Number of decided hits of stream sid queued and not yet returned by
  * oasm_flush (no device work is started).  sid = OASM_ALL_STREAMS gives the
  * total over every open stream: the size oasm_drain needs. */

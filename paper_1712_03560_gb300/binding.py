@@ -99,6 +99,28 @@ class oasm_trace(ctypes.Structure):
                 ("reserved", ctypes.c_uint32)]
 
 
+_u32p = ctypes.POINTER(ctypes.c_uint32)
+_u64p = ctypes.POINTER(ctypes.c_uint64)
+_szp = ctypes.POINTER(ctypes.c_size_t)
+SERVE_OP_TYPES = {
+    "open_streams": ctypes.CFUNCTYPE(ctypes.c_int32, ctypes.c_void_p, ctypes.c_uint32, _u32p, _u32p),
+    "feed_many": ctypes.CFUNCTYPE(ctypes.c_int32, ctypes.c_void_p, ctypes.c_uint32, _u32p,
+                                  ctypes.POINTER(ctypes.c_uint8), _u64p, _u32p),
+    "end_streams": ctypes.CFUNCTYPE(ctypes.c_int32, ctypes.c_void_p, ctypes.c_uint32, _u32p),
+    "close_streams": ctypes.CFUNCTYPE(ctypes.c_int32, ctypes.c_void_p, ctypes.c_uint32, _u32p),
+    "step_begin": ctypes.CFUNCTYPE(ctypes.c_int32, ctypes.c_void_p),
+    "step_end": ctypes.CFUNCTYPE(ctypes.c_int32, ctypes.c_void_p),
+    "ready": ctypes.CFUNCTYPE(ctypes.c_int32, ctypes.c_void_p, ctypes.c_uint32, _szp),
+    "drain": ctypes.CFUNCTYPE(ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                              _szp),
+    "get_stats": ctypes.CFUNCTYPE(ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p),
+}
+
+
+class oasm_serve_ops(ctypes.Structure):
+    _fields_ = [("handle", ctypes.c_void_p)] + [(k, t) for k, t in SERVE_OP_TYPES.items()]
+
+
 class oasm_replay_stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in ("steps", "packets", "bytes", "kept", "n_out",
                                                 "streams_admitted", "max_waiting_streams")] + \
@@ -117,7 +139,7 @@ EXPORTS = ["oasm_config_default", "oasm_rules_default", "oasm_create", "oasm_cre
            "oasm_measure_int_peak", "oasm_measure_int_peak_mix", "oasm_scan_ends_noalloc",
            "oasm_stream_state_size",
            "oasm_save_stream", "oasm_restore_stream", "oasm_replay", "oasm_register_host",
-           "oasm_unregister_host", "oasm_step_begin", "oasm_step_end",
+           "oasm_unregister_host", "oasm_step_begin", "oasm_step_end", "oasm_replay_ops",
            "oasm_piece_filter_choice", "oasm_selftest_wait", "oasm_get_tuning",
            "oasm_set_tuning"]
 
@@ -182,6 +204,9 @@ def load(path: str | None = None):
                                         u64, vp, u64, ctypes.POINTER(u64), vp], i32),
             "oasm_replay": ([vp, ctypes.POINTER(oasm_trace), i32, u64, vp, vp, ctypes.c_size_t,
                              ctypes.POINTER(oasm_replay_stats)], i32),
+            "oasm_replay_ops": ([ctypes.POINTER(oasm_serve_ops), ctypes.POINTER(oasm_trace), i32,
+                                 u64, vp, vp, ctypes.c_size_t,
+                                 ctypes.POINTER(oasm_replay_stats)], i32),
             "oasm_register_host": ([vp, vp, ctypes.c_size_t], i32),
             "oasm_piece_filter_choice": ([u8pp, ctypes.POINTER(u32), ctypes.POINTER(u32), u32, u32,
                                           vp], i32),
@@ -577,6 +602,32 @@ def oasm_replay(ctx, times, streams, offs, lens, last, payload, n_streams: int,
         raise OasmError(rc, f"replay kept {stats['kept']} hits, more than out_cap={cap}")
     hits = out[: rs.n_out] if out is not None else None
     return done, hits, stats
+
+
+def oasm_replay_ops(ops: dict, times, streams, offs, lens, last, payload, n_streams: int,
+                    realtime: bool = False, max_batch_bytes: int = 32 << 20):
+    """The native serving loop driven through a table of Python callables
+    (keys of SERVE_OP_TYPES, each taking the C arguments after the handle;
+    get_stats may be left out) instead of a context.  Returns (rc, done_at,
+    stats); the loop's own error code is returned, not raised."""
+    cb = {k: SERVE_OP_TYPES[k](lambda *a, f=f: int(f(*a[1:]))) for k, f in ops.items()}
+    table = oasm_serve_ops(None, *[cb.get(k, SERVE_OP_TYPES[k]()) for k in SERVE_OP_TYPES])
+    t = np.ascontiguousarray(times, dtype=np.float64)
+    st_ = np.ascontiguousarray(streams, dtype=np.uint32)
+    of = np.ascontiguousarray(offs, dtype=np.uint64)
+    ln = np.ascontiguousarray(lens, dtype=np.uint32)
+    la = np.ascontiguousarray(last, dtype=np.uint8)
+    pay = _u8(payload)
+    n = t.size
+    tr = oasm_trace(t.ctypes.data, st_.ctypes.data, of.ctypes.data, ln.ctypes.data,
+                    la.ctypes.data, pay.ctypes.data, n, int(n_streams), 0)
+    done = np.full(n, np.nan)
+    rs = oasm_replay_stats()
+    rc = load().oasm_replay_ops(ctypes.byref(table), ctypes.byref(tr), 1 if realtime else 0,
+                                int(max_batch_bytes), done.ctypes.data, None, 0,
+                                ctypes.byref(rs))
+    stats = {f[0]: getattr(rs, f[0]) for f in oasm_replay_stats._fields_}
+    return int(rc), done, stats
 
 
 class Matcher:

@@ -9,8 +9,11 @@
 // order, and is admitted in FIFO order when a closing stream frees a slot.
 // The step that ingests a stream's last packet also ends it; its slot is
 // freed after the drain.  The same scheduler is written in Python in
-// serve.py (tested there against a fake library); this one removes the
-// interpreter from the loop.
+// serve.py; this one removes the interpreter from the loop.  The loop calls
+// the library through a table of entry points (oasm_serve_ops): oasm_replay
+// binds the table to a context, and a caller may bind it to anything with
+// the same contract (the tests bind it to a fake on the CPU to inject
+// admission refusals and failing steps).
 #include <algorithm>
 #include <chrono>
 #include <cstring>
@@ -32,10 +35,22 @@ double seconds_since(Clock::time_point t0) {
 
 extern "C" {
 
-int oasm_replay(oasm_ctx* ctx, const oasm_trace* tr, int realtime, uint64_t max_batch_bytes,
-                double* done_at, oasm_hit* out, size_t out_cap, oasm_replay_stats* rs) {
-  if (!ctx || !tr || !rs || (tr->n_packets && (!tr->t || !tr->stream || !tr->off || !tr->len ||
-                                                !tr->last || !tr->payload)))
+int oasm_replay_ops(const oasm_serve_ops* ops, const oasm_trace* tr, int realtime,
+                    uint64_t max_batch_bytes, double* done_at, oasm_hit* out, size_t out_cap,
+                    oasm_replay_stats* rs) {
+  if (!ops || !ops->open_streams || !ops->feed_many || !ops->end_streams || !ops->close_streams ||
+      !ops->step_begin || !ops->step_end || !ops->ready || !ops->drain)
+    return OASM_EINVAL;
+  void* const h = ops->handle;
+  auto get_stats = [&](oasm_stats* st) -> int {
+    if (!ops->get_stats) {
+      memset(st, 0, sizeof *st);
+      return OASM_OK;
+    }
+    return ops->get_stats(h, st);
+  };
+  if (!tr || !rs || (tr->n_packets && (!tr->t || !tr->stream || !tr->off || !tr->len ||
+                                        !tr->last || !tr->payload)))
     return OASM_EINVAL;
   if (max_batch_bytes == 0) return OASM_EINVAL;
   const uint64_t n = tr->n_packets;
@@ -63,7 +78,7 @@ int oasm_replay(oasm_ctx* ctx, const oasm_trace* tr, int realtime, uint64_t max_
     got.assign(k, 0);
     uint32_t opened = 0;
     if (k) {
-      const int r = oasm_open_streams(ctx, uint32_t(k), got.data(), &opened);
+      const int r = ops->open_streams(h, uint32_t(k), got.data(), &opened);
       if (r) return r;
     }
     got.resize(opened);
@@ -78,7 +93,7 @@ int oasm_replay(oasm_ctx* ctx, const oasm_trace* tr, int realtime, uint64_t max_
   uint64_t prev_bytes = 0;
   // library counters: at the start, and before the step in flight was launched
   oasm_stats st0{}, st_launch{}, st_now{};
-  if ((rc = oasm_get_stats(ctx, &st0))) return rc;
+  if ((rc = get_stats(&st0))) return rc;
   while (i < n || !waiting.empty() || n_held || inflight) {
     const double now = seconds_since(t0);
     const uint64_t j =
@@ -169,17 +184,17 @@ int oasm_replay(oasm_ctx* ctx, const oasm_trace* tr, int realtime, uint64_t max_
         bytes += tr->len[q];
         if (tr->last[q]) ending.push_back(b_sid[b]);
       }
-      if ((rc = oasm_feed_many(ctx, uint32_t(batch.size()), b_sid.data(), tr->payload,
-                               b_off.data(), b_len.data())))
+      if ((rc = ops->feed_many(h, uint32_t(batch.size()), b_sid.data(), tr->payload, b_off.data(),
+                                b_len.data())))
         return rc;
-      if (!ending.empty() && (rc = oasm_end_streams(ctx, uint32_t(ending.size()), ending.data())))
+      if (!ending.empty() && (rc = ops->end_streams(h, uint32_t(ending.size()), ending.data())))
         return rc;
     }
     // (2) finish the previous step: its hits are queued now
     double t_prev_end = 0;
     const bool had_prev = inflight;
     if (inflight) {
-      if ((rc = oasm_step_end(ctx))) return rc;
+      if ((rc = ops->step_end(h))) return rc;
       t_prev_end = seconds_since(t0);
       inflight = false;
     }
@@ -187,18 +202,18 @@ int oasm_replay(oasm_ctx* ctx, const oasm_trace* tr, int realtime, uint64_t max_
     // its ended streams while the device works
     const double ts = seconds_since(t0);
     oasm_stats st_prev_launch = st_launch;
-    if ((rc = oasm_get_stats(ctx, &st_now))) return rc;  // after the previous step's end
+    if ((rc = get_stats(&st_now))) return rc;  // after the previous step's end
     if (!batch.empty()) {
       st_launch = st_now;
-      if ((rc = oasm_step_begin(ctx))) return rc;
+      if ((rc = ops->step_begin(h))) return rc;
       inflight = true;
     }
     if (had_prev) {
       size_t nr = 0;
-      if ((rc = oasm_ready(ctx, OASM_ALL_STREAMS, &nr))) return rc;
+      if ((rc = ops->ready(h, OASM_ALL_STREAMS, &nr))) return rc;
       drained.resize(nr);
       size_t nd = 0;
-      if ((rc = oasm_drain(ctx, nr ? drained.data() : nullptr, nr, &nd))) return rc;
+      if ((rc = ops->drain(h, nr ? drained.data() : nullptr, nr, &nd))) return rc;
       for (size_t r = 0; r < nd; ++r) {
         drained[r].stream_id = ext_of[drained[r].stream_id];  // external stream ids
         if (out && n_out < out_cap) out[n_out++] = drained[r];
@@ -218,7 +233,7 @@ int oasm_replay(oasm_ctx* ctx, const oasm_trace* tr, int realtime, uint64_t max_
         rs->slowest_buffer_grows = st_now.buffer_grows - st_prev_launch.buffer_grows;
       }
       if (!prev_ending.empty()) {  // their last decisions are drained: free the slots
-        if ((rc = oasm_close_streams(ctx, uint32_t(prev_ending.size()), prev_ending.data())))
+        if ((rc = ops->close_streams(h, uint32_t(prev_ending.size()), prev_ending.data())))
           return rc;
         for (uint32_t sd : prev_ending) sid_of[ext_of[sd]] = -2;
         open_now -= prev_ending.size();
@@ -239,11 +254,46 @@ int oasm_replay(oasm_ctx* ctx, const oasm_trace* tr, int realtime, uint64_t max_
   }
   rs->wall_s = seconds_since(t0);
   rs->n_out = n_out;
-  if ((rc = oasm_get_stats(ctx, &st_now))) return rc;
+  if ((rc = get_stats(&st_now))) return rc;
   rs->reruns = st_now.reruns - st0.reruns;
   rs->graph_builds = st_now.graph_builds - st0.graph_builds;
   rs->buffer_grows = st_now.buffer_grows - st0.buffer_grows;
   return rs->kept > n_out && out ? OASM_ETRUNC : OASM_OK;
+}
+
+// The table bound to a context: the library's own entry points.
+static int ctx_open_streams(void* h, uint32_t n, uint32_t* sids, uint32_t* n_opened) {
+  return oasm_open_streams(static_cast<oasm_ctx*>(h), n, sids, n_opened);
+}
+static int ctx_feed_many(void* h, uint32_t n, const uint32_t* sid, const uint8_t* buf,
+                         const uint64_t* off, const uint32_t* len) {
+  return oasm_feed_many(static_cast<oasm_ctx*>(h), n, sid, buf, off, len);
+}
+static int ctx_end_streams(void* h, uint32_t n, const uint32_t* sids) {
+  return oasm_end_streams(static_cast<oasm_ctx*>(h), n, sids);
+}
+static int ctx_close_streams(void* h, uint32_t n, const uint32_t* sids) {
+  return oasm_close_streams(static_cast<oasm_ctx*>(h), n, sids);
+}
+static int ctx_step_begin(void* h) { return oasm_step_begin(static_cast<oasm_ctx*>(h)); }
+static int ctx_step_end(void* h) { return oasm_step_end(static_cast<oasm_ctx*>(h)); }
+static int ctx_ready(void* h, uint32_t sid, size_t* n) {
+  return oasm_ready(static_cast<oasm_ctx*>(h), sid, n);
+}
+static int ctx_drain(void* h, oasm_hit* out, size_t cap, size_t* n_out) {
+  return oasm_drain(static_cast<oasm_ctx*>(h), out, cap, n_out);
+}
+static int ctx_get_stats(void* h, oasm_stats* st) {
+  return oasm_get_stats(static_cast<oasm_ctx*>(h), st);
+}
+
+int oasm_replay(oasm_ctx* ctx, const oasm_trace* tr, int realtime, uint64_t max_batch_bytes,
+                double* done_at, oasm_hit* out, size_t out_cap, oasm_replay_stats* rs) {
+  if (!ctx) return OASM_EINVAL;
+  const oasm_serve_ops ops{ctx,           ctx_open_streams, ctx_feed_many, ctx_end_streams,
+                           ctx_close_streams, ctx_step_begin, ctx_step_end, ctx_ready,
+                           ctx_drain,     ctx_get_stats};
+  return oasm_replay_ops(&ops, tr, realtime, max_batch_bytes, done_at, out, out_cap, rs);
 }
 
 }  // extern "C"

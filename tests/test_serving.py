@@ -179,6 +179,146 @@ def test_scheduler_realtime_pacing_batches_arrivals():
     assert np.isfinite(res["p99_ms"])
 
 
+class NativeFake:
+    """A fake library for the native serving loop (oasm_replay_ops): the same
+    bookkeeping as FakeLib, called from C through the entry-point table.
+    mem_streams < slots refuses admission for memory below the slot count;
+    fail_step = n makes the n-th step report a device-wait timeout."""
+    OASM_ETIMEOUT = -5
+
+    def __init__(self, slots, mem_streams=None, fail_step=None):
+        self.slots = slots
+        self.mem = slots if mem_streams is None else mem_streams
+        self.fail_step = fail_step
+        self.open, self.data, self.ended, self.log = set(), {}, set(), []
+        self.steps = 0
+        self.pending = False
+
+    def ops(self):
+        import ctypes
+
+        def open_streams(n, sids, n_opened):
+            got = 0
+            for s in range(self.slots):
+                if got == n or len(self.open) >= self.mem:
+                    break
+                if s not in self.open:
+                    self.open.add(s)
+                    self.data[s] = bytearray()
+                    self.log.append(("open", s))
+                    sids[got] = s
+                    got += 1
+            n_opened[0] = got
+            return 0
+
+        def feed_many(n, sid, buf, off, ln):
+            base = ctypes.addressof(buf.contents)
+            for j in range(n):
+                s = sid[j]
+                assert s in self.open and s not in self.ended
+                self.data[s] += ctypes.string_at(base + off[j], ln[j])
+            self.pending = True
+            return 0
+
+        def end_streams(n, sids):
+            for j in range(n):
+                self.ended.add(sids[j])
+            return 0
+
+        def close_streams(n, sids):
+            for j in range(n):
+                s = sids[j]
+                assert s in self.ended, "closed before its end was processed"
+                self.log.append(("close", s, bytes(self.data[s])))
+                self.open.discard(s)
+                self.ended.discard(s)
+            return 0
+
+        def step_begin():
+            self.steps += 1
+            self.log.append(("step",))
+            return 0
+
+        def step_end():
+            return self.OASM_ETIMEOUT if self.steps == self.fail_step else 0
+
+        def ready(sid, n):
+            n[0] = 0
+            return 0
+
+        def drain(out, cap, n):
+            n[0] = 0
+            return 0
+
+        return dict(open_streams=open_streams, feed_many=feed_many, end_streams=end_streams,
+                    close_streams=close_streams, step_begin=step_begin, step_end=step_end,
+                    ready=ready, drain=drain)
+
+
+def native_replay(tr, fake, budget):
+    from paper_1712_03560_gb300 import binding as B
+    return B.oasm_replay_ops(fake.ops(), tr.times, tr.streams, tr.offs, tr.lens, tr.last,
+                             tr.payload, tr.n_streams, realtime=False, max_batch_bytes=budget)
+
+
+def peak_open(log):
+    live, peak = 0, 0
+    for e in log:
+        live += {"open": 1, "close": -1}.get(e[0], 0)
+        peak = max(peak, live)
+    return peak
+
+
+@pytest.mark.parametrize("slots,budget", [(3, 1 << 30), (5, 3000), (64, 1 << 30), (2, 1500)])
+def test_native_scheduler_feeds_every_packet_once_in_stream_order(slots, budget):
+    """The native loop (oasm_replay_ops) against a fake library on the CPU:
+    every stream opened, fed exactly its packets in order, ended and closed;
+    never more streams open than slots."""
+    tr = W.served(seed=3, n_streams=12, n_sig=4, gbps=1.0, duration=0.004, life=0.4)
+    fake = NativeFake(slots)
+    rc, done, st = native_replay(tr, fake, budget)
+    assert rc == 0
+    got = sorted(e[2] for e in fake.log if e[0] == "close")
+    assert got == sorted(bytes(t) for t in tr.stream_texts() if t.size)
+    assert st["packets"] == tr.n_packets and st["bytes"] == int(tr.lens.sum())
+    assert st["streams_admitted"] == sum(1 for t in tr.stream_texts() if t.size)
+    assert np.isfinite(done).all()
+    assert peak_open(fake.log) <= slots
+    if slots < 12:
+        assert st["max_waiting_streams"] > 0
+
+
+def test_native_scheduler_waits_out_admission_refused_by_memory():
+    """Host fault injection in the native loop: admission refused for memory
+    while slots are free; streams wait and every packet is still fed once,
+    in order."""
+    tr = W.served(seed=5, n_streams=10, n_sig=4, gbps=1.0, duration=0.004, life=0.4)
+    fake = NativeFake(slots=8, mem_streams=3)
+    rc, done, st = native_replay(tr, fake, 4000)
+    assert rc == 0
+    got = sorted(e[2] for e in fake.log if e[0] == "close")
+    assert got == sorted(bytes(t) for t in tr.stream_texts() if t.size)
+    assert st["max_waiting_streams"] > 0
+    assert peak_open(fake.log) <= 3
+
+
+def test_native_scheduler_reports_no_admission_possible():
+    """No stream fits the memory budget at all: OASM_ENOMEM, not a hang."""
+    tr = W.served(seed=7, n_streams=4, n_sig=4, gbps=1.0, duration=0.002, life=0.4)
+    rc, _, _ = native_replay(tr, NativeFake(slots=4, mem_streams=0), 4000)
+    assert rc == -2
+
+
+def test_native_scheduler_surfaces_a_failed_step():
+    """Host fault injection in the native loop: a step whose end reports a
+    device-wait timeout ends the replay with that error at once."""
+    tr = W.served(seed=6, n_streams=6, n_sig=4, gbps=1.0, duration=0.004, life=0.4)
+    fake = NativeFake(6, fail_step=3)
+    rc, _, _ = native_replay(tr, fake, 2000)
+    assert rc == NativeFake.OASM_ETIMEOUT
+    assert fake.steps == 3
+
+
 @pytest.mark.gpu
 @pytest.mark.parametrize("slots,budget,realtime,engine",
                          [(4096, 1 << 30, False, "python"), (24, 20000, False, "python"),
