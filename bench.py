@@ -49,12 +49,14 @@ OPS_PER_WORD_STEP = 16  # integer ops of one 32-bit column step of the scan
 # minimums, and a compare and a select for the substitution cost
 OPS_PER_DP_CELL = 7
 WEIGHTED_DEFAULT_COSTS = (1, 2, 2)
-# DRAM bytes per scan launch and text byte, from an ncu capture of one step's
-# four scan launches on the 64 MiB DNA dictionary with the current kernels
-# (69.0, 75.4, 75.9 and 70.1 MB, mean 72.6 MB per launch for 64 MiB);
-# traffic scales with the text
-SCAN_DRAM_BYTES_PER_TEXT_BYTE = {"dictionary_dna": 72.6e6 / (64 << 20),
-                                 "dictionary_dna_64m": 72.6e6 / (64 << 20)}
+# DRAM bytes per scan launch and text byte, from an ncu capture of the current
+# scan kernels (traffic scales with the text: each launch reads it once); a
+# workload without a capture of the current kernels reports traffic null
+SCAN_DRAM_BYTES_PER_TEXT_BYTE = {
+    # the Zipf byte dictionary's six scan launches on a 256 MiB text: 293.6 MB
+    # per launch (mean of 12, profiles/scan_cut_kernel_bytes_zipf_256m.md)
+    "bytes_zipf": 293.58e6 / (256 << 20),
+    "bytes_zipf_256m": 293.58e6 / (256 << 20)}
 # integer lanes per SM that can issue one integer instruction per clock (four
 # sub-partitions of 32 lanes): the derived peak is SMs x 128 x SM clock
 INT_LANES_PER_SM = 128
@@ -604,7 +606,7 @@ def measure_workload(args, name, dev, steps, warmup, *, rank=0, world=1, dist=No
         units = "executed dynamic-program cells (32 W rows per pattern) x 7 ops"
         kname, opu = "wscan_kernel (weighted wave-front, all classes of a step)", OPS_PER_DP_CELL
     tpb = None if args.costs is not None else SCAN_DRAM_BYTES_PER_TEXT_BYTE.get(name)
-    traffic = tpb * wl.text_bytes / launches_step if tpb else None
+    traffic = tpb * wl.text_bytes if tpb else None  # bytes per scan launch
     hbm_peak = measured_hbm_gbs()
     peak = derived["tops"]
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
@@ -628,7 +630,7 @@ def measure_workload(args, name, dev, steps, warmup, *, rank=0, world=1, dist=No
     # ---- end to end through host buffers (pinned-free: oasm_feed copies the
     # caller's pageable bytes into the library's pinned staging)
     e2e = None
-    if with_e2e:
+    if with_e2e and not args.no_e2e:
         host = [np.ascontiguousarray(t) for t in wl.texts]
         step_host(host)
         torch.cuda.synchronize()
@@ -675,7 +677,7 @@ def measure_workload(args, name, dev, steps, warmup, *, rank=0, world=1, dist=No
         return res
 
     want = idx = text = None
-    if with_cpu and world == 1:
+    if with_cpu and not args.no_cpu and world == 1:
         cpu, (idx, text, ores) = cpu_baseline(wl, args.cpu_seconds, args.costs, args.output)
         res["cpu_baseline"] = cpu
         # the sampled patterns' GPU output must equal the oracle's on that sample
