@@ -54,7 +54,7 @@ WEIGHTED_DEFAULT_COSTS = (1, 2, 2)
 # workload without a capture of the current kernels reports traffic null
 SCAN_DRAM_BYTES_PER_TEXT_BYTE = {
     # the Zipf byte dictionary's six scan launches on a 256 MiB text: 293.6 MB
-    # per launch (mean of 12, profiles/scan_cut_kernel_bytes_zipf_256m.md)
+    # per launch (mean of the 12 launches of two steps)
     "bytes_zipf": 293.58e6 / (256 << 20),
     "bytes_zipf_256m": 293.58e6 / (256 << 20)}
 # integer lanes per SM that can issue one integer instruction per clock (four
