@@ -663,6 +663,16 @@ int oasm_flush(oasm_ctx* ctx, uint32_t sid, int end_of_stream, oasm_hit* out, si
     if ((rc = run_step(ctx))) return rc;
   }
   StreamRec& s = ctx->streams[sid];
+  if (s.lent_n) {  // the last step's records, where that step left them
+    const size_t n = std::min(cap, s.lent_n);
+    if (n && !out) return fail(ctx, OASM_EINVAL, "null output array");
+    if (n) parallel_copy({CopyTask{out, s.lent, n}});
+    s.lent += n;
+    s.lent_n -= n;
+    if (n_out) *n_out = n;
+    if (!s.lent_n) s.lent = nullptr;
+    return s.lent_n ? OASM_ETRUNC : OASM_OK;
+  }
   merge_runs(s);
   const size_t avail = s.ready.size() - s.head;
   const size_t n = std::min(cap, avail);
@@ -693,13 +703,13 @@ int oasm_drain(oasm_ctx* ctx, oasm_hit* out, size_t cap, size_t* n_out) {
   bool trunc = false;
   for (uint32_t sid = 0; sid < ctx->streams.size(); ++sid) {
     StreamRec& s = ctx->streams[sid];
-    if (!s.open || s.head == s.ready.size()) continue;
+    if (!s.open || (s.head == s.ready.size() && !s.lent_n)) continue;
     if (got == cap) {
       trunc = true;
       break;
     }
     merge_runs(s);
-    const size_t avail = s.ready.size() - s.head;
+    const size_t avail = s.lent_n ? s.lent_n : s.ready.size() - s.head;
     const size_t take = std::min(avail, cap - got);
     plan.push_back(Copy{sid, got, take});
     got += take;
@@ -713,11 +723,17 @@ int oasm_drain(oasm_ctx* ctx, oasm_hit* out, size_t cap, size_t* n_out) {
   tasks.reserve(plan.size());
   for (const Copy& c : plan) {
     const StreamRec& s = ctx->streams[c.sid];
-    tasks.push_back(CopyTask{out + c.off, s.ready.data() + s.head, c.n});
+    tasks.push_back(CopyTask{out + c.off, s.lent_n ? s.lent : s.ready.data() + s.head, c.n});
   }
   parallel_copy(tasks);
   for (const Copy& c : plan) {
     StreamRec& s = ctx->streams[c.sid];
+    if (s.lent_n) {
+      s.lent += c.n;
+      s.lent_n -= c.n;
+      if (!s.lent_n) s.lent = nullptr;
+      continue;
+    }
     s.head += c.n;
     if (s.head == s.ready.size()) {
       s.ready.clear();
@@ -733,14 +749,15 @@ int oasm_ready(oasm_ctx* ctx, uint32_t sid, size_t* n) {
   if (ctx && n && sid == OASM_ALL_STREAMS) {
     size_t tot = 0;
     for (const StreamRec& s : ctx->streams)
-      if (s.open) tot += s.ready.size() - s.head;
+      if (s.open) tot += s.ready.size() - s.head + s.lent_n;
     *n = tot;
     return OASM_OK;
   }
   int rc = check_sid(ctx, sid);
   if (rc) return rc;
   if (!n) return OASM_EINVAL;
-  *n = ctx->streams[sid].ready.size() - ctx->streams[sid].head;
+  const StreamRec& s = ctx->streams[sid];
+  *n = s.ready.size() - s.head + s.lent_n;
   return OASM_OK;
 }
 

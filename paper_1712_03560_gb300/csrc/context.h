@@ -195,6 +195,13 @@ struct StreamRec {
   HitVec ready;                 // decided hits; [head, end) not yet returned
   size_t head = 0;
   std::vector<size_t> runs;     // starts of canonically sorted runs in `ready`
+  // The last step's records of this stream, left where that step put them (the
+  // context's pinned record buffer) when the queue above was empty: a drain
+  // or flush copies them out once instead of twice.  The next step copies
+  // them into `ready` before it writes the buffer again (finish_step); while
+  // lent_n > 0, `ready` is empty.
+  const oasm_hit* lent = nullptr;
+  size_t lent_n = 0;
 };
 
 inline bool canon_less(const oasm_hit& a, const oasm_hit& b) {

@@ -368,7 +368,22 @@ int finish_step(oasm_ctx* ctx, StepPlan& pl, const WorkItem* d_items, bool* over
   ctx->st.prefilter_candidates += c.n_pref;
   ctx->st.hits += c.n_hits;
   ctx->st.kept += c.n_out;
-  // records -> streams
+  // records -> streams.  Records still lent from the pinned buffer (not yet
+  // drained) move into their streams' queues before the buffer is reused.
+  {
+    std::vector<CopyTask> keep;
+    for (StreamRec& sr : ctx->streams)
+      if (sr.lent_n) {
+        sr.ready.clear();
+        sr.head = 0;
+        sr.runs.assign(1, 0);
+        sr.ready.resize(sr.lent_n);
+        keep.push_back(CopyTask{sr.ready.data(), sr.lent, sr.lent_n});
+        sr.lent = nullptr;
+        sr.lent_n = 0;
+      }
+    if (!keep.empty()) parallel_copy(keep);
+  }
   if (c.n_out) {
     const size_t n = size_t(c.n_out);
     if (n > ctx->h_out_cap) {
@@ -402,22 +417,27 @@ int finish_step(oasm_ctx* ctx, StepPlan& pl, const WorkItem* d_items, bool* over
                 [](const auto& a, const auto& b) { return a.first < b.first; });
       for (auto& f : found) starts.insert(starts.end(), f.second.begin(), f.second.end());
     }
+    // a stream with an empty queue borrows its run where it is (no copy);
+    // the others append it to their queues as a new sorted run
     const size_t nr = starts.size();
-    std::vector<oasm_hit*> dst(nr);
+    std::vector<CopyTask> tasks;
     for (size_t r = 0; r < nr; ++r) {
       const size_t b = starts[r], e = (r + 1 < nr) ? starts[r + 1] : n;
       StreamRec& sr = ctx->streams[recs[b].stream_id];
+      if (sr.head == sr.ready.size()) {
+        sr.ready.clear();
+        sr.runs.clear();
+        sr.head = 0;
+        sr.lent = recs + b;
+        sr.lent_n = e - b;
+        continue;
+      }
       const size_t old = sr.ready.size();
       sr.runs.push_back(old);
       sr.ready.resize(old + (e - b));
-      dst[r] = sr.ready.data() + old;
+      tasks.push_back(CopyTask{sr.ready.data() + old, recs + b, e - b});
     }
-    std::vector<CopyTask> tasks(nr);
-    for (size_t r = 0; r < nr; ++r) {
-      const size_t b = starts[r], e = (r + 1 < nr) ? starts[r + 1] : n;
-      tasks[r] = CopyTask{dst[r], recs + b, e - b};
-    }
-    parallel_copy(tasks);
+    if (!tasks.empty()) parallel_copy(tasks);
   }
   return OASM_OK;
 }
