@@ -664,7 +664,8 @@ def measure_workload(args, name, dev, steps, warmup, *, rank=0, world=1, dist=No
            "host_ms_per_step": host_step_ms,
            "library_host_ms_per_step": {k: st[k] / steps for k in
                                         ("host_plan_ms", "host_launch_ms", "host_wait_ms",
-                                         "host_post_ms")},
+                                         "host_post_ms", "host_copy_ms")},
+           "record_bytes_per_step": st["record_bytes"] / steps,
            "candidates_per_step": st["candidates"] / steps,
            "hits_per_step": st["hits"] / steps,
            "gpu_launches": int(st["launches"]),
@@ -802,7 +803,9 @@ def extra_entry(m: dict) -> dict:
             "occurrences_per_step": m["occurrences_per_step"],
             "kernel_ms": m["kernel_ms"],
             "scan_share_of_step": m["kernel_ms"]["scan_ms"] / max(m["ms_per_step"], 1e-9),
-            "host_ms_per_step": m["host_ms_per_step"]}
+            "host_ms_per_step": m["host_ms_per_step"],
+            "library_host_ms_per_step": m["library_host_ms_per_step"],
+            "record_bytes_per_step": m["record_bytes_per_step"]}
 
 
 def main():
@@ -843,6 +846,7 @@ def main():
         "prefilter": m["prefilter"],
         "host_ms_per_step": m["host_ms_per_step"],
         "library_host_ms_per_step": m["library_host_ms_per_step"],
+        "record_bytes_per_step": m["record_bytes_per_step"],
         "candidates_per_step": m["candidates_per_step"],
         "hits_per_step": m["hits_per_step"],
         "gpu_launches": m["gpu_launches"],

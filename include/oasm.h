@@ -161,6 +161,9 @@ typedef struct {
     uint64_t buffer_grows;   /* device or pinned host buffers reallocated larger
                                 (each a cudaMalloc or cudaHostAlloc on the call's
                                 path, and a free of the old buffer) */
+    double host_copy_ms;     /* part of host_post_ms: waiting for the copy of a
+                                step's records to pinned host memory */
+    uint64_t record_bytes;   /* bytes of records copied to the host */
 } oasm_stats;
 
 /* Fills *cfg / *rules with the defaults described above. */

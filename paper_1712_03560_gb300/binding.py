@@ -79,7 +79,8 @@ class oasm_stats(ctypes.Structure):
                 ("prefilter_ms", ctypes.c_double), ("prefilter_candidates", ctypes.c_uint64),
                 ("host_plan_ms", ctypes.c_double), ("host_launch_ms", ctypes.c_double),
                 ("host_wait_ms", ctypes.c_double), ("host_post_ms", ctypes.c_double),
-                ("buffer_grows", ctypes.c_uint64)]
+                ("buffer_grows", ctypes.c_uint64), ("host_copy_ms", ctypes.c_double),
+                ("record_bytes", ctypes.c_uint64)]
 
 
 class oasm_costs(ctypes.Structure):

@@ -98,9 +98,10 @@ void free_ctx(oasm_ctx* c) {
   f(c->arena.p); f(c->upload.p); f(c->stage[0].d.p); f(c->stage[1].d.p); f(c->cand.p); f(c->keys.p);
   f(c->keys_alt.p); f(c->out.p); f(c->pool_hdr.p); f(c->pool_mem.p); f(c->pair_pool.p);
   f(c->out_sorted.p); f(c->okeys.p); f(c->okeys_alt.p); f(c->ovals.p); f(c->ovals_alt.p);
-  f(c->d_ctr); f(c->d_hist);
+  f(c->d_ctr); f(c->d_hist); f(c->run_start.p);
   for (const auto& r : c->host_ranges) cudaHostUnregister(const_cast<uint8_t*>(r.host));
   if (c->h_ctr) cudaFreeHost(c->h_ctr);
+  if (c->h_run_start) cudaFreeHost(c->h_run_start);
   for (auto& sg : c->stage)
     if (sg.h) cudaFreeHost(sg.h);
   if (c->h_upload) cudaFreeHost(c->h_upload);

@@ -349,6 +349,9 @@ struct oasm_ctx {
   DevArray<WinHdr> pool_hdr;
   DevArray<MemRow> pool_mem;
   DevArray<int32_t> pair_pool;
+  DevArray<unsigned long long> run_start;  // [n_items + 1] records of each work item
+  unsigned long long* h_run_start = nullptr;  // pinned copy, read after the step
+  size_t h_run_start_cap = 0;
   StepCounters* d_ctr = nullptr;
   StepCounters* h_ctr = nullptr;
   unsigned int* d_hist = nullptr;

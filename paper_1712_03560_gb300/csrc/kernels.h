@@ -124,5 +124,9 @@ cudaError_t launch_permute(const DevHit* src, const uint32_t* idx, DevHit* dst,
 cudaError_t launch_filter(const StepParams& p, const unsigned long long* sorted, cudaStream_t s);
 cudaError_t launch_finalize(const StepParams& p, cudaStream_t s);
 cudaError_t launch_tails(const StepParams& p, cudaStream_t s);
+// start[w] = first canonically sorted record of work item w, w = 0..n_items
+// (start[n_items] = the record count), from the sorted record keys
+cudaError_t launch_runs(const unsigned long long* sorted_keys, const StepParams& p,
+                        unsigned long long* start, cudaStream_t s);
 
 }  // namespace oasm

@@ -627,6 +627,33 @@ __global__ void tails_kernel(const StepParams P) {
   }
 }
 
+// Run boundaries of the canonically sorted records: the records of work item
+// w are [start[w], start[w + 1]), the first index whose key belongs to a pair
+// of item w or later (binary search over the sorted keys; pair = item x n_pat
+// + pattern sits above bit `shift`).  start[n_items] = the record count.
+__global__ void runs_kernel(const unsigned long long* __restrict__ keys,
+                            const unsigned long long* count, unsigned long long cap,
+                            uint32_t n_items, uint32_t n_pat, int shift,
+                            unsigned long long* __restrict__ start) {
+  const uint32_t w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w > n_items) return;
+  const unsigned long long n = min(*count, cap);
+  if (w == n_items) {
+    start[w] = n;
+    return;
+  }
+  const unsigned long long first_pair = (unsigned long long)w * n_pat;
+  unsigned long long lo = 0, hi = n;  // first index with pair >= first_pair
+  while (lo < hi) {
+    const unsigned long long mid = (lo + hi) >> 1;
+    if ((keys[mid] >> shift) < first_pair)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  start[w] = lo;
+}
+
 int grid_for(unsigned long long n, int threads, int cap_blocks) {
   unsigned long long b = (n + threads - 1) / threads;
   if (b < 1) b = 1;
@@ -685,6 +712,14 @@ cudaError_t launch_filter(const StepParams& p, const unsigned long long* sorted,
 cudaError_t launch_finalize(const StepParams& p, cudaStream_t s) {
   const unsigned long long npairs = (unsigned long long)p.n_items * p.n_pat;
   finalize_kernel<<<grid_for(npairs, 256, p.num_sms * 16), 256, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_runs(const unsigned long long* sorted_keys, const StepParams& p,
+                        unsigned long long* start, cudaStream_t s) {
+  const uint32_t n = p.n_items + 1;
+  runs_kernel<<<(n + 255) / 256, 256, 0, s>>>(sorted_keys, &p.ctr->n_out, p.cap_out, p.n_items,
+                                              p.n_pat, p.start_bits + kLowBits, start);
   return cudaGetLastError();
 }
 

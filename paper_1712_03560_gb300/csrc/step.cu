@@ -218,7 +218,12 @@ int enqueue_step(oasm_ctx* ctx, StepPlan& pl, const WorkItem* d_items, const Reg
     topo_add(0x200 + nl);
     CK(launch_permute(ctx->out.p, vs, ctx->out_sorted.p, &ctx->d_ctr->n_out, P.cap_out,
                       ctx->num_sms, s));
-    ctx->st.launches += uint64_t(nl) + 1;
+    // where each work item's (stream's) run of records starts
+    CK(launch_runs(ks, P, ctx->run_start.p, s));
+    CK(cudaMemcpyAsync(ctx->h_run_start, ctx->run_start.p,
+                       (size_t(n_items) + 1) * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                       s));
+    ctx->st.launches += uint64_t(nl) + 2;
   }
   if (tm) CK(record_event(ctx, ctx->ev[5], s));
   CK(cudaMemcpyAsync(ctx->h_ctr, ctx->d_ctr, sizeof(StepCounters), cudaMemcpyDeviceToHost, s));
@@ -397,33 +402,24 @@ int finish_step(oasm_ctx* ctx, StepPlan& pl, const WorkItem* d_items, bool* over
       }
       ctx->h_out_cap = n;
     }
-    CK(cudaMemcpy(ctx->h_out, ctx->out_sorted.p, n * sizeof(DevHit), cudaMemcpyDeviceToHost));
-    // sorted by work item first: one contiguous, already canonical run per
-    // stream.  Run starts are found and the runs copied into the streams'
-    // queues on several host threads when the output is large.
+    // one copy on the context's stream (bounded wait); the run of each work
+    // item (one stream) was located on the device
+    const auto t_copy = std::chrono::steady_clock::now();
+    CK(cudaMemcpyAsync(ctx->h_out, ctx->out_sorted.p, n * sizeof(DevHit), cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CK(cudaEventRecord(ctx->done, ctx->stream));
+    if ((rc = wait_event(ctx, ctx->done))) return rc;
+    ctx->st.host_copy_ms += ms_since(t_copy);
+    ctx->st.record_bytes += n * sizeof(DevHit);
     const oasm_hit* recs = reinterpret_cast<const oasm_hit*>(ctx->h_out);
-    std::vector<size_t> starts;
-    {
-      std::mutex mu;
-      std::vector<std::pair<size_t, std::vector<size_t>>> found;
-      parallel_parts(n, size_t(1) << 20, [&](size_t lo, size_t hi) {
-        std::vector<size_t> v;
-        for (size_t i = lo; i < hi; ++i)
-          if (i == 0 || recs[i].stream_id != recs[i - 1].stream_id) v.push_back(i);
-        std::lock_guard<std::mutex> g(mu);
-        found.emplace_back(lo, std::move(v));
-      });
-      std::sort(found.begin(), found.end(),
-                [](const auto& a, const auto& b) { return a.first < b.first; });
-      for (auto& f : found) starts.insert(starts.end(), f.second.begin(), f.second.end());
-    }
+    const unsigned long long* rs = ctx->h_run_start;
     // a stream with an empty queue borrows its run where it is (no copy);
     // the others append it to their queues as a new sorted run
-    const size_t nr = starts.size();
     std::vector<CopyTask> tasks;
-    for (size_t r = 0; r < nr; ++r) {
-      const size_t b = starts[r], e = (r + 1 < nr) ? starts[r + 1] : n;
-      StreamRec& sr = ctx->streams[recs[b].stream_id];
+    for (size_t it = 0; it < pl.items.size(); ++it) {
+      const size_t b = size_t(rs[it]), e = size_t(rs[it + 1]);
+      if (e <= b) continue;
+      StreamRec& sr = ctx->streams[pl.sids[it]];
       if (sr.head == sr.ready.size()) {
         sr.ready.clear();
         sr.runs.clear();
@@ -485,6 +481,16 @@ int step_begin(oasm_ctx* ctx) {
     if ((rc = ensure(ctx, ctx->keys_alt, h0, "hit keys"))) return rc;
   }
   if (!ctx->out.p && (rc = ensure_out(ctx, 1 << 16))) return rc;
+  if ((rc = ensure(ctx, ctx->run_start, pl.items.size() + 1, "record runs"))) return rc;
+  if (ctx->h_run_start_cap < pl.items.size() + 1) {
+    uint8_t* p = reinterpret_cast<uint8_t*>(ctx->h_run_start);
+    size_t cap_bytes = ctx->h_run_start_cap * sizeof(unsigned long long);
+    if ((rc = ensure_host(ctx, &p, &cap_bytes, (pl.items.size() + 1) * sizeof(unsigned long long),
+                          0)))
+      return rc;
+    ctx->h_run_start = reinterpret_cast<unsigned long long*>(p);
+    ctx->h_run_start_cap = cap_bytes / sizeof(unsigned long long);
+  }
   if (ctx->n_pref_pat && !ctx->pset.p &&
       (rc = ensure_pow2(ctx, ctx->pset, size_t(1) << 20, "piece filter set")))
     return rc;
