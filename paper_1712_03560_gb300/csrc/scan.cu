@@ -446,11 +446,22 @@ __device__ void scan_dict(const ScanArgs& A, const char* peq, uint8_t* tbuf, uin
         s0[g] = s[g];
         cnt[g] = 0;
       }
+      // the sign of cnt is set once a step had s < 0.  Two consecutive
+      // scores differ by at most 1, so the sum of a pair is negative exactly
+      // when one of the two is: one add per pair, one OR per two pairs
+      int sp[GPW], pa[GPW];
 #pragma unroll
       for (int j = 0; j < kBlk; ++j) {
         step_all(tv[j]);
 #pragma unroll
-        for (int g = 0; g < GPW; ++g) cnt[g] |= s[g];  // sign set once a step had s < 0
+        for (int g = 0; g < GPW; ++g) {
+          if ((j & 1) == 0)
+            sp[g] = s[g];
+          else if ((j & 3) == 1)
+            pa[g] = sp[g] + s[g];
+          else
+            cnt[g] |= pa[g] | (sp[g] + s[g]);
+        }
       }
       bool any = false;
 #pragma unroll
@@ -807,13 +818,20 @@ __device__ void scan_dict_cut(const ScanArgs& A, const char* peq0, const uint32_
     if (!full) {
       const uint32_t P0 = Pv[0], M0 = Mv[0];
       const int s00 = s0;
-      int act = 0;
+      // the sign of act is set once a step had D[32] <= K (pairs of
+      // consecutive steps summed, as in the one-pass scan)
+      int act = 0, sp = 0, pa = 0;
 #pragma unroll
       for (int j = 0; j < kBlk; ++j) {
         const uint32_t eq0 =
             *reinterpret_cast<const uint32_t*>(peq0 + fma_dbl(tv[j], rowb, lane_off));
         cut_word0_step(Pv[0], Mv[0], s0, eq0, two);
-        act |= s0;  // sign set once a step had D[32] <= K
+        if ((j & 1) == 0)
+          sp = s0;
+        else if ((j & 3) == 1)
+          pa = sp + s0;
+        else
+          act |= pa | (sp + s0);
       }
       if (!__any_sync(kFull, act < 0)) return;
       // a lane's first 32 rows came within K: the block again, every word
