@@ -96,6 +96,9 @@ def parse():
                     help="rules.output: the filtered occurrence set (OASM, default), every "
                          "Less Naive end, or every hit of Eq. 2 unfiltered (the raw counts of "
                          "the paper's Table 1 comparison)")
+    ap.add_argument("--record-order", type=int, default=0, choices=[0, 1, 2],
+                    help="cfg.record_order (filtered output): 0 automatic, 1 records written "
+                         "in canonical order by the filter, 2 appended then sorted")
     ap.add_argument("--tuning-cache", default=None,
                     help="JSON file of autotuned launch settings keyed by GPU and pattern "
                          "set: reused when the key is there, written after tuning otherwise")
@@ -465,7 +468,7 @@ def run_config(args, wl, desc, world: int) -> dict:
             if wl.text_bytes > (129 << 20) else "input smaller than L2",
             "parallelism": f"replicas x{world}",
             "prefilter_piece": args.prefilter, "graphs": args.graphs,
-            "output": args.output,
+            "output": args.output, "record_order": args.record_order,
             "costs": None if args.costs is None else dict(zip(("sub", "ins", "del"), args.costs))}
 
 
@@ -482,7 +485,8 @@ def measure_workload(args, name, dev, steps, warmup, *, rank=0, world=1, dist=No
     rules = None if args.output == "filtered" else {"output": args.output}
     ctx = B.oasm_create(wl.patterns, wl.ks, rules,
                         {"device": dev, "timing": 1, "max_streams": max(64, len(wl.texts)),
-                         "prefilter_piece": args.prefilter, "graphs": args.graphs},
+                         "prefilter_piece": args.prefilter, "graphs": args.graphs,
+                         "record_order": args.record_order},
                         costs=args.costs)
     stream = torch.cuda.ExternalStream(B.oasm_cuda_stream(ctx), device=dev)
     dtexts = [torch.from_numpy(t).to(f"cuda:{dev}") for t in wl.texts]
@@ -703,7 +707,8 @@ def measure_workload(args, name, dev, steps, warmup, *, rank=0, world=1, dist=No
             args.costs is None and args.output == "filtered":
         ctx2 = B.oasm_create(wl.patterns, wl.ks, None,
                              {"device": dev, "timing": 1, "max_streams": max(64, len(wl.texts)),
-                              "prefilter_piece": 1, "graphs": args.graphs})
+                              "prefilter_piece": 1, "graphs": args.graphs,
+                              "record_order": args.record_order})
         try:
             stream2 = torch.cuda.ExternalStream(B.oasm_cuda_stream(ctx2), device=dev)
             if not args.no_autotune:

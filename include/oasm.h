@@ -120,6 +120,17 @@ typedef struct {
                                   of them comes within K of a match (the rows below
                                   then all exceed K), every word otherwise; same
                                   output.  1: every word at every step */
+    int32_t record_order;      /* filtered output only; same records either way.
+                                  0 (default): automatic.  1: the filter writes
+                                  each piece's records at a position fixed by the
+                                  piece's place among the sorted hits, and a scan
+                                  of the counts gives the output offsets
+                                  (canonical order without a record sort; needs
+                                  K_max + 1 spare record slots per stream and
+                                  pattern).  2: records are appended as decided,
+                                  then sorted.  Automatic takes 1 unless a step's
+                                  streams x patterns x (K_max + 1) exceeds its hit
+                                  capacity */
 } oasm_config;
 
 /* One occurrence added to S (or, for the raw outputs, one hit/end). */

@@ -57,7 +57,7 @@ class oasm_config(ctypes.Structure):
                 ("flush_timeout_ms", ctypes.c_uint32), ("cuda_stream", ctypes.c_void_p),
                 ("myers_only", ctypes.c_int32), ("graphs", ctypes.c_int32),
                 ("groups_per_warp", ctypes.c_uint32), ("prefilter_piece", ctypes.c_uint32),
-                ("full_words", ctypes.c_int32)]
+                ("full_words", ctypes.c_int32), ("record_order", ctypes.c_int32)]
 
 
 class oasm_hit(ctypes.Structure):

@@ -55,10 +55,11 @@ int ensure_host(oasm_ctx* ctx, uint8_t** p, size_t* cap, size_t n, size_t keep) 
   return OASM_OK;
 }
 
-int ensure_out(oasm_ctx* ctx, size_t n) {
+int ensure_out(oasm_ctx* ctx, size_t n, bool ordered) {
   int rc;
-  if ((rc = ensure(ctx, ctx->out, n, "records"))) return rc;
   if ((rc = ensure(ctx, ctx->out_sorted, n, "records"))) return rc;
+  if (ordered) return OASM_OK;  // written in order: no emission buffer, keys or sort
+  if ((rc = ensure(ctx, ctx->out, n, "records"))) return rc;
   if ((rc = ensure(ctx, ctx->okeys, n, "record keys"))) return rc;
   if ((rc = ensure(ctx, ctx->okeys_alt, n, "record keys"))) return rc;
   if ((rc = ensure(ctx, ctx->ovals, n, "record order"))) return rc;
@@ -98,7 +99,7 @@ void free_ctx(oasm_ctx* c) {
   f(c->arena.p); f(c->upload.p); f(c->stage[0].d.p); f(c->stage[1].d.p); f(c->cand.p); f(c->keys.p);
   f(c->keys_alt.p); f(c->out.p); f(c->pool_hdr.p); f(c->pool_mem.p); f(c->pair_pool.p);
   f(c->out_sorted.p); f(c->okeys.p); f(c->okeys_alt.p); f(c->ovals.p); f(c->ovals_alt.p);
-  f(c->d_ctr); f(c->d_hist); f(c->run_start.p);
+  f(c->d_ctr); f(c->d_hist); f(c->run_start.p); f(c->rtmp.p); f(c->seg.p); f(c->seg_part.p);
   for (const auto& r : c->host_ranges) cudaHostUnregister(const_cast<uint8_t*>(r.host));
   if (c->h_ctr) cudaFreeHost(c->h_ctr);
   if (c->h_run_start) cudaFreeHost(c->h_run_start);
@@ -216,10 +217,11 @@ int oasm_create_weighted(const uint8_t* const* pat, const uint32_t* len, const u
   }
   if (cfg && (cfg->groups_per_warp > 2 || cfg->tile_warps > 16 ||
               (cfg->prefilter_piece > 1 && (cfg->prefilter_piece < 4 || cfg->prefilter_piece > 128)) ||
-              cfg->full_words < 0 || cfg->full_words > 1)) {
+              cfg->full_words < 0 || cfg->full_words > 1 || cfg->record_order < 0 ||
+              cfg->record_order > 2)) {
     g_create_err =
         "config: groups_per_warp must be 0, 1 or 2; tile_warps 0..16; prefilter_piece 0, 1 or "
-        "4..128; full_words 0 or 1";
+        "4..128; full_words 0 or 1; record_order 0, 1 or 2";
     return OASM_EINVAL;
   }
   if (costs && (costs->sub < 1 || costs->sub > 255 || costs->ins < 1 || costs->ins > 255 ||

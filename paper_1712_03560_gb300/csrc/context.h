@@ -250,6 +250,7 @@ struct StepPlan {
   size_t arena_bytes = 0;
   int sb = 1, kb = 10;
   uint64_t new_bytes = 0;
+  bool ordered = false;              // records written in canonical order (no record sort)
 };
 
 // Pinned host staging for fed bytes, with its device copy.  Two of them
@@ -349,6 +350,9 @@ struct oasm_ctx {
   DevArray<WinHdr> pool_hdr;
   DevArray<MemRow> pool_mem;
   DevArray<int32_t> pair_pool;
+  DevArray<DevHit> rtmp;             // ordered records by segment position
+  DevArray<uint32_t> seg;             // segment counts, then output offsets
+  DevArray<unsigned long long> seg_part;  // the scan's per-block sums
   DevArray<unsigned long long> run_start;  // [n_items + 1] records of each work item
   unsigned long long* h_run_start = nullptr;  // pinned copy, read after the step
   size_t h_run_start_cap = 0;
@@ -386,7 +390,9 @@ namespace oasm {
 
 int fail(oasm_ctx* c, int code, const char* fmt, ...);
 int ensure_host(oasm_ctx* ctx, uint8_t** p, size_t* cap, size_t n, size_t keep);
-int ensure_out(oasm_ctx* ctx, size_t n);
+// Output record buffers for n records; `ordered` steps need only the
+// canonically ordered one.
+int ensure_out(oasm_ctx* ctx, size_t n, bool ordered = false);
 int bits_for(uint64_t v);  // bits needed to hold 0..v
 
 int wait_event(oasm_ctx* ctx, cudaEvent_t ev);
@@ -395,7 +401,11 @@ int build_prefilter(oasm_ctx* ctx, const std::vector<char>& pref);
 int build_tables(oasm_ctx* ctx);
 void choose_piece_filter(const uint8_t* const* pat, const uint32_t* len, const uint32_t* k,
                          uint32_t n, uint32_t piece, uint8_t* on_filter);
-StepParams make_params(oasm_ctx* ctx, const WorkItem* d_items, uint32_t n_items, int sb, int kb);
+StepParams make_params(oasm_ctx* ctx, const WorkItem* d_items, uint32_t n_items, int sb, int kb,
+                       bool ordered = false);
+// Chooses whether the step writes its records in canonical order and sizes
+// the buffers that path needs.
+int prepare_records(oasm_ctx* ctx, StepPlan& pl);
 int bucket_gpw(const oasm_ctx* ctx, const Bucket& b);
 int64_t region_len(oasm_ctx* ctx, const Bucket& b, int64_t total_ends);
 int plan_step(oasm_ctx* ctx, StepPlan& pl);

@@ -122,7 +122,21 @@ cudaError_t launch_permute(const DevHit* src, const uint32_t* idx, DevHit* dst,
                            const unsigned long long* count, unsigned long long cap,
                            int num_sms, cudaStream_t s);
 cudaError_t launch_filter(const StepParams& p, const unsigned long long* sorted, cudaStream_t s);
-cudaError_t launch_finalize(const StepParams& p, cudaStream_t s);
+// Carried windows: kFinFlush emits the decidable ones of pairs without hits,
+// kFinCommit writes the new window state; kFinAll does both.
+constexpr int kFinFlush = 1, kFinCommit = 2, kFinAll = 3;
+cudaError_t launch_finalize(const StepParams& p, const unsigned long long* sorted, int phase,
+                            cudaStream_t s);
+// Ordered records (p.ordered).  The scan turns the segment counts into
+// offsets (the total into ctr->n_out, overflow bit 2 past cap_out); the emit
+// moves the records into dst in canonical order and each work item's first
+// record into run_start.  part holds ordered_scan_blocks() entries; p.seg
+// must hold ordered_seg_len(p.cap_rtmp) entries, all zero before the filter.
+int ordered_scan_blocks(int num_sms);
+size_t ordered_seg_len(size_t cap_rtmp);
+cudaError_t launch_ordered_scan(const StepParams& p, unsigned long long* part, cudaStream_t s);
+cudaError_t launch_ordered_emit(const StepParams& p, const unsigned long long* sorted,
+                                DevHit* dst, unsigned long long* run_start, cudaStream_t s);
 cudaError_t launch_tails(const StepParams& p, cudaStream_t s);
 // start[w] = first canonically sorted record of work item w, w = 0..n_items
 // (start[n_items] = the record count), from the sorted record keys

@@ -111,7 +111,8 @@ struct StepCounters {
   unsigned long long n_pool;
   unsigned long long word_steps;
   unsigned int overflow;     // bit 0 candidates, 1 hits, 2 outputs, 3 pool,
-                             // 5 the prefilter's candidate set (with bit 0)
+                             // 5 the prefilter's candidate set (with bit 0),
+                             // 6 an ordered record outside its segment (a bug)
   unsigned int pad;
   unsigned long long n_pref;  // distinct (pattern, end) pairs the prefilter proposed
 };
@@ -174,7 +175,21 @@ struct StepParams {
   int32_t* pair_pool;            // [n_items * n_pat] pool index or -1
   StepCounters* ctr;
   int32_t num_sms;               // the device's SM count (grid sizes of the step kernels)
-  int32_t pad_sms;
+  // Records in canonical order without a record sort (filtered output).  A
+  // pair's segments are its pieces of sorted hits and, for a pair without
+  // hits, the decision of its carried window.  A segment writes its records
+  // to rtmp from the position of its first hit h: h + (pair + 1) * head, or
+  // h + pair * head for a pair's first segment, which may add up to head =
+  // kmax + 1 records of the window carried in from the previous step.  Every
+  // record is one hit of its segment (or a carried row), so segments never
+  // overlap, and positions follow the canonical order (pair, decided_at, k).
+  // seg[pos] holds the segment's record count; an exclusive scan turns the
+  // counts into output offsets.
+  int32_t ordered;
+  int32_t head;
+  DevHit* rtmp;                  // [cap_rtmp]
+  uint32_t* seg;                 // [cap_rtmp + 1], zero before the filter
+  unsigned long long cap_rtmp;   // >= cap_hits + n_items * n_pat * head
   // key packing
   int32_t start_bits;            // bits of start - base_pos
   int32_t key_bits;              // total significant bits of a key

@@ -14,6 +14,7 @@
 //   finalize  installs the new pending windows, decides carried windows of
 //             pairs without hits, and the tails kernel keeps the last T
 //             symbols of every stream for the next step.
+#include <algorithm>
 #include <utility>
 
 #include "kernels.h"
@@ -408,15 +409,12 @@ struct Window {
   int pend;
   int idx;
   MemRow rows[kMaxK + 1];
+  unsigned long long rpos;  // ordered records: the segment's first position
+  uint32_t nrec;            // records the segment wrote so far
 };
 
-__device__ void emit(const StepParams& P, uint32_t pair, int p, int lv, const MemRow& r, int64_t f,
-                     const WorkItem& w) {
-  const unsigned long long o = atomicAdd(&P.ctr->n_out, 1ull);
-  if (o >= P.cap_out) {
-    atomicOr(&P.ctr->overflow, 4u);
-    return;
-  }
+__device__ void emit(const StepParams& P, Window& W, uint32_t pair, int p, int lv,
+                     const MemRow& r, int64_t f, const WorkItem& w) {
   DevHit h;
   h.start = uint64_t(r.start);
   h.decided_at = uint64_t(f);
@@ -424,7 +422,23 @@ __device__ void emit(const StepParams& P, uint32_t pair, int p, int lv, const Me
   h.slot = w.slot;
   h.len = uint32_t(r.len);
   h.k = uint32_t(lv);
+  if (P.ordered) {
+    const unsigned long long o = W.rpos + W.nrec++;
+    if (o < P.cap_rtmp) P.rtmp[o] = h;
+    else atomicOr(&P.ctr->overflow, 64u);
+    return;
+  }
+  const unsigned long long o = atomicAdd(&P.ctr->n_out, 1ull);
+  if (o >= P.cap_out) {
+    atomicOr(&P.ctr->overflow, 4u);
+    return;
+  }
   put_record(P, o, h, out_key(P, pair, w, f, lv, r.len, P.m[p], P.K[p]));
+}
+
+// A segment's record count, read by the scan (ordered records).
+__device__ __forceinline__ void close_segment(const StepParams& P, const Window& W) {
+  if (P.ordered && W.nrec) P.seg[W.rpos] = W.nrec;
 }
 
 // Validation complete at f (Sec. 4.2): the highest-priority occurrence is
@@ -442,7 +456,7 @@ __device__ void flush(const StepParams& P, Window& W, uint32_t pair, int p, int 
     const int64_t lhs = (f - r.start + 1) - acc;
     const bool keep = (lv == W.idx) || (P.rules.cmp == OASM_CMP_GT ? lhs > r.len : lhs >= r.len);
     if (keep) {
-      emit(P, pair, p, lv, r, f, w);
+      emit(P, W, pair, p, lv, r, f, w);
       acc = (P.rules.acc == OASM_ACC_SUM) ? acc + r.len : r.len;
     }
   }
@@ -524,6 +538,8 @@ __global__ void __launch_bounds__(128)
     Wn.pend = 0;
     Wn.idx = K;
     for (int lv = 0; lv <= K; ++lv) Wn.rows[lv].valid = 0;
+    Wn.rpos = h + (unsigned long long)(first ? pair : pair + 1) * unsigned(P.head);
+    Wn.nrec = 0;
     int64_t maxend = INT64_MIN;
     if (first && chdr.pend) {
       Wn.pend = 1;
@@ -579,10 +595,32 @@ __global__ void __launch_bounds__(128)
         P.pair_pool[pair] = int32_t(q);
       }
     }
+    close_segment(P, Wn);
   }
 }
 
-__global__ void finalize_kernel(const StepParams P) {
+// First index of the sorted hit keys S[0, n) whose pair is >= pr.
+__device__ __forceinline__ unsigned long long pair_lower_bound(const unsigned long long* S,
+                                                               unsigned long long n,
+                                                               unsigned long long pr, int shift) {
+  unsigned long long lo = 0, hi = n;
+  while (lo < hi) {
+    const unsigned long long mid = (lo + hi) >> 1;
+    if ((S[mid] >> shift) < pr)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+// Phase kFinFlush emits the records of carried windows that pairs without
+// hits can now decide; kFinCommit installs the step's new windows (and
+// clears the decided ones) in the stream state.  The ordered record path
+// runs the two apart, so the state changes only once the record count is
+// known to fit (a step that overflows is re-run from unchanged state).
+__global__ void finalize_kernel(const StepParams P, const unsigned long long* __restrict__ S,
+                                int phase) {
   if (P.ctr->overflow) return;
   const unsigned long long npairs = (unsigned long long)P.n_items * P.n_pat;
   const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
@@ -595,16 +633,32 @@ __global__ void finalize_kernel(const StepParams P) {
     MemRow* rows = P.mem + size_t(w.slot) * P.mem_stride + P.mem_off[p];
     const int32_t q = P.pair_pool[pr];
     if (q >= 0) {
+      if (!(phase & kFinCommit)) continue;
       *hd = P.pool_hdr[q];
       for (int lv = 0; lv <= K; ++lv) rows[lv] = P.pool_mem[size_t(q) * (kMaxK + 1) + lv];
     } else if (hd->pend) {
       const MemRow& top = rows[hd->idx];
       if (w.eos || top.start + top.len - 1 <= f_new(w, m, K)) {
+        if (!(phase & kFinFlush)) {
+          WinHdr z;
+          z.pend = 0;
+          z.idx = K;
+          *hd = z;
+          for (int lv = 0; lv <= K; ++lv) rows[lv].valid = 0;
+          continue;
+        }
         Window Wn;
         Wn.pend = 1;
         Wn.idx = hd->idx;
         for (int lv = 0; lv <= K; ++lv) Wn.rows[lv] = rows[lv];
+        Wn.nrec = 0;
+        Wn.rpos = 0;
+        if (P.ordered)  // a pair without hits: its segment is the pair's head
+          Wn.rpos = pair_lower_bound(S, min(P.ctr->n_hits, P.cap_hits), pr,
+                                     P.start_bits + kLowBits) + pr * unsigned(P.head);
         flush(P, Wn, uint32_t(pr), p, K, w);
+        close_segment(P, Wn);
+        if (!(phase & kFinCommit)) continue;
         WinHdr z;
         z.pend = 0;
         z.idx = K;
@@ -652,6 +706,161 @@ __global__ void runs_kernel(const unsigned long long* __restrict__ keys,
       hi = mid;
   }
   start[w] = lo;
+}
+
+// ------------------------------------------------- ordered records
+// Exclusive scan of the segment counts seg[0, N] in place, N = hits + pairs
+// x head (seg[N] = 0 before: it becomes the record total), as three kernels:
+// per-block sums, a scan of those sums, and a per-block rescan from its
+// offset.  Each block owns a contiguous chunk of kScanTile-element tiles.
+constexpr int kScanThreads = 256;
+constexpr int kScanPer = 4;  // elements per thread and tile (one 16-byte load)
+constexpr int kScanTile = kScanThreads * kScanPer;
+constexpr int kScanMaxBlocks = 1024;
+
+__device__ __forceinline__ unsigned long long seg_count(const StepParams& P) {
+  return min(P.ctr->n_hits, P.cap_hits) +
+         (unsigned long long)P.n_items * P.n_pat * unsigned(P.head) + 1;
+}
+
+__device__ __forceinline__ unsigned long long scan_chunk(unsigned long long n) {
+  const unsigned long long tiles = (n + kScanTile - 1) / kScanTile;
+  return (tiles + gridDim.x - 1) / gridDim.x * kScanTile;
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+    seg_reduce_kernel(const StepParams P, unsigned long long* __restrict__ part) {
+  __shared__ unsigned long long ws[kScanThreads / 32];
+  const unsigned long long n = seg_count(P);
+  const unsigned long long chunk = scan_chunk(n);
+  const unsigned long long b0 = chunk * blockIdx.x, b1 = min(n, b0 + chunk);
+  unsigned long long acc = 0;
+  // seg is zero-filled to a whole tile past n: whole 16-byte loads
+  for (unsigned long long i = b0 + threadIdx.x * kScanPer; i < b1; i += kScanTile) {
+    const uint4 v = *reinterpret_cast<const uint4*>(P.seg + i);
+    acc += (unsigned long long)v.x + v.y + v.z + v.w;
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(kFull, acc, o);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long t = 0;
+    for (int w = 0; w < kScanThreads / 32; ++w) t += ws[w];
+    part[blockIdx.x] = t;
+  }
+}
+
+// One block: exclusive offsets of the block sums; the total is the record
+// count (checked against the output capacity).
+__global__ void __launch_bounds__(kScanMaxBlocks)
+    seg_top_kernel(const StepParams P, unsigned long long* __restrict__ part, int nblocks) {
+  __shared__ unsigned long long ws[kScanMaxBlocks / 32];
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const unsigned long long v = t < nblocks ? part[t] : 0ull;
+  unsigned long long incl = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long u = __shfl_up_sync(kFull, incl, o);
+    if (lane >= o) incl += u;
+  }
+  if (lane == 31) ws[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    unsigned long long x = ws[lane];
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long u = __shfl_up_sync(kFull, x, o);
+      if (lane >= o) x += u;
+    }
+    ws[lane] = x;  // inclusive sums of the warps
+  }
+  __syncthreads();
+  const unsigned long long before = (warp ? ws[warp - 1] : 0ull) + incl - v;
+  if (t < nblocks) part[t] = before;
+  if (t == kScanMaxBlocks - 1) {
+    const unsigned long long total = before + v;
+    P.ctr->n_out = total;
+    if (total > P.cap_out) atomicOr(&P.ctr->overflow, 4u);
+  }
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+    seg_down_kernel(const StepParams P, const unsigned long long* __restrict__ part) {
+  __shared__ uint32_t ws[kScanThreads / 32];
+  __shared__ uint32_t tile_total;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const unsigned long long n = seg_count(P);
+  const unsigned long long chunk = scan_chunk(n);
+  const unsigned long long b0 = chunk * blockIdx.x, b1 = min(n, b0 + chunk);
+  uint32_t run = uint32_t(part[blockIdx.x]);  // offsets fit 32 bits (cap_out does)
+  for (unsigned long long base = b0; base < b1; base += kScanTile) {
+    const unsigned long long i = base + unsigned(t) * kScanPer;
+    uint4 v = *reinterpret_cast<const uint4*>(P.seg + i);
+    const uint32_t s = v.x + v.y + v.z + v.w;
+    uint32_t incl = s;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t u = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += u;
+    }
+    if (lane == 31) ws[warp] = incl;
+    __syncthreads();
+    if (t == 0) {
+      uint32_t acc = 0;
+      for (int w = 0; w < kScanThreads / 32; ++w) {
+        const uint32_t c = ws[w];
+        ws[w] = acc;
+        acc += c;
+      }
+      tile_total = acc;
+    }
+    __syncthreads();
+    uint32_t e = run + ws[warp] + incl - s;
+    const uint32_t a = v.x, b = v.y, c = v.z;
+    v.x = e;
+    v.y = e += a;
+    v.z = e += b;
+    v.w = e + c;
+    if (i < b1) {
+      if (i + kScanPer <= b1) {
+        *reinterpret_cast<uint4*>(P.seg + i) = v;
+      } else {
+        const uint32_t o4[4] = {v.x, v.y, v.z, v.w};
+        for (int q = 0; q < kScanPer && i + q < b1; ++q) P.seg[i + q] = o4[q];
+      }
+    }
+    run += tile_total;
+    __syncthreads();
+  }
+}
+
+// Segment c holds seg[c + 1] - seg[c] records at rtmp[c ...): they go to
+// the output at seg[c].
+__global__ void compact_kernel(const StepParams P, DevHit* __restrict__ dst) {
+  const unsigned long long n = seg_count(P) - 1;
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long c = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; c < n;
+       c += stride) {
+    const uint32_t a = P.seg[c], b = P.seg[c + 1];
+    if (b <= a || b > P.cap_out) continue;
+    const uint4* src = reinterpret_cast<const uint4*>(P.rtmp + c);
+    uint4* out = reinterpret_cast<uint4*>(dst + a);
+    for (uint32_t q = 0; q < 2 * (b - a); ++q) out[q] = src[q];
+  }
+}
+
+// start[w] = the first output record of work item w: the offset of the head
+// segment of its first pair (w x n_pat); start[n_items] = the record count.
+__global__ void runs_ordered_kernel(const StepParams P, const unsigned long long* __restrict__ S,
+                                    unsigned long long* __restrict__ start) {
+  const uint32_t w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w > P.n_items) return;
+  const unsigned long long n = seg_count(P) - 1;
+  if (w == P.n_items) {
+    start[w] = P.seg[n];
+    return;
+  }
+  const unsigned long long pr = (unsigned long long)w * P.n_pat;
+  const unsigned long long h =
+      pair_lower_bound(S, min(P.ctr->n_hits, P.cap_hits), pr, P.start_bits + kLowBits);
+  start[w] = P.seg[h + pr * unsigned(P.head)];
 }
 
 int grid_for(unsigned long long n, int threads, int cap_blocks) {
@@ -709,9 +918,32 @@ cudaError_t launch_filter(const StepParams& p, const unsigned long long* sorted,
   return cudaGetLastError();
 }
 
-cudaError_t launch_finalize(const StepParams& p, cudaStream_t s) {
+cudaError_t launch_finalize(const StepParams& p, const unsigned long long* sorted, int phase,
+                            cudaStream_t s) {
   const unsigned long long npairs = (unsigned long long)p.n_items * p.n_pat;
-  finalize_kernel<<<grid_for(npairs, 256, p.num_sms * 16), 256, 0, s>>>(p);
+  finalize_kernel<<<grid_for(npairs, 256, p.num_sms * 16), 256, 0, s>>>(p, sorted, phase);
+  return cudaGetLastError();
+}
+
+int ordered_scan_blocks(int num_sms) { return std::min(kScanMaxBlocks, num_sms * 4); }
+
+size_t ordered_seg_len(size_t cap_rtmp) {
+  return (cap_rtmp + 1 + kScanTile - 1) / kScanTile * kScanTile;
+}
+
+cudaError_t launch_ordered_scan(const StepParams& p, unsigned long long* part, cudaStream_t s) {
+  const int nb = ordered_scan_blocks(p.num_sms);
+  seg_reduce_kernel<<<nb, kScanThreads, 0, s>>>(p, part);
+  seg_top_kernel<<<1, kScanMaxBlocks, 0, s>>>(p, part, nb);
+  seg_down_kernel<<<nb, kScanThreads, 0, s>>>(p, part);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ordered_emit(const StepParams& p, const unsigned long long* sorted,
+                                DevHit* dst, unsigned long long* run_start, cudaStream_t s) {
+  compact_kernel<<<grid_for(p.cap_rtmp, 256, p.num_sms * 8), 256, 0, s>>>(p, dst);
+  const uint32_t n = p.n_items + 1;
+  runs_ordered_kernel<<<(n + 255) / 256, 256, 0, s>>>(p, sorted, run_start);
   return cudaGetLastError();
 }
 

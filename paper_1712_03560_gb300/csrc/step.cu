@@ -161,7 +161,7 @@ int enqueue_step(oasm_ctx* ctx, StepPlan& pl, const WorkItem* d_items, const Reg
     ctx->st.launches += 1;
     ctx->st.scan_launches += 1;
   }
-  StepParams P = make_params(ctx, d_items, n_items, pl.sb, pl.kb);
+  StepParams P = make_params(ctx, d_items, n_items, pl.sb, pl.kb, pl.ordered);
   if (ctx->n_pref_pat) {
     const size_t nb = ctx->buckets.size();
     PrefArgs f{};
@@ -200,15 +200,33 @@ int enqueue_step(oasm_ctx* ctx, StepPlan& pl, const WorkItem* d_items, const Reg
     topo_add(0x100 + nl);
     ctx->st.launches += uint64_t(nl);
     if (tm) CK(record_event(ctx, ctx->ev[4], s));
-    CK(launch_filter(P, sorted, s));
-    CK(launch_finalize(P, s));
-    ctx->st.launches += 2;
+    if (pl.ordered) {
+      // records by segment; the window state is written only after the scan
+      // has checked that the records fit (a re-run starts from it unchanged)
+      CK(cudaMemsetAsync(ctx->seg.p, 0, ordered_seg_len(ctx->rtmp.cap) * sizeof(uint32_t), s));
+      CK(launch_filter(P, sorted, s));
+      CK(launch_finalize(P, sorted, kFinFlush, s));
+      CK(launch_ordered_scan(P, ctx->seg_part.p, s));
+      CK(launch_finalize(P, sorted, kFinCommit, s));
+      ctx->st.launches += 6;
+    } else {
+      CK(launch_filter(P, sorted, s));
+      CK(launch_finalize(P, sorted, kFinAll, s));
+      ctx->st.launches += 2;
+    }
   } else if (tm) {
     CK(record_event(ctx, ctx->ev[4], s));
   }
   CK(launch_tails(P, s));
   ctx->st.launches += 1;
-  {  // emitted records -> canonical order (work item, pattern, decided_at, k, length)
+  if (pl.ordered) {  // records from their segments to their offsets: canonical order
+    CK(launch_ordered_emit(P, sorted, ctx->out_sorted.p, ctx->run_start.p, s));
+    topo_add(0x300);
+    CK(cudaMemcpyAsync(ctx->h_run_start, ctx->run_start.p,
+                       (size_t(n_items) + 1) * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                       s));
+    ctx->st.launches += 2;
+  } else {  // emitted records -> canonical order (work item, pattern, decided_at, k, length)
     int nl = 0;
     unsigned long long* ks = nullptr;
     uint32_t* vs = nullptr;
@@ -238,11 +256,31 @@ double ms_since(std::chrono::steady_clock::time_point t0) {
 
 // Launches one step's device work (as a graph or directly) and records the
 // completion event; returns without waiting.
+// The ordered record path (filtered output) replaces the per-record atomics,
+// the record sort and the permutation by a scan over the segment counts.  Its
+// extra room, `head` slots per pair, pays when pairs are few against the hit
+// capacity (one text and many patterns, many texts with many hits); steps of
+// many pairs and few hits (a served batch) keep the sort.
+int prepare_records(oasm_ctx* ctx, StepPlan& pl) {
+  const size_t npairs = pl.items.size() * size_t(ctx->n_pat);
+  const size_t head = size_t(ctx->kmax) + 1;
+  const size_t cap_hits = std::min(ctx->keys.cap, ctx->keys_alt.cap);
+  const int ro = ctx->cfg.record_order;
+  pl.ordered = ctx->rules.output == OASM_OUT_FILTERED &&
+               (ro == 1 || (ro == 0 && npairs * head <= cap_hits));
+  if (!pl.ordered) return OASM_OK;
+  int rc;
+  if ((rc = ensure(ctx, ctx->rtmp, cap_hits + npairs * head, "ordered records"))) return rc;
+  if ((rc = ensure(ctx, ctx->seg, ordered_seg_len(ctx->rtmp.cap), "record segments"))) return rc;
+  return ensure(ctx, ctx->seg_part, size_t(ordered_scan_blocks(ctx->num_sms)), "record scan");
+}
+
 int launch_step(oasm_ctx* ctx, StepPlan& pl, const WorkItem* d_items, const Region* d_regions,
                 const CopyChunk* d_chunks) {
   const auto t_launch = std::chrono::steady_clock::now();
   cudaStream_t s = ctx->stream;
   int rc;
+  if ((rc = prepare_records(ctx, pl))) return rc;
   if (ctx->cfg.graphs) {
     // capture the step, then update the cached executable graph in place when
     // the step has the same shape (kernel arguments and grids may differ)
@@ -319,7 +357,8 @@ int finish_step(oasm_ctx* ctx, StepPlan& pl, const WorkItem* d_items, bool* over
     std::chrono::steady_clock::time_point t;
     ~PostTimer() { c->st.host_post_ms += ms_since(t); }
   } post_timer{ctx, t_post};
-  const StepParams P = make_params(ctx, d_items, uint32_t(pl.items.size()), pl.sb, pl.kb);
+  const StepParams P = make_params(ctx, d_items, uint32_t(pl.items.size()), pl.sb, pl.kb,
+                                  pl.ordered);
   if (rc) return rc;
   const StepCounters c = *ctx->h_ctr;
   if (ctx->debug)
@@ -330,6 +369,8 @@ int finish_step(oasm_ctx* ctx, StepPlan& pl, const WorkItem* d_items, bool* over
             (size_t)P.cap_hits, c.n_out, P.cap_out, c.n_pool, P.cap_pool);
   if (c.overflow & (1u << 16))
     return fail(ctx, OASM_ETIMEOUT, "a bounded wait for a TMA copy ran out in the scan");
+  if (c.overflow & 64u)
+    return fail(ctx, OASM_ECUDA, "internal error: an ordered record fell outside its segment");
   *overflow = c.overflow != 0;
   if (*overflow) {
     // grow what was too small; the step is re-run from unchanged state
@@ -341,7 +382,7 @@ int finish_step(oasm_ctx* ctx, StepPlan& pl, const WorkItem* d_items, bool* over
       if ((rc = ensure(ctx, ctx->keys_alt, want, "hit keys"))) return rc;
     }
     if ((c.overflow & 4u) || c.n_out > P.cap_out)
-      if ((rc = ensure_out(ctx, size_t(c.n_out * 5 / 4 + 1024)))) return rc;
+      if ((rc = ensure_out(ctx, size_t(c.n_out * 5 / 4 + 1024), pl.ordered))) return rc;
     if (c.overflow & 32u)  // the piece filter's set filled up: room for 4x its inserts
       if ((rc = ensure_pow2(ctx, ctx->pset, size_t(c.n_pref) * 4, "piece filter set"))) return rc;
     if ((c.overflow & 8u) || c.n_pool > P.cap_pool) {

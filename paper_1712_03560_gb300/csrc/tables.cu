@@ -396,7 +396,8 @@ int build_tables(oasm_ctx* ctx) {
   return OASM_OK;
 }
 
-StepParams make_params(oasm_ctx* ctx, const WorkItem* d_items, uint32_t n_items, int sb, int kb) {
+StepParams make_params(oasm_ctx* ctx, const WorkItem* d_items, uint32_t n_items, int sb, int kb,
+                       bool ordered) {
   StepParams P{};
   P.m = ctx->d_m;
   P.K = ctx->d_K;
@@ -425,8 +426,10 @@ StepParams make_params(oasm_ctx* ctx, const WorkItem* d_items, uint32_t n_items,
   P.out = ctx->out.p;
   P.okeys = ctx->okeys.p;
   P.ovals = ctx->ovals.p;
-  P.cap_out = std::min({ctx->out.cap, ctx->out_sorted.cap, ctx->okeys.cap, ctx->okeys_alt.cap,
-                        ctx->ovals.cap, ctx->ovals_alt.cap, size_t(0xffffffffu)});
+  P.cap_out = ordered ? std::min(ctx->out_sorted.cap, size_t(0xffffffffu))
+                      : std::min({ctx->out.cap, ctx->out_sorted.cap, ctx->okeys.cap,
+                                  ctx->okeys_alt.cap, ctx->ovals.cap, ctx->ovals_alt.cap,
+                                  size_t(0xffffffffu)});
   P.pool_hdr = ctx->pool_hdr.p;
   P.pool_mem = ctx->pool_mem.p;
   P.cap_pool = std::min(ctx->pool_hdr.cap, ctx->pool_mem.cap / (kMaxK + 1));
@@ -435,6 +438,13 @@ StepParams make_params(oasm_ctx* ctx, const WorkItem* d_items, uint32_t n_items,
   P.num_sms = ctx->num_sms;
   P.start_bits = sb;
   P.key_bits = kb;
+  if (ordered) {
+    P.ordered = 1;
+    P.head = ctx->kmax + 1;
+    P.rtmp = ctx->rtmp.p;
+    P.seg = ctx->seg.p;
+    P.cap_rtmp = ctx->rtmp.cap;
+  }
   return P;
 }
 

@@ -71,7 +71,8 @@ def test_strerror_and_null_safety():
 
 @pytest.mark.parametrize("field,value", [("groups_per_warp", 3), ("prefilter_piece", 2),
                                          ("prefilter_piece", 129), ("tile_warps", 17),
-                                         ("full_words", 2), ("full_words", -1)])
+                                         ("full_words", 2), ("full_words", -1),
+                                         ("record_order", 3), ("record_order", -1)])
 def test_create_rejects_bad_config(field, value):
     """Config fields out of range are rejected on the host, before any device work."""
     lib = B.load()

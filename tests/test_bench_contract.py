@@ -31,7 +31,7 @@ def test_reference_arm_prints_one_contract_line(extra):
                                     else None)
     # the workload keys are the ones the GPU arm prints for the same arguments
     for k in ("workload", "text_bytes", "patterns", "l2", "parallelism", "prefilter_piece",
-              "graphs", "output", "costs"):
+              "graphs", "output", "record_order", "costs"):
         assert k in d["config"], k
     assert d["config"]["output"] == (extra[1] if "--output" in extra else "filtered")
 
@@ -41,5 +41,5 @@ def test_bench_help_lists_the_options():
                        capture_output=True, text=True, timeout=120, cwd=ROOT)
     assert r.returncode == 0
     for opt in ("--gpus", "--steps", "--warmup", "--impl", "--workload", "--costs",
-                "--graphs", "--tuning-cache"):
+                "--graphs", "--tuning-cache", "--record-order"):
         assert opt in r.stdout
