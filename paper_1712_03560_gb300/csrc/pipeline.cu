@@ -305,31 +305,32 @@ __global__ void __launch_bounds__(kSortThreads)
 // Stable scatter.  Each block first finds where its keys of each digit go:
 // all keys of smaller digits, plus the keys of its digit in earlier blocks
 // (thread d walks column d of the block-major histogram, coalesced across
-// threads).  It then walks its contiguous chunk in tiles of 256 keys; inside
-// a tile, ranks come from warp matching (lane order) and per-warp digit
-// counts (warp order); across tiles a running base per digit.
+// threads).  It then walks its contiguous chunk in tiles of kSortTile keys.
+// A warp ranks its keys round by round (32 consecutive keys per round,
+// warp matching for the lanes of one digit, a running count per digit);
+// per-digit scans over the warps and over the digits give every key its
+// place in the tile sorted by digit, in shared memory; the tile then goes
+// out with consecutive threads writing consecutive keys of one digit's run.
+constexpr int kSortPer = 8;                             // keys per thread and tile
+constexpr int kSortTile = kSortThreads * kSortPer;      // 2,048
 __global__ void __launch_bounds__(kSortThreads)
     rs_scatter(const unsigned long long* __restrict__ in, unsigned long long* __restrict__ out,
                const uint32_t* __restrict__ vin, uint32_t* __restrict__ vout,
                const unsigned long long* count, unsigned long long cap, int shift,
                const unsigned int* __restrict__ hist) {
+  __shared__ unsigned long long skey[kSortTile];
+  __shared__ uint32_t sval[kSortTile];
   __shared__ unsigned int wcnt[kSortWarps][256];
-  __shared__ unsigned int woff[kSortWarps][256];
-  __shared__ unsigned int base[256];
+  __shared__ unsigned int base[256];    // global position of the digit's next key
+  __shared__ unsigned int tstart[256];  // the digit's first slot in the sorted tile
   __shared__ unsigned int wsum[kSortWarps];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int d0 = threadIdx.x;  // the digit this thread keeps the counts of
   const unsigned long long n = min(*count, cap);
   if (sort_chunk(n) * blockIdx.x >= n) return;  // no keys for this block
-  {
-    const int d = threadIdx.x;
-    unsigned int tot = 0, pre = 0;
-    for (int b = 0; b < int(gridDim.x); ++b) {
-      const unsigned int v = hist[b * 256 + d];
-      tot += v;
-      if (b < int(blockIdx.x)) pre += v;
-    }
-    // exclusive scan of the digit totals across the block
-    unsigned int incl = tot;
+  // exclusive scan of 256 values held one per thread (v = this thread's)
+  auto block_excl = [&](unsigned int v) -> unsigned int {
+    unsigned int incl = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const unsigned int t = __shfl_up_sync(kFull, incl, o);
@@ -339,41 +340,74 @@ __global__ void __launch_bounds__(kSortThreads)
     __syncthreads();
     unsigned int wpre = 0;
     for (int w = 0; w < warp; ++w) wpre += wsum[w];
-    base[d] = wpre + incl - tot + pre;
+    __syncthreads();  // wsum is reused by the next call
+    return wpre + incl - v;
+  };
+  {
+    unsigned int tot = 0, pre = 0;
+    for (int b = 0; b < int(gridDim.x); ++b) {
+      const unsigned int v = hist[b * 256 + d0];
+      tot += v;
+      if (b < int(blockIdx.x)) pre += v;
+    }
+    base[d0] = block_excl(tot) + pre;
   }
-  for (int w = 0; w < kSortWarps; ++w) wcnt[w][threadIdx.x] = 0;
-  __syncthreads();
   const unsigned long long chunk = sort_chunk(n);
   const unsigned long long b0 = chunk * blockIdx.x, b1 = min(n, b0 + chunk);
   const unsigned lt = (1u << lane) - 1u;
-  for (unsigned long long t0 = b0; t0 < b1; t0 += kSortThreads) {
-    const unsigned long long i = t0 + threadIdx.x;
-    const bool ok = i < b1;
-    const unsigned long long key = ok ? in[i] : 0ull;
-    const uint32_t val = (ok && vin) ? vin[i] : 0u;
-    const unsigned d = ok ? unsigned((key >> shift) & 255u) : 256u;
-    const unsigned peers = __match_any_sync(kFull, d);
-    const unsigned rank = __popc(peers & lt);
-    if (ok && rank == 0) wcnt[warp][d] = __popc(peers);
+  for (unsigned long long t0 = b0; t0 < b1; t0 += kSortTile) {
+    const int tn = int(min((unsigned long long)kSortTile, b1 - t0));
+#pragma unroll
+    for (int w = 0; w < kSortWarps; ++w) wcnt[w][d0] = 0;
     __syncthreads();
-    {
-      const int dg = threadIdx.x;  // one digit per thread
-      unsigned int run = base[dg];
-      for (int w = 0; w < kSortWarps; ++w) {
-        const unsigned int c = wcnt[w][dg];
-        woff[w][dg] = run;
-        run += c;
-        wcnt[w][dg] = 0;
+    unsigned long long key[kSortPer];
+    uint32_t val[kSortPer];
+    unsigned int dig[kSortPer], rank[kSortPer];
+#pragma unroll
+    for (int r = 0; r < kSortPer; ++r) {
+      const int e = warp * (kSortPer * 32) + r * 32 + lane;  // tile index: warp-major
+      const bool ok = e < tn;
+      key[r] = ok ? in[t0 + e] : 0ull;
+      val[r] = (ok && vin) ? vin[t0 + e] : 0u;
+      const unsigned d = ok ? unsigned((key[r] >> shift) & 255u) : 256u;
+      dig[r] = d;
+      const unsigned peers = __match_any_sync(kFull, d);
+      const unsigned below = __popc(peers & lt);
+      rank[r] = ok ? wcnt[warp][d & 255u] + below : 0u;
+      __syncwarp();
+      if (ok && below == 0) wcnt[warp][d] += __popc(peers);
+      __syncwarp();
+    }
+    __syncthreads();
+    // per digit: offsets of the warps' keys, then the digit's start in the tile
+    unsigned int run = 0;
+#pragma unroll
+    for (int w = 0; w < kSortWarps; ++w) {
+      const unsigned int c = wcnt[w][d0];
+      wcnt[w][d0] = run;
+      run += c;
+    }
+    const unsigned int ts = block_excl(run);
+    tstart[d0] = ts;
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kSortPer; ++r) {
+      if (dig[r] < 256u) {
+        const unsigned int pos = tstart[dig[r]] + wcnt[warp][dig[r]] + rank[r];
+        skey[pos] = key[r];
+        sval[pos] = val[r];
       }
-      base[dg] = run;
     }
     __syncthreads();
-    if (ok) {
-      const unsigned int pos = woff[warp][d] + rank;
-      out[pos] = key;
-      if (vout) vout[pos] = val;
+    for (int e = threadIdx.x; e < tn; e += kSortThreads) {
+      const unsigned long long k = skey[e];
+      const unsigned d = unsigned((k >> shift) & 255u);
+      const unsigned int g = base[d] + unsigned(e) - tstart[d];
+      out[g] = k;
+      if (vout) vout[g] = sval[e];
     }
     __syncthreads();
+    base[d0] += run;
   }
 }
 
