@@ -45,9 +45,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 OPS_PER_WORD_STEP = 16  # integer ops of one 32-bit column step of the scan
-# integer ops of one cell of the weighted dynamic program: three adds, two
-# minimums, and a compare and a select for the substitution cost
-OPS_PER_DP_CELL = 7
+# integer ops of one cell of the weighted dynamic program: two cells (one per
+# 16-bit half) share 5 operations -- the symbol test, its 0/1 by a 16x2
+# minimum, the substitution cost by a multiply-add, two 16x2 add-minimums
+OPS_PER_DP_CELL = 2.5
 WEIGHTED_DEFAULT_COSTS = (1, 2, 2)
 # DRAM bytes per scan launch and text byte, from an ncu capture of the current
 # scan kernels (traffic scales with the text: each launch reads it once); a
@@ -600,6 +601,7 @@ def measure_workload(args, name, dev, steps, warmup, *, rank=0, world=1, dist=No
     units = ("executed lane word-steps x 16 ops (a packed lane counts once; a cut-off "
              "class counts word 0 of every step plus the words its full form ran)")
     kname, opu = "scan_kernel (all classes of a step)", OPS_PER_WORD_STEP
+    mix = "scan_step"
     if args.costs is not None:
         # weighted path: a unit is one cell of the dynamic program; executed
         # cells count every row of a pattern's 32 W-row column
@@ -607,8 +609,10 @@ def measure_workload(args, name, dev, steps, warmup, *, rank=0, world=1, dist=No
         achieved_alg = cells_alg * OPS_PER_DP_CELL / launches_step / (scan_ms_launch * 1e-3) / 1e12
         achieved = st["word_steps"] / max(1, steps) * OPS_PER_DP_CELL / launches_step \
             / (scan_ms_launch * 1e-3) / 1e12
-        units = "executed dynamic-program cells (32 W rows per pattern) x 7 ops"
+        units = ("executed dynamic-program cells (32 W rows per pattern) x 2.5 ops (5 per "
+                 "pair of cells in 16-bit halves)")
         kname, opu = "wscan_kernel (weighted wave-front, all classes of a step)", OPS_PER_DP_CELL
+        mix = "weighted_step"
     tpb = None if args.costs is not None else SCAN_DRAM_BYTES_PER_TEXT_BYTE.get(name)
     traffic = tpb * wl.text_bytes if tpb else None  # bytes per scan launch
     hbm_peak = measured_hbm_gbs()
@@ -625,8 +629,8 @@ def measure_workload(args, name, dev, steps, warmup, *, rank=0, world=1, dist=No
                     "frac": traffic / (scan_ms_launch * 1e-3) / 1e9 / hbm_peak[0],
                     "peak_source": hbm_peak[1]},
                 "measured_peaks_tops": peaks,
-                "peak_measured_mix": peaks["scan_step"],
-                "frac_of_measured_mix": achieved / peaks["scan_step"],
+                "peak_measured_mix": peaks[mix], "measured_mix": mix,
+                "frac_of_measured_mix": achieved / peaks[mix],
                 "kernel": kname, "kernel_ms_per_launch": scan_ms_launch,
                 "launches_per_step": launches_step,
                 "ops_per_word_step": opu}

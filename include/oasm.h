@@ -465,6 +465,9 @@ int oasm_autotune(oasm_ctx *ctx, const uint8_t *dsample, size_t n, char *report,
  *      multiply-adds, 2 high-word multiply-adds for the score, 1 or for the
  *      candidate flag, 1 byte permute), spread over the ALU and FMA pipes as
  *      in the scan
+ *   3  three pairs of cells of the weighted wave-front (oasm_create_weighted)
+ *      in its forms, 5 operations a pair: a logic op, a 16x2 three-way
+ *      minimum, a multiply-add, two 16x2 fused add-minimums
  * *ops_per_s receives integer operations per second over the whole GPU (best
  * of five timed launches), *ms (may be NULL) the time of that launch.
  * OASM_EINVAL for another mix or a NULL ops_per_s.

@@ -431,13 +431,13 @@ def oasm_measure_int_peak(device: int = 0):
     return ops.value, ms.value
 
 
-INT_MIXES = {"alu": 0, "multiply_add": 1, "scan_step": 2}
+INT_MIXES = {"alu": 0, "multiply_add": 1, "scan_step": 2, "weighted_step": 3}
 
 
 def oasm_measure_int_peak_mix(device: int = 0, mix: str = "scan_step"):
     """(integer ops per second, ms of the best launch) of one mix of
-    INT_MIXES: the ALU pipe alone, integer multiply-adds alone, or the scan's
-    column step."""
+    INT_MIXES: the ALU pipe alone, integer multiply-adds alone, the scan's
+    column step, or the weighted wave-front's cell pairs."""
     ops, ms = ctypes.c_double(), ctypes.c_double()
     _check(load().oasm_measure_int_peak_mix(device, INT_MIXES[mix], ctypes.byref(ops),
                                             ctypes.byref(ms)))

@@ -14,6 +14,11 @@
 //                 size: they stay on the FMA pipe), 2 high-word multiply-adds
 //                 by 2 (the score), 1 or (the candidate flag), 1 byte permute
 //                 (the symbol): the issue rate the scan itself can reach.
+//   3 weighted:   three pairs of dynamic-program cells (16-bit halves) in the
+//                 forms of the weighted wave-front, 5 operations a pair: the
+//                 symbol test (lop3), its 0/1 (a 16x2 three-way minimum), the
+//                 substitution cost added by a multiply-add, two 16x2 fused
+//                 add-minimums.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -64,6 +69,18 @@ __device__ __forceinline__ void mix_step(uint32_t& x, uint32_t& y, uint32_t& t, 
         "mad.lo.u32 %1, %1, %2, %0;\n\t"
         "mad.lo.u32 %2, %2, %0, %1;"
         : "+r"(x), "+r"(y), "+r"(t));
+  } else if constexpr (MIX == 3) {
+    // x: the left cell pair, y: the diagonal, t: the cell above, f: pattern
+    // symbols; two stands in for the costs (a kernel argument)
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const uint32_t miss = __vimin3_u16x2((f ^ x) & 0x00ff00ffu, 0x10001u, 0x10001u);
+      const uint32_t ds = miss * two + y;
+      const uint32_t v = __viaddmin_u16x2(t, two, __viaddmin_u16x2(x, two, ds));
+      y = x;
+      x = v;
+      t = v ^ rowb;
+    }
   } else {
     // x: Pv, y: Mv, t: the score, f: the candidate flag; the match mask and
     // address come from them
@@ -200,6 +217,7 @@ extern "C" int oasm_measure_int_peak_mix(int device, int mix, double* ops_per_s,
     case 0: return measure_mix<0>(device, ops_per_s, ms);
     case 1: return measure_mix<1>(device, ops_per_s, ms);
     case 2: return measure_mix<2>(device, ops_per_s, ms);
+    case 3: return measure_mix<3>(device, ops_per_s, ms);
     default: return OASM_EINVAL;
   }
 }

@@ -996,7 +996,7 @@ __global__ void __launch_bounds__(512) scan_kernel(const ScanArgs A) {
 // Integer edit costs (oasm_create_weighted): Eq. 1 with costs c_sub, c_ins,
 // c_del and Sellers' zero row, filled as a wave-front over anti-diagonals
 // (the paper's own order of evaluation, Sec. 3, Fig. 1(b)), one warp per
-// (group, region).  A group is a column of 32 lanes x R rows holding several
+// (pair of groups, region).  A group is a column of 32 lanes x R rows holding several
 // patterns, each in a run of whole lanes that ends at the last row of its
 // last lane.  At step s lane l fills column e = x0 + s - l: the row above its
 // first row at columns e and e - 1 is lane l - 1's last row at steps s - 1
@@ -1007,23 +1007,33 @@ __global__ void __launch_bounds__(512) scan_kernel(const ScanArgs A) {
 // arithmetic per step).  The last row of a pattern's last lane is D[e]: a
 // candidate end when it is <= K (the bit-parallel scan's test).
 //
-// Per cell: three adds, two minimums and a compare-select for the
-// substitution cost (with equal insertion and deletion costs, kEq, one add
-// fewer: min(left + c, up + c) = min(left, up) + c); per lane and step one
-// shuffle, one shared-memory load, the zero-row mask and the candidate bit.
+// Two groups per warp, one in each 16-bit half of every register: a lane's
+// row q holds the cell of group A in bits 0-15 and that of group B in bits
+// 16-31.  Cell values stay below 2^15 (at most l_p x c_del <= 128 x 255, plus
+// one cost in a sum), so a 32-bit add never carries from one half into the
+// other, and the 16x2 minimum forms act on both cells at once.  Per pair of
+// cells: the symbol test as a three-input logic op ((p ^ t) & row mask: 0 on a
+// match and on a wild row), its 0/1 per half by a 16x2 minimum with 1, the
+// substitution cost added to the diagonal by one multiply-add (the 0/1 halves
+// times c_sub cannot carry either), and the two other costs by the fused
+// add-minimum forms.  Per lane and step, shared by the 8 cells: one shuffle,
+// one shared-memory load, the zero-row masks and the two candidate bits.
 template <int R, bool kPro, bool kEq>
-__device__ __forceinline__ void wdp_step(uint32_t& vout, int (&col)[R], int& up_prev,
-                                         const uint32_t (&pc)[R], const int (&csub)[R], int ci,
-                                         int cd, uint32_t keep, uint32_t sym, bool active) {
-  const int up_cur = int(__shfl_up_sync(kFull, vout, 1) & keep);
-  int diag = up_prev, up = up_cur;
-  int nv[R];
+__device__ __forceinline__ void wdp_step(uint32_t& vout, uint32_t (&col)[R], uint32_t& up_prev,
+                                         const uint32_t (&pc)[R], const uint32_t (&mk)[R],
+                                         uint32_t cs, uint32_t ci2, uint32_t cd2, uint32_t keep,
+                                         uint32_t sym, bool active) {
+  const uint32_t up_cur = __shfl_up_sync(kFull, vout, 1) & keep;
+  const uint32_t sym2 = sym * 0x10001u;
+  uint32_t diag = up_prev, up = up_cur;
+  uint32_t nv[R];
 #pragma unroll
   for (int q = 0; q < R; ++q) {
-    const int left = col[q];
-    const int sub = (pc[q] == sym) ? 0 : csub[q];
-    const int v = kEq ? min(diag + sub, min(left, up) + ci)
-                      : min(min(diag + sub, left + ci), up + cd);
+    const uint32_t left = col[q];
+    const uint32_t miss = __vimin3_u16x2((pc[q] ^ sym2) & mk[q], 0x10001u, 0x10001u);
+    const uint32_t ds = miss * cs + diag;  // diagonal + substitution cost, per half
+    const uint32_t v = kEq ? __viaddmin_u16x2(__vimin3_u16x2(left, up, up), ci2, ds)
+                           : __viaddmin_u16x2(up, cd2, __viaddmin_u16x2(left, ci2, ds));
     diag = left;
     nv[q] = v;
     up = v;
@@ -1032,47 +1042,81 @@ __device__ __forceinline__ void wdp_step(uint32_t& vout, int (&col)[R], int& up_
 #pragma unroll
     for (int q = 0; q < R; ++q) col[q] = nv[q];
     up_prev = up_cur;
-    vout = uint32_t(nv[R - 1]);
+    vout = nv[R - 1];
   }
 }
 
-template <int R, bool kEq>
-__global__ void __launch_bounds__(512) wscan_kernel(const ScanArgs A) {
-  __shared__ uint8_t sb[16][64];  // per warp: the previous and the current 32-symbol block
-  const int ng = A.n_groups;
-  const int g = blockIdx.x % ng;
-  const int rb = blockIdx.x / ng;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int r = rb * A.warps + warp;
-  if (r >= A.n_regions || warp >= 16) return;  // the whole warp leaves together
-  const Region Rg = A.regions[r];
-  const WorkItem wi = A.items[Rg.wi];
-  const LaneGroup& G = A.groups[g];
-  const int pid = G.pat[lane], K = G.K[lane];  // pid >= 0: the last lane of a pattern
-  const int ci = A.c_ins, cd = A.c_del;
+// One group's rows in this lane, into half `h` (0: bits 0-15, 1: bits 16-31)
+// of the packed registers.  A missing group (an odd group count) is all wild
+// rows of a first lane: its cells stay 0 and it reports nothing.
+template <int R>
+__device__ __forceinline__ void wdp_load_group(const ScanArgs& A, int g, int lane, int h,
+                                               uint32_t (&pc)[R], uint32_t (&mk)[R],
+                                               uint32_t (&col)[R], uint32_t& keep,
+                                               uint32_t& up_prev) {
+  const int sh = 16 * h;
+  if (g >= A.n_groups) return;  // zeros: wild, first lane
   const uint32_t* wr = A.wrow + size_t(g) * 32 * R;
-  uint32_t pc[R];
-  int csub[R], col[R];
   bool first = false;
 #pragma unroll
   for (int q = 0; q < R; ++q) {
     const uint32_t w = wr[R * lane + q];
     const bool wild = (w & kWildRow) != 0;
     first = (w & kWFirstLane) != 0;
-    pc[q] = wild ? kWildRow : (w & 0xffu);  // a wild row never equals a symbol
-    csub[q] = wild ? 0 : A.c_sub;
-    col[q] = int((w >> 16) & 0xffu) * cd;  // column x0 - 1: row i of a pattern costs i deletions
+    if (!wild) {
+      pc[q] |= (w & 0xffu) << sh;
+      mk[q] |= 0xffu << sh;
+    }
+    // column x0 - 1: row i of a pattern costs i deletions
+    col[q] |= (((w >> 16) & 0xffu) * uint32_t(A.c_del)) << sh;
   }
-  const uint32_t keep = first ? 0u : 0xffffffffu;  // lane 0 is always a first lane
-  uint32_t vout = uint32_t(col[R - 1]);
-  int up_prev = (first || lane == 0) ? 0 : int((wr[R * lane - 1] >> 16) & 0xffu) * cd;
+  if (!first) keep |= 0xffffu << sh;  // lane 0 is always a first lane
+  if (!first && lane > 0)
+    up_prev |= (((wr[R * lane - 1] >> 16) & 0xffu) * uint32_t(A.c_del)) << sh;
+}
+
+template <int R, bool kEq>
+__global__ void __launch_bounds__(512) wscan_kernel(const ScanArgs A) {
+  __shared__ uint8_t sb[16][64];  // per warp: the previous and the current 32-symbol block
+  const int ngp = (A.n_groups + 1) / 2;  // group pairs
+  const int gp = blockIdx.x % ngp;
+  const int rb = blockIdx.x / ngp;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int r = rb * A.warps + warp;
+  if (r >= A.n_regions || warp >= 16) return;  // the whole warp leaves together
+  const Region Rg = A.regions[r];
+  const WorkItem wi = A.items[Rg.wi];
+  const int gA = 2 * gp, gB = 2 * gp + 1;
+  const bool hasB = gB < A.n_groups;
+  const LaneGroup& GA = A.groups[gA];
+  // pid >= 0: the last lane of a pattern
+  const int pidA = GA.pat[lane], KA = GA.K[lane];
+  const int pidB = hasB ? A.groups[gB].pat[lane] : -1, KB = hasB ? A.groups[gB].K[lane] : 0;
+  const uint32_t ci2 = uint32_t(A.c_ins) * 0x10001u, cd2 = uint32_t(A.c_del) * 0x10001u;
+  const uint32_t cs = uint32_t(A.c_sub);
+  uint32_t pc[R], mk[R], col[R], keep = 0, up_prev = 0;
+#pragma unroll
+  for (int q = 0; q < R; ++q) pc[q] = mk[q] = col[q] = 0u;
+  wdp_load_group<R>(A, gA, lane, 0, pc, mk, col, keep, up_prev);
+  wdp_load_group<R>(A, gB, lane, 1, pc, mk, col, keep, up_prev);
+  uint32_t vout = col[R - 1];
+  // bit 15 (31) of kc - D is set iff D <= K in group A (B): each half is
+  // K + 2^15 - D, in (0, 2^16) because D <= 128 x 255 < 2^15
+  const uint32_t kc = (uint32_t(KB + 0x8000) << 16) | uint32_t(KA + 0x8000);
   const int64_t a = Rg.a, b = Rg.b;
   if (b <= a) return;
-  const int64_t x0 = a - G.ov;  // warm-up: the group's largest l_p + K - 1
-  int64_t rep_lo = max(a, wi.e_prev - 2 * int64_t(K));
-  rep_lo = max(rep_lo, int64_t(0));
-  // lane l reports the ends in [rep_lo, b) at steps rep_lo - x0 + l ..
-  const int t_lo = int(rep_lo - x0 + lane), t_hi = pid >= 0 ? int(b - x0 + lane) : t_lo;
+  const int ov = hasB ? max(GA.ov, A.groups[gB].ov) : GA.ov;
+  const int64_t x0 = a - ov;  // warm-up: the pair's largest l_p + K - 1
+  auto report_window = [&](int K, int pid, int& t_lo, int& t_hi) {
+    int64_t rep_lo = max(a, wi.e_prev - 2 * int64_t(K));
+    rep_lo = max(rep_lo, int64_t(0));
+    // lane l reports the ends in [rep_lo, b) at steps rep_lo - x0 + l ..
+    t_lo = int(rep_lo - x0 + lane);
+    t_hi = pid >= 0 ? int(b - x0 + lane) : t_lo;
+  };
+  int tloA, thiA, tloB, thiB;
+  report_window(KA, pidA, tloA, thiA);
+  report_window(KB, pidB, tloB, thiB);
   const int nblk = int((b - x0 + 31 + 31) / 32);
   const uint8_t* src = A.arena + (int64_t(wi.arena_base) + (x0 - wi.base_pos));
   // step j of block v: lane l needs t[x0 + 32 v + j - l] = sb[warp][32 - l + j]
@@ -1087,23 +1131,30 @@ __global__ void __launch_bounds__(512) wscan_kernel(const ScanArgs A) {
     pb = nb;
     __syncwarp();
     if (v + 1 < nblk) nb = src[32 * (v + 1) + lane];  // next block, read ahead
-    uint32_t cm = 0;
+    uint32_t cmA = 0, cmB = 0;
     if (v == 0) {  // lane l starts at step l (column x0)
 #pragma unroll
       for (int j = 0; j < 32; ++j) {
-        wdp_step<R, true, kEq>(vout, col, up_prev, pc, csub, ci, cd, keep, mys[j], j >= lane);
-        cm = __funnelshift_l(uint32_t(col[R - 1] - K - 1), cm, 1);
+        wdp_step<R, true, kEq>(vout, col, up_prev, pc, mk, cs, ci2, cd2, keep, mys[j], j >= lane);
+        const uint32_t z = kc - col[R - 1];
+        cmB = __funnelshift_l(z, cmB, 1);
+        cmA = __funnelshift_l(z << 16, cmA, 1);
       }
     } else {
 #pragma unroll
       for (int j = 0; j < 32; ++j) {
-        wdp_step<R, false, kEq>(vout, col, up_prev, pc, csub, ci, cd, keep, mys[j], true);
-        cm = __funnelshift_l(uint32_t(col[R - 1] - K - 1), cm, 1);
+        wdp_step<R, false, kEq>(vout, col, up_prev, pc, mk, cs, ci2, cd2, keep, mys[j], true);
+        const uint32_t z = kc - col[R - 1];
+        cmB = __funnelshift_l(z, cmB, 1);
+        cmA = __funnelshift_l(z << 16, cmA, 1);
       }
     }
-    const uint32_t c = cm & block_mask32(t_lo, t_hi, v);
-    if (__any_sync(kFull, c != 0))
-      em.put(A, lane, c, x0 + 32 * v - lane, Rg.wi, pid, wi.base_pos, 31);
+    const uint32_t cA = cmA & block_mask32(tloA, thiA, v);
+    const uint32_t cB = cmB & block_mask32(tloB, thiB, v);
+    if (__any_sync(kFull, (cA | cB) != 0)) {
+      em.put(A, lane, cA, x0 + 32 * v - lane, Rg.wi, pidA, wi.base_pos, 31);
+      em.put(A, lane, cB, x0 + 32 * v - lane, Rg.wi, pidB, wi.base_pos, 31);
+    }
   }
   em.finish(A, lane);
 }
@@ -1111,7 +1162,8 @@ __global__ void __launch_bounds__(512) wscan_kernel(const ScanArgs A) {
 template <int R>
 cudaError_t launch_wdp(const ScanArgs& a, cudaStream_t st) {
   if (a.warps < 1 || a.warps > 16) return cudaErrorInvalidValue;
-  const long long grid = (long long)((a.n_regions + a.warps - 1) / a.warps) * a.n_groups;
+  const long long grid =
+      (long long)((a.n_regions + a.warps - 1) / a.warps) * ((a.n_groups + 1) / 2);
   if (grid <= 0) return cudaSuccess;
   if (a.c_ins == a.c_del)
     wscan_kernel<R, true><<<unsigned(grid), a.warps * 32, 0, st>>>(a);

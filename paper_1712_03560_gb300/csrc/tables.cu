@@ -463,7 +463,8 @@ int64_t region_len(oasm_ctx* ctx, const Bucket& b, int64_t total_ends) {
     return std::max<int64_t>(16 * b.max_nseg, (r + 15) & ~int64_t(15));
   }
   const double target_warps = double(ctx->num_sms) * 48.0 * 4.0;
-  const int gpw = bucket_gpw(ctx, b);
+  // the weighted path runs two groups per warp (16-bit halves)
+  const int gpw = b.algo == kAlgoWeighted ? 2 : bucket_gpw(ctx, b);
   const double warps_per_region = double((b.groups.size() + gpw - 1) / gpw);
   double r = double(total_ends) * warps_per_region / target_warps * b.region_scale;
   const double lane_min = std::max(64.0, 4.0 * b.ov_max);

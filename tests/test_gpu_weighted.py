@@ -184,3 +184,33 @@ def test_weighted_stream_moves_to_another_weighted_context():
     finally:
         B.oasm_destroy(a)
         B.oasm_destroy(b)
+
+
+@pytest.mark.parametrize("costs", [(2, 254, 255), (255, 255, 255), (9, 255, 1)])
+def test_weighted_large_costs_long_patterns(costs):
+    """Costs up to 255 with patterns of 100..128 symbols: cell values reach
+    l_p x c_del (at most 32,640, one cost more in a sum), the range the
+    kernel's 16-bit halves must hold.  Copies planted with substitutions only
+    (the cheap edit for the first cost set) and exact copies; whole output
+    against the oracle, in one feed and in pieces."""
+    rng = np.random.default_rng(1300 + costs[0])
+    alphabet = np.arange(256, dtype=np.uint8)
+    pats, ks = [], []
+    for _ in range(40):
+        m = int(rng.integers(100, 129))
+        pats.append(alphabet[rng.integers(0, 256, size=m)])
+        ks.append(int(rng.integers(0, 16)))
+    text = alphabet[rng.integers(0, 256, size=30000)]
+    for p in pats[:20]:
+        cp = p.copy()
+        for pos in rng.integers(0, p.size, size=int(rng.integers(0, 4))):
+            cp[pos] = rng.integers(0, 256)
+        W.plant(rng, text, cp)
+    want = oracle_rows(pats, ks, text, costs=costs)
+    got, _ = run_gpu(pats, ks, text, costs=costs)
+    assert canon(got) == want
+    got2, _ = run_gpu(pats, ks, text, splits=np.sort(rng.integers(0, text.size, size=4)),
+                      costs=costs)
+    assert canon(got2) == want
+    if costs[0] == 2:
+        assert len(want) >= 10
