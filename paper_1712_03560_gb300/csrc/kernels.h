@@ -9,7 +9,8 @@ namespace oasm {
 // Forward scan (Sellers search, bit-parallel) over one word-count class.
 struct ScanArgs {
   const LaneGroup* groups;   // [n_groups]
-  const uint32_t* peq;       // [n_groups][256 symbols][W words][32 lanes]
+  const uint32_t* peq;       // [n_groups][256 symbols][W words][32 lanes]; automaton
+                             // classes of K = 2: [n_groups][256][B, B >> 1][32]
   int32_t n_groups;
   int32_t W;
   const Region* regions;     // [n_regions]
@@ -50,11 +51,19 @@ constexpr int kWRows = 4;
 constexpr uint32_t kWildRow = 0x100u;
 constexpr uint32_t kWFirstLane = 1u << 24;
 
+// Words per symbol row of a class's staged table: W for the Myers/Hyyro
+// classes, word 0 only for the cut-off classes, the match mask B for the
+// automaton classes of K = 0 and 1, and B and B >> 1 for those of K = 2 (see
+// nfa_step in scan.cu).
+inline int staged_words(int W, int algo) {
+  return algo == kAlgoCut ? 1 : algo == 3 ? 2 : (algo >= 1 && algo <= 2) ? 1 : W;
+}
+
 // Shared memory of one scan block: the Peq tables of its gpw lane groups (256
-// rows of W x 32 words each; word 0 only for the cut-off classes), two text
-// buffers per warp (dictionary mapping) and the mbarriers.
+// rows of staged_words x 32 words each), two text buffers per warp
+// (dictionary mapping) and the mbarriers.
 inline size_t scan_smem_bytes(int W, int warps, int chunk, int gpw = 1, int algo = 0) {
-  const int w = algo == kAlgoCut ? 1 : W;
+  const int w = staged_words(W, algo);
   return size_t(256) * 128 * w * gpw + size_t(warps) * 2 * chunk + size_t(1 + 2 * warps) * 8;
 }
 

@@ -514,18 +514,42 @@ __device__ void scan_dict(const ScanArgs& A, const char* peq, uint8_t* tbuf, uin
 // position, reached from the always-active empty prefix).  The last bit of
 // R'_K is set exactly when D[e] <= K, the candidate test of the Myers scan.
 //
+// For j >= 1 the last term already holds E, so the E of the match term adds
+// nothing, and (R_j << 1) & B = (R_j & Bs) << 1 with Bs = B >> 1 (a second
+// table word per symbol).  Both shifted terms then share one shift:
+//   R'_j = (((R_j & Bs) | W_j-1) << 1) | E | R_j-1,  W_j = R_j | R'_j
+// four operations per level (three at the last), against five.  Measured on
+// GB300, the K = 2 classes gain from it (10 operations a step instead of 12);
+// at K = 1 the one operation saved costs more in registers (the second load)
+// than it gains, so K <= 1 keeps the first form and its one-word table.
+//
 // Several short patterns share one lane word: each left shift carries the
 // last bit of one pattern into the first bit of the next, and every shifted
 // term is OR-ed with E, which sets that first bit anyway, so the patterns do
 // not interact.  Lane masks: E = the first bits, LAST = the last bits.
 template <int KL>
-__device__ __forceinline__ void nfa_step(uint32_t (&R)[KL + 1], uint32_t B, uint32_t E) {
-  uint32_t prev_old = R[0];
-  R[0] = ((R[0] << 1) | E) & B;
+__device__ __forceinline__ void nfa_step(uint32_t (&R)[KL + 1], uint32_t B, uint32_t Bs,
+                                         uint32_t E) {
+  if constexpr (KL < 2) {
+    uint32_t prev_old = R[0];
+    R[0] = ((R[0] << 1) | E) & B;
+#pragma unroll
+    for (int j = 1; j <= KL; ++j) {
+      const uint32_t old = R[j];
+      R[j] = (((old << 1) | E) & B) | prev_old | ((prev_old | R[j - 1]) << 1) | E;
+      prev_old = old;
+    }
+    return;
+  }
+  const uint32_t r0 = R[0];
+  R[0] = ((r0 << 1) | E) & B;
+  uint32_t w = r0 | R[0];
+  uint32_t prev_old = r0;
 #pragma unroll
   for (int j = 1; j <= KL; ++j) {
     const uint32_t old = R[j];
-    R[j] = (((old << 1) | E) & B) | prev_old | ((prev_old | R[j - 1]) << 1) | E;
+    R[j] = ((((old & Bs) | w) << 1) | E) | prev_old;
+    if (j < KL) w = old | R[j];
     prev_old = old;
   }
 }
@@ -534,13 +558,28 @@ __device__ __forceinline__ void nfa_step(uint32_t (&R)[KL + 1], uint32_t B, uint
 // zero below bit 0 trivially, so (x << 1) | E equals x * 2 + E (no carry
 // reaches bit 0) and each shift-or is one multiply-add.
 template <int KL>
-__device__ __forceinline__ void nfa_step_single(uint32_t (&R)[KL + 1], uint32_t B, uint32_t E) {
-  uint32_t prev_old = R[0];
-  R[0] = mad_lo(R[0], 2u, E) & B;
+__device__ __forceinline__ void nfa_step_single(uint32_t (&R)[KL + 1], uint32_t B, uint32_t Bs,
+                                                uint32_t E) {
+  if constexpr (KL < 2) {
+    uint32_t prev_old = R[0];
+    R[0] = mad_lo(R[0], 2u, E) & B;
+#pragma unroll
+    for (int j = 1; j <= KL; ++j) {
+      const uint32_t old = R[j];
+      R[j] = (mad_lo(old, 2u, E) & B) | prev_old | mad_lo(prev_old | R[j - 1], 2u, E);
+      prev_old = old;
+    }
+    return;
+  }
+  const uint32_t r0 = R[0];
+  R[0] = mad_lo(r0, 2u, E) & B;
+  uint32_t w = r0 | R[0];
+  uint32_t prev_old = r0;
 #pragma unroll
   for (int j = 1; j <= KL; ++j) {
     const uint32_t old = R[j];
-    R[j] = (mad_lo(old, 2u, E) & B) | prev_old | mad_lo(prev_old | R[j - 1], 2u, E);
+    R[j] = mad_lo((old & Bs) | w, 2u, E) | prev_old;
+    if (j < KL) w = old | R[j];
     prev_old = old;
   }
 }
@@ -557,7 +596,8 @@ template <int KL, bool SINGLE, int GPW>
 __device__ void scan_dict_nfa(const ScanArgs& A, const char* peq, uint8_t* tbuf, uint32_t bar0,
                               const GroupSet<GPW>& GS, const Region& R, const WorkItem& wi,
                               int lane) {
-  constexpr uint32_t kPeqBytes = 256u * 128u;
+  constexpr uint32_t kRow = KL == 2 ? 256u : 128u;  // B (and B >> 1 at K = 2) per symbol
+  constexpr uint32_t kPeqBytes = 256u * kRow;
   LaneSetup L[GPW];
   int ns[GPW];
   uint32_t E[GPW], LAST[GPW];
@@ -579,14 +619,16 @@ __device__ void scan_dict_nfa(const ScanArgs& A, const char* peq, uint8_t* tbuf,
   // (the automaton's immediate-2 multiply-adds and address stay as they are:
   // measured, moving them to runtime multipliers slowed the K = 2 class)
   auto step_all = [&](uint32_t sym) {
-    const uint32_t addr = mad_lo(sym, 128u, lane_off);
+    const uint32_t addr = mad_lo(sym, kRow, lane_off);
 #pragma unroll
     for (int g = 0; g < GPW; ++g) {
-      const uint32_t B = *reinterpret_cast<const uint32_t*>(peq + g * kPeqBytes + addr);
+      const char* row = peq + g * kPeqBytes + addr;
+      const uint32_t B = *reinterpret_cast<const uint32_t*>(row);
+      const uint32_t Bs = KL == 2 ? *reinterpret_cast<const uint32_t*>(row + 128) : 0u;
       if (SINGLE)
-        nfa_step_single<KL>(Rs[g], B, E[g]);
+        nfa_step_single<KL>(Rs[g], B, Bs, E[g]);
       else
-        nfa_step<KL>(Rs[g], B, E[g]);
+        nfa_step<KL>(Rs[g], B, Bs, E[g]);
     }
   };
   // per-slot step masks of group g, recorded while replaying or recording
@@ -925,7 +967,7 @@ __global__ void __launch_bounds__(512) scan_cut_kernel(const ScanArgs A) {
 template <int W, bool kDict, int ALG, int GPW>
 __global__ void __launch_bounds__(512) scan_kernel(const ScanArgs A) {
   extern __shared__ __align__(128) uint8_t smem[];
-  constexpr uint32_t kPeqBytes = 256u * 128u * W;
+  constexpr uint32_t kPeqBytes = 256u * 128u * (ALG == 3 ? 2 : ALG > 0 ? 1 : W);
   const int ngb = (A.n_groups + GPW - 1) / GPW;
   const int g0 = (blockIdx.x % ngb) * GPW;
   const int rb = blockIdx.x / ngb;
@@ -1177,7 +1219,7 @@ cudaError_t launch_w(const ScanArgs& a0, cudaStream_t st) {
   ScanArgs a = a0;
   a.two = 2u;
   a.row_bytes = 128u * W;  // one symbol's row of the group's table
-  const size_t smem = scan_smem_bytes(W, a.warps, kDict ? a.chunk : 0, GPW);
+  const size_t smem = scan_smem_bytes(W, a.warps, kDict ? a.chunk : 0, GPW, ALG);
   const long long blocks_r = (a.n_regions + a.warps - 1) / a.warps;
   const long long grid = blocks_r * ((a.n_groups + GPW - 1) / GPW);
   if (grid <= 0) return cudaSuccess;

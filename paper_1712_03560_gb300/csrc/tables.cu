@@ -347,6 +347,17 @@ int build_tables(oasm_ctx* ctx) {
       CK(cudaMemcpy(bk.d_peq_hi, peq.data(), peq.size() * 4, cudaMemcpyHostToDevice));
       peq.swap(w0);
     }
+    if (algo == 3) {
+      // automaton classes of K = 2: each symbol row holds the match masks B
+      // and B >> 1
+      std::vector<uint32_t> two(bk.groups.size() * size_t(256) * 64);
+      for (size_t r = 0; r < bk.groups.size() * size_t(256); ++r)
+        for (size_t l = 0; l < 32; ++l) {
+          two[r * 64 + l] = peq[r * 32 + l];
+          two[r * 64 + 32 + l] = peq[r * 32 + l] >> 1;
+        }
+      peq.swap(two);
+    }
     CK(cudaMalloc(&bk.d_peq, peq.size() * 4));
     CK(cudaMemcpy(bk.d_peq, peq.data(), peq.size() * 4, cudaMemcpyHostToDevice));
     ctx->buckets.push_back(bk);
