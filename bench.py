@@ -484,8 +484,9 @@ def measure_workload(args, name, dev, steps, warmup, *, rank=0, world=1, dist=No
 
     wl, desc = make_workload(name, rank, args.text_mib if name == args.workload else None)
     rules = None if args.output == "filtered" else {"output": args.output}
+    # two sets of streams are open at once in the pipelined steps below
     ctx = B.oasm_create(wl.patterns, wl.ks, rules,
-                        {"device": dev, "timing": 1, "max_streams": max(64, len(wl.texts)),
+                        {"device": dev, "timing": 1, "max_streams": max(64, 2 * len(wl.texts)),
                          "prefilter_piece": args.prefilter, "graphs": args.graphs,
                          "record_order": args.record_order},
                         costs=args.costs)
@@ -513,40 +514,59 @@ def measure_workload(args, name, dev, steps, warmup, *, rank=0, world=1, dist=No
     host_ms = {"submit": 0.0, "step": 0.0, "drain": 0.0, "close": 0.0}
     drain_buf = [None]
 
-    def run_one(submit):
+    def timed(phase, fn, *a):
         t0 = time.perf_counter()
-        sids = B.oasm_open_streams(ctx, len(wl.texts))
-        submit(sids.tolist())
-        B.oasm_end_streams(ctx, sids)
-        t1 = time.perf_counter()
-        B.oasm_step(ctx)
-        t2 = time.perf_counter()
-        out = B.oasm_drain(ctx, drain_buf[0])
+        r = fn(*a)
+        host_ms[phase] += (time.perf_counter() - t0) * 1e3
+        return r
+
+    def open_feed(c, submit):
+        sids = B.oasm_open_streams(c, len(wl.texts))
+        submit(c, sids.tolist())
+        B.oasm_end_streams(c, sids)
+        return sids
+
+    def drain(c):
+        out = B.oasm_drain(c, drain_buf[0])
         n = len(out)
         if drain_buf[0] is None or drain_buf[0].size < n:  # reused from the next step on
             drain_buf[0] = np.empty(max(1024, n * 5 // 4), dtype=B.HIT_DTYPE)
-        t3 = time.perf_counter()
-        B.oasm_close_streams(ctx, sids)
-        t4 = time.perf_counter()
-        for k, a, b in (("submit", t0, t1), ("step", t1, t2), ("drain", t2, t3), ("close", t3, t4)):
-            host_ms[k] += (b - a) * 1e3
-        return n
+        return out
 
-    def step_device():
-        def submit(sids):
-            for s, t in zip(sids, dtexts):
-                B.oasm_feed_device(ctx, s, t)
-        return run_one(submit)
+    def pipeline(c, submit, nsteps):
+        """nsteps steps, each over the whole workload, software-pipelined through
+        the split step (oasm_step_begin / oasm_step_end): while step i runs on
+        the device, the host drains and closes step i - 1's streams (their
+        records' copy to the host overlaps step i) and opens and feeds step i +
+        1's.  Returns the last step's records."""
+        cur = timed("submit", open_feed, c, submit)
+        prev, out = None, None
+        for i in range(nsteps):
+            timed("step", B.oasm_step_begin, c)
+            if prev is not None:
+                out = timed("drain", drain, c)
+                timed("close", B.oasm_close_streams, c, prev)
+            nxt = timed("submit", open_feed, c, submit) if i + 1 < nsteps else None
+            timed("step", B.oasm_step_end, c)
+            prev, cur = cur, nxt
+        out = timed("drain", drain, c)
+        timed("close", B.oasm_close_streams, c, prev)
+        return out
 
-    def step_host(host_texts):
-        def submit(sids):
-            for s, t in zip(sids, host_texts):
-                B.oasm_feed(ctx, s, t)
-        return run_one(submit)
+    def feed_device(c, sids):
+        for sd, t in zip(sids, dtexts):
+            B.oasm_feed_device(c, sd, t)
 
-    kept = 0
-    for _ in range(warmup):
-        kept = step_device()
+    def steps_device(nsteps):
+        return len(pipeline(ctx, feed_device, nsteps))
+
+    def steps_host(host_texts, nsteps):
+        def feed_host(c, sids):
+            for sd, t in zip(sids, host_texts):
+                B.oasm_feed(c, sd, t)
+        return len(pipeline(ctx, feed_host, nsteps))
+
+    kept = steps_device(warmup)
 
     # ---- timed region: device-resident inputs
     if dist:
@@ -562,8 +582,7 @@ def measure_workload(args, name, dev, steps, warmup, *, rank=0, world=1, dist=No
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
-    for _ in range(steps):
-        kept = step_device()
+    kept = steps_device(steps)
     ev1.record(stream)
     ev1.synchronize()
     torch.cuda.synchronize()
@@ -640,14 +659,12 @@ def measure_workload(args, name, dev, steps, warmup, *, rank=0, world=1, dist=No
     e2e = None
     if with_e2e and not args.no_e2e:
         host = [np.ascontiguousarray(t) for t in wl.texts]
-        step_host(host)
+        steps_host(host, 1)
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
         t0 = time.perf_counter()
-        kept_h = 0
-        for _ in range(steps):
-            kept_h = step_host(host)
+        kept_h = steps_host(host, steps)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         if dist:
@@ -710,7 +727,8 @@ def measure_workload(args, name, dev, steps, warmup, *, rank=0, world=1, dist=No
     if with_alt and args.prefilter == 0 and not args.no_alt and world == 1 and \
             args.costs is None and args.output == "filtered":
         ctx2 = B.oasm_create(wl.patterns, wl.ks, None,
-                             {"device": dev, "timing": 1, "max_streams": max(64, len(wl.texts)),
+                             {"device": dev, "timing": 1,
+                              "max_streams": max(64, 2 * len(wl.texts)),
                               "prefilter_piece": 1, "graphs": args.graphs,
                               "record_order": args.record_order})
         try:
@@ -720,23 +738,13 @@ def measure_workload(args, name, dev, steps, warmup, *, rank=0, world=1, dist=No
                 B.oasm_autotune(ctx2, big[: min(big.numel(), 32 << 20)])
             last = [None]
 
-            def step2():
-                sids = B.oasm_open_streams(ctx2, len(dtexts))
-                for sd, t in zip(sids.tolist(), dtexts):
-                    B.oasm_feed_device(ctx2, sd, t)
-                B.oasm_end_streams(ctx2, sids)
-                B.oasm_step(ctx2)
-                last[0] = B.oasm_drain(ctx2)
-                B.oasm_close_streams(ctx2, sids)
-            for _ in range(warmup):
-                step2()
+            pipeline(ctx2, feed_device, warmup)
             torch.cuda.synchronize()
             B.oasm_reset_stats(ctx2)
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream2)
-            for _ in range(steps):
-                step2()
+            last[0] = pipeline(ctx2, feed_device, steps).copy()
             e1.record(stream2)
             e1.synchronize()
             ms2 = e0.elapsed_time(e1)

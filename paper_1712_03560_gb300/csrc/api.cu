@@ -57,7 +57,8 @@ int ensure_host(oasm_ctx* ctx, uint8_t** p, size_t* cap, size_t n, size_t keep) 
 
 int ensure_out(oasm_ctx* ctx, size_t n, bool ordered) {
   int rc;
-  if ((rc = ensure(ctx, ctx->out_sorted, n, "records"))) return rc;
+  if ((rc = ensure(ctx, ctx->out_sorted[0], n, "records"))) return rc;
+  if ((rc = ensure(ctx, ctx->out_sorted[1], n, "records"))) return rc;
   if (ordered) return OASM_OK;  // written in order: no emission buffer, keys or sort
   if ((rc = ensure(ctx, ctx->out, n, "records"))) return rc;
   if ((rc = ensure(ctx, ctx->okeys, n, "record keys"))) return rc;
@@ -98,7 +99,8 @@ void free_ctx(oasm_ctx* c) {
   f(c->d_tails); f(c->d_hdr); f(c->d_mem);
   f(c->arena.p); f(c->upload.p); f(c->stage[0].d.p); f(c->stage[1].d.p); f(c->cand.p); f(c->keys.p);
   f(c->keys_alt.p); f(c->out.p); f(c->pool_hdr.p); f(c->pool_mem.p); f(c->pair_pool.p);
-  f(c->out_sorted.p); f(c->okeys.p); f(c->okeys_alt.p); f(c->ovals.p); f(c->ovals_alt.p);
+  if (c->copy_stream) cudaStreamSynchronize(c->copy_stream);
+  f(c->out_sorted[0].p); f(c->out_sorted[1].p); f(c->okeys.p); f(c->okeys_alt.p); f(c->ovals.p); f(c->ovals_alt.p);
   f(c->d_ctr); f(c->d_hist); f(c->run_start.p); f(c->rtmp.p); f(c->seg.p); f(c->seg_part.p);
   for (const auto& r : c->host_ranges) cudaHostUnregister(const_cast<uint8_t*>(r.host));
   if (c->h_ctr) cudaFreeHost(c->h_ctr);
@@ -106,7 +108,11 @@ void free_ctx(oasm_ctx* c) {
   for (auto& sg : c->stage)
     if (sg.h) cudaFreeHost(sg.h);
   if (c->h_upload) cudaFreeHost(c->h_upload);
-  if (c->h_out) cudaFreeHost(c->h_out);
+  for (auto* h : c->h_out)
+    if (h) cudaFreeHost(h);
+  for (auto& e : c->copy_done)
+    if (e) cudaEventDestroy(e);
+  if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
   for (auto& e : c->ev) if (e) cudaEventDestroy(e);
   for (auto& g : c->graphs)
     if (g.exec) cudaGraphExecDestroy(g.exec);
@@ -337,8 +343,13 @@ int oasm_create_weighted(const uint8_t* const* pat, const uint32_t* len, const u
   for (auto& e : ctx->ev)
     if (cudaEventCreate(&e) != cudaSuccess) return bail(fail(ctx, OASM_ECUDA, "event"));
   if (cudaEventCreateWithFlags(&ctx->done, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&ctx->staged, cudaEventDisableTiming) != cudaSuccess)
+      cudaEventCreateWithFlags(&ctx->staged, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->copy_done[0], cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->copy_done[1], cudaEventDisableTiming) != cudaSuccess)
     return bail(fail(ctx, OASM_ECUDA, "event"));
+  // the records' copies to the host run on their own stream, beside the next step
+  if (cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking) != cudaSuccess)
+    return bail(fail(ctx, OASM_ECUDA, "cudaStreamCreate failed"));
   *out = ctx;
   return OASM_OK;
 }
@@ -383,6 +394,8 @@ int oasm_close_stream(oasm_ctx* ctx, uint32_t sid) {
       std::binary_search(ctx->flight.pl.sids.begin(), ctx->flight.pl.sids.end(), sid) &&
       (rc = step_end(ctx)))  // the stream is part of the step in flight
     return rc;
+  // records on their way may belong to this slot: they land before it is reused
+  if ((rc = settle_records(ctx))) return rc;
   StreamRec& s = ctx->streams[sid];
   for (const Piece& pc : s.pieces)
     if (!pc.dev) ctx->stage[pc.sb].pending -= pc.n;
@@ -665,6 +678,7 @@ int oasm_flush(oasm_ctx* ctx, uint32_t sid, int end_of_stream, oasm_hit* out, si
   if (s0.pending > 0 || s0.eos_pending) {
     if ((rc = run_step(ctx))) return rc;
   }
+  if ((rc = settle_records(ctx))) return rc;
   StreamRec& s = ctx->streams[sid];
   if (s.lent_n) {  // the last step's records, where that step left them
     const size_t n = std::min(cap, s.lent_n);
@@ -696,6 +710,7 @@ int oasm_drain(oasm_ctx* ctx, oasm_hit* out, size_t cap, size_t* n_out) {
   oasm::NvtxRange nvtx_("oasm_drain");
   if (!ctx) return OASM_EINVAL;
   if (n_out) *n_out = 0;
+  if (const int rc = settle_records(ctx)) return rc;
   // plan: streams in id order, each stream's queue already one canonical run
   struct Copy {
     uint32_t sid;
@@ -750,6 +765,7 @@ int oasm_drain(oasm_ctx* ctx, oasm_hit* out, size_t cap, size_t* n_out) {
 
 int oasm_ready(oasm_ctx* ctx, uint32_t sid, size_t* n) {
   if (ctx && n && sid == OASM_ALL_STREAMS) {
+    if (const int rc = settle_records(ctx)) return rc;
     size_t tot = 0;
     for (const StreamRec& s : ctx->streams)
       if (s.open) tot += s.ready.size() - s.head + s.lent_n;
@@ -759,6 +775,7 @@ int oasm_ready(oasm_ctx* ctx, uint32_t sid, size_t* n) {
   int rc = check_sid(ctx, sid);
   if (rc) return rc;
   if (!n) return OASM_EINVAL;
+  if ((rc = settle_records(ctx))) return rc;
   const StreamRec& s = ctx->streams[sid];
   *n = s.ready.size() - s.head + s.lent_n;
   return OASM_OK;
@@ -774,6 +791,7 @@ int oasm_save_stream(oasm_ctx* ctx, uint32_t sid, void* buf, size_t cap, size_t*
   int rc = check_sid(ctx, sid);
   if (rc) return rc;
   if ((rc = step_end(ctx))) return rc;
+  if ((rc = settle_records(ctx))) return rc;
   const size_t need = state_bytes(ctx);
   if (n) *n = need;
   const StreamRec& s = ctx->streams[sid];

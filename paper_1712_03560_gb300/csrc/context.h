@@ -195,13 +195,27 @@ struct StreamRec {
   HitVec ready;                 // decided hits; [head, end) not yet returned
   size_t head = 0;
   std::vector<size_t> runs;     // starts of canonically sorted runs in `ready`
-  // The last step's records of this stream, left where that step put them (the
-  // context's pinned record buffer) when the queue above was empty: a drain
-  // or flush copies them out once instead of twice.  The next step copies
-  // them into `ready` before it writes the buffer again (finish_step); while
-  // lent_n > 0, `ready` is empty.
+  // A step's records of this stream, left where that step put them (one of
+  // the context's two pinned record buffers, lent_buf) when the queue above
+  // was empty: a drain or flush copies them out once instead of twice.  They
+  // move into `ready` before that buffer is written again or before a later
+  // step's records join them; while lent_n > 0, `ready` is empty.
   const oasm_hit* lent = nullptr;
   size_t lent_n = 0;
+  int lent_buf = 0;
+};
+
+// A finished step whose records are still on their way to the host: the
+// copy into pinned buffer `buf` runs on the context's copy stream while the
+// caller goes on (a next step may already run on the device).  The first
+// call that needs the queues waits for it and hands the records to their
+// streams (settle_records).
+struct PendingRecords {
+  bool on = false;
+  int buf = 0;
+  size_t n = 0;
+  std::vector<uint32_t> sids;                 // stream of each work item
+  std::vector<unsigned long long> run_start;  // [items + 1] first record of each
 };
 
 inline bool canon_less(const oasm_hit& a, const oasm_hit& b) {
@@ -344,7 +358,14 @@ struct oasm_ctx {
   DevArray<uint8_t> arena, upload;
   DevArray<Candidate> cand;
   DevArray<unsigned long long> keys, keys_alt;
-  DevArray<DevHit> out, out_sorted;
+  DevArray<DevHit> out;
+  // canonically ordered records, two buffers: a step writes rec_buf while the
+  // previous step's records may still be copied out of the other
+  DevArray<DevHit> out_sorted[2];
+  int rec_buf = 0;
+  PendingRecords pend;
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t copy_done[2] = {};
   DevArray<unsigned long long> okeys, okeys_alt;
   DevArray<uint32_t> ovals, ovals_alt;
   DevArray<WinHdr> pool_hdr;
@@ -361,8 +382,8 @@ struct oasm_ctx {
   unsigned int* d_hist = nullptr;
   uint8_t* h_upload = nullptr;
   size_t h_upload_cap = 0;
-  DevHit* h_out = nullptr;
-  size_t h_out_cap = 0;
+  DevHit* h_out[2] = {};      // pinned record buffers, one per out_sorted buffer
+  size_t h_out_cap[2] = {};
   cudaEvent_t ev[9] = {};  // 0-5 step phases, 6-7 autotune, 8 piece filter start
   cudaEvent_t done = nullptr;
   cudaEvent_t staged = nullptr;  // host staging copies of the step in flight done
@@ -416,6 +437,9 @@ double ms_since(std::chrono::steady_clock::time_point t0);
 int launch_step(oasm_ctx* ctx, StepPlan& pl, const WorkItem* d_items, const Region* d_regions,
                 const CopyChunk* d_chunks);
 int finish_step(oasm_ctx* ctx, StepPlan& pl, const WorkItem* d_items, bool* overflow);
+// Waits for the records of the last finished step to reach the host and
+// hands them to their streams' queues (no-op when none are on the way).
+int settle_records(oasm_ctx* ctx);
 void release_stages(oasm_ctx* ctx);
 int step_begin(oasm_ctx* ctx);
 int step_end(oasm_ctx* ctx);

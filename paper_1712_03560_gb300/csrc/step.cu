@@ -220,7 +220,7 @@ int enqueue_step(oasm_ctx* ctx, StepPlan& pl, const WorkItem* d_items, const Reg
   CK(launch_tails(P, s));
   ctx->st.launches += 1;
   if (pl.ordered) {  // records from their segments to their offsets: canonical order
-    CK(launch_ordered_emit(P, sorted, ctx->out_sorted.p, ctx->run_start.p, s));
+    CK(launch_ordered_emit(P, sorted, ctx->out_sorted[ctx->rec_buf].p, ctx->run_start.p, s));
     topo_add(0x300);
     CK(cudaMemcpyAsync(ctx->h_run_start, ctx->run_start.p,
                        (size_t(n_items) + 1) * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
@@ -234,7 +234,7 @@ int enqueue_step(oasm_ctx* ctx, StepPlan& pl, const WorkItem* d_items, const Reg
                 &ctx->d_ctr->n_out, P.cap_out, 0, pl.kb, ctx->d_hist, ctx->sort_blocks};
     CK(launch_sort(sa, &ks, &vs, &nl, s));
     topo_add(0x200 + nl);
-    CK(launch_permute(ctx->out.p, vs, ctx->out_sorted.p, &ctx->d_ctr->n_out, P.cap_out,
+    CK(launch_permute(ctx->out.p, vs, ctx->out_sorted[ctx->rec_buf].p, &ctx->d_ctr->n_out, P.cap_out,
                       ctx->num_sms, s));
     // where each work item's (stream's) run of records starts
     CK(launch_runs(ks, P, ctx->run_start.p, s));
@@ -414,12 +414,17 @@ int finish_step(oasm_ctx* ctx, StepPlan& pl, const WorkItem* d_items, bool* over
   ctx->st.prefilter_candidates += c.n_pref;
   ctx->st.hits += c.n_hits;
   ctx->st.kept += c.n_out;
-  // records -> streams.  Records still lent from the pinned buffer (not yet
-  // drained) move into their streams' queues before the buffer is reused.
-  {
+  // records -> streams, asynchronously: the previous step's records (if still
+  // on their way) go to their queues first, which keeps each queue in step
+  // order; this step's records start their copy into pinned buffer b and go
+  // to the queues when a call needs them, or at the next step's end, while
+  // the caller (and the next step on the device) go on.
+  if ((rc = settle_records(ctx))) return rc;
+  const int b = ctx->rec_buf;
+  {  // records lent from buffer b (two steps old) move to their queues first
     std::vector<CopyTask> keep;
     for (StreamRec& sr : ctx->streams)
-      if (sr.lent_n) {
+      if (sr.lent_n && sr.lent_buf == b) {
         sr.ready.clear();
         sr.head = 0;
         sr.runs.assign(1, 0);
@@ -432,50 +437,82 @@ int finish_step(oasm_ctx* ctx, StepPlan& pl, const WorkItem* d_items, bool* over
   }
   if (c.n_out) {
     const size_t n = size_t(c.n_out);
-    if (n > ctx->h_out_cap) {
-      if (ctx->h_out) cudaFreeHost(ctx->h_out);
-      ctx->h_out = nullptr;
-      ctx->h_out_cap = 0;
+    if (n > ctx->h_out_cap[b]) {
+      if (ctx->h_out[b]) cudaFreeHost(ctx->h_out[b]);
+      ctx->h_out[b] = nullptr;
+      ctx->h_out_cap[b] = 0;
       ctx->st.buffer_grows += 1;
-      if (cudaHostAlloc(&ctx->h_out, n * sizeof(DevHit), cudaHostAllocDefault) != cudaSuccess) {
+      if (cudaHostAlloc(&ctx->h_out[b], n * sizeof(DevHit), cudaHostAllocDefault) !=
+          cudaSuccess) {
         cudaGetLastError();
         return fail(ctx, OASM_ENOMEM, "pinned allocation for %zu records failed", n);
       }
-      ctx->h_out_cap = n;
+      ctx->h_out_cap[b] = n;
     }
-    // one copy on the context's stream (bounded wait); the run of each work
-    // item (one stream) was located on the device
-    const auto t_copy = std::chrono::steady_clock::now();
-    CK(cudaMemcpyAsync(ctx->h_out, ctx->out_sorted.p, n * sizeof(DevHit), cudaMemcpyDeviceToHost,
-                       ctx->stream));
-    CK(cudaEventRecord(ctx->done, ctx->stream));
-    if ((rc = wait_event(ctx, ctx->done))) return rc;
-    ctx->st.host_copy_ms += ms_since(t_copy);
+    // the step's work is complete (its event was waited for above), so the
+    // copy stream needs no dependency on the step's stream
+    CK(cudaMemcpyAsync(ctx->h_out[b], ctx->out_sorted[b].p, n * sizeof(DevHit),
+                       cudaMemcpyDeviceToHost, ctx->copy_stream));
+    CK(cudaEventRecord(ctx->copy_done[b], ctx->copy_stream));
     ctx->st.record_bytes += n * sizeof(DevHit);
-    const oasm_hit* recs = reinterpret_cast<const oasm_hit*>(ctx->h_out);
-    const unsigned long long* rs = ctx->h_run_start;
-    // a stream with an empty queue borrows its run where it is (no copy);
-    // the others append it to their queues as a new sorted run
-    std::vector<CopyTask> tasks;
-    for (size_t it = 0; it < pl.items.size(); ++it) {
-      const size_t b = size_t(rs[it]), e = size_t(rs[it + 1]);
-      if (e <= b) continue;
-      StreamRec& sr = ctx->streams[pl.sids[it]];
-      if (sr.head == sr.ready.size()) {
-        sr.ready.clear();
-        sr.runs.clear();
-        sr.head = 0;
-        sr.lent = recs + b;
-        sr.lent_n = e - b;
-        continue;
-      }
-      const size_t old = sr.ready.size();
-      sr.runs.push_back(old);
-      sr.ready.resize(old + (e - b));
-      tasks.push_back(CopyTask{sr.ready.data() + old, recs + b, e - b});
-    }
-    if (!tasks.empty()) parallel_copy(tasks);
+    PendingRecords& pr = ctx->pend;
+    pr.on = true;
+    pr.buf = b;
+    pr.n = n;
+    pr.sids = pl.sids;
+    pr.run_start.assign(ctx->h_run_start, ctx->h_run_start + pl.items.size() + 1);
   }
+  ctx->rec_buf ^= 1;
+  return OASM_OK;
+}
+
+int settle_records(oasm_ctx* ctx) {
+  PendingRecords& pr = ctx->pend;
+  if (!pr.on) return OASM_OK;
+  pr.on = false;
+  const auto t_copy = std::chrono::steady_clock::now();
+  const int rc = wait_event(ctx, ctx->copy_done[pr.buf]);
+  ctx->st.host_copy_ms += ms_since(t_copy);
+  if (rc) return rc;
+  const oasm_hit* recs = reinterpret_cast<const oasm_hit*>(ctx->h_out[pr.buf]);
+  // a stream whose queue is empty borrows its run where it is (no copy); the
+  // others append it to their queues as a new sorted run (records lent from
+  // the other buffer move into the queue first)
+  std::vector<CopyTask> first, tasks;
+  for (size_t it = 0; it + 1 < pr.run_start.size(); ++it) {
+    const size_t lo = size_t(pr.run_start[it]), hi = size_t(pr.run_start[it + 1]);
+    if (hi <= lo) continue;
+    StreamRec& sr = ctx->streams[pr.sids[it]];
+    if (sr.lent_n) {
+      sr.ready.clear();
+      sr.head = 0;
+      sr.runs.assign(1, 0);
+      sr.ready.resize(sr.lent_n);
+      first.push_back(CopyTask{sr.ready.data(), sr.lent, sr.lent_n});
+      sr.lent = nullptr;
+      sr.lent_n = 0;
+    }
+  }
+  if (!first.empty()) parallel_copy(first);
+  for (size_t it = 0; it + 1 < pr.run_start.size(); ++it) {
+    const size_t lo = size_t(pr.run_start[it]), hi = size_t(pr.run_start[it + 1]);
+    if (hi <= lo) continue;
+    StreamRec& sr = ctx->streams[pr.sids[it]];
+    if (sr.head == sr.ready.size()) {
+      sr.ready.clear();
+      sr.runs.clear();
+      sr.head = 0;
+      sr.lent = recs + lo;
+      sr.lent_n = hi - lo;
+      sr.lent_buf = pr.buf;
+      continue;
+    }
+    const size_t old = sr.ready.size();
+    sr.runs.push_back(old);
+    sr.ready.resize(old + (hi - lo));
+    tasks.push_back(CopyTask{sr.ready.data() + old, recs + lo, hi - lo});
+  }
+  if (!tasks.empty()) parallel_copy(tasks);
   return OASM_OK;
 }
 

@@ -437,8 +437,9 @@ StepParams make_params(oasm_ctx* ctx, const WorkItem* d_items, uint32_t n_items,
   P.out = ctx->out.p;
   P.okeys = ctx->okeys.p;
   P.ovals = ctx->ovals.p;
-  P.cap_out = ordered ? std::min(ctx->out_sorted.cap, size_t(0xffffffffu))
-                      : std::min({ctx->out.cap, ctx->out_sorted.cap, ctx->okeys.cap,
+  const size_t cap_sorted = ctx->out_sorted[ctx->rec_buf].cap;
+  P.cap_out = ordered ? std::min(cap_sorted, size_t(0xffffffffu))
+                      : std::min({ctx->out.cap, cap_sorted, ctx->okeys.cap,
                                   ctx->okeys_alt.cap, ctx->ovals.cap, ctx->ovals_alt.cap,
                                   size_t(0xffffffffu)});
   P.pool_hdr = ctx->pool_hdr.p;

@@ -164,3 +164,61 @@ def test_both_orders_equal_on_a_dictionary():
     b, _ = run_gpu(pats, ks, text, cfg={"record_order": 2})
     assert len(a) > 1000
     assert a == b
+
+
+@pytest.mark.parametrize("ro", ORDERS)
+def test_split_steps_overlap_the_record_copy(ro):
+    """The pipelined pattern of bench.py: while step i runs on the device the
+    host drains and closes step i - 1's streams (whose records are still being
+    copied to the host) and opens and feeds step i + 1's.  Four steps of three
+    fresh streams each; every stream's records against the oracle, in
+    canonical order as drained."""
+    rng = np.random.default_rng(931)
+    pats, ks, _ = random_case(rng, 4, 30, 6, 40, 10, kmax=3)
+    sets = []
+    for i in range(4):
+        texts = []
+        for j in range(3):
+            t = W.iid_dna(rng, 15000 + 4000 * j + 1000 * i)
+            for p, k in zip(pats[:10], ks[:10]):
+                W.plant(rng, t, W.edit_copy(rng, p, k, W.DNA))
+            texts.append(t)
+        sets.append(texts)
+    ctx = B.oasm_create(pats, ks, None, {"max_streams": 8, "record_order": ro})
+    got = {}
+
+    def open_feed(i):
+        sids = []
+        for t in sets[i]:
+            s = B.oasm_open_stream(ctx)
+            B.oasm_feed(ctx, s, t)
+            B.oasm_end_stream(ctx, s)
+            sids.append(s)
+        return sids
+
+    def drain_close(i, sids):
+        out = B.oasm_drain(ctx)
+        col = [int(r["stream_id"]) for r in out]
+        assert col == sorted(col)
+        for j, s in enumerate(sids):
+            mine = rows_of(out[np.array(col, dtype=np.int64) == s])
+            assert in_canonical_order(mine)
+            got[(i, j)] = mine
+        for s in sids:
+            B.oasm_close_stream(ctx, s)
+
+    try:
+        cur, prev = open_feed(0), None
+        for i in range(4):
+            B.oasm_step_begin(ctx)
+            if prev is not None:
+                drain_close(i - 1, prev)
+            nxt = open_feed(i + 1) if i + 1 < 4 else None
+            B.oasm_step_end(ctx)
+            prev, cur = cur, nxt
+        drain_close(3, prev)
+    finally:
+        B.oasm_destroy(ctx)
+    for i in range(4):
+        for j in range(3):
+            assert canon(got[(i, j)]) == oracle_rows(pats, ks, sets[i][j]), (i, j)
