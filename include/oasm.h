@@ -280,12 +280,19 @@ int oasm_step(oasm_ctx *ctx);
  * oasm_step_begin plans one step over the input pending now and launches it;
  * it returns once the step's host bytes are on the device (the host may then
  * feed more input, open and end streams, and drain earlier hits).
- * oasm_step_end waits for that step and queues its decided hits.  A call
- * that needs a quiet context (oasm_step, oasm_flush, oasm_close_stream,
- * oasm_save_stream, oasm_restore_stream, oasm_autotune) finishes a step in
- * flight first.  oasm_step_begin returns OASM_ESTATE if a step is already in
- * flight; with no pending input it launches nothing and oasm_step_end is a
- * no-op. */
+ * oasm_step_end waits for that step and starts the copy of its decided hits
+ * to the host; it returns without waiting for that copy, which then overlaps
+ * whatever the caller does next (a next oasm_step_begin included).  The hits
+ * reach their streams' queues at the first call that reads a queue
+ * (oasm_flush, oasm_drain, oasm_ready, oasm_close_stream, oasm_save_stream)
+ * or at the next step's end, whichever comes first; the order of each
+ * stream's hits is unchanged.  A call that needs a quiet context (oasm_step,
+ * oasm_flush, oasm_close_stream, oasm_save_stream, oasm_restore_stream,
+ * oasm_autotune) finishes a step in flight first.  oasm_step_begin returns
+ * OASM_ESTATE if a step is already in flight; with no pending input it
+ * launches nothing and oasm_step_end is a no-op.  Pipelined use: begin step
+ * i, drain and close step i - 1's streams, open and feed step i + 1's, end
+ * step i. */
 int oasm_step_begin(oasm_ctx *ctx);
 int oasm_step_end(oasm_ctx *ctx);
 
