@@ -249,8 +249,11 @@ int oasm_end_streams(oasm_ctx *ctx, uint32_t n, const uint32_t *sids);
 int oasm_close_streams(oasm_ctx *ctx, uint32_t n, const uint32_t *sids);
 
 /* Appends n bytes (host memory) to stream sid.  The bytes are copied into
- * pinned staging memory; `chunk` may be reused when the call returns.  No
- * device work is started until oasm_step / oasm_flush. */
+ * pinned staging memory; `chunk` may be reused when the call returns.  If
+ * they lie inside a range registered with oasm_register_host, they are not
+ * copied: the step reads them where they are (zero copy), and `chunk` must
+ * stay unchanged until a step has consumed them.  No device work is started
+ * until oasm_step / oasm_flush. */
 int oasm_feed(oasm_ctx *ctx, uint32_t sid, const uint8_t *chunk, size_t n);
 
 /* Appends many packets to many streams in one call (the ingest of a serving

@@ -453,6 +453,15 @@ int oasm_feed(oasm_ctx* ctx, uint32_t sid, const uint8_t* chunk, size_t n) {
   if (!chunk) return fail(ctx, OASM_EINVAL, "null chunk");
   StreamRec& s = ctx->streams[sid];
   if (s.eos_pending) return fail(ctx, OASM_ESTATE, "stream %u has a pending end", sid);
+  // zero copy: bytes inside a registered range become a device piece that the
+  // gather kernel reads straight from host memory (no staging copy)
+  for (const auto& r : ctx->host_ranges)
+    if (chunk >= r.host && chunk + n <= r.host + r.bytes) {
+      s.pieces.push_back(Piece{true, r.dev + (chunk - r.host), 0, n});
+      s.pending += n;
+      s.clean = false;
+      return OASM_OK;
+    }
   Stage* sg = &ctx->stage[ctx->cur_stage];
   if (sg->used + n > ctx->stage_limit && sg->used > 0) {
     if ((rc = run_step(ctx))) return rc;

@@ -730,3 +730,29 @@ def test_tuning_moves_between_contexts():
     finally:
         B.oasm_destroy(a)
         B.oasm_destroy(b)
+
+
+def test_feed_from_registered_host_memory():
+    """oasm_feed of bytes inside a range registered with oasm_register_host
+    reads them where they are (zero copy); bytes outside it go through the
+    pinned staging buffer.  Both kinds of piece in one stream, over two
+    steps: the output equals the oracle's."""
+    rng = np.random.default_rng(61)
+    pats, ks, text = random_case(rng, 4, 20, 6, 40, 50000, kmax=3)
+    buf = np.ascontiguousarray(text.copy())
+    reg = buf[:30000]
+    ctx = B.oasm_create(pats, ks)
+    try:
+        B.oasm_register_host(ctx, reg)
+        sid = B.oasm_open_stream(ctx)
+        B.oasm_feed(ctx, sid, buf[:12000])          # registered: zero copy
+        part = B.oasm_flush(ctx, sid)
+        B.oasm_feed(ctx, sid, buf[12000:30000])     # registered: zero copy
+        B.oasm_feed(ctx, sid, buf[30000:])          # outside: staged
+        rest = B.oasm_flush(ctx, sid, end_of_stream=True)
+        B.oasm_unregister_host(ctx, reg)
+    finally:
+        B.oasm_destroy(ctx)
+    got = [(int(r["pattern_id"]), int(r["decided_at"]), int(r["k"]), int(r["start"]),
+            int(r["len"])) for r in np.concatenate([part, rest])]
+    assert canon(got) == oracle_rows(pats, ks, text)
