@@ -650,14 +650,17 @@ int oasm_step(oasm_ctx* ctx) {
   return run_step(ctx);
 }
 
+// Both halves of a split step push the same NVTX range as oasm_step, so a
+// profiler filter on "oasm_step" sees every step's kernels however the step
+// was launched (a re-run after a buffer grew is launched from oasm_step_end).
 int oasm_step_begin(oasm_ctx* ctx) {
-  oasm::NvtxRange nvtx_("oasm_step_begin");
+  oasm::NvtxRange nvtx_("oasm_step");
   if (!ctx) return OASM_EINVAL;
   return step_begin(ctx);
 }
 
 int oasm_step_end(oasm_ctx* ctx) {
-  oasm::NvtxRange nvtx_("oasm_step_end");
+  oasm::NvtxRange nvtx_("oasm_step");
   if (!ctx) return OASM_EINVAL;
   return step_end(ctx);
 }
