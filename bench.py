@@ -54,10 +54,10 @@ WEIGHTED_DEFAULT_COSTS = (1, 2, 2)
 # scan kernels (traffic scales with the text: each launch reads it once); a
 # workload without a capture of the current kernels reports traffic null
 SCAN_DRAM_BYTES_PER_TEXT_BYTE = {
-    # the Zipf byte dictionary's six scan launches on a 256 MiB text: 293.5 MB
+    # the Zipf byte dictionary's six scan launches on a 256 MiB text: 292.8 MB
     # per launch (mean of the 12 launches of two steps)
-    "bytes_zipf": 293.48e6 / (256 << 20),
-    "bytes_zipf_256m": 293.48e6 / (256 << 20)}
+    "bytes_zipf": 292.84e6 / (256 << 20),
+    "bytes_zipf_256m": 292.84e6 / (256 << 20)}
 # integer lanes per SM that can issue one integer instruction per clock (four
 # sub-partitions of 32 lanes): the derived peak is SMs x 128 x SM clock
 INT_LANES_PER_SM = 128
