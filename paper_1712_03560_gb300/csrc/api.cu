@@ -335,7 +335,7 @@ int oasm_create_weighted(const uint8_t* const* pat, const uint32_t* len, const u
   for (uint32_t i = 0; i < S; ++i) ctx->free_slots.push(i);
   if (cudaMalloc(&ctx->d_ctr, sizeof(StepCounters)) != cudaSuccess ||
       cudaHostAlloc(&ctx->h_ctr, sizeof(StepCounters), cudaHostAllocDefault) != cudaSuccess ||
-      cudaMalloc(&ctx->d_hist, size_t(256) * ctx->sort_blocks * 4) != cudaSuccess) {
+      cudaMalloc(&ctx->d_hist, size_t(kSortMaxBins) * ctx->sort_blocks * 4) != cudaSuccess) {
     cudaGetLastError();
     fail(ctx, OASM_ENOMEM, "step counters");
     return bail(OASM_ENOMEM);

@@ -287,48 +287,56 @@ __device__ __forceinline__ unsigned long long sort_chunk(unsigned long long n) {
   return even > 1024ull ? even : 1024ull;
 }
 
+// D-bit digits (8 or 9: a 9-bit digit saves a pass where the key width
+// needs it); kSortPer digits of 2^D are owned by each thread, consecutive.
+template <int D>
 __global__ void __launch_bounds__(kSortThreads)
     rs_hist(const unsigned long long* __restrict__ keys, const unsigned long long* count,
             unsigned long long cap, int shift, unsigned int* hist) {
-  __shared__ unsigned int h[256];
-  h[threadIdx.x] = 0;
+  constexpr int kBins = 1 << D;
+  __shared__ unsigned int h[kBins];
+  for (int d = threadIdx.x; d < kBins; d += kSortThreads) h[d] = 0;
   __syncthreads();
   const unsigned long long n = min(*count, cap);
   const unsigned long long chunk = sort_chunk(n);
   const unsigned long long b0 = chunk * blockIdx.x, b1 = min(n, b0 + chunk);
   for (unsigned long long i = b0 + threadIdx.x; i < b1; i += blockDim.x)
-    atomicAdd(&h[(keys[i] >> shift) & 255u], 1u);
+    atomicAdd(&h[(keys[i] >> shift) & (kBins - 1u)], 1u);
   __syncthreads();
-  hist[blockIdx.x * 256 + threadIdx.x] = h[threadIdx.x];  // block-major
+  for (int d = threadIdx.x; d < kBins; d += kSortThreads)
+    hist[blockIdx.x * kBins + d] = h[d];  // block-major
 }
 
 // Stable scatter.  Each block first finds where its keys of each digit go:
 // all keys of smaller digits, plus the keys of its digit in earlier blocks
-// (thread d walks column d of the block-major histogram, coalesced across
-// threads).  It then walks its contiguous chunk in tiles of kSortTile keys.
-// A warp ranks its keys round by round (32 consecutive keys per round,
-// warp matching for the lanes of one digit, a running count per digit);
-// per-digit scans over the warps and over the digits give every key its
-// place in the tile sorted by digit, in shared memory; the tile then goes
-// out with consecutive threads writing consecutive keys of one digit's run.
+// (each thread walks its digits' columns of the block-major histogram).  It
+// then walks its contiguous chunk in tiles of kSortTile keys.  A warp ranks
+// its keys round by round (32 consecutive keys per round, warp matching for
+// the lanes of one digit, a running count per digit); per-digit scans over
+// the warps and over the digits give every key its place in the tile sorted
+// by digit, in shared memory; the tile then goes out with consecutive
+// threads writing consecutive keys of one digit's run.
 constexpr int kSortPer = 8;                             // keys per thread and tile
 constexpr int kSortTile = kSortThreads * kSortPer;      // 2,048
+template <int D>
 __global__ void __launch_bounds__(kSortThreads)
     rs_scatter(const unsigned long long* __restrict__ in, unsigned long long* __restrict__ out,
                const uint32_t* __restrict__ vin, uint32_t* __restrict__ vout,
                const unsigned long long* count, unsigned long long cap, int shift,
                const unsigned int* __restrict__ hist) {
+  constexpr int kBins = 1 << D;
+  constexpr int kOwn = kBins / kSortThreads;  // digits per thread: 1 or 2
   __shared__ unsigned long long skey[kSortTile];
   __shared__ uint32_t sval[kSortTile];
-  __shared__ unsigned int wcnt[kSortWarps][256];
-  __shared__ unsigned int base[256];    // global position of the digit's next key
-  __shared__ unsigned int tstart[256];  // the digit's first slot in the sorted tile
+  __shared__ unsigned int wcnt[kSortWarps][kBins];
+  __shared__ unsigned int base[kBins];    // global position of the digit's next key
+  __shared__ unsigned int tstart[kBins];  // the digit's first slot in the sorted tile
   __shared__ unsigned int wsum[kSortWarps];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int d0 = threadIdx.x;  // the digit this thread keeps the counts of
+  const int d0 = threadIdx.x * kOwn;  // this thread's digits: d0 .. d0 + kOwn - 1
   const unsigned long long n = min(*count, cap);
   if (sort_chunk(n) * blockIdx.x >= n) return;  // no keys for this block
-  // exclusive scan of 256 values held one per thread (v = this thread's)
+  // exclusive scan of one value per thread, in thread order
   auto block_excl = [&](unsigned int v) -> unsigned int {
     unsigned int incl = v;
 #pragma unroll
@@ -344,13 +352,25 @@ __global__ void __launch_bounds__(kSortThreads)
     return wpre + incl - v;
   };
   {
-    unsigned int tot = 0, pre = 0;
+    unsigned int tot[kOwn], pre[kOwn], sum = 0;
+#pragma unroll
+    for (int q = 0; q < kOwn; ++q) tot[q] = pre[q] = 0;
     for (int b = 0; b < int(gridDim.x); ++b) {
-      const unsigned int v = hist[b * 256 + d0];
-      tot += v;
-      if (b < int(blockIdx.x)) pre += v;
+#pragma unroll
+      for (int q = 0; q < kOwn; ++q) {
+        const unsigned int v = hist[b * kBins + d0 + q];
+        tot[q] += v;
+        if (b < int(blockIdx.x)) pre[q] += v;
+      }
     }
-    base[d0] = block_excl(tot) + pre;
+#pragma unroll
+    for (int q = 0; q < kOwn; ++q) sum += tot[q];
+    unsigned int run = block_excl(sum);
+#pragma unroll
+    for (int q = 0; q < kOwn; ++q) {
+      base[d0 + q] = run + pre[q];
+      run += tot[q];
+    }
   }
   const unsigned long long chunk = sort_chunk(n);
   const unsigned long long b0 = chunk * blockIdx.x, b1 = min(n, b0 + chunk);
@@ -358,7 +378,9 @@ __global__ void __launch_bounds__(kSortThreads)
   for (unsigned long long t0 = b0; t0 < b1; t0 += kSortTile) {
     const int tn = int(min((unsigned long long)kSortTile, b1 - t0));
 #pragma unroll
-    for (int w = 0; w < kSortWarps; ++w) wcnt[w][d0] = 0;
+    for (int w = 0; w < kSortWarps; ++w)
+#pragma unroll
+      for (int q = 0; q < kOwn; ++q) wcnt[w][d0 + q] = 0;
     __syncthreads();
     unsigned long long key[kSortPer];
     uint32_t val[kSortPer];
@@ -369,30 +391,40 @@ __global__ void __launch_bounds__(kSortThreads)
       const bool ok = e < tn;
       key[r] = ok ? in[t0 + e] : 0ull;
       val[r] = (ok && vin) ? vin[t0 + e] : 0u;
-      const unsigned d = ok ? unsigned((key[r] >> shift) & 255u) : 256u;
+      const unsigned d = ok ? unsigned((key[r] >> shift) & (kBins - 1u)) : unsigned(kBins);
       dig[r] = d;
       const unsigned peers = __match_any_sync(kFull, d);
       const unsigned below = __popc(peers & lt);
-      rank[r] = ok ? wcnt[warp][d & 255u] + below : 0u;
+      rank[r] = ok ? wcnt[warp][d & (kBins - 1u)] + below : 0u;
       __syncwarp();
       if (ok && below == 0) wcnt[warp][d] += __popc(peers);
       __syncwarp();
     }
     __syncthreads();
     // per digit: offsets of the warps' keys, then the digit's start in the tile
-    unsigned int run = 0;
+    unsigned int cnt[kOwn], sum = 0;
 #pragma unroll
-    for (int w = 0; w < kSortWarps; ++w) {
-      const unsigned int c = wcnt[w][d0];
-      wcnt[w][d0] = run;
-      run += c;
+    for (int q = 0; q < kOwn; ++q) {
+      unsigned int run = 0;
+#pragma unroll
+      for (int w = 0; w < kSortWarps; ++w) {
+        const unsigned int c = wcnt[w][d0 + q];
+        wcnt[w][d0 + q] = run;
+        run += c;
+      }
+      cnt[q] = run;
+      sum += run;
     }
-    const unsigned int ts = block_excl(run);
-    tstart[d0] = ts;
+    unsigned int ts = block_excl(sum);
+#pragma unroll
+    for (int q = 0; q < kOwn; ++q) {
+      tstart[d0 + q] = ts;
+      ts += cnt[q];
+    }
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < kSortPer; ++r) {
-      if (dig[r] < 256u) {
+      if (dig[r] < unsigned(kBins)) {
         const unsigned int pos = tstart[dig[r]] + wcnt[warp][dig[r]] + rank[r];
         skey[pos] = key[r];
         sval[pos] = val[r];
@@ -401,13 +433,14 @@ __global__ void __launch_bounds__(kSortThreads)
     __syncthreads();
     for (int e = threadIdx.x; e < tn; e += kSortThreads) {
       const unsigned long long k = skey[e];
-      const unsigned d = unsigned((k >> shift) & 255u);
+      const unsigned d = unsigned((k >> shift) & (kBins - 1u));
       const unsigned int g = base[d] + unsigned(e) - tstart[d];
       out[g] = k;
       if (vout) vout[g] = sval[e];
     }
     __syncthreads();
-    base[d0] += run;
+#pragma unroll
+    for (int q = 0; q < kOwn; ++q) base[d0 + q] += cnt[q];
   }
 }
 
@@ -926,9 +959,17 @@ cudaError_t launch_sort(const SortArgs& a, unsigned long long** keys_out, uint32
   uint32_t* va = a.vals;
   uint32_t* vb = a.vals_alt;
   int nl = 0;
-  for (int shift = a.lo_bit; shift < a.hi_bit; shift += 8) {
-    rs_hist<<<a.nblocks, kSortThreads, 0, s>>>(ka, a.count, a.cap, shift, a.hist);
-    rs_scatter<<<a.nblocks, kSortThreads, 0, s>>>(ka, kb, va, vb, a.count, a.cap, shift, a.hist);
+  const int D = sort_digit_bits(a.lo_bit, a.hi_bit);
+  for (int shift = a.lo_bit; shift < a.hi_bit; shift += D) {
+    if (D == 9) {
+      rs_hist<9><<<a.nblocks, kSortThreads, 0, s>>>(ka, a.count, a.cap, shift, a.hist);
+      rs_scatter<9><<<a.nblocks, kSortThreads, 0, s>>>(ka, kb, va, vb, a.count, a.cap, shift,
+                                                        a.hist);
+    } else {
+      rs_hist<8><<<a.nblocks, kSortThreads, 0, s>>>(ka, a.count, a.cap, shift, a.hist);
+      rs_scatter<8><<<a.nblocks, kSortThreads, 0, s>>>(ka, kb, va, vb, a.count, a.cap, shift,
+                                                        a.hist);
+    }
     nl += 2;
     std::swap(ka, kb);
     std::swap(va, vb);

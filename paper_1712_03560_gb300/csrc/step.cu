@@ -197,7 +197,7 @@ int enqueue_step(oasm_ctx* ctx, StepPlan& pl, const WorkItem* d_items, const Reg
     SortArgs sa{P.keys, P.keys_alt, nullptr, nullptr, &ctx->d_ctr->n_hits, P.cap_hits,
                 kKBits, pl.kb, ctx->d_hist, ctx->sort_blocks};
     CK(launch_sort(sa, &sorted, nullptr, &nl, s));
-    topo_add(0x100 + nl);
+    topo_add(0x100 + nl + 0x80 * (sort_digit_bits(kKBits, pl.kb) == 9));
     ctx->st.launches += uint64_t(nl);
     if (tm) CK(record_event(ctx, ctx->ev[4], s));
     if (pl.ordered) {
@@ -233,7 +233,7 @@ int enqueue_step(oasm_ctx* ctx, StepPlan& pl, const WorkItem* d_items, const Reg
     SortArgs sa{ctx->okeys.p, ctx->okeys_alt.p, ctx->ovals.p, ctx->ovals_alt.p,
                 &ctx->d_ctr->n_out, P.cap_out, 0, pl.kb, ctx->d_hist, ctx->sort_blocks};
     CK(launch_sort(sa, &ks, &vs, &nl, s));
-    topo_add(0x200 + nl);
+    topo_add(0x200 + nl + 0x80 * (sort_digit_bits(0, pl.kb) == 9));
     CK(launch_permute(ctx->out.p, vs, ctx->out_sorted[ctx->rec_buf].p, &ctx->d_ctr->n_out, P.cap_out,
                       ctx->num_sms, s));
     // where each work item's (stream's) run of records starts
