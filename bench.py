@@ -306,8 +306,8 @@ def filter_mask(patterns, ks, piece: int) -> list:
 
 
 def measured_hbm_gbs():
-    """HBM copy bandwidth measured on this GPU pool (the driver's file), else
-    the fallback figure."""
+    """HBM copy bandwidth from MEASURED_PEAKS.json (a copy kernel measured on
+    this GPU model), else the fallback figure."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             return float(json.load(f)["hbm_gbs"]), "measured"
