@@ -264,7 +264,7 @@ int oasm_create_weighted(const uint8_t* const* pat, const uint32_t* len, const u
   }
   cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device);
   if (ctx->num_sms < 1) ctx->num_sms = 1;
-  ctx->sort_blocks = 2 * ctx->num_sms;
+  ctx->sort_blocks = 4 * ctx->num_sms;
   {
     int max_smem = 0;
     cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);

@@ -400,7 +400,7 @@ struct oasm_ctx {
   std::vector<GraphSlot> graphs;
   uint64_t graph_clock = 0;
   uint64_t step_topo = 0;    // topology of the step being enqueued
-  int sort_blocks = 2 * 152; // radix-sort blocks: two per SM
+  int sort_blocks = 4 * 152; // radix-sort blocks: four per SM
   bool capturing = false;
 
   oasm_stats st{};

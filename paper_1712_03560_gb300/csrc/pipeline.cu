@@ -300,8 +300,18 @@ __global__ void __launch_bounds__(kSortThreads)
   const unsigned long long n = min(*count, cap);
   const unsigned long long chunk = sort_chunk(n);
   const unsigned long long b0 = chunk * blockIdx.x, b1 = min(n, b0 + chunk);
-  for (unsigned long long i = b0 + threadIdx.x; i < b1; i += blockDim.x)
-    atomicAdd(&h[(keys[i] >> shift) & (kBins - 1u)], 1u);
+  const unsigned long long bd = blockDim.x;
+  unsigned long long i = b0 + threadIdx.x;
+  // four loads in flight per thread, then their four counts
+  for (; i + 3 * bd < b1; i += 4 * bd) {
+    const unsigned long long k0 = keys[i], k1 = keys[i + bd], k2 = keys[i + 2 * bd],
+                             k3 = keys[i + 3 * bd];
+    atomicAdd(&h[(k0 >> shift) & (kBins - 1u)], 1u);
+    atomicAdd(&h[(k1 >> shift) & (kBins - 1u)], 1u);
+    atomicAdd(&h[(k2 >> shift) & (kBins - 1u)], 1u);
+    atomicAdd(&h[(k3 >> shift) & (kBins - 1u)], 1u);
+  }
+  for (; i < b1; i += bd) atomicAdd(&h[(keys[i] >> shift) & (kBins - 1u)], 1u);
   __syncthreads();
   for (int d = threadIdx.x; d < kBins; d += kSortThreads)
     hist[blockIdx.x * kBins + d] = h[d];  // block-major
