@@ -109,15 +109,9 @@ cudaError_t prepare_prefilter_kernel(int max_smem_bytes);
 
 cudaError_t launch_verify(const StepParams& p, cudaStream_t s);
 
-// Digit width of the radix sort over bits [lo, hi): 9 where that takes
-// fewer passes than 8 (e.g. 35 bits: 4 passes instead of 5), else 8.
-inline int sort_digit_bits(int lo, int hi) {
-  const int b = hi - lo;
-  return (b + 8) / 9 < (b + 7) / 8 ? 9 : 8;
-}
-constexpr int kSortMaxBins = 512;
+constexpr int kSortMaxBins = 256;  // 8-bit digits
 
-// Stable LSD radix sort (8- or 9-bit digits) of keys by bits [lo_bit, hi_bit),
+// Stable LSD radix sort (8-bit digits) of keys by bits [lo_bit, hi_bit),
 // with an optional 32-bit payload.  The element count is read on the device
 // from *count (clamped to cap).  On return *keys_out / *vals_out point at
 // whichever buffer of each pair holds the sorted data.

@@ -287,13 +287,11 @@ __device__ __forceinline__ unsigned long long sort_chunk(unsigned long long n) {
   return even > 1024ull ? even : 1024ull;
 }
 
-// D-bit digits (8 or 9: a 9-bit digit saves a pass where the key width
-// needs it); kSortPer digits of 2^D are owned by each thread, consecutive.
-template <int D>
+// 8-bit digits: one digit per thread in the per-digit scans.
+constexpr int kBins = 256;
 __global__ void __launch_bounds__(kSortThreads)
     rs_hist(const unsigned long long* __restrict__ keys, const unsigned long long* count,
             unsigned long long cap, int shift, unsigned int* hist) {
-  constexpr int kBins = 1 << D;
   __shared__ unsigned int h[kBins];
   for (int d = threadIdx.x; d < kBins; d += kSortThreads) h[d] = 0;
   __syncthreads();
@@ -319,7 +317,7 @@ __global__ void __launch_bounds__(kSortThreads)
 
 // Stable scatter.  Each block first finds where its keys of each digit go:
 // all keys of smaller digits, plus the keys of its digit in earlier blocks
-// (each thread walks its digits' columns of the block-major histogram).  It
+// (thread d walks column d of the block-major histogram).  It
 // then walks its contiguous chunk in tiles of kSortTile keys.  A warp ranks
 // its keys round by round (32 consecutive keys per round, warp matching for
 // the lanes of one digit, a running count per digit); per-digit scans over
@@ -328,14 +326,12 @@ __global__ void __launch_bounds__(kSortThreads)
 // threads writing consecutive keys of one digit's run.
 constexpr int kSortPer = 8;                             // keys per thread and tile
 constexpr int kSortTile = kSortThreads * kSortPer;      // 2,048
-template <int D>
 __global__ void __launch_bounds__(kSortThreads)
     rs_scatter(const unsigned long long* __restrict__ in, unsigned long long* __restrict__ out,
                const uint32_t* __restrict__ vin, uint32_t* __restrict__ vout,
                const unsigned long long* count, unsigned long long cap, int shift,
                const unsigned int* __restrict__ hist) {
-  constexpr int kBins = 1 << D;
-  constexpr int kOwn = kBins / kSortThreads;  // digits per thread: 1 or 2
+  constexpr int kOwn = kBins / kSortThreads;  // digits per thread: 1
   __shared__ unsigned long long skey[kSortTile];
   __shared__ uint32_t sval[kSortTile];
   __shared__ unsigned int wcnt[kSortWarps][kBins];
@@ -969,17 +965,9 @@ cudaError_t launch_sort(const SortArgs& a, unsigned long long** keys_out, uint32
   uint32_t* va = a.vals;
   uint32_t* vb = a.vals_alt;
   int nl = 0;
-  const int D = sort_digit_bits(a.lo_bit, a.hi_bit);
-  for (int shift = a.lo_bit; shift < a.hi_bit; shift += D) {
-    if (D == 9) {
-      rs_hist<9><<<a.nblocks, kSortThreads, 0, s>>>(ka, a.count, a.cap, shift, a.hist);
-      rs_scatter<9><<<a.nblocks, kSortThreads, 0, s>>>(ka, kb, va, vb, a.count, a.cap, shift,
-                                                        a.hist);
-    } else {
-      rs_hist<8><<<a.nblocks, kSortThreads, 0, s>>>(ka, a.count, a.cap, shift, a.hist);
-      rs_scatter<8><<<a.nblocks, kSortThreads, 0, s>>>(ka, kb, va, vb, a.count, a.cap, shift,
-                                                        a.hist);
-    }
+  for (int shift = a.lo_bit; shift < a.hi_bit; shift += 8) {
+    rs_hist<<<a.nblocks, kSortThreads, 0, s>>>(ka, a.count, a.cap, shift, a.hist);
+    rs_scatter<<<a.nblocks, kSortThreads, 0, s>>>(ka, kb, va, vb, a.count, a.cap, shift, a.hist);
     nl += 2;
     std::swap(ka, kb);
     std::swap(va, vb);

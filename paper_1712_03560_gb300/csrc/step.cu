@@ -56,8 +56,11 @@ int plan_step(oasm_ctx* ctx, StepPlan& pl) {
   if (pl.items.empty()) return OASM_OK;
   uint64_t maxspan = 1;
   for (const auto& w : pl.items) maxspan = std::max<uint64_t>(maxspan, uint64_t(w.e_new - w.base_pos));
-  const int pb = bits_for(uint64_t(pl.items.size()) * ctx->n_pat - 1);
-  pl.sb = bits_for(maxspan);
+  // pair bits (none when the step has one pair) and start bits: a start or
+  // decision point lies below e_new, so start - base_pos < maxspan
+  const uint64_t npairs = uint64_t(pl.items.size()) * ctx->n_pat;
+  const int pb = npairs > 1 ? bits_for(npairs - 1) : 0;
+  pl.sb = bits_for(maxspan - 1);
   pl.kb = pb + pl.sb + kLowBits;
   if (pl.kb > 64)
     return fail(ctx, OASM_EINVAL, "step too large for 64-bit hit keys (%d bits)", pl.kb);
@@ -197,7 +200,7 @@ int enqueue_step(oasm_ctx* ctx, StepPlan& pl, const WorkItem* d_items, const Reg
     SortArgs sa{P.keys, P.keys_alt, nullptr, nullptr, &ctx->d_ctr->n_hits, P.cap_hits,
                 kKBits, pl.kb, ctx->d_hist, ctx->sort_blocks};
     CK(launch_sort(sa, &sorted, nullptr, &nl, s));
-    topo_add(0x100 + nl + 0x80 * (sort_digit_bits(kKBits, pl.kb) == 9));
+    topo_add(0x100 + nl);
     ctx->st.launches += uint64_t(nl);
     if (tm) CK(record_event(ctx, ctx->ev[4], s));
     if (pl.ordered) {
@@ -233,7 +236,7 @@ int enqueue_step(oasm_ctx* ctx, StepPlan& pl, const WorkItem* d_items, const Reg
     SortArgs sa{ctx->okeys.p, ctx->okeys_alt.p, ctx->ovals.p, ctx->ovals_alt.p,
                 &ctx->d_ctr->n_out, P.cap_out, 0, pl.kb, ctx->d_hist, ctx->sort_blocks};
     CK(launch_sort(sa, &ks, &vs, &nl, s));
-    topo_add(0x200 + nl + 0x80 * (sort_digit_bits(0, pl.kb) == 9));
+    topo_add(0x200 + nl);
     CK(launch_permute(ctx->out.p, vs, ctx->out_sorted[ctx->rec_buf].p, &ctx->d_ctr->n_out, P.cap_out,
                       ctx->num_sms, s));
     // where each work item's (stream's) run of records starts
