@@ -172,8 +172,10 @@ typedef struct {
     uint64_t buffer_grows;   /* device or pinned host buffers reallocated larger
                                 (each a cudaMalloc or cudaHostAlloc on the call's
                                 path, and a free of the old buffer) */
-    double host_copy_ms;     /* part of host_post_ms: waiting for the copy of a
-                                step's records to pinned host memory */
+    double host_copy_ms;     /* host time waiting for the copy of a step's records
+                                to pinned host memory (the copy runs beside the
+                                caller; this is what remained when the records were
+                                first needed) */
     uint64_t record_bytes;   /* bytes of records copied to the host */
 } oasm_stats;
 
