@@ -257,8 +257,6 @@ double ms_since(std::chrono::steady_clock::time_point t0) {
   return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
 }
 
-// Launches one step's device work (as a graph or directly) and records the
-// completion event; returns without waiting.
 // The ordered record path (filtered output) replaces the per-record atomics,
 // the record sort and the permutation by a scan over the segment counts.  Its
 // extra room, `head` slots per pair, pays when pairs are few against the hit
@@ -278,6 +276,8 @@ int prepare_records(oasm_ctx* ctx, StepPlan& pl) {
   return ensure(ctx, ctx->seg_part, size_t(ordered_scan_blocks(ctx->num_sms)), "record scan");
 }
 
+// Launches one step's device work (as a graph or directly) and records the
+// completion event; returns without waiting.
 int launch_step(oasm_ctx* ctx, StepPlan& pl, const WorkItem* d_items, const Region* d_regions,
                 const CopyChunk* d_chunks) {
   const auto t_launch = std::chrono::steady_clock::now();
